@@ -1,0 +1,580 @@
+/*
+ * FP64 CPU oracle for the voxel-cone-tracing hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * load this file; it exists so that the CUDA library can be compared with a
+ * plain, slow, obviously correct restatement of the method.  It shares no
+ * code, header, table or constant with the CUDA library.
+ *
+ * What it computes, in the thesis's order (B. Kahl, "Real-Time Global
+ * Illumination Using OpenGL And Voxel Cone Tracing", 2019):
+ *
+ *  - mip pyramid: each level halves every dimension and each texel is the
+ *    plain average of its 2x2x2 children (Ch. 4.3.3 "Mipmaps" and "Texture
+ *    Filtering": a factor-2 minification makes every texel contribute, and
+ *    Ch. 5.4.4 builds the levels right after voxelization);
+ *  - sample(position, diameter): mip level = log2(diameter / voxel size) and a
+ *    linear-in-level, trilinear-in-space lookup with texel centres at
+ *    (i + 1/2) h_l (Ch. 4.5, colour supersampler; Ch. 4.3.3 textureLod);
+ *  - the cone trace (Ch. 4.3.2, volume ray marching): diameter
+ *    d = 2 t tan(gamma/2), sample at p = x + t w, front-to-back accumulation
+ *    of colour and occlusion, advance t by beta * d, stop once the occlusion
+ *    reaches 1 (plus a maximum distance, see below);
+ *  - the per-pixel cone set (Ch. 4.2: diffuse cones over the normal
+ *    hemisphere, one specular cone along the reflection direction, one
+ *    occlusion cone per light) and the weighted diffuse sum (Ch. 4.1 / 4.2.2:
+ *    one BRDF weight per cone).
+ *
+ * Readings of passages the thesis leaves open or garbled (the same readings
+ * are used by the CUDA path; they are inputs or fixed choices, not shared
+ * code):
+ *  - colour accumulation is c <- c + (1 - alpha) a_s c_s (the printed line
+ *    also scales the running colour by alpha, which is not front-to-back
+ *    compositing);
+ *  - the level is log2(d / h0) with h0 the level-0 voxel edge, clamped to
+ *    [0, L-1]; the fractional part blends two adjacent levels;
+ *  - texels outside the grid read as zero (empty space);
+ *  - the march also stops once t exceeds t_max (the listing has no bound);
+ *  - the start offset is t0 = t0_voxels * h0 and the cone apex is moved
+ *    normal_offset_voxels * h0 along the surface normal;
+ *  - the tangent frame for the diffuse table is T = normalize(a x n),
+ *    B = n x T with a = (1,0,0) if |n_x| < 0.9 else (0,1,0);
+ *  - the specular aperture grows linearly with roughness between
+ *    spec_aperture_min (at roughness_min) and spec_aperture_max (at 1).
+ *
+ * All arithmetic is double precision; the build uses -ffp-contract=off so
+ * that results do not depend on the host's fused multiply-add.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_MAX_DIFFUSE 32
+
+typedef struct {
+  int32_t n_diffuse;
+  int32_t spec_enable;
+  int32_t occ_enable;
+  int32_t pad;
+  double diffuse_dir[ORC_MAX_DIFFUSE][3];
+  double diffuse_weight[ORC_MAX_DIFFUSE];
+  double diffuse_aperture;
+  double spec_aperture_min, spec_aperture_max, roughness_min;
+  double occ_aperture;
+  double light_dir[3];
+  double beta, t0_voxels, normal_offset_voxels, t_max;
+} orc_params;
+
+/* A pyramid: `levels` dense arrays [z][y][x][4] of doubles, level l has
+ * n >> l texels per axis, stored back to back starting with level 0.  The
+ * grid covers [origin, origin + size]^3 in scene units. */
+typedef struct {
+  const double *data;
+  int32_t n, levels;
+  double origin[3], size;
+} orc_grid;
+
+/* Per-view G-buffer as the caller holds it (float32 inputs). */
+typedef struct {
+  int32_t width, height;
+  const float *position; /* [H*W*3] */
+  const float *normal;   /* [H*W*3] */
+  const float *roughness; /* [H*W] or NULL */
+  const uint8_t *mask;    /* [H*W] or NULL */
+  double camera[3];
+} orc_view;
+
+int orc_version(void) { return 1; }
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+size_t orc_level_offset(int n, int level) {
+  size_t off = 0;
+  for (int l = 0; l < level; ++l) {
+    size_t m = (size_t)(n >> l);
+    off += m * m * m * 4;
+  }
+  return off;
+}
+
+/* ---------------------------------------------------------------------- */
+/* mip pyramid (Ch. 4.3.3)                                                 */
+/* ---------------------------------------------------------------------- */
+void orc_build_mips(const double *level0, int n, int levels, double *pyr) {
+  size_t m0 = (size_t)n * n * n * 4;
+  memcpy(pyr, level0, m0 * sizeof(double));
+  for (int l = 1; l < levels; ++l) {
+    const double *src = pyr + orc_level_offset(n, l - 1);
+    double *dst = pyr + orc_level_offset(n, l);
+    int nc = n >> (l - 1), np = n >> l;
+#pragma omp parallel for
+    for (int z = 0; z < np; ++z)
+      for (int y = 0; y < np; ++y)
+        for (int x = 0; x < np; ++x)
+          for (int c = 0; c < 4; ++c) {
+            double s = 0.0;
+            for (int dz = 0; dz < 2; ++dz)
+              for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                  size_t i = (((size_t)(2 * z + dz) * nc + (2 * y + dy)) * nc +
+                              (2 * x + dx)) * 4 + c;
+                  s += src[i];
+                }
+            dst[(((size_t)z * np + y) * np + x) * 4 + c] = s / 8.0;
+          }
+  }
+}
+
+/* Adjoint of orc_build_mips: given dL/d(level l) for every level (same
+ * layout as the pyramid), push each coarse gradient down to its children
+ * (each child receives 1/8 of its parent's), coarse to fine, then add the
+ * level-0 result into grad0. */
+void orc_mip_adjoint(double *gpyr, int n, int levels, double *grad0) {
+  for (int l = levels - 1; l >= 1; --l) {
+    const double *gp = gpyr + orc_level_offset(n, l);
+    double *gc = gpyr + orc_level_offset(n, l - 1);
+    int nc = n >> (l - 1), np = n >> l;
+#pragma omp parallel for
+    for (int z = 0; z < nc; ++z)
+      for (int y = 0; y < nc; ++y)
+        for (int x = 0; x < nc; ++x)
+          for (int c = 0; c < 4; ++c)
+            gc[(((size_t)z * nc + y) * nc + x) * 4 + c] +=
+                gp[(((size_t)(z / 2) * np + y / 2) * np + x / 2) * 4 + c] / 8.0;
+  }
+  size_t m0 = (size_t)n * n * n * 4;
+  for (size_t i = 0; i < m0; ++i) grad0[i] += gpyr[i];
+}
+
+/* ---------------------------------------------------------------------- */
+/* sampling (Ch. 4.5 colour supersampler, Ch. 4.3.3 texture filtering)      */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+  int level[2];
+  double level_w[2];
+  int base[2][3]; /* lower corner texel per axis                        */
+  double frac[2][3];
+} orc_stencil;
+
+/* q: grid-normalized position ([0,1]^3 spans the grid), lambda: level. */
+static void stencil(int n, int levels, const double q[3], double lambda,
+                    orc_stencil *s) {
+  double lc = lambda;
+  if (!(lc > 0.0)) lc = 0.0; /* also maps NaN / -inf to level 0 */
+  if (lc > levels - 1) lc = levels - 1;
+  int l0 = (int)floor(lc);
+  int l1 = l0 + 1 < levels ? l0 + 1 : levels - 1;
+  double f = lc - l0;
+  s->level[0] = l0;
+  s->level[1] = l1;
+  s->level_w[0] = 1.0 - f;
+  s->level_w[1] = f;
+  for (int k = 0; k < 2; ++k) {
+    int nl = n >> s->level[k];
+    for (int a = 0; a < 3; ++a) {
+      double u = q[a] * nl - 0.5;
+      double i0 = floor(u);
+      s->base[k][a] = (int)i0;
+      s->frac[k][a] = u - i0;
+    }
+  }
+}
+
+static double corner_weight(const orc_stencil *s, int k, int dx, int dy,
+                            int dz) {
+  double wx = dx ? s->frac[k][0] : 1.0 - s->frac[k][0];
+  double wy = dy ? s->frac[k][1] : 1.0 - s->frac[k][1];
+  double wz = dz ? s->frac[k][2] : 1.0 - s->frac[k][2];
+  return s->level_w[k] * wx * wy * wz;
+}
+
+static void apply_stencil(const orc_grid *g, const orc_stencil *s,
+                          double out[4]) {
+  out[0] = out[1] = out[2] = out[3] = 0.0;
+  for (int k = 0; k < 2; ++k) {
+    int nl = g->n >> s->level[k];
+    const double *lv = g->data + orc_level_offset(g->n, s->level[k]);
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          int x = s->base[k][0] + dx, y = s->base[k][1] + dy,
+              z = s->base[k][2] + dz;
+          if (x < 0 || y < 0 || z < 0 || x >= nl || y >= nl || z >= nl)
+            continue; /* outside the grid: empty */
+          double w = corner_weight(s, k, dx, dy, dz);
+          const double *v = lv + (((size_t)z * nl + y) * nl + x) * 4;
+          for (int c = 0; c < 4; ++c) out[c] += w * v[c];
+        }
+  }
+}
+
+static void to_grid(const orc_grid *g, const double p[3], double q[3]) {
+  for (int a = 0; a < 3; ++a) q[a] = (p[a] - g->origin[a]) / g->size;
+}
+
+/* sample(position, diameter) of Ch. 4.5 in scene units. */
+void orc_sample(const double *pyr, int n, int levels, const double *origin,
+                double size, const double *p, double diameter, double *out) {
+  orc_grid g = {pyr, n, levels, {origin[0], origin[1], origin[2]}, size};
+  double q[3];
+  to_grid(&g, p, q);
+  double h0 = size / n;
+  orc_stencil s;
+  stencil(n, levels, q, log2(diameter / h0), &s);
+  apply_stencil(&g, &s, out);
+}
+
+/* Lookup at an explicit level (for tests of the filter itself). */
+void orc_sample_lod(const double *pyr, int n, int levels, const double *q,
+                    double lambda, double *out) {
+  orc_grid g = {pyr, n, levels, {0.0, 0.0, 0.0}, 1.0};
+  orc_stencil s;
+  stencil(n, levels, q, lambda, &s);
+  apply_stencil(&g, &s, out);
+}
+
+/* ---------------------------------------------------------------------- */
+/* one cone (Ch. 4.3.2 volume ray marching)                                */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+  double t, a, c[3], trans; /* step position, sample alpha/colour, T_k   */
+  orc_stencil st;
+} orc_step;
+
+typedef struct {
+  double c[3], alpha;
+  int64_t steps;
+  double margin; /* min |t - t_max| / t_max over the tested t values      */
+} orc_cone_result;
+
+/* Marches one cone.  If `rec` is non-NULL the per-step state is stored
+ * there (capacity `cap`) for the adjoint. */
+static void march(const orc_grid *g, const double o[3], const double w[3],
+                  double aperture, const orc_params *P, orc_cone_result *res,
+                  orc_step *rec, int64_t cap) {
+  double h0 = g->size / g->n;
+  double tan_half = tan(0.5 * aperture);
+  double t = P->t0_voxels * h0;
+  double alpha = 0.0, c[3] = {0.0, 0.0, 0.0};
+  double margin = INFINITY;
+  int64_t k = 0;
+  for (;;) {
+    double m = fabs(t - P->t_max) / P->t_max;
+    if (m < margin) margin = m;
+    if (!(alpha < 1.0 && t <= P->t_max)) break;
+    double d = 2.0 * t * tan_half; /* sampling diameter */
+    double p[3], q[3];
+    for (int a = 0; a < 3; ++a) p[a] = o[a] + t * w[a];
+    to_grid(g, p, q);
+    orc_stencil st;
+    stencil(g->n, g->levels, q, log2(d / h0), &st);
+    double v[4];
+    apply_stencil(g, &st, v);
+    if (rec && k < cap) {
+      rec[k].t = t;
+      rec[k].a = v[3];
+      rec[k].c[0] = v[0];
+      rec[k].c[1] = v[1];
+      rec[k].c[2] = v[2];
+      rec[k].trans = 1.0 - alpha;
+      rec[k].st = st;
+    }
+    double wgt = (1.0 - alpha) * v[3];
+    for (int ch = 0; ch < 3; ++ch) c[ch] += wgt * v[ch];
+    alpha += wgt;
+    t += P->beta * d;
+    ++k;
+  }
+  for (int ch = 0; ch < 3; ++ch) res->c[ch] = c[ch];
+  res->alpha = alpha;
+  res->steps = k;
+  res->margin = margin;
+}
+
+/* Public single-cone entry (scene units). */
+void orc_trace_cone(const double *pyr, int n, int levels, const double *origin,
+                    double size, const double *apex, const double *dir,
+                    double aperture, const orc_params *P, double *out_rgba,
+                    int64_t *steps) {
+  orc_grid g = {pyr, n, levels, {origin[0], origin[1], origin[2]}, size};
+  orc_cone_result r;
+  march(&g, apex, dir, aperture, P, &r, NULL, 0);
+  out_rgba[0] = r.c[0];
+  out_rgba[1] = r.c[1];
+  out_rgba[2] = r.c[2];
+  out_rgba[3] = r.alpha;
+  if (steps) *steps = r.steps;
+}
+
+/* ---------------------------------------------------------------------- */
+/* per-pixel cone set (Ch. 4.2)                                            */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+  int count;
+  int kind[ORC_MAX_DIFFUSE + 2]; /* 0 diffuse, 1 specular, 2 occlusion */
+  double weight[ORC_MAX_DIFFUSE + 2];
+  double dir[ORC_MAX_DIFFUSE + 2][3];
+  double aperture[ORC_MAX_DIFFUSE + 2];
+  double apex[3];
+} orc_coneset;
+
+static void normalize3(double v[3]) {
+  double l = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  v[0] /= l;
+  v[1] /= l;
+  v[2] /= l;
+}
+
+static void cross3(const double a[3], const double b[3], double r[3]) {
+  r[0] = a[1] * b[2] - a[2] * b[1];
+  r[1] = a[2] * b[0] - a[0] * b[2];
+  r[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+void orc_tangent_frame(const double *nrm, double *T, double *B) {
+  double a[3] = {0.0, 0.0, 0.0};
+  if (fabs(nrm[0]) < 0.9)
+    a[0] = 1.0;
+  else
+    a[1] = 1.0;
+  cross3(a, nrm, T);
+  normalize3(T);
+  cross3(nrm, T, B);
+}
+
+static void cone_set(const orc_grid *g, const orc_view *v, size_t px,
+                     const orc_params *P, orc_coneset *cs) {
+  double x[3], nrm[3];
+  for (int a = 0; a < 3; ++a) {
+    x[a] = v->position[3 * px + a];
+    nrm[a] = v->normal[3 * px + a];
+  }
+  double h0 = g->size / g->n;
+  for (int a = 0; a < 3; ++a)
+    cs->apex[a] = x[a] + P->normal_offset_voxels * h0 * nrm[a];
+  double T[3], B[3];
+  orc_tangent_frame(nrm, T, B);
+  int c = 0;
+  for (int k = 0; k < P->n_diffuse; ++k, ++c) {
+    const double *d = P->diffuse_dir[k];
+    cs->kind[c] = 0;
+    cs->weight[c] = P->diffuse_weight[k];
+    cs->aperture[c] = P->diffuse_aperture;
+    for (int a = 0; a < 3; ++a)
+      cs->dir[c][a] = T[a] * d[0] + B[a] * d[1] + nrm[a] * d[2];
+  }
+  if (P->spec_enable) {
+    double view[3];
+    for (int a = 0; a < 3; ++a) view[a] = x[a] - v->camera[a];
+    normalize3(view);
+    double vn = view[0] * nrm[0] + view[1] * nrm[1] + view[2] * nrm[2];
+    cs->kind[c] = 1;
+    cs->weight[c] = 1.0;
+    for (int a = 0; a < 3; ++a) cs->dir[c][a] = view[a] - 2.0 * vn * nrm[a];
+    double ap = P->spec_aperture_min;
+    if (v->roughness) {
+      double f = (v->roughness[px] - P->roughness_min) / (1.0 - P->roughness_min);
+      if (f < 0.0) f = 0.0;
+      if (f > 1.0) f = 1.0;
+      ap = P->spec_aperture_min + f * (P->spec_aperture_max - P->spec_aperture_min);
+    }
+    cs->aperture[c] = ap;
+    ++c;
+  }
+  if (P->occ_enable) {
+    cs->kind[c] = 2;
+    cs->weight[c] = 1.0;
+    cs->aperture[c] = P->occ_aperture;
+    for (int a = 0; a < 3; ++a) cs->dir[c][a] = P->light_dir[a];
+    ++c;
+  }
+  cs->count = c;
+}
+
+/* The cone set of one pixel, for tests of the per-pixel set-up: apex[3],
+ * and per cone kind / weight / aperture / direction[3].  Returns the count. */
+int orc_cone_set(const double *origin, double size, int n, const orc_view *v,
+                 int64_t px, const orc_params *P, double *apex, int *kind,
+                 double *weight, double *aperture, double *dir) {
+  orc_grid g = {NULL, n, 1, {origin[0], origin[1], origin[2]}, size};
+  orc_coneset cs;
+  cone_set(&g, v, (size_t)px, P, &cs);
+  for (int a = 0; a < 3; ++a) apex[a] = cs.apex[a];
+  for (int c = 0; c < cs.count; ++c) {
+    kind[c] = cs.kind[c];
+    weight[c] = cs.weight[c];
+    aperture[c] = cs.aperture[c];
+    for (int a = 0; a < 3; ++a) dir[3 * c + a] = cs.dir[c][a];
+  }
+  return cs.count;
+}
+
+/*
+ * Traces the pixels `idx[0..count)` of one view (all pixels if idx == NULL,
+ * count = W*H).  Outputs are per listed pixel: D[4], S[4], Vis[1].
+ * steps[3] accumulates the number of samples per cone kind, cones[3] the
+ * number of cones, margin receives min |t - t_max| / t_max.
+ */
+void orc_trace(const double *pyr, int n, int levels, const double *origin,
+               double size, const orc_view *v, const orc_params *P,
+               const int64_t *idx, int64_t count, double *D, double *S,
+               double *Vis, int64_t *steps, int64_t *cones, double *margin) {
+  orc_grid g = {pyr, n, levels, {origin[0], origin[1], origin[2]}, size};
+  int64_t st[3] = {0, 0, 0}, cn[3] = {0, 0, 0};
+  double mg = INFINITY;
+#pragma omp parallel
+  {
+    int64_t lst[3] = {0, 0, 0}, lcn[3] = {0, 0, 0};
+    double lmg = INFINITY;
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t i = 0; i < count; ++i) {
+      size_t px = idx ? (size_t)idx[i] : (size_t)i;
+      double *d = D + 4 * i, *s = S + 4 * i;
+      d[0] = d[1] = d[2] = d[3] = 0.0;
+      s[0] = s[1] = s[2] = s[3] = 0.0;
+      Vis[i] = 1.0;
+      if (v->mask && !v->mask[px]) continue;
+      orc_coneset cs;
+      cone_set(&g, v, px, P, &cs);
+      for (int c = 0; c < cs.count; ++c) {
+        orc_cone_result r;
+        march(&g, cs.apex, cs.dir[c], cs.aperture[c], P, &r, NULL, 0);
+        lst[cs.kind[c]] += r.steps;
+        lcn[cs.kind[c]] += 1;
+        if (r.margin < lmg) lmg = r.margin;
+        if (cs.kind[c] == 0) {
+          for (int ch = 0; ch < 3; ++ch) d[ch] += cs.weight[c] * r.c[ch];
+          d[3] += cs.weight[c] * r.alpha;
+        } else if (cs.kind[c] == 1) {
+          for (int ch = 0; ch < 3; ++ch) s[ch] = r.c[ch];
+          s[3] = r.alpha;
+        } else {
+          Vis[i] = 1.0 - r.alpha;
+        }
+      }
+    }
+#pragma omp critical
+    {
+      for (int k = 0; k < 3; ++k) {
+        st[k] += lst[k];
+        cn[k] += lcn[k];
+      }
+      if (lmg < mg) mg = lmg;
+    }
+  }
+  if (steps)
+    for (int k = 0; k < 3; ++k) steps[k] += st[k];
+  if (cones)
+    for (int k = 0; k < 3; ++k) cones[k] += cn[k];
+  if (margin && mg < *margin) *margin = mg;
+}
+
+/* ---------------------------------------------------------------------- */
+/* adjoint                                                                 */
+/* ---------------------------------------------------------------------- */
+/*
+ * For one cone with samples (c_k, a_k), k = 0..K-1, and transmittance
+ * T_k = prod_{j<k} (1 - a_j):
+ *   C = sum_k T_k a_k c_k,   A = 1 - prod_k (1 - a_k).
+ *   dC/dc_k = T_k a_k
+ *   dC/da_k = T_k (c_k - R_{k+1}),  R_k = a_k c_k + (1 - a_k) R_{k+1}, R_K = 0
+ *   dA/da_k = T_k Q_{k+1},          Q_k = (1 - a_k) Q_{k+1},           Q_K = 1
+ * The step schedule does not depend on the voxel values (only the stopping
+ * step does, which is piecewise constant), so these are the derivatives.
+ */
+static void cone_adjoint(const orc_grid *g, double *gpyr, const orc_step *rec,
+                         int64_t K, const double gc[3], double ga) {
+  double R[3] = {0.0, 0.0, 0.0}, Q = 1.0;
+  for (int64_t k = K - 1; k >= 0; --k) {
+    const orc_step *s = rec + k;
+    double dc[3], da = 0.0;
+    for (int ch = 0; ch < 3; ++ch) {
+      dc[ch] = gc[ch] * s->trans * s->a;
+      da += gc[ch] * s->trans * (s->c[ch] - R[ch]);
+    }
+    da += ga * s->trans * Q;
+    for (int ch = 0; ch < 3; ++ch) R[ch] = s->a * s->c[ch] + (1.0 - s->a) * R[ch];
+    Q = (1.0 - s->a) * Q;
+    for (int lk = 0; lk < 2; ++lk) {
+      int nl = g->n >> s->st.level[lk];
+      double *lv = gpyr + orc_level_offset(g->n, s->st.level[lk]);
+      for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+          for (int dx = 0; dx < 2; ++dx) {
+            int x = s->st.base[lk][0] + dx, y = s->st.base[lk][1] + dy,
+                z = s->st.base[lk][2] + dz;
+            if (x < 0 || y < 0 || z < 0 || x >= nl || y >= nl || z >= nl)
+              continue;
+            double w = corner_weight(&s->st, lk, dx, dy, dz);
+            if (w == 0.0) continue;
+            double *t = lv + (((size_t)z * nl + y) * nl + x) * 4;
+            for (int ch = 0; ch < 3; ++ch) {
+#pragma omp atomic
+              t[ch] += w * dc[ch];
+            }
+#pragma omp atomic
+            t[3] += w * da;
+          }
+    }
+  }
+}
+
+/*
+ * Gradient of L with respect to the level-0 grid, given dL/dD, dL/dS and
+ * dL/dVis for the listed pixels (same layout as orc_trace's outputs).
+ * gpyr is caller scratch of orc_level_offset(n, levels) doubles (zeroed
+ * here); the level-0 gradient is ADDED into grad0 ([n][n][n][4]).
+ */
+void orc_trace_backward(const double *pyr, int n, int levels,
+                        const double *origin, double size, const orc_view *v,
+                        const orc_params *P, const int64_t *idx, int64_t count,
+                        const double *gD, const double *gS, const double *gV,
+                        double *gpyr, double *grad0) {
+  orc_grid g = {pyr, n, levels, {origin[0], origin[1], origin[2]}, size};
+  memset(gpyr, 0, orc_level_offset(n, levels) * sizeof(double));
+#pragma omp parallel
+  {
+    int64_t cap = 4096;
+    orc_step *rec = (orc_step *)malloc(sizeof(orc_step) * cap);
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t i = 0; i < count; ++i) {
+      size_t px = idx ? (size_t)idx[i] : (size_t)i;
+      if (v->mask && !v->mask[px]) continue;
+      orc_coneset cs;
+      cone_set(&g, v, px, P, &cs);
+      for (int c = 0; c < cs.count; ++c) {
+        orc_cone_result r;
+        march(&g, cs.apex, cs.dir[c], cs.aperture[c], P, &r, rec, cap);
+        if (r.steps > cap) { /* grow and redo */
+          cap = r.steps;
+          rec = (orc_step *)realloc(rec, sizeof(orc_step) * cap);
+          march(&g, cs.apex, cs.dir[c], cs.aperture[c], P, &r, rec, cap);
+        }
+        double gc[3] = {0.0, 0.0, 0.0}, ga = 0.0;
+        if (cs.kind[c] == 0) {
+          for (int ch = 0; ch < 3; ++ch) gc[ch] = cs.weight[c] * gD[4 * i + ch];
+          ga = cs.weight[c] * gD[4 * i + 3];
+        } else if (cs.kind[c] == 1) {
+          for (int ch = 0; ch < 3; ++ch) gc[ch] = gS[4 * i + ch];
+          ga = gS[4 * i + 3];
+        } else {
+          ga = gV ? -gV[i] : 0.0;
+        }
+        cone_adjoint(&g, gpyr, rec, r.steps, gc, ga);
+      }
+    }
+    free(rec);
+  }
+  orc_mip_adjoint(gpyr, n, levels, grad0);
+}

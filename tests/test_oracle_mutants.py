@@ -1,0 +1,72 @@
+"""Plants plausible mistakes in a copy of the oracle (on the CPU) and checks
+that the pins in ``oracle_pins.py`` catch every one of them.
+
+The committed oracle source is never modified: each mutant is a text
+substitution written to a temporary directory and compiled separately.
+"""
+import os
+
+import pytest
+
+import oracle
+import oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "vct_oracle.c")
+
+MUTANTS = {
+    "texel centre dropped": ("double u = q[a] * nl - 0.5;", "double u = q[a] * nl;"),
+    "x/z transposed in lookup": (
+        "const double *v = lv + (((size_t)z * nl + y) * nl + x) * 4;",
+        "const double *v = lv + (((size_t)x * nl + y) * nl + z) * 4;"),
+    "printed colour line taken literally": (
+        "for (int ch = 0; ch < 3; ++ch) c[ch] += wgt * v[ch];",
+        "for (int ch = 0; ch < 3; ++ch) c[ch] = alpha * c[ch] + wgt * v[ch];"),
+    "level from diameter / scene size": (
+        "stencil(g->n, g->levels, q, log2(d / h0), &st);",
+        "stencil(g->n, g->levels, q, log2(d / g->size), &st);"),
+    "reflection sign": ("cs->dir[c][a] = view[a] - 2.0 * vn * nrm[a];",
+                        "cs->dir[c][a] = view[a] + 2.0 * vn * nrm[a];"),
+    "step ignores beta": ("t += P->beta * d;", "t += d;"),
+    "mip divides by 4": ("dst[(((size_t)z * np + y) * np + x) * 4 + c] = s / 8.0;",
+                         "dst[(((size_t)z * np + y) * np + x) * 4 + c] = s / 4.0;"),
+    "level blend swapped": ("s->level_w[0] = 1.0 - f;\n  s->level_w[1] = f;",
+                            "s->level_w[0] = f;\n  s->level_w[1] = 1.0 - f;"),
+    "left-handed frame": ("cross3(nrm, T, B);", "cross3(T, nrm, B);"),
+    "apex offset into the surface": (
+        "cs->apex[a] = x[a] + P->normal_offset_voxels * h0 * nrm[a];",
+        "cs->apex[a] = x[a] - P->normal_offset_voxels * h0 * nrm[a];"),
+    "clamp-to-edge instead of border zero": (
+        "continue; /* outside the grid: empty */",
+        "{ x = x < 0 ? 0 : (x >= nl ? nl - 1 : x); y = y < 0 ? 0 : (y >= nl ? nl - 1 : y);"
+        " z = z < 0 ? 0 : (z >= nl ? nl - 1 : z); }"),
+    "adjoint drops Q": ("da += ga * s->trans * Q;", "da += ga * Q;"),
+    "adjoint suffix not attenuated": (
+        "R[ch] = s->a * s->c[ch] + (1.0 - s->a) * R[ch];",
+        "R[ch] = s->a * s->c[ch] + R[ch];"),
+    "mip adjoint weight": ("gp[(((size_t)(z / 2) * np + y / 2) * np + x / 2) * 4 + c] / 8.0;",
+                           "gp[(((size_t)(z / 2) * np + y / 2) * np + x / 2) * 4 + c] / 4.0;"),
+    "diffuse weight dropped": ("d[ch] += cs.weight[c] * r.c[ch];", "d[ch] += r.c[ch];"),
+    "transmittance not stored": ("rec[k].trans = 1.0 - alpha;", "rec[k].trans = 1.0;"),
+}
+
+CHECKS = [name for name in dir(pins) if name.startswith("check_")]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    with open(SRC) as f:
+        text = f.read()
+    assert text.count(old) == 1, f"mutation anchor not unique/found: {old!r}"
+    src = tmp_path / "vct_oracle_mutant.c"
+    src.write_text(text.replace(old, new))
+    lib = oracle.load_library(oracle.compile_source([str(src)], out_dir=str(tmp_path),
+                                                    tag="mutant"))
+    caught = []
+    with oracle.using(lib):
+        for check in CHECKS:
+            try:
+                getattr(pins, check)()
+            except AssertionError:
+                caught.append(check)
+    assert caught, f"no pin caught the planted mistake '{name}'"
