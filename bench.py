@@ -1,0 +1,390 @@
+"""Benchmark of the voxel-cone-tracing hot path on GB300.
+
+One step = one frame of the 256^3 room workload: Morton packing + mip build
+of the resident level-0 grid (vct_build_mips) followed by the trace of a
+1920x1080 G-buffer with 9 diffuse + 1 specular + 1 occlusion cone per pixel
+(vct_trace).  The metric is cone samples per second (Gcone-samples/s); the
+1080p trace time is reported beside it.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this project
+has: the thesis ships no runnable code here) on the host cores.
+Under torchrun each rank traces its own replica of the frame (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+TEXEL_BYTES = {"f32": 16, "f16": 8}
+PIXEL_IO_BYTES = 12 + 12 + 4 + 1 + 16 + 16 + 4  # pos, normal, roughness, mask; D, S, Vis
+TRACE_SOURCES = ["paper_2104_00618_gb300/csrc/trace.cu",
+                 "paper_2104_00618_gb300/csrc/trace_common.cuh",
+                 "paper_2104_00618_gb300/csrc/vct_internal.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--dtype", choices=["f32", "f16"], default="f32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only warm-up + timed frames (for ncu captures); no e2e/extras/baseline")
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def sources_hash(files) -> str:
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(f"{kernel}|{workload}")
+    if not e or e.get("sources") != sources_hash(TRACE_SOURCES):
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_workload(width=1920, height=1080):
+    import vct_synth as vs
+    return vs.config_room_1080p(width=width, height=height)
+
+
+def cpu_baseline(cfg, frac=1.0 / 8.0, seed=0):
+    """The FP64 oracle as it stands, on this host's cores: full FP64 mip build
+    plus a seeded pixel subset, extrapolated to one frame."""
+    import oracle
+    scene, view, prm = cfg["scenes"][0], cfg["views"][0], cfg["params"]
+    npx = view["width"] * view["height"]
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(npx, int(npx * frac), replace=False))
+    t0 = time.perf_counter()
+    O = oracle.build_mips(scene["grid"])
+    t1 = time.perf_counter()
+    r = oracle.trace(O, view, prm, idx=idx)
+    t2 = time.perf_counter()
+    samples = int(np.sum(r["steps"]))
+    frame_s = (t1 - t0) + (t2 - t1) / frac
+    return {"value": samples / frac / frame_s / 1e9, "unit": "Gcone-samples/s",
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 mip build of the 256^3 grid ({t1 - t0:.2f} s) + trace of "
+                      f"{len(idx)} seeded pixels ({frac:.3f} of the 1920x1080 frame, "
+                      f"{samples} samples, {t2 - t1:.2f} s), extrapolated to one frame",
+            "frame_s": frame_s}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2104_00618_gb300 as vct
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    cfg = make_workload(args.width, args.height)
+    scene, hv, prm = cfg["scenes"][0], cfg["views"][0], cfg["params"]
+    n = scene["n"]
+    level0 = torch.from_numpy(scene["grid"]).to(dev)
+    view = vct.View.from_host(hv, device=dev)
+    P = vct.Pyramid(n, None, args.dtype, device=dev)
+    params = vct.make_params(prm)
+    tws = torch.zeros(256, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        vct.build_mips(level0, out=P)
+        if ev is not None:
+            ev[0].record(stream)
+        vct.trace([P], [view], params, workspace=tws)
+        if ev is not None:
+            ev[1].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    stats = vct.read_stats(tws)
+    samples = int(sum(stats["samples"]))
+    if args.profile:
+        for _ in range(args.steps):
+            step()
+        torch.cuda.synchronize()
+        return {"profile": True, "samples_per_frame": samples, "width": args.width,
+                "height": args.height, "steps": args.steps, "warmup": max(3, args.warmup)}
+
+    clocks = ClockSampler(dev.index)
+    tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e_start.record(stream)
+    for i in range(args.steps):
+        step(tev[i])
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = e_start.elapsed_time(e_end)
+    trace_ms = [a.elapsed_time(b) for a, b in tev]
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    trace_avg = sum(trace_ms) / len(trace_ms)
+    value = samples * ws * args.steps / (total_ms / 1e3) / 1e9
+
+    # e2e: host buffers, copies inside the timed region
+    e2e = run_e2e(torch, vct, dev, scene, hv, params, args, stream)
+
+    line = None
+    if rank == 0:
+        hbm, peak_kind = measured_peaks()
+        algo_bytes = samples * 16 * TEXEL_BYTES[args.dtype] + hv["width"] * hv["height"] * PIXEL_IO_BYTES
+        achieved = algo_bytes / (trace_avg / 1e3) / 1e9
+        workload = f"room{n}_1080p_{args.dtype}"
+        traffic = ncu_traffic("trace_kernel", workload)
+        line = {
+            "metric": "Gcone-samples/s (256^3 room, 1920x1080, 11 cones/px: mip build + trace)",
+            "value": value, "unit": "Gcone-samples/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.dtype == "f32" else "f16-storage/f32-compute",
+            "data": "synthetic (seeded box room, raycast G-buffer)",
+            "config": {"workload": workload, "grid": n, "levels": P.levels, "width": hv["width"],
+                       "height": hv["height"], "cones_per_px": 11,
+                       "samples_per_frame": samples, "trace_ms": trace_avg,
+                       "l2": "inputs larger than L2 (268 MB level-0 grid, 307 MB pyramid)",
+                       "parallelism": f"replica x{ws}"},
+            "trace_ms": trace_avg,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "kernel": "trace_kernel", "peak_source": peak_kind,
+                         "algorithmic_bytes_per_launch": algo_bytes},
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": 3 * args.steps,
+        }
+        if not args.no_extras:
+            line["extras"] = run_extras(torch, vct, dev, args)
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(cfg)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+def run_e2e(torch, vct, dev, scene, hv, params, args, stream, steps=None):
+    steps = steps or max(3, min(args.steps, 10))
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_grid = pin(scene["grid"])
+    h_pos, h_nrm = pin(hv["position"]), pin(hv["normal"])
+    h_rough, h_mask = pin(hv["roughness"]), pin(hv["mask"])
+    npx = hv["width"] * hv["height"]
+    h_D = torch.empty((npx, 4)).pin_memory()
+    h_S = torch.empty((npx, 4)).pin_memory()
+    h_V = torch.empty((npx,)).pin_memory()
+    d_grid = torch.empty_like(h_grid, device=dev)
+    view = vct.View.from_host(hv, device=dev)
+    P = vct.Pyramid(scene["n"], None, args.dtype, device=dev)
+    tws = torch.zeros(256, dtype=torch.uint8, device=dev)
+
+    def one():
+        d_grid.copy_(h_grid, non_blocking=True)
+        view.position.copy_(h_pos, non_blocking=True)
+        view.normal.copy_(h_nrm, non_blocking=True)
+        view.roughness.copy_(h_rough, non_blocking=True)
+        view.mask.copy_(h_mask, non_blocking=True)
+        vct.build_mips(d_grid, out=P)
+        vct.trace([P], [view], params, workspace=tws)
+        h_D.copy_(view.out_diffuse, non_blocking=True)
+        h_S.copy_(view.out_specular, non_blocking=True)
+        h_V.copy_(view.out_visibility, non_blocking=True)
+
+    for _ in range(2):
+        one()
+    torch.cuda.synchronize()
+    samples = int(sum(vct.read_stats(tws)["samples"]))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        one()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    h2d = sum(t.numel() * t.element_size() for t in (h_grid, h_pos, h_nrm, h_rough, h_mask))
+    d2h = sum(t.numel() * t.element_size() for t in (h_D, h_S, h_V))
+    return {"value": samples / (ms / 1e3) / 1e9, "unit": "Gcone-samples/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
+
+
+def run_extras(torch, vct, dev, args):
+    """Secondary measurements: FP16 storage on the same frame."""
+    out = {}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    cfg = make_workload()
+    scene, view, prm = cfg["scenes"][0], cfg["views"][0], cfg["params"]
+    npx = view["width"] * view["height"]
+    frac = 1.0 / 64.0
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(npx, int(npx * frac), replace=False))
+    t0 = time.perf_counter()
+    O = oracle.build_mips(scene["grid"])
+    t_mip = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        oracle.trace(O, view, prm, idx=idx)
+    t0 = time.perf_counter()
+    samples = 0
+    for _ in range(args.steps):
+        r = oracle.trace(O, view, prm, idx=idx)
+        samples += int(np.sum(r["steps"]))
+    t_trace = (time.perf_counter() - t0) / args.steps
+    samples //= args.steps
+    frame_s = t_mip + t_trace / frac
+    value = samples / frac / frame_s / 1e9
+    base = {"kind": "oracle", "cores": oracle.num_threads(), "value": value,
+            "unit": "Gcone-samples/s",
+            "sample": f"each step traces {len(idx)} seeded pixels ({frac:.4f} of the frame); "
+                      f"the FP64 mip build ({t_mip:.2f} s, once) is added per frame"}
+    return {"metric": "Gcone-samples/s (256^3 room, 1920x1080, 11 cones/px: mip build + trace)",
+            "value": value, "unit": "Gcone-samples/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": frame_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "room256_1080p_f32"}, "impl": "reference",
+            "cpu_baseline": base,
+            "e2e": {"value": value, "unit": "Gcone-samples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

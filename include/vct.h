@@ -1,0 +1,287 @@
+/*
+ * vct.h — C ABI of the GB300 voxel-cone-tracing library (libvct.so).
+ *
+ * The library implements the data-parallel hot path of voxel cone tracing as
+ * defined in B. Kahl, "Real-Time Global Illumination Using OpenGL And Voxel
+ * Cone Tracing" (2019):
+ *   - building the mip pyramid of an RGBA voxel grid by 2x2x2 averaging
+ *     (Ch. 4.3.3, "Mipmaps" and "Texture Filtering"; Ch. 5.4.4 voxelize()),
+ *   - for every G-buffer pixel, marching diffuse cones over the normal
+ *     hemisphere, one specular cone along the reflection direction and one
+ *     occlusion cone towards the light (Ch. 4.2), each by the volume ray
+ *     march of Ch. 4.3.2 (diameter d = 2 t tan(gamma/2), step t += beta d,
+ *     front-to-back accumulation) with the sampler of Ch. 4.5 (mip level
+ *     log2(d / voxel size), quadrilinear lookup),
+ *   - and the adjoint of both (no counterpart in the thesis).
+ *
+ * Conventions for every entry point
+ *   - Device pointers are caller-owned CUDA device memory; the library never
+ *     allocates, frees or retains them past the call.  Host pointers (the
+ *     structs below) are read during the call only.
+ *   - All work is enqueued asynchronously on `stream` (a cudaStream_t; NULL is
+ *     the legacy default stream).  A return value other than VCT_OK means
+ *     that nothing was enqueued (argument validation) or that a launch failed
+ *     (VCT_ERR_CUDA).  Faults inside kernels surface at the caller's next
+ *     synchronisation.  The library never aborts, exits or throws.
+ *   - vct_last_error() returns a thread-local description of the last
+ *     failure on the calling thread.
+ *   - Scene units: the grid of a pyramid spans [origin, origin + size]^3.
+ *     Level 0 has n voxels per axis (voxel edge h0 = size / n); level l has
+ *     n >> l texels per axis with centres at origin + (i + 1/2) size/(n>>l).
+ *     Texels outside the grid read as zero (empty space).
+ */
+#ifndef VCT_H
+#define VCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t without including the CUDA headers. */
+typedef struct CUstream_st *vct_stream_t;
+
+typedef enum {
+  VCT_OK = 0,
+  VCT_ERR_INVALID_ARG = 1, /* a pointer, size or parameter is out of range   */
+  VCT_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed     */
+  VCT_ERR_WORKSPACE = 3,   /* workspace missing or smaller than required      */
+  VCT_ERR_UNSUPPORTED = 4, /* valid request this build does not implement     */
+  VCT_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up              */
+} vct_status;
+
+typedef enum { VCT_F32 = 0, VCT_F16 = 1 } vct_dtype;
+
+#define VCT_MAX_DIFFUSE 32
+#define VCT_MAX_PYRAMIDS 8
+#define VCT_MAX_LEVELS 11
+
+/* ------------------------------------------------------------------------ */
+/* Pyramid storage                                                          */
+/* ------------------------------------------------------------------------ */
+/*
+ * A mip pyramid in caller-owned device memory (Ch. 4.3.3).
+ *
+ * Layout of `data` (vct_pyramid_bytes() bytes, 256-byte aligned):
+ *   [256-byte header][level 0][level 1]...[level levels-1][FP32 staging]
+ * Each level starts at vct_pyramid_level_offset().  Within level l the texel
+ * at integer coordinates (x, y, z) sits at index morton(x, y, z), the bit
+ * interleave with x in bits 0,3,6,..., y in bits 1,4,7,... and z in bits
+ * 2,5,8,...  Because every level edge is a power of two this is the same as
+ * 8x8x8 bricks stored in Morton order of their brick coordinates with the
+ * texels of each brick in Morton order, and the 8 children of texel j of
+ * level l+1 are texels 8j..8j+7 of level l.  A texel is RGBA: four float32
+ * (16 bytes) for VCT_F32 or four IEEE binary16 (8 bytes) for VCT_F16.  The
+ * header holds a device status word written by bounded waits
+ * (vct_pyramid_status).  The FP32 staging area exists for VCT_F16 only and
+ * holds the unrounded values of one intermediate level during the build.
+ */
+typedef struct {
+  int32_t n;        /* level-0 voxels per axis: a power of two in [2, 1024]  */
+  int32_t levels;   /* number of levels, 1 .. log2(n) + 1                    */
+  int32_t dtype;    /* vct_dtype of the stored texels                        */
+  int32_t reserved; /* must be 0                                             */
+  float origin[3];  /* scene position of the grid's minimum corner           */
+  float size;       /* scene edge length of the grid, > 0                    */
+  void *data;       /* device memory, >= vct_pyramid_bytes(n, levels, dtype) */
+  uint64_t bytes;   /* size of `data` in bytes                               */
+} vct_pyramid;
+
+/* Bytes a pyramid of this shape needs; 0 if the shape is invalid. */
+size_t vct_pyramid_bytes(int32_t n, int32_t levels, int32_t dtype);
+
+/* Byte offset of `level` from pyramid.data; 0 if the arguments are invalid
+ * (level 0 itself starts at 256). */
+uint64_t vct_pyramid_level_offset(int32_t n, int32_t levels, int32_t dtype,
+                                  int32_t level);
+
+/*
+ * Builds every level of `pyr` from a dense level-0 grid (rows a1 + a2 of the
+ * hot path: Morton packing fused with the 2x2x2 box filter of Ch. 4.3.3).
+ *   level0_dense: device float32 [n][n][n][4] laid out z, y, x, channel
+ *                 (RGB radiance, A opacity), 16-byte aligned, read only.
+ *   pyr:          describes the destination; pyr->data is written.
+ * Level l+1 is the plain average of the 8 children of level l, computed in
+ * float32 from the float32 values of level l; VCT_F16 pyramids store each
+ * level rounded to nearest-even after it has been computed in float32.
+ * Errors: VCT_ERR_INVALID_ARG for a NULL or misaligned pointer, a bad shape
+ * or pyr->bytes too small; VCT_ERR_CUDA if a launch fails.
+ */
+vct_status vct_build_mips(const float *level0_dense, const vct_pyramid *pyr,
+                          vct_stream_t stream);
+
+/*
+ * Copies level `level` of `pyr` into a dense float32 array
+ * [m][m][m][4] (m = n >> level, z, y, x, channel) at `dense_out` (device).
+ */
+vct_status vct_pyramid_read_level(const vct_pyramid *pyr, int32_t level,
+                                  float *dense_out, vct_stream_t stream);
+
+/*
+ * Synchronises `stream`, then reads and clears the status word in the
+ * pyramid header.  Returns VCT_ERR_TIMEOUT if a kernel that wrote this
+ * pyramid gave up a bounded wait (the pyramid contents are then undefined),
+ * VCT_OK otherwise.
+ */
+vct_status vct_pyramid_status(const vct_pyramid *pyr, vct_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Cone tracing                                                             */
+/* ------------------------------------------------------------------------ */
+/*
+ * Cone set and march parameters (the thesis's VoxSettings, Ch. 5.4.4).
+ * Angles are full aperture angles in radians (Ch. 4.2.2, gamma).
+ */
+typedef struct {
+  int32_t n_diffuse;   /* number of diffuse cones, 0 .. VCT_MAX_DIFFUSE    */
+  int32_t spec_enable; /* 1: trace the specular cone                        */
+  int32_t occ_enable;  /* 1: trace the occlusion cone towards light_dir     */
+  int32_t flags;       /* reserved, must be 0                               */
+  /* Diffuse axes in the pixel's tangent frame (T, B, N): the scene
+   * direction is T*d[0] + B*d[1] + N*d[2] with N the pixel normal,
+   * T = normalize(a x N), B = N x T, a = (1,0,0) if |N.x| < 0.9 else
+   * (0,1,0).  Used as given (not renormalised). */
+  float diffuse_dir[VCT_MAX_DIFFUSE][3];
+  float diffuse_weight[VCT_MAX_DIFFUSE]; /* D = sum_k weight_k (c_k, a_k)   */
+  float diffuse_aperture;                /* in (0, pi)                       */
+  /* Specular cone along the reflection of the view ray about N; aperture
+   * = min + clamp((rho - roughness_min) / (1 - roughness_min), 0, 1)
+   *   * (max - min) with rho the pixel roughness (min if no roughness). */
+  float spec_aperture_min, spec_aperture_max, roughness_min;
+  float occ_aperture;    /* occlusion cone aperture, in (0, pi)              */
+  float light_dir[3];    /* unit vector towards the (directional) light      */
+  float beta;            /* step factor: t += beta * d (Ch. 4.3.2), > 0      */
+  float t0_voxels;       /* first sample at t0 = t0_voxels * h0, > 0         */
+  float normal_offset_voxels; /* apex = x + normal_offset_voxels * h0 * N    */
+  float t_max;           /* the march stops once t > t_max (scene units)     */
+} vct_trace_params;
+
+/*
+ * One view: a G-buffer and its outputs (all device memory, row-major
+ * pixels p = y * width + x).  Masked pixels (mask[p] == 0) get D = S = 0
+ * and Vis = 1.
+ */
+typedef struct {
+  int32_t width, height; /* >= 1                                             */
+  int32_t pyramid;       /* index into the pyramids passed with the views    */
+  int32_t reserved;      /* must be 0                                        */
+  const float *position; /* [H*W*3] surface position, scene units            */
+  const float *normal;   /* [H*W*3] unit surface normal                      */
+  const float *roughness;/* [H*W] in [0,1], or NULL                          */
+  const uint8_t *mask;   /* [H*W], or NULL (every pixel valid)               */
+  float camera[3];       /* eye position (specular view vector x - camera)   */
+  float pad;
+  float *out_diffuse;    /* [H*W*4] D = sum_k w_k (rgb_k, alpha_k), or NULL   */
+  float *out_specular;   /* [H*W*4] S = (rgb, alpha) of the specular cone     */
+  float *out_visibility; /* [H*W] Vis = 1 - alpha of the occlusion cone       */
+} vct_view;
+
+/* Launch shape of the trace kernels (see vct_autotune_trace). */
+typedef struct {
+  int32_t tile_w, tile_h;   /* pixels per work item (queue granularity)      */
+  int32_t lanes_per_pixel;  /* 1, 2, 4 or 8 lanes share one pixel's cones    */
+  int32_t ctas_per_sm;      /* persistent CTAs per SM; 0 = occupancy limit   */
+} vct_launch_config;
+
+/* Per-call counters left in the trace workspace (device memory). */
+typedef struct {
+  uint64_t samples[3]; /* samples taken by diffuse, specular, occlusion cones */
+  uint64_t cones[3];   /* cones traced per kind                               */
+  uint32_t queue;      /* work-queue cursor (internal)                        */
+  uint32_t status;     /* VCT_ERR_TIMEOUT if a bounded wait gave up           */
+} vct_trace_stats;
+
+/* Device workspace bytes vct_trace needs (a vct_trace_stats, padded). */
+size_t vct_trace_workspace_bytes(void);
+
+/*
+ * Traces every pixel of every view (rows a3-a6 of the hot path) in one
+ * persistent launch per group of up to 256 views: CTAs pull pixel tiles
+ * from a queue in `workspace` and march each pixel's cones.
+ *   pyrs[n_pyramids]: pyramids referenced by views[i].pyramid (any dtype).
+ *   params:           cone set and march parameters (host memory).
+ *   cfg:              launch shape, or NULL for the tuned / default shape.
+ *   workspace:        device memory >= vct_trace_workspace_bytes(); zeroed
+ *                     at the start of the call; after the stream reaches the
+ *                     end of the call it holds a vct_trace_stats.
+ * Sampling: level lambda = log2(2 t tan(gamma/2) / h0) clamped to
+ * [0, levels-1]; trilinear at floor(lambda) and floor(lambda)+1, linear in
+ * frac(lambda); colour c += (1 - alpha) a_s c_s, alpha += (1 - alpha) a_s;
+ * float32 arithmetic throughout (FP16 pyramids are widened on load).
+ * Errors: VCT_ERR_INVALID_ARG (NULL pointers where required, bad shapes or
+ * parameters, pyramid index out of range), VCT_ERR_WORKSPACE, VCT_ERR_CUDA.
+ */
+vct_status vct_trace(const vct_pyramid *pyrs, int32_t n_pyramids,
+                     const vct_view *views, int32_t n_views,
+                     const vct_trace_params *params,
+                     const vct_launch_config *cfg, void *workspace,
+                     size_t workspace_bytes, vct_stream_t stream);
+
+/*
+ * Times every candidate launch shape (tile 4x8, 8x8, 8x16, 16x16 x
+ * lanes_per_pixel 1, 2, 4, 8) on the given views, synchronously, and caches
+ * the fastest under (device, dtype of pyrs[0], n of pyrs[0], tracing of the
+ * specular/occlusion cones); vct_trace with cfg == NULL then uses it.  The
+ * views' outputs are overwritten.  `best` (host, may be NULL) receives the
+ * choice.
+ */
+vct_status vct_autotune_trace(const vct_pyramid *pyrs, int32_t n_pyramids,
+                              const vct_view *views, int32_t n_views,
+                              const vct_trace_params *params, void *workspace,
+                              size_t workspace_bytes, vct_stream_t stream,
+                              vct_launch_config *best);
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint                                                                  */
+/* ------------------------------------------------------------------------ */
+/* Upstream gradients of one view (device, same layouts as the outputs). */
+typedef struct {
+  const float *grad_diffuse;    /* [H*W*4] dL/dD, or NULL (zero)             */
+  const float *grad_specular;   /* [H*W*4] dL/dS, or NULL (zero)             */
+  const float *grad_visibility; /* [H*W]   dL/dVis, or NULL (zero)           */
+} vct_view_grad;
+
+/* Device workspace bytes vct_trace_backward needs for `pyr` (a float32
+ * gradient pyramid plus a header). */
+size_t vct_trace_backward_workspace_bytes(const vct_pyramid *pyr);
+
+/*
+ * Gradient of a loss with respect to the dense level-0 grid (rows a7 + a8):
+ * recomputes each cone's march, walks it backwards to form the derivatives
+ * of the front-to-back accumulation, scatters them through the quadrilinear
+ * weights into a float32 gradient pyramid in `workspace`, then pushes each
+ * level down to its children (1/8 each) and ADDS the level-0 result into
+ * grad_level0_dense (device float32 [n][n][n][4], z, y, x, channel).
+ * Every view must use pyramid index 0 (`pyr`), which must be VCT_F32
+ * (VCT_ERR_UNSUPPORTED otherwise).  Scatter order is not deterministic.
+ */
+vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
+                              const vct_view_grad *grads, int32_t n_views,
+                              const vct_trace_params *params,
+                              const vct_launch_config *cfg,
+                              float *grad_level0_dense, void *workspace,
+                              size_t workspace_bytes, vct_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics                                                              */
+/* ------------------------------------------------------------------------ */
+const char *vct_status_string(vct_status status);
+const char *vct_last_error(void);
+int32_t vct_version(void);
+
+/*
+ * Failure-path check of the bounded device waits: launches one CTA that
+ * waits on an mbarrier nothing ever arrives at, with the same bounded-wait
+ * routine the pipelined kernels use, giving up after about `max_ns`
+ * nanoseconds; it then writes VCT_ERR_TIMEOUT to *flag_dev (device uint32).
+ * Nothing is in flight when it gives up.
+ */
+vct_status vct_debug_wait_probe(uint32_t *flag_dev, uint64_t max_ns,
+                                vct_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VCT_H */

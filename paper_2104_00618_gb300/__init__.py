@@ -1,0 +1,291 @@
+"""GB300 voxel cone tracing: Python binding of libvct (argument marshalling only).
+
+Every step of the hot path runs in the CUDA kernels behind ``include/vct.h``;
+this module allocates caller-owned device buffers with PyTorch, fills the C
+structs and calls the C ABI on PyTorch's current stream.  There is no
+fallback: if libvct cannot be built or loaded, every call raises.
+
+Main entry points
+    build_mips(level0, ...)          -> Pyramid            (rows a1 + a2)
+    trace(pyramids, views, params)   -> per-view outputs   (rows a3 .. a6)
+    trace_backward(...)              -> dL/d level-0 grid   (rows a7 + a8)
+    TraceFn / render(...)            -> torch.autograd wrapper
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _abi
+from ._abi import (VCT_F16, VCT_F32, VctError, VctLaunchConfig, VctPyramid, VctTraceParams,
+                   VctTraceStats, VctView, VctViewGrad, check, load)
+
+__all__ = ["Pyramid", "build_mips", "read_level", "pyramid_status", "make_params", "trace",
+           "trace_backward", "autotune", "read_stats", "TraceFn", "render", "VctError",
+           "launch_config", "num_levels", "lib"]
+
+DTYPES = {"f32": VCT_F32, "f16": VCT_F16, VCT_F32: VCT_F32, VCT_F16: VCT_F16}
+
+
+def lib():
+    return load()
+
+
+def _stream(stream=None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def num_levels(n: int) -> int:
+    return n.bit_length()
+
+
+def launch_config(tile_w=8, tile_h=8, lanes_per_pixel=1, ctas_per_sm=0) -> VctLaunchConfig:
+    return VctLaunchConfig(tile_w, tile_h, lanes_per_pixel, ctas_per_sm)
+
+
+# ---------------------------------------------------------------------------
+# pyramids
+# ---------------------------------------------------------------------------
+class Pyramid:
+    """A pyramid in a caller-owned (PyTorch) device buffer."""
+
+    def __init__(self, n: int, levels: int | None = None, dtype="f32",
+                 origin=(0.0, 0.0, 0.0), size: float = 1.0, device=None):
+        self.n = int(n)
+        self.levels = num_levels(n) if levels is None else int(levels)
+        self.dtype = DTYPES[dtype]
+        self.origin = tuple(float(v) for v in origin)
+        self.size = float(size)
+        nbytes = lib().vct_pyramid_bytes(self.n, self.levels, self.dtype)
+        if nbytes == 0:
+            raise VctError(_abi.VCT_ERR_INVALID_ARG,
+                           f"invalid pyramid shape n={n} levels={levels} dtype={dtype}")
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        self.storage = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+
+    def struct(self) -> VctPyramid:
+        return VctPyramid(self.n, self.levels, self.dtype, 0, (ctypes.c_float * 3)(*self.origin),
+                          self.size, self.storage.data_ptr(), self.storage.numel())
+
+    def level_offset(self, level: int) -> int:
+        return int(lib().vct_pyramid_level_offset(self.n, self.levels, self.dtype, level))
+
+
+def build_mips(level0: torch.Tensor, levels: int | None = None, dtype="f32",
+               origin=(0.0, 0.0, 0.0), size: float = 1.0, out: Pyramid | None = None,
+               stream=None) -> Pyramid:
+    """Morton-pack a dense float32 [n,n,n,4] (z,y,x,c) grid and build its mips."""
+    if level0.dtype != torch.float32 or not level0.is_cuda or level0.dim() != 4 \
+            or level0.shape[3] != 4 or not level0.is_contiguous():
+        raise VctError(_abi.VCT_ERR_INVALID_ARG,
+                       "level0 must be a contiguous CUDA float32 tensor [n, n, n, 4]")
+    n = level0.shape[0]
+    pyr = out if out is not None else Pyramid(n, levels, dtype, origin, size, level0.device)
+    p = pyr.struct()
+    check(lib().vct_build_mips(_ptr(level0), ctypes.byref(p), _stream(stream)), "vct_build_mips")
+    return pyr
+
+
+def read_level(pyr: Pyramid, level: int, stream=None) -> torch.Tensor:
+    m = pyr.n >> level
+    out = torch.empty((m, m, m, 4), dtype=torch.float32, device=pyr.storage.device)
+    p = pyr.struct()
+    check(lib().vct_pyramid_read_level(ctypes.byref(p), level, _ptr(out), _stream(stream)),
+          "vct_pyramid_read_level")
+    return out
+
+
+def pyramid_status(pyr: Pyramid, stream=None) -> None:
+    p = pyr.struct()
+    check(lib().vct_pyramid_status(ctypes.byref(p), _stream(stream)), "vct_pyramid_status")
+
+
+# ---------------------------------------------------------------------------
+# parameters and views
+# ---------------------------------------------------------------------------
+def make_params(prm: dict) -> VctTraceParams:
+    """vct_trace_params from a plain dict (keys as in include/vct.h)."""
+    P = VctTraceParams()
+    nd = int(prm["n_diffuse"])
+    P.n_diffuse = nd
+    dirs = torch.as_tensor(prm["diffuse_dir"], dtype=torch.float32).reshape(-1, 3)
+    wts = torch.as_tensor(prm["diffuse_weight"], dtype=torch.float32).reshape(-1)
+    for k in range(min(nd, _abi.MAX_DIFFUSE)):
+        for a in range(3):
+            P.diffuse_dir[k][a] = float(dirs[k, a])
+        P.diffuse_weight[k] = float(wts[k])
+    P.diffuse_aperture = float(prm["diffuse_aperture"])
+    P.spec_enable = int(prm["spec_enable"])
+    P.occ_enable = int(prm["occ_enable"])
+    P.flags = int(prm.get("flags", 0))
+    P.spec_aperture_min = float(prm["spec_aperture_min"])
+    P.spec_aperture_max = float(prm["spec_aperture_max"])
+    P.roughness_min = float(prm["roughness_min"])
+    P.occ_aperture = float(prm["occ_aperture"])
+    light = torch.as_tensor(prm["light_dir"], dtype=torch.float32).reshape(3)
+    for a in range(3):
+        P.light_dir[a] = float(light[a])
+    P.beta = float(prm["beta"])
+    P.t0_voxels = float(prm["t0_voxels"])
+    P.normal_offset_voxels = float(prm["normal_offset_voxels"])
+    P.t_max = float(prm["t_max"])
+    return P
+
+
+@dataclass
+class View:
+    """Device G-buffer of one view plus its output buffers."""
+    width: int
+    height: int
+    position: torch.Tensor
+    normal: torch.Tensor
+    camera: tuple
+    roughness: torch.Tensor | None = None
+    mask: torch.Tensor | None = None
+    pyramid: int = 0
+    out_diffuse: torch.Tensor | None = None
+    out_specular: torch.Tensor | None = None
+    out_visibility: torch.Tensor | None = None
+    keep: list = field(default_factory=list)
+
+    @staticmethod
+    def from_host(v: dict, device="cuda", outputs=True, non_blocking=False) -> "View":
+        """Copies a host G-buffer dict (numpy/tensors) to the device."""
+        def dev(a, dt):
+            if a is None:
+                return None
+            t = torch.as_tensor(a)
+            return t.to(device=device, dtype=dt, non_blocking=non_blocking).contiguous()
+        w, h = int(v["width"]), int(v["height"])
+        view = View(w, h, dev(v["position"], torch.float32), dev(v["normal"], torch.float32),
+                    tuple(float(c) for c in v["camera"]),
+                    dev(v.get("roughness"), torch.float32), dev(v.get("mask"), torch.uint8),
+                    int(v.get("pyramid", 0)))
+        if outputs:
+            view.alloc_outputs()
+        return view
+
+    def alloc_outputs(self, diffuse=True, specular=True, visibility=True):
+        dev = self.position.device
+        npx = self.width * self.height
+        self.out_diffuse = torch.empty((npx, 4), device=dev) if diffuse else None
+        self.out_specular = torch.empty((npx, 4), device=dev) if specular else None
+        self.out_visibility = torch.empty((npx,), device=dev) if visibility else None
+        return self
+
+    def struct(self) -> VctView:
+        return VctView(self.width, self.height, self.pyramid, 0, _ptr(self.position),
+                       _ptr(self.normal), _ptr(self.roughness), _ptr(self.mask),
+                       (ctypes.c_float * 3)(*self.camera), 0.0, _ptr(self.out_diffuse),
+                       _ptr(self.out_specular), _ptr(self.out_visibility))
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.zeros(max(256, nbytes), dtype=torch.uint8, device=device)
+
+
+def read_stats(workspace: torch.Tensor) -> dict:
+    raw = workspace[:ctypes.sizeof(VctTraceStats)].cpu().numpy().tobytes()
+    st = VctTraceStats.from_buffer_copy(raw)
+    return {"samples": list(st.samples), "cones": list(st.cones), "status": int(st.status)}
+
+
+def trace(pyramids, views, params, cfg: VctLaunchConfig | None = None,
+          workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Traces every view into its output buffers; returns the workspace
+    (read it with read_stats after the stream has reached this call)."""
+    pyrs = list(pyramids) if isinstance(pyramids, (list, tuple)) else [pyramids]
+    vs = list(views) if isinstance(views, (list, tuple)) else [views]
+    P = params if isinstance(params, VctTraceParams) else make_params(params)
+    parr = (VctPyramid * len(pyrs))(*[p.struct() for p in pyrs])
+    varr = (VctView * len(vs))(*[v.struct() for v in vs])
+    dev = pyrs[0].storage.device
+    ws = workspace if workspace is not None else _workspace(lib().vct_trace_workspace_bytes(), dev)
+    check(lib().vct_trace(parr, len(pyrs), varr, len(vs), ctypes.byref(P),
+                          None if cfg is None else ctypes.byref(cfg), _ptr(ws), ws.numel(),
+                          _stream(stream)), "vct_trace")
+    return ws
+
+
+def autotune(pyramids, views, params, workspace=None, stream=None) -> VctLaunchConfig:
+    pyrs = list(pyramids) if isinstance(pyramids, (list, tuple)) else [pyramids]
+    vs = list(views) if isinstance(views, (list, tuple)) else [views]
+    P = params if isinstance(params, VctTraceParams) else make_params(params)
+    parr = (VctPyramid * len(pyrs))(*[p.struct() for p in pyrs])
+    varr = (VctView * len(vs))(*[v.struct() for v in vs])
+    ws = workspace if workspace is not None else _workspace(
+        lib().vct_trace_workspace_bytes(), pyrs[0].storage.device)
+    best = VctLaunchConfig()
+    check(lib().vct_autotune_trace(parr, len(pyrs), varr, len(vs), ctypes.byref(P), _ptr(ws),
+                                   ws.numel(), _stream(stream), ctypes.byref(best)),
+          "vct_autotune_trace")
+    return best
+
+
+def backward_workspace(pyr: Pyramid) -> torch.Tensor:
+    p = pyr.struct()
+    nbytes = lib().vct_trace_backward_workspace_bytes(ctypes.byref(p))
+    return torch.empty(nbytes, dtype=torch.uint8, device=pyr.storage.device)
+
+
+def trace_backward(pyr: Pyramid, views, grads, params, grad_level0: torch.Tensor | None = None,
+                   cfg: VctLaunchConfig | None = None, workspace: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    """Accumulates dL/d(level-0 grid) into grad_level0 ([n,n,n,4] float32).
+    grads: per view (grad_D [H*W,4] | None, grad_S | None, grad_Vis [H*W] | None)."""
+    vs = list(views) if isinstance(views, (list, tuple)) else [views]
+    P = params if isinstance(params, VctTraceParams) else make_params(params)
+    if grad_level0 is None:
+        grad_level0 = torch.zeros((pyr.n,) * 3 + (4,), dtype=torch.float32,
+                                  device=pyr.storage.device)
+    ws = workspace if workspace is not None else backward_workspace(pyr)
+    p = pyr.struct()
+    varr = (VctView * len(vs))(*[v.struct() for v in vs])
+    keep = []
+    garr = (VctViewGrad * len(vs))()
+    for i, g in enumerate(grads):
+        gd, gs, gv = (None if t is None else t.contiguous() for t in g)
+        keep.extend(t for t in (gd, gs, gv) if t is not None)
+        garr[i] = VctViewGrad(_ptr(gd), _ptr(gs), _ptr(gv))
+    check(lib().vct_trace_backward(ctypes.byref(p), varr, garr, len(vs), ctypes.byref(P),
+                                   None if cfg is None else ctypes.byref(cfg), _ptr(grad_level0),
+                                   _ptr(ws), ws.numel(), _stream(stream)),
+          "vct_trace_backward")
+    return grad_level0
+
+
+# ---------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------
+class TraceFn(torch.autograd.Function):
+    """(level-0 grid) -> (D, S, Vis) of one view; backward through the cone
+    march and the mip box filter by the hand-written adjoint kernels."""
+
+    @staticmethod
+    def forward(ctx, level0, view: View, params, levels, origin, size):
+        pyr = build_mips(level0.detach().contiguous(), levels, "f32", origin, size)
+        v = dataclasses.replace(view, keep=[])
+        v.alloc_outputs()
+        trace(pyr, [v], params)
+        ctx.pyr, ctx.view, ctx.params = pyr, v, params
+        return v.out_diffuse, v.out_specular, v.out_visibility
+
+    @staticmethod
+    def backward(ctx, gD, gS, gV):
+        grad = trace_backward(ctx.pyr, [ctx.view], [(gD, gS, gV)], ctx.params)
+        return grad, None, None, None, None, None
+
+
+def render(level0: torch.Tensor, view: View, params, levels=None, origin=(0.0, 0.0, 0.0),
+           size: float = 1.0):
+    """Differentiable (D, S, Vis) of one view from a level-0 grid."""
+    P = params if isinstance(params, VctTraceParams) else make_params(params)
+    return TraceFn.apply(level0, view, P, levels, origin, size)

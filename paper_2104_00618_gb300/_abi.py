@@ -1,0 +1,121 @@
+"""ctypes mirror of include/vct.h and the loader of libvct.so."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+MAX_DIFFUSE = 32
+MAX_PYRAMIDS = 8
+MAX_LEVELS = 11
+
+VCT_OK, VCT_ERR_INVALID_ARG, VCT_ERR_CUDA, VCT_ERR_WORKSPACE, VCT_ERR_UNSUPPORTED, \
+    VCT_ERR_TIMEOUT = range(6)
+VCT_F32, VCT_F16 = 0, 1
+
+_c_i32, _c_u64, _c_f32, _vp = ctypes.c_int32, ctypes.c_uint64, ctypes.c_float, ctypes.c_void_p
+
+
+class VctPyramid(ctypes.Structure):
+    _fields_ = [("n", _c_i32), ("levels", _c_i32), ("dtype", _c_i32), ("reserved", _c_i32),
+                ("origin", _c_f32 * 3), ("size", _c_f32), ("data", _vp), ("bytes", _c_u64)]
+
+
+class VctTraceParams(ctypes.Structure):
+    _fields_ = [("n_diffuse", _c_i32), ("spec_enable", _c_i32), ("occ_enable", _c_i32),
+                ("flags", _c_i32),
+                ("diffuse_dir", (_c_f32 * 3) * MAX_DIFFUSE),
+                ("diffuse_weight", _c_f32 * MAX_DIFFUSE),
+                ("diffuse_aperture", _c_f32),
+                ("spec_aperture_min", _c_f32), ("spec_aperture_max", _c_f32),
+                ("roughness_min", _c_f32), ("occ_aperture", _c_f32),
+                ("light_dir", _c_f32 * 3), ("beta", _c_f32), ("t0_voxels", _c_f32),
+                ("normal_offset_voxels", _c_f32), ("t_max", _c_f32)]
+
+
+class VctView(ctypes.Structure):
+    _fields_ = [("width", _c_i32), ("height", _c_i32), ("pyramid", _c_i32), ("reserved", _c_i32),
+                ("position", _vp), ("normal", _vp), ("roughness", _vp), ("mask", _vp),
+                ("camera", _c_f32 * 3), ("pad", _c_f32),
+                ("out_diffuse", _vp), ("out_specular", _vp), ("out_visibility", _vp)]
+
+
+class VctLaunchConfig(ctypes.Structure):
+    _fields_ = [("tile_w", _c_i32), ("tile_h", _c_i32), ("lanes_per_pixel", _c_i32),
+                ("ctas_per_sm", _c_i32)]
+
+
+class VctTraceStats(ctypes.Structure):
+    _fields_ = [("samples", ctypes.c_uint64 * 3), ("cones", ctypes.c_uint64 * 3),
+                ("queue", ctypes.c_uint32), ("status", ctypes.c_uint32)]
+
+
+class VctViewGrad(ctypes.Structure):
+    _fields_ = [("grad_diffuse", _vp), ("grad_specular", _vp), ("grad_visibility", _vp)]
+
+
+EXPORTS = {
+    "vct_pyramid_bytes": (ctypes.c_size_t, [_c_i32, _c_i32, _c_i32]),
+    "vct_pyramid_level_offset": (_c_u64, [_c_i32, _c_i32, _c_i32, _c_i32]),
+    "vct_build_mips": (_c_i32, [_vp, ctypes.POINTER(VctPyramid), _vp]),
+    "vct_pyramid_read_level": (_c_i32, [ctypes.POINTER(VctPyramid), _c_i32, _vp, _vp]),
+    "vct_pyramid_status": (_c_i32, [ctypes.POINTER(VctPyramid), _vp]),
+    "vct_trace_workspace_bytes": (ctypes.c_size_t, []),
+    "vct_trace": (_c_i32, [ctypes.POINTER(VctPyramid), _c_i32, ctypes.POINTER(VctView), _c_i32,
+                           ctypes.POINTER(VctTraceParams), ctypes.POINTER(VctLaunchConfig), _vp,
+                           ctypes.c_size_t, _vp]),
+    "vct_autotune_trace": (_c_i32, [ctypes.POINTER(VctPyramid), _c_i32, ctypes.POINTER(VctView),
+                                    _c_i32, ctypes.POINTER(VctTraceParams), _vp, ctypes.c_size_t,
+                                    _vp, ctypes.POINTER(VctLaunchConfig)]),
+    "vct_trace_backward_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(VctPyramid)]),
+    "vct_trace_backward": (_c_i32, [ctypes.POINTER(VctPyramid), ctypes.POINTER(VctView),
+                                    ctypes.POINTER(VctViewGrad), _c_i32,
+                                    ctypes.POINTER(VctTraceParams),
+                                    ctypes.POINTER(VctLaunchConfig), _vp, _vp, ctypes.c_size_t,
+                                    _vp]),
+    "vct_status_string": (ctypes.c_char_p, [_c_i32]),
+    "vct_last_error": (ctypes.c_char_p, []),
+    "vct_version": (_c_i32, []),
+    "vct_debug_wait_probe": (_c_i32, [_vp, _c_u64, _vp]),
+}
+
+_LOCK = threading.Lock()
+_LIB = None
+
+
+class VctError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libvct.so (building it first if needed).  Raises if unavailable:
+    there is no fallback implementation."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libvct.so not found at {path}; run the build first")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+        return lib
+
+
+def check(status: int, what: str) -> None:
+    if status != VCT_OK:
+        lib = load()
+        raise VctError(status, f"{what}: {lib.vct_status_string(status).decode()}: "
+                               f"{lib.vct_last_error().decode()}")

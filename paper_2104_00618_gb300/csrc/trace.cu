@@ -1,0 +1,206 @@
+// Forward cone trace (rows a3-a6): persistent CTAs pull pixel tiles from a
+// queue; every pixel marches its diffuse, specular and occlusion cones
+// through the Morton-ordered pyramid (Ch. 4.2, Ch. 4.3.2, Ch. 4.5).
+#include "trace_common.cuh"
+
+namespace vct {
+
+namespace {
+
+// Finds the view whose tile range holds `item` (views sorted by tile_begin).
+template <typename Launch>
+__device__ __forceinline__ int find_view(const Launch &L, int item) {
+  int lo = 0, hi = L.n_views - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (L.views[mid].tile_begin <= item)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// One cone: returns (rgb, alpha) and, in `trans`, the transmittance
+// T = prod_k (1 - a_k).  The thesis's occlusion update alpha += (1 - alpha) a_s
+// is carried as T (alpha = 1 - T, the same recurrence) so that T, the colour
+// weights T_k a_k and the visibility keep their relative precision as alpha
+// approaches one; the loop runs while alpha = 1 - T < 1 in float32.
+template <int DT>
+__device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const float w[3],
+                                        const ConeConst &cc, float T0, uint32_t &nsamp,
+                                        float &trans) {
+  float cr = 0.f, cg = 0.f, cb = 0.f, tr = 1.f;
+  int k = 0;
+  for (; k < cc.kmax; ++k) {
+    if (!((1.0f - tr) < 1.0f)) break;
+    float T, lam;
+    step_at(cc, T0, k, T, lam);
+    const float F[3] = {fmaf(T, w[0], A.Of[0]), fmaf(T, w[1], A.Of[1]), fmaf(T, w[2], A.Of[2])};
+    const float4 s = sample<DT>(P, A, F, lam);
+    const float wg = tr * s.w;  // front-to-back weight T_k a_s
+    cr = fmaf(wg, s.x, cr);
+    cg = fmaf(wg, s.y, cg);
+    cb = fmaf(wg, s.z, cb);
+    tr *= 1.0f - s.w;
+  }
+  nsamp += (uint32_t)k;
+  trans = tr;
+  return make_float4(cr, cg, cb, 1.0f - tr);
+}
+
+// Each warp works independently: it takes a tile of pixels from the queue
+// and covers it in rounds of 32 / LPP pixels (LPP lanes share one pixel's
+// cones).  No block-wide barrier anywhere.
+template <int LPP, int DT>
+__global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(const __grid_constant__ TraceLaunch L) {
+  constexpr int kPixPerRound = 32 / LPP;
+  uint32_t n_samp[3] = {0u, 0u, 0u}, n_cone[3] = {0u, 0u, 0u};
+  const int lane = threadIdx.x & 31;
+  const int slot = lane % LPP;
+  const int pr = lane / LPP;
+  const int n_cones = L.n_diffuse + L.spec_enable + L.occ_enable;
+  const float T0 = (float)L.t0_vox;
+
+  for (;;) {
+    const int item = next_item(L.queue);
+    if (item >= L.total_tiles) break;
+    const int vi = find_view(L, item);
+    const DevView &V = L.views[vi];
+    const DevPyr &P = L.pyr[V.pyr];
+    const int t = item - V.tile_begin;
+    const int tx0 = (t % V.tiles_x) * L.tile_w;
+    const int ty0 = (t / V.tiles_x) * L.tile_h;
+    const int tile_pix = L.tile_w * L.tile_h;
+
+    for (int base = 0; base < tile_pix; base += kPixPerRound) {
+      const int pi = base + pr;
+      const int px = tx0 + pi % L.tile_w;
+      const int py = ty0 + pi / L.tile_w;
+      const bool inimg = pi < tile_pix && px < V.W && py < V.H;
+      const int p = py * V.W + px;
+      bool active = inimg && (V.mask == nullptr || V.mask[p] != 0);
+
+      float4 D = make_float4(0.f, 0.f, 0.f, 0.f), S = D;
+      float vis = 0.f;  // transmittance of the occlusion cone, summed over the pixel's lanes
+      int has_occ = 0;
+      if (active) {
+        float x[3], n[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          x[a] = V.pos[3 * p + a];
+          n[a] = V.nrm[3 * p + a];
+        }
+        Apex A;
+        make_apex(P, x, n, L.normal_offset, A);
+        float Tf[3], Bf[3];
+        tangent_frame(n, Tf, Bf);
+        for (int c = slot; c < n_cones; c += LPP) {
+          const ConeSel cs = select_cone(c, L.spec_enable, L.occ_enable);
+          float w[3];
+          ConeConst cc;
+          if (cs.kind == kSpecular) {
+            reflect_dir(x, V.cam, n, w);
+            cc = spec_const(P, L.spec_gmin, L.spec_gmax, L.rough_min, L.beta, L.t0_vox,
+                            V.rough, p);
+          } else if (cs.kind == kOcclusion) {
+            w[0] = L.light[0];
+            w[1] = L.light[1];
+            w[2] = L.light[2];
+            cc = P.occ;
+          } else {
+            const float *d = L.diffuse_dir[cs.diffuse_index];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) w[a] = fmaf(Tf[a], d[0], fmaf(Bf[a], d[1], n[a] * d[2]));
+            cc = P.diffuse;
+          }
+          float trans;
+          const float4 r = march<DT>(P, A, w, cc, T0, n_samp[cs.kind], trans);
+          n_cone[cs.kind] += 1u;
+          if (cs.kind == kDiffuse) {
+            const float wt = L.diffuse_weight[cs.diffuse_index];
+            D.x = fmaf(wt, r.x, D.x);
+            D.y = fmaf(wt, r.y, D.y);
+            D.z = fmaf(wt, r.z, D.z);
+            D.w = fmaf(wt, r.w, D.w);
+          } else if (cs.kind == kSpecular) {
+            S = r;
+          } else {
+            vis = trans;
+            has_occ = 1;
+          }
+        }
+      }
+      // Combine the lanes that share a pixel.
+#pragma unroll
+      for (int m = 1; m < LPP; m <<= 1) {
+        D.x += __shfl_xor_sync(0xffffffffu, D.x, m);
+        D.y += __shfl_xor_sync(0xffffffffu, D.y, m);
+        D.z += __shfl_xor_sync(0xffffffffu, D.z, m);
+        D.w += __shfl_xor_sync(0xffffffffu, D.w, m);
+        S.x += __shfl_xor_sync(0xffffffffu, S.x, m);
+        S.y += __shfl_xor_sync(0xffffffffu, S.y, m);
+        S.z += __shfl_xor_sync(0xffffffffu, S.z, m);
+        S.w += __shfl_xor_sync(0xffffffffu, S.w, m);
+        vis += __shfl_xor_sync(0xffffffffu, vis, m);
+        has_occ |= __shfl_xor_sync(0xffffffffu, has_occ, m);
+      }
+      if (inimg && slot == 0) {
+        if (V.outD) reinterpret_cast<float4 *>(V.outD)[p] = D;
+        if (V.outS) reinterpret_cast<float4 *>(V.outS)[p] = S;
+        if (V.outV) V.outV[p] = has_occ ? vis : 1.0f;
+      }
+    }
+  }
+  // Per-kind sample and cone counters: one atomic per warp.
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const uint32_t s = __reduce_add_sync(0xffffffffu, n_samp[k]);
+    const uint32_t c = __reduce_add_sync(0xffffffffu, n_cone[k]);
+    if ((threadIdx.x & 31) == 0) {
+      if (s) atomicAdd(L.stats + k, (unsigned long long)s);
+      if (c) atomicAdd(L.stats + 3 + k, (unsigned long long)c);
+    }
+  }
+}
+
+template <int LPP, int DT>
+cudaError_t launch_t(const TraceLaunch &L, int grid, cudaStream_t s) {
+  trace_kernel<LPP, DT><<<grid, kTraceThreads, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+template <int LPP, int DT>
+int occ_t() {
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<LPP, DT>, kTraceThreads, 0);
+  return b;
+}
+
+}  // namespace
+
+static_assert(sizeof(TraceLaunch) <= 32000, "trace launch parameters exceed the 32 KB limit");
+
+cudaError_t launch_trace(const TraceLaunch &L, int lpp, int dtype, int grid, cudaStream_t s) {
+  const bool h = dtype == VCT_F16;
+  switch (lpp) {
+    case 1: return h ? launch_t<1, VCT_F16>(L, grid, s) : launch_t<1, VCT_F32>(L, grid, s);
+    case 2: return h ? launch_t<2, VCT_F16>(L, grid, s) : launch_t<2, VCT_F32>(L, grid, s);
+    case 4: return h ? launch_t<4, VCT_F16>(L, grid, s) : launch_t<4, VCT_F32>(L, grid, s);
+    case 8: return h ? launch_t<8, VCT_F16>(L, grid, s) : launch_t<8, VCT_F32>(L, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int trace_occupancy(int lpp, int dtype) {
+  const bool h = dtype == VCT_F16;
+  switch (lpp) {
+    case 1: return h ? occ_t<1, VCT_F16>() : occ_t<1, VCT_F32>();
+    case 2: return h ? occ_t<2, VCT_F16>() : occ_t<2, VCT_F32>();
+    case 4: return h ? occ_t<4, VCT_F16>() : occ_t<4, VCT_F32>();
+    case 8: return h ? occ_t<8, VCT_F16>() : occ_t<8, VCT_F32>();
+    default: return 0;
+  }
+}
+
+}  // namespace vct

@@ -1,0 +1,535 @@
+// C ABI of libvct: argument validation, pyramid layout, launch assembly and
+// the launch-shape tuner.  Every entry point returns a vct_status and records
+// a thread-local message on failure; nothing aborts or throws across the ABI.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "vct_internal.cuh"
+
+using namespace vct;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+vct_status fail(vct_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+vct_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(VCT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+bool finite(float v) { return std::isfinite(v); }
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+bool shape_ok(int n, int levels, int dtype) {
+  return is_pow2(n) && n >= 2 && n <= 1024 && levels >= 1 && levels <= ilog2(n) + 1 &&
+         (dtype == VCT_F32 || dtype == VCT_F16);
+}
+
+vct_status check_pyramid(const vct_pyramid *p, const char *what) {
+  if (!p) return fail(VCT_ERR_INVALID_ARG, "%s: NULL pyramid", what);
+  if (!shape_ok(p->n, p->levels, p->dtype) || p->reserved != 0)
+    return fail(VCT_ERR_INVALID_ARG, "%s: bad pyramid shape n=%d levels=%d dtype=%d", what, p->n,
+                p->levels, p->dtype);
+  if (!(p->size > 0.0f) || !finite(p->size) || !finite(p->origin[0]) || !finite(p->origin[1]) ||
+      !finite(p->origin[2]))
+    return fail(VCT_ERR_INVALID_ARG, "%s: bad pyramid origin/size", what);
+  if (!p->data || !aligned(p->data, 256))
+    return fail(VCT_ERR_INVALID_ARG, "%s: pyramid data NULL or not 256-byte aligned", what);
+  const Layout L = make_layout(p->n, p->levels, p->dtype);
+  if (p->bytes < L.total)
+    return fail(VCT_ERR_INVALID_ARG, "%s: pyramid bytes %llu < required %llu", what,
+                (unsigned long long)p->bytes, (unsigned long long)L.total);
+  return VCT_OK;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point.
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+// ---------------------------------------------------------------------------
+// trace parameters
+// ---------------------------------------------------------------------------
+constexpr double kPi = 3.14159265358979323846;
+
+bool aperture_ok(float g) { return finite(g) && g > 0.0f && g < (float)kPi; }
+
+vct_status check_params(const vct_trace_params *P) {
+  if (!P) return fail(VCT_ERR_INVALID_ARG, "params: NULL");
+  if (P->n_diffuse < 0 || P->n_diffuse > VCT_MAX_DIFFUSE)
+    return fail(VCT_ERR_INVALID_ARG, "params: n_diffuse %d out of [0, %d]", P->n_diffuse,
+                VCT_MAX_DIFFUSE);
+  if ((P->spec_enable != 0 && P->spec_enable != 1) || (P->occ_enable != 0 && P->occ_enable != 1))
+    return fail(VCT_ERR_INVALID_ARG, "params: spec_enable/occ_enable must be 0 or 1");
+  if (P->flags != 0) return fail(VCT_ERR_UNSUPPORTED, "params: flags %d not supported", P->flags);
+  if (P->n_diffuse > 0 && !aperture_ok(P->diffuse_aperture))
+    return fail(VCT_ERR_INVALID_ARG, "params: diffuse_aperture must be in (0, pi)");
+  for (int k = 0; k < P->n_diffuse; ++k)
+    if (!finite(P->diffuse_dir[k][0]) || !finite(P->diffuse_dir[k][1]) ||
+        !finite(P->diffuse_dir[k][2]) || !finite(P->diffuse_weight[k]))
+      return fail(VCT_ERR_INVALID_ARG, "params: diffuse cone %d not finite", k);
+  if (P->spec_enable) {
+    if (!aperture_ok(P->spec_aperture_min) || !aperture_ok(P->spec_aperture_max))
+      return fail(VCT_ERR_INVALID_ARG, "params: specular apertures must be in (0, pi)");
+    if (!finite(P->roughness_min) || P->roughness_min >= 1.0f)
+      return fail(VCT_ERR_INVALID_ARG, "params: roughness_min must be < 1");
+  }
+  if (P->occ_enable) {
+    if (!aperture_ok(P->occ_aperture))
+      return fail(VCT_ERR_INVALID_ARG, "params: occ_aperture must be in (0, pi)");
+    if (!finite(P->light_dir[0]) || !finite(P->light_dir[1]) || !finite(P->light_dir[2]))
+      return fail(VCT_ERR_INVALID_ARG, "params: light_dir not finite");
+  }
+  if (!(P->beta > 0.0f) || !finite(P->beta) || !(P->t0_voxels > 0.0f) || !finite(P->t0_voxels) ||
+      !(P->t_max > 0.0f) || !finite(P->t_max) || !finite(P->normal_offset_voxels))
+    return fail(VCT_ERR_INVALID_ARG, "params: beta, t0_voxels, t_max must be > 0 and finite");
+  return VCT_OK;
+}
+
+vct_status fill_pyr(const vct_pyramid &p, const vct_trace_params &P, DevPyr &d) {
+  const Layout L = make_layout(p.n, p.levels, p.dtype);
+  memset(&d, 0, sizeof(d));
+  for (int l = 0; l < p.levels; ++l)
+    d.lvl[l] = static_cast<const uint8_t *>(p.data) + L.level_off[l];
+  for (int a = 0; a < 3; ++a) d.origin[a] = p.origin[a];
+  d.scale = (double)p.n / (double)p.size;
+  d.tmax_vox = (double)P.t_max * d.scale;
+  d.n = p.n;
+  d.levels = p.levels;
+  d.dtype = p.dtype;
+  const double beta = P.beta, t0 = P.t0_voxels;
+  auto mk = [&](float g, ConeConst &c, const char *name) -> vct_status {
+    c = cone_const((double)g, beta, t0, d.tmax_vox);
+    if (c.kmax > kMaxSteps)
+      return fail(VCT_ERR_INVALID_ARG, "params: %s cone needs more than %d steps", name,
+                  kMaxSteps);
+    return VCT_OK;
+  };
+  vct_status st = VCT_OK;
+  if (P.n_diffuse > 0 && (st = mk(P.diffuse_aperture, d.diffuse, "diffuse")) != VCT_OK) return st;
+  if (P.occ_enable && (st = mk(P.occ_aperture, d.occ, "occlusion")) != VCT_OK) return st;
+  if (P.spec_enable) {
+    if ((st = mk(P.spec_aperture_min, d.spec_fixed, "specular")) != VCT_OK) return st;
+    ConeConst tmp;
+    if ((st = mk(P.spec_aperture_max, tmp, "specular")) != VCT_OK) return st;
+  }
+  return VCT_OK;
+}
+
+template <typename LaunchT>
+void fill_common(const vct_trace_params &P, LaunchT &L) {
+  L.n_diffuse = P.n_diffuse;
+  L.spec_enable = P.spec_enable;
+  L.occ_enable = P.occ_enable;
+  for (int k = 0; k < VCT_MAX_DIFFUSE; ++k) {
+    for (int a = 0; a < 3; ++a) L.diffuse_dir[k][a] = k < P.n_diffuse ? P.diffuse_dir[k][a] : 0.f;
+    L.diffuse_weight[k] = k < P.n_diffuse ? P.diffuse_weight[k] : 0.f;
+  }
+  for (int a = 0; a < 3; ++a) L.light[a] = P.light_dir[a];
+  L.normal_offset = P.normal_offset_voxels;
+  L.spec_gmin = P.spec_aperture_min;
+  L.spec_gmax = P.spec_aperture_max;
+  L.rough_min = P.roughness_min;
+  L.beta = P.beta;
+  L.t0_vox = P.t0_voxels;
+}
+
+vct_status check_view(const vct_view &v, int i, int n_pyr, bool need_outputs) {
+  if (v.width < 1 || v.height < 1 || (int64_t)v.width * v.height > (int64_t)1 << 29)
+    return fail(VCT_ERR_INVALID_ARG, "view %d: bad size %dx%d", i, v.width, v.height);
+  if (v.pyramid < 0 || v.pyramid >= n_pyr || v.reserved != 0)
+    return fail(VCT_ERR_INVALID_ARG, "view %d: pyramid index %d out of range", i, v.pyramid);
+  if (!v.position || !v.normal || !aligned(v.position, 4) || !aligned(v.normal, 4))
+    return fail(VCT_ERR_INVALID_ARG, "view %d: position/normal NULL or misaligned", i);
+  if (v.roughness && !aligned(v.roughness, 4))
+    return fail(VCT_ERR_INVALID_ARG, "view %d: roughness misaligned", i);
+  if ((v.out_diffuse && !aligned(v.out_diffuse, 16)) ||
+      (v.out_specular && !aligned(v.out_specular, 16)) ||
+      (v.out_visibility && !aligned(v.out_visibility, 4)))
+    return fail(VCT_ERR_INVALID_ARG, "view %d: outputs must be 16-byte aligned", i);
+  if (need_outputs && !v.out_diffuse && !v.out_specular && !v.out_visibility)
+    return fail(VCT_ERR_INVALID_ARG, "view %d: no output buffer", i);
+  if (!finite(v.camera[0]) || !finite(v.camera[1]) || !finite(v.camera[2]))
+    return fail(VCT_ERR_INVALID_ARG, "view %d: camera not finite", i);
+  return VCT_OK;
+}
+
+void fill_view(const vct_view &v, int tile_w, int tile_h, int &tile_cursor, DevView &d) {
+  d.pos = v.position;
+  d.nrm = v.normal;
+  d.rough = v.roughness;
+  d.mask = v.mask;
+  d.outD = v.out_diffuse;
+  d.outS = v.out_specular;
+  d.outV = v.out_visibility;
+  for (int a = 0; a < 3; ++a) d.cam[a] = v.camera[a];
+  d.W = v.width;
+  d.H = v.height;
+  d.pyr = v.pyramid;
+  d.tiles_x = (v.width + tile_w - 1) / tile_w;
+  d.tile_begin = tile_cursor;
+  tile_cursor += d.tiles_x * ((v.height + tile_h - 1) / tile_h);
+}
+
+bool cfg_ok(const vct_launch_config &c) {
+  const int lpp = c.lanes_per_pixel;
+  return c.tile_w >= 1 && c.tile_h >= 1 && c.tile_w * c.tile_h <= 4096 &&
+         (lpp == 1 || lpp == 2 || lpp == 4 || lpp == 8) && c.ctas_per_sm >= 0 &&
+         c.ctas_per_sm <= 32;
+}
+
+// Launch-shape cache filled by vct_autotune_trace.
+using TuneKey = std::tuple<int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, vct_launch_config> g_tuned;
+
+TuneKey tune_key(const vct_pyramid *pyrs, const vct_view *views, const vct_trace_params *P) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return TuneKey(dev, pyrs[0].dtype, pyrs[0].n, P->spec_enable, P->occ_enable,
+                 views[0].roughness != nullptr);
+}
+
+vct_launch_config default_cfg() { return vct_launch_config{8, 8, 1, 0}; }
+
+vct_launch_config pick_cfg(const vct_launch_config *cfg, const vct_pyramid *pyrs,
+                           const vct_view *views, const vct_trace_params *P) {
+  if (cfg) return *cfg;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_tuned.find(tune_key(pyrs, views, P));
+  return it == g_tuned.end() ? default_cfg() : it->second;
+}
+
+struct TraceStatsLayout {
+  static constexpr size_t queue_off = offsetof(vct_trace_stats, queue);
+};
+
+}  // namespace
+
+extern "C" {
+
+const char *vct_status_string(vct_status s) {
+  switch (s) {
+    case VCT_OK: return "VCT_OK";
+    case VCT_ERR_INVALID_ARG: return "VCT_ERR_INVALID_ARG";
+    case VCT_ERR_CUDA: return "VCT_ERR_CUDA";
+    case VCT_ERR_WORKSPACE: return "VCT_ERR_WORKSPACE";
+    case VCT_ERR_UNSUPPORTED: return "VCT_ERR_UNSUPPORTED";
+    case VCT_ERR_TIMEOUT: return "VCT_ERR_TIMEOUT";
+  }
+  return "VCT_ERR_UNKNOWN";
+}
+
+const char *vct_last_error(void) { return g_last_error.c_str(); }
+
+int32_t vct_version(void) { return 1; }
+
+size_t vct_pyramid_bytes(int32_t n, int32_t levels, int32_t dtype) {
+  if (!shape_ok(n, levels, dtype)) return 0;
+  return (size_t)make_layout(n, levels, dtype).total;
+}
+
+uint64_t vct_pyramid_level_offset(int32_t n, int32_t levels, int32_t dtype, int32_t level) {
+  if (!shape_ok(n, levels, dtype) || level < 0 || level >= levels) return 0;
+  return make_layout(n, levels, dtype).level_off[level];
+}
+
+vct_status vct_build_mips(const float *level0_dense, const vct_pyramid *pyr, vct_stream_t stream) {
+  vct_status st = check_pyramid(pyr, "vct_build_mips");
+  if (st != VCT_OK) return st;
+  if (!level0_dense || !aligned(level0_dense, 16))
+    return fail(VCT_ERR_INVALID_ARG, "vct_build_mips: level0 NULL or not 16-byte aligned");
+  auto enc = encode_fn();
+  if (!enc) return fail(VCT_ERR_CUDA, "vct_build_mips: cuTensorMapEncodeTiled unavailable");
+  const int n = pyr->n, B = pack_block(n);
+  alignas(64) CUtensorMap map;
+  cuuint64_t dims[4] = {4, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n};
+  cuuint64_t strides[3] = {16, 16ull * n, 16ull * n * n};
+  cuuint32_t box[4] = {4, (cuuint32_t)B, (cuuint32_t)B, (cuuint32_t)B};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(level0_dense),
+                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(VCT_ERR_CUDA, "vct_build_mips: tensor map encode failed (%d)", (int)r);
+  cudaError_t e = launch_pack_mips(level0_dense, *pyr, map, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "vct_build_mips launch");
+  return VCT_OK;
+}
+
+vct_status vct_pyramid_read_level(const vct_pyramid *pyr, int32_t level, float *dense_out,
+                                  vct_stream_t stream) {
+  vct_status st = check_pyramid(pyr, "vct_pyramid_read_level");
+  if (st != VCT_OK) return st;
+  if (level < 0 || level >= pyr->levels)
+    return fail(VCT_ERR_INVALID_ARG, "vct_pyramid_read_level: level %d out of range", level);
+  if (!dense_out || !aligned(dense_out, 16))
+    return fail(VCT_ERR_INVALID_ARG, "vct_pyramid_read_level: output NULL or misaligned");
+  cudaError_t e = launch_read_level(*pyr, level, dense_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "vct_pyramid_read_level launch");
+  return VCT_OK;
+}
+
+vct_status vct_pyramid_status(const vct_pyramid *pyr, vct_stream_t stream) {
+  vct_status st = check_pyramid(pyr, "vct_pyramid_status");
+  if (st != VCT_OK) return st;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "vct_pyramid_status sync");
+  uint32_t word = 0, zero = 0;
+  e = cudaMemcpy(&word, pyr->data, 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(pyr->data, &zero, 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "vct_pyramid_status copy");
+  if (word == (uint32_t)VCT_ERR_TIMEOUT)
+    return fail(VCT_ERR_TIMEOUT, "a kernel gave up a bounded wait while building this pyramid");
+  return VCT_OK;
+}
+
+size_t vct_trace_workspace_bytes(void) { return 256; }
+
+static vct_status trace_impl(const vct_pyramid *pyrs, int32_t n_pyr, const vct_view *views,
+                             int32_t n_views, const vct_trace_params *params,
+                             const vct_launch_config &cfg, void *workspace,
+                             size_t workspace_bytes, cudaStream_t stream, bool zero_stats) {
+  auto L = std::make_unique<TraceLaunch>();
+  memset(L.get(), 0, sizeof(TraceLaunch));
+  fill_common(*params, *L);
+  for (int i = 0; i < n_pyr; ++i) {
+    vct_status st = fill_pyr(pyrs[i], *params, L->pyr[i]);
+    if (st != VCT_OK) return st;
+  }
+  L->tile_w = cfg.tile_w;
+  L->tile_h = cfg.tile_h;
+  uint8_t *ws = static_cast<uint8_t *>(workspace);
+  L->stats = reinterpret_cast<unsigned long long *>(ws);
+  L->queue = reinterpret_cast<unsigned *>(ws + TraceStatsLayout::queue_off);
+  cudaError_t e;
+  if (zero_stats && (e = cudaMemsetAsync(ws, 0, sizeof(vct_trace_stats), stream)) != cudaSuccess)
+    return cuda_fail(e, "vct_trace workspace clear");
+  int per_sm = cfg.ctas_per_sm;
+  if (per_sm == 0) per_sm = std::max(1, trace_occupancy(cfg.lanes_per_pixel, pyrs[0].dtype));
+  const int sms = sm_count();
+  for (int v0 = 0; v0 < n_views; v0 += kMaxViewsPerLaunch) {
+    const int nv = std::min(kMaxViewsPerLaunch, n_views - v0);
+    int cursor = 0;
+    bool mixed = false;
+    for (int i = 0; i < nv; ++i) {
+      fill_view(views[v0 + i], cfg.tile_w, cfg.tile_h, cursor, L->views[i]);
+      mixed |= pyrs[views[v0 + i].pyramid].dtype != pyrs[views[v0].pyramid].dtype;
+    }
+    if (mixed)
+      return fail(VCT_ERR_UNSUPPORTED, "vct_trace: views of one call must use pyramids of one dtype");
+    L->n_views = nv;
+    L->total_tiles = cursor;
+    if (v0 > 0 && (e = cudaMemsetAsync(L->queue, 0, 4, stream)) != cudaSuccess)
+      return cuda_fail(e, "vct_trace queue clear");
+    const int grid = std::max(1, std::min(cursor, per_sm * sms));
+    e = launch_trace(*L, cfg.lanes_per_pixel, pyrs[views[v0].pyramid].dtype, grid, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "vct_trace launch");
+  }
+  return VCT_OK;
+}
+
+static vct_status trace_checks(const vct_pyramid *pyrs, int32_t n_pyr, const vct_view *views,
+                               int32_t n_views, const vct_trace_params *params,
+                               void *workspace, size_t workspace_bytes) {
+  if (!pyrs || n_pyr < 1 || n_pyr > VCT_MAX_PYRAMIDS)
+    return fail(VCT_ERR_INVALID_ARG, "vct_trace: need 1..%d pyramids", VCT_MAX_PYRAMIDS);
+  for (int i = 0; i < n_pyr; ++i) {
+    vct_status st = check_pyramid(pyrs + i, "vct_trace");
+    if (st != VCT_OK) return st;
+  }
+  if (!views || n_views < 1) return fail(VCT_ERR_INVALID_ARG, "vct_trace: no views");
+  vct_status st = check_params(params);
+  if (st != VCT_OK) return st;
+  for (int i = 0; i < n_views; ++i)
+    if ((st = check_view(views[i], i, n_pyr, true)) != VCT_OK) return st;
+  if (!workspace || workspace_bytes < vct_trace_workspace_bytes() || !aligned(workspace, 8))
+    return fail(VCT_ERR_WORKSPACE, "vct_trace: workspace needs %zu bytes, 8-byte aligned",
+                vct_trace_workspace_bytes());
+  return VCT_OK;
+}
+
+vct_status vct_trace(const vct_pyramid *pyrs, int32_t n_pyr, const vct_view *views,
+                     int32_t n_views, const vct_trace_params *params,
+                     const vct_launch_config *cfg, void *workspace, size_t workspace_bytes,
+                     vct_stream_t stream) {
+  vct_status st = trace_checks(pyrs, n_pyr, views, n_views, params, workspace, workspace_bytes);
+  if (st != VCT_OK) return st;
+  const vct_launch_config c = pick_cfg(cfg, pyrs, views, params);
+  if (!cfg_ok(c)) return fail(VCT_ERR_INVALID_ARG, "vct_trace: bad launch config");
+  return trace_impl(pyrs, n_pyr, views, n_views, params, c, workspace, workspace_bytes,
+                    (cudaStream_t)stream, true);
+}
+
+vct_status vct_autotune_trace(const vct_pyramid *pyrs, int32_t n_pyr, const vct_view *views,
+                              int32_t n_views, const vct_trace_params *params, void *workspace,
+                              size_t workspace_bytes, vct_stream_t stream,
+                              vct_launch_config *best) {
+  vct_status st = trace_checks(pyrs, n_pyr, views, n_views, params, workspace, workspace_bytes);
+  if (st != VCT_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(VCT_ERR_CUDA, "vct_autotune_trace: event create failed");
+  const int tiles[4][2] = {{4, 8}, {8, 8}, {8, 16}, {16, 16}};
+  const int lpps[4] = {1, 2, 4, 8};
+  float best_ms = 1e30f;
+  vct_launch_config bc = default_cfg();
+  for (auto &t : tiles)
+    for (int lpp : lpps) {
+      vct_launch_config c{t[0], t[1], lpp, 0};
+      float ms_sum = 0.f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, s);
+        st = trace_impl(pyrs, n_pyr, views, n_views, params, c, workspace, workspace_bytes, s, true);
+        cudaEventRecord(e1, s);
+        if (st != VCT_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          st = fail(VCT_ERR_CUDA, "vct_autotune_trace: kernel failed");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) ms_sum += ms;  // first run warms caches
+      }
+      if (st != VCT_OK) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return st;
+      }
+      if (ms_sum < best_ms) {
+        best_ms = ms_sum;
+        bc = c;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tuned[tune_key(pyrs, views, params)] = bc;
+  }
+  if (best) *best = bc;
+  return VCT_OK;
+}
+
+size_t vct_trace_backward_workspace_bytes(const vct_pyramid *pyr) {
+  if (!pyr || !shape_ok(pyr->n, pyr->levels, pyr->dtype)) return 0;
+  return (size_t)make_layout(pyr->n, pyr->levels, VCT_F32).total;
+}
+
+vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
+                              const vct_view_grad *grads, int32_t n_views,
+                              const vct_trace_params *params, const vct_launch_config *cfg,
+                              float *grad_level0_dense, void *workspace, size_t workspace_bytes,
+                              vct_stream_t stream) {
+  vct_status st = check_pyramid(pyr, "vct_trace_backward");
+  if (st != VCT_OK) return st;
+  if (pyr->dtype != VCT_F32)
+    return fail(VCT_ERR_UNSUPPORTED, "vct_trace_backward: only VCT_F32 pyramids are supported");
+  if (!views || !grads || n_views < 1)
+    return fail(VCT_ERR_INVALID_ARG, "vct_trace_backward: no views");
+  if ((st = check_params(params)) != VCT_OK) return st;
+  for (int i = 0; i < n_views; ++i) {
+    if ((st = check_view(views[i], i, 1, false)) != VCT_OK) return st;
+    const vct_view_grad &g = grads[i];
+    if ((g.grad_diffuse && !aligned(g.grad_diffuse, 16)) ||
+        (g.grad_specular && !aligned(g.grad_specular, 16)) ||
+        (g.grad_visibility && !aligned(g.grad_visibility, 4)))
+      return fail(VCT_ERR_INVALID_ARG, "view %d: gradients must be 16-byte aligned", i);
+  }
+  if (!grad_level0_dense || !aligned(grad_level0_dense, 16))
+    return fail(VCT_ERR_INVALID_ARG, "vct_trace_backward: grad_level0 NULL or misaligned");
+  const Layout gl = make_layout(pyr->n, pyr->levels, VCT_F32);
+  if (!workspace || workspace_bytes < gl.total || !aligned(workspace, 256))
+    return fail(VCT_ERR_WORKSPACE, "vct_trace_backward: workspace needs %llu bytes, 256-byte aligned",
+                (unsigned long long)gl.total);
+  vct_launch_config c = cfg ? *cfg : vct_launch_config{8, 8, 1, 0};
+  if (!cfg_ok(c)) return fail(VCT_ERR_INVALID_ARG, "vct_trace_backward: bad launch config");
+
+  auto L = std::make_unique<BwdLaunch>();
+  memset(L.get(), 0, sizeof(BwdLaunch));
+  fill_common(*params, *L);
+  if ((st = fill_pyr(*pyr, *params, L->pyr)) != VCT_OK) return st;
+  uint8_t *ws = static_cast<uint8_t *>(workspace);
+  for (int l = 0; l < pyr->levels; ++l) L->gpyr_lvl[l] = reinterpret_cast<float *>(ws + gl.level_off[l]);
+  L->queue = reinterpret_cast<unsigned *>(ws);
+  L->tile_w = c.tile_w;
+  L->tile_h = c.tile_h;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(ws, 0, gl.total, s);
+  if (e != cudaSuccess) return cuda_fail(e, "vct_trace_backward workspace clear");
+  int per_sm = c.ctas_per_sm ? c.ctas_per_sm : std::max(1, trace_bwd_occupancy(c.lanes_per_pixel));
+  const int sms = sm_count();
+  for (int v0 = 0; v0 < n_views; v0 += kMaxBwdViewsPerLaunch) {
+    const int nv = std::min(kMaxBwdViewsPerLaunch, n_views - v0);
+    int cursor = 0;
+    for (int i = 0; i < nv; ++i) {
+      fill_view(views[v0 + i], c.tile_w, c.tile_h, cursor, L->views[i].v);
+      L->views[i].v.pyr = 0;
+      L->views[i].gD = grads[v0 + i].grad_diffuse;
+      L->views[i].gS = grads[v0 + i].grad_specular;
+      L->views[i].gV = grads[v0 + i].grad_visibility;
+    }
+    L->n_views = nv;
+    L->total_tiles = cursor;
+    if (v0 > 0 && (e = cudaMemsetAsync(L->queue, 0, 4, s)) != cudaSuccess)
+      return cuda_fail(e, "vct_trace_backward queue clear");
+    const int grid = std::max(1, std::min(cursor, per_sm * sms));
+    e = launch_trace_bwd(*L, c.lanes_per_pixel, grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "vct_trace_backward launch");
+  }
+  e = launch_mip_adjoint(reinterpret_cast<const float *>(ws), gl, pyr->n, pyr->levels,
+                         grad_level0_dense, s);
+  if (e != cudaSuccess) return cuda_fail(e, "vct_trace_backward mip adjoint launch");
+  return VCT_OK;
+}
+
+vct_status vct_debug_wait_probe(uint32_t *flag_dev, uint64_t max_ns, vct_stream_t stream) {
+  if (!flag_dev || !aligned(flag_dev, 4))
+    return fail(VCT_ERR_INVALID_ARG, "vct_debug_wait_probe: flag NULL or misaligned");
+  if (max_ns == 0 || max_ns > 10000000000ull)
+    return fail(VCT_ERR_INVALID_ARG, "vct_debug_wait_probe: max_ns must be in (0, 1e10]");
+  cudaError_t e = launch_wait_probe(flag_dev, max_ns, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "vct_debug_wait_probe launch");
+  return VCT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,267 @@
+// Internal definitions shared by the libvct translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vct.h"
+
+namespace vct {
+
+constexpr int kHeaderBytes = 256;
+constexpr int kTraceThreads = 256;      // one CTA shape for every trace kernel
+#ifndef VCT_TRACE_MIN_BLOCKS
+#define VCT_TRACE_MIN_BLOCKS 3
+#endif
+constexpr int kTraceMinBlocks = VCT_TRACE_MIN_BLOCKS;  // register budget: 65536 / (256 * this)
+constexpr int kMaxViewsPerLaunch = 224;  // keeps the forward launch under 32 KB
+constexpr int kMaxBwdViewsPerLaunch = 128;
+constexpr int kMaxSteps = 1 << 16;       // per-cone step cap (parameter check)
+
+// ---------------------------------------------------------------------------
+// pyramid layout (host and device)
+// ---------------------------------------------------------------------------
+__host__ __device__ inline uint64_t align256(uint64_t x) { return (x + 255ull) & ~255ull; }
+__host__ __device__ inline int texel_bytes(int dtype) { return dtype == VCT_F16 ? 8 : 16; }
+__host__ __device__ inline uint64_t level_texels(int n, int l) {
+  uint64_t m = (uint64_t)(n >> l);
+  return m * m * m;
+}
+__host__ __device__ inline int ilog2(int n) {
+  int k = 0;
+  while ((1 << (k + 1)) <= n) ++k;
+  return k;
+}
+// Edge of the block one CTA of the fused pack/mip kernel handles.
+__host__ __device__ inline int pack_block(int n) { return n < 16 ? n : 16; }
+
+struct Layout {
+  uint64_t level_off[VCT_MAX_LEVELS];  // bytes from data
+  uint64_t staging_off[2];             // FP32 staging (VCT_F16 only)
+  uint64_t total;
+};
+
+__host__ __device__ inline Layout make_layout(int n, int levels, int dtype) {
+  Layout L{};
+  uint64_t off = kHeaderBytes;
+  int tb = texel_bytes(dtype);
+  for (int l = 0; l < levels; ++l) {
+    L.level_off[l] = off;
+    off += align256(level_texels(n, l) * tb);
+  }
+  if (dtype == VCT_F16) {
+    int m0 = ilog2(pack_block(n));
+    L.staging_off[0] = off;
+    off += align256(level_texels(n, m0) * 16);
+    L.staging_off[1] = off;
+    off += align256(level_texels(n, m0 < ilog2(n) ? m0 + 1 : m0) * 16);
+  }
+  L.total = off;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// Morton helpers: x in bits 0,3,6..., y in 1,4,7..., z in 2,5,8...
+// ---------------------------------------------------------------------------
+constexpr uint32_t kMortonX = 0x09249249u;  // bits 0,3,...,27 (10 coordinate bits)
+
+__host__ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+// spread3(v + 1) from s = spread3(v) (10-bit wrap-around).
+__host__ __device__ __forceinline__ uint32_t spread3_inc(uint32_t s) {
+  return (s - kMortonX) & kMortonX;
+}
+__host__ __device__ __forceinline__ uint32_t compact3(uint32_t v) {
+  v &= 0x09249249u;
+  v = (v | (v >> 2)) & 0x030C30C3u;
+  v = (v | (v >> 4)) & 0x0300F00Fu;
+  v = (v | (v >> 8)) & 0x030000FFu;
+  v = (v | (v >> 16)) & 0x000003FFu;
+  return v;
+}
+__host__ __device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+  return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+
+// ---------------------------------------------------------------------------
+// texel load/store
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 ld_texel(const float4 *p) { return __ldg(p); }
+__device__ __forceinline__ float4 ld_texel(const uint2 *p) {
+  uint2 u = __ldg(p);
+  __half2 a = *reinterpret_cast<__half2 *>(&u.x);
+  __half2 b = *reinterpret_cast<__half2 *>(&u.y);
+  float2 fa = __half22float2(a), fb = __half22float2(b);
+  return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+__device__ __forceinline__ uint2 pack_half4(float4 v) {
+  __half2 a = __floats2half2_rn(v.x, v.y);
+  __half2 b = __floats2half2_rn(v.z, v.w);
+  uint2 u;
+  u.x = *reinterpret_cast<uint32_t *>(&a);
+  u.y = *reinterpret_cast<uint32_t *>(&b);
+  return u;
+}
+
+// ---------------------------------------------------------------------------
+// bounded waits (every device-side wait gives up after a time budget)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of `bar` to complete; gives up after max_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint64_t max_ns) {
+  uint64_t t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer_ns() - t0 > max_ns) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void *smem_dst, const CUtensorMap *map,
+                                            uint64_t *bar, int c0, int c1, int c2,
+                                            int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+
+constexpr uint64_t kWaitBudgetNs = 2000000000ull;  // 2 s
+
+// ---------------------------------------------------------------------------
+// trace launch description (kernel parameter, < 32 KB)
+// ---------------------------------------------------------------------------
+// Per-cone-kind march constants.  T (t in level-0 voxel units) at step k is
+// T0 * 2^(k * l2r) with l2r = log2(1 + 2 beta tan(gamma/2)) (the thesis's
+// t += beta * 2 t tan(gamma/2) in closed form), and the level at step k is
+// lam0 + k * l2r with lam0 = log2(2 T0 tan(gamma/2)).  hi/lo pairs carry the
+// FP64 values to ~2^-48.
+struct ConeConst {
+  float l2r_hi, l2r_lo, lam0_hi, lam0_lo;
+  int kmax;  // number of steps with t <= t_max
+  int pad;
+};
+
+struct DevPyr {
+  const uint8_t *lvl[VCT_MAX_LEVELS];  // level base pointers
+  double origin[3];
+  double scale;  // n / size: scene units -> level-0 voxel units
+  double tmax_vox;  // t_max in level-0 voxel units
+  int n, levels, dtype, pad;
+  ConeConst diffuse, occ, spec_fixed;
+};
+
+struct DevView {
+  const float *pos, *nrm, *rough;
+  const uint8_t *mask;
+  float *outD, *outS, *outV;
+  float cam[3];
+  int W, H, pyr, tiles_x, tile_begin;
+};
+
+struct TraceLaunch {
+  int n_views, total_tiles, tile_w, tile_h;
+  int n_diffuse, spec_enable, occ_enable, pad0;
+  float diffuse_dir[VCT_MAX_DIFFUSE][3];
+  float diffuse_weight[VCT_MAX_DIFFUSE];
+  float light[3];
+  float normal_offset;  // voxels
+  double spec_gmin, spec_gmax, rough_min, beta, t0_vox;
+  unsigned *queue;
+  unsigned long long *stats;  // vct_trace_stats::samples / cones
+  DevPyr pyr[VCT_MAX_PYRAMIDS];
+  DevView views[kMaxViewsPerLaunch];
+};
+
+struct BwdView {
+  DevView v;
+  const float *gD, *gS, *gV;
+};
+
+struct BwdLaunch {
+  int n_views, total_tiles, tile_w, tile_h;
+  int n_diffuse, spec_enable, occ_enable, pad0;
+  float diffuse_dir[VCT_MAX_DIFFUSE][3];
+  float diffuse_weight[VCT_MAX_DIFFUSE];
+  float light[3];
+  float normal_offset;
+  double spec_gmin, spec_gmax, rough_min, beta, t0_vox;
+  unsigned *queue;
+  float *gpyr_lvl[VCT_MAX_LEVELS];  // float32 gradient pyramid levels
+  DevPyr pyr;
+  BwdView views[kMaxBwdViewsPerLaunch];
+};
+
+// March constants of a cone of full aperture `gamma` (FP64).
+__host__ __device__ inline ConeConst cone_const(double gamma, double beta, double t0_vox,
+                                                double tmax_vox) {
+  ConeConst c{};
+  double th = tan(0.5 * gamma);
+  double x = 2.0 * beta * th;
+  double l2r = log1p(x) / 0.69314718055994530942;
+  double lam0 = log2(2.0 * t0_vox * th);
+  int kmax = 0;
+  if (t0_vox <= tmax_vox) {
+    double e = log2(tmax_vox / t0_vox) / l2r;
+    double kf = floor(e) + 1.0;
+    kmax = kf > (double)kMaxSteps ? kMaxSteps + 1 : (int)kf;
+  }
+  c.l2r_hi = (float)l2r;
+  c.l2r_lo = (float)(l2r - (double)c.l2r_hi);
+  c.lam0_hi = (float)lam0;
+  c.lam0_lo = (float)(lam0 - (double)c.lam0_hi);
+  c.kmax = kmax;
+  return c;
+}
+
+// Host entry points implemented in the .cu files (internal linkage across TUs).
+cudaError_t launch_pack_mips(const float *level0, const vct_pyramid &pyr,
+                             const CUtensorMap &map, cudaStream_t s);
+cudaError_t launch_read_level(const vct_pyramid &pyr, int level, float *out, cudaStream_t s);
+cudaError_t launch_mip_adjoint(const float *gpyr_base, const Layout &gl, int n, int levels,
+                               float *grad0, cudaStream_t s);
+cudaError_t launch_wait_probe(uint32_t *flag, uint64_t max_ns, cudaStream_t s);
+cudaError_t launch_trace(const TraceLaunch &L, int lpp, int dtype, int grid, cudaStream_t s);
+int trace_occupancy(int lpp, int dtype);
+cudaError_t launch_trace_bwd(const BwdLaunch &L, int lpp, int grid, cudaStream_t s);
+int trace_bwd_occupancy(int lpp);
+
+}  // namespace vct

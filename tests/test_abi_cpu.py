@@ -1,0 +1,98 @@
+"""The C ABI library builds, loads and exports every declared entry point;
+host-side validation and layout queries work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2104_00618_gb300 as vct
+from paper_2104_00618_gb300 import _abi
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                      "include", "vct.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vct_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return _abi.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(_abi.EXPORTS), "binding and header disagree"
+
+
+def test_struct_sizes_match_header_layout():
+    assert ctypes.sizeof(_abi.VctPyramid) == 48
+    assert ctypes.sizeof(_abi.VctView) == 88
+    assert ctypes.sizeof(_abi.VctLaunchConfig) == 16
+    assert ctypes.sizeof(_abi.VctTraceStats) == 56
+    assert ctypes.sizeof(_abi.VctTraceParams) == 16 + 32 * 12 + 32 * 4 + 4 * 5 + 12 + 16
+
+
+def test_pyramid_layout(lib):
+    for n in (2, 8, 64, 256, 1024):
+        L = n.bit_length()
+        for dt, tb in ((0, 16), (1, 8)):
+            off = 256
+            for l in range(L):
+                assert lib.vct_pyramid_level_offset(n, L, dt, l) == off
+                m = n >> l
+                off += (m ** 3 * tb + 255) // 256 * 256
+            total = lib.vct_pyramid_bytes(n, L, dt)
+            assert total >= off
+            if dt == 0:
+                assert total == off
+    assert lib.vct_pyramid_bytes(3, 1, 0) == 0        # not a power of two
+    assert lib.vct_pyramid_bytes(2048, 12, 0) == 0    # too large
+    assert lib.vct_pyramid_bytes(64, 8, 0) == 0       # too many levels
+    assert lib.vct_pyramid_bytes(64, 7, 2) == 0       # bad dtype
+
+
+def test_status_strings(lib):
+    assert lib.vct_status_string(0) == b"VCT_OK"
+    assert lib.vct_status_string(5) == b"VCT_ERR_TIMEOUT"
+    assert lib.vct_version() == 1
+
+
+def test_validation_without_gpu(lib):
+    # every one of these is rejected before any CUDA call
+    assert lib.vct_build_mips(None, None, None) == _abi.VCT_ERR_INVALID_ARG
+    p = _abi.VctPyramid(64, 7, 0, 0, (ctypes.c_float * 3)(0, 0, 0), 1.0, 256, 10)
+    assert lib.vct_build_mips(None, ctypes.byref(p), None) == _abi.VCT_ERR_INVALID_ARG
+    assert b"bytes" in lib.vct_last_error()
+    assert lib.vct_trace(None, 0, None, 0, None, None, None, 0, None) == _abi.VCT_ERR_INVALID_ARG
+    prm = vct.make_params({"n_diffuse": 1, "diffuse_dir": [[0, 0, 1]], "diffuse_weight": [1],
+                           "diffuse_aperture": 0.0, "spec_enable": 0, "occ_enable": 0,
+                           "spec_aperture_min": 0.1, "spec_aperture_max": 0.1,
+                           "roughness_min": 0.05, "occ_aperture": 0.5, "light_dir": [0, 1, 0],
+                           "beta": 0.5, "t0_voxels": 1.0, "normal_offset_voxels": 1.0,
+                           "t_max": 1.0})
+    p = _abi.VctPyramid(64, 7, 0, 0, (ctypes.c_float * 3)(0, 0, 0), 1.0, 256,
+                        lib.vct_pyramid_bytes(64, 7, 0))
+    v = _abi.VctView()
+    v.width, v.height, v.position, v.normal, v.out_diffuse = 4, 4, 1024, 2048, 4096
+    st = lib.vct_trace(ctypes.byref(p), 1, ctypes.byref(v), 1, ctypes.byref(prm), None,
+                       None, 0, None)
+    assert st == _abi.VCT_ERR_INVALID_ARG and b"aperture" in lib.vct_last_error()
+    prm.diffuse_aperture = 0.5
+    st = lib.vct_trace(ctypes.byref(p), 1, ctypes.byref(v), 1, ctypes.byref(prm), None,
+                       None, 0, None)
+    assert st == _abi.VCT_ERR_WORKSPACE
+    p16 = _abi.VctPyramid(64, 7, 1, 0, (ctypes.c_float * 3)(0, 0, 0), 1.0, 256,
+                          lib.vct_pyramid_bytes(64, 7, 1))
+    g = _abi.VctViewGrad()
+    st = lib.vct_trace_backward(ctypes.byref(p16), ctypes.byref(v), ctypes.byref(g), 1,
+                                ctypes.byref(prm), None, None, None, 0, None)
+    assert st == _abi.VCT_ERR_UNSUPPORTED
+    assert lib.vct_debug_wait_probe(None, 10, None) == _abi.VCT_ERR_INVALID_ARG

@@ -1,0 +1,318 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2104_00618_gb300 as vct
+import vct_synth as vs
+from gpu_cases import FP32_BOUND, compare, gpu_pyramid, gpu_trace, room_case, worst
+from metrics import report
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    vct.lib()
+
+
+# ---------------------------------------------------------------------------
+# a1 + a2: packing and mip build
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [2, 4, 8, 16, 32, 64, 128])
+def test_mips_fp32_match_oracle(n):
+    rng = np.random.default_rng(n)
+    g = rng.random((n, n, n, 4)).astype(np.float32)
+    P = gpu_pyramid(g)
+    O = oracle.build_mips(g)
+    vct.pyramid_status(P)
+    for l in range(P.levels):
+        got = vct.read_level(P, l).cpu().numpy().astype(np.float64)
+        want = O.level(l)
+        if l == 0:
+            assert np.array_equal(got, want), "level 0 must round-trip exactly"
+        else:
+            assert np.max(np.abs(got - want) / np.abs(want).clip(1e-30)) < 2e-6, (n, l)
+
+
+@pytest.mark.parametrize("n,levels", [(64, 3), (64, 5), (32, 1), (256, 9)])
+def test_mips_partial_levels_and_large(n, levels):
+    rng = np.random.default_rng(100 + n)
+    g = (rng.random((n, n, n, 4)) * (rng.random((n, n, n, 1)) < 0.2)).astype(np.float32)
+    P = gpu_pyramid(g, levels=levels)
+    O = oracle.build_mips(g, levels=levels)
+    for l in range(levels):
+        got = vct.read_level(P, l).cpu().numpy().astype(np.float64)
+        want = O.level(l)
+        assert np.allclose(got, want, rtol=2e-6, atol=1e-12), (n, levels, l)
+
+
+@pytest.mark.parametrize("n", [8, 64, 256])
+def test_mips_fp16_within_rounding(n):
+    rng = np.random.default_rng(200 + n)
+    g = rng.random((n, n, n, 4)).astype(np.float32)
+    P = gpu_pyramid(g, dtype="f16")
+    O = oracle.build_mips(g)
+    for l in range(P.levels):
+        got = vct.read_level(P, l).cpu().numpy().astype(np.float64)
+        want = O.level(l)
+        # one rounding to binary16 of a float32 value computed from float32 values
+        assert np.all(np.abs(got - want) <= 2.0 ** -11 * np.abs(want) + 1e-6 * np.abs(want)
+                      + 2.0 ** -24), (n, l)
+
+
+def test_mips_mean_preserved_on_gpu():
+    c = vs.config_small_fp32()
+    g = c["scenes"][0]["grid"]
+    P = gpu_pyramid(g)
+    m0 = g.reshape(-1, 4).astype(np.float64).mean(0)
+    for l in range(P.levels):
+        lv = vct.read_level(P, l).cpu().numpy().astype(np.float64)
+        assert np.allclose(lv.reshape(-1, 4).mean(0), m0, rtol=1e-6), l
+
+
+# ---------------------------------------------------------------------------
+# a3 - a6: the trace
+# ---------------------------------------------------------------------------
+def test_empty_grid_gives_no_indirect_light():
+    scene, view, prm = room_case(n=32, width=40, height=24)
+    P = gpu_pyramid(np.zeros((32, 32, 32, 4), np.float32))
+    (D, S, V), _ = gpu_trace([P], [view], prm)[0][0], None
+    assert np.all(D == 0) and np.all(S == 0) and np.all(V == 1.0)
+
+
+def test_small_config_full_frame():
+    """64^3, 12 boxes, 128x128 surface samples, 6x60deg + 10deg cones."""
+    c = vs.config_small_fp32()
+    prm = c["params"]
+    view = c["views"][0]
+    P = gpu_pyramid(c["scenes"][0]["grid"])
+    O = oracle.build_mips(c["scenes"][0]["grid"])
+    (out,), stats = gpu_trace([P], [view], prm)
+    ref = oracle.trace(O, view, prm)
+    res = compare(out, ref, prm=prm)
+    print("small config errors (max, mean):", {k: (v[0].max(), v[1].max()) for k, v in res.items()})
+    assert ref["margin"] > 1e-9
+    assert worst(res) <= FP32_BOUND, res
+    # Sample counts: float32 alpha rounds to exactly 1 (ending the march)
+    # while the float64 alpha is still 1 - 1e-8 or so, so the GPU may take
+    # fewer samples on saturated cones; the dropped terms are below 6e-8.
+    for k in range(2):
+        assert 0 <= ref["steps"][k] - stats["samples"][k] <= 0.01 * ref["steps"][k]
+        assert stats["cones"][k] == ref["cones"][k]
+
+
+@pytest.mark.parametrize("tile", [(4, 8), (8, 8), (8, 16), (16, 16)])
+@pytest.mark.parametrize("lpp", [1, 2, 4, 8])
+def test_room_ragged_all_launch_shapes(tile, lpp):
+    """Room scene, ragged 203x117 view, roughness, 10% masked, 9 diffuse +
+    specular + occlusion cones, under every candidate launch shape."""
+    scene, view, prm = _room_fixture()
+    O = _room_oracle()
+    P = gpu_pyramid(scene["grid"])
+    (out,), stats = gpu_trace([P], [view], prm, cfg=vct.launch_config(*tile, lpp))
+    res = compare(out, O, prm=prm)
+    assert worst(res) <= FP32_BOUND, (tile, lpp, res)
+    m = view["mask"] == 0
+    assert np.all(out[0][m] == 0) and np.all(out[1][m] == 0) and np.all(out[2][m] == 1)
+
+
+_ROOM = {}
+
+
+def _room_fixture():
+    if "case" not in _ROOM:
+        _ROOM["case"] = room_case()
+    return _ROOM["case"]
+
+
+def _room_oracle():
+    if "ref" not in _ROOM:
+        scene, view, prm = _room_fixture()
+        _ROOM["ref"] = oracle.trace(oracle.build_mips(scene["grid"]), view, prm)
+    return _ROOM["ref"]
+
+
+def test_room_1080p_full_size_sampled():
+    """The 256^3 room at 1920x1080 in the default launch shape; 20000 seeded
+    pixels checked against the oracle one by one."""
+    c = vs.config_room_1080p()
+    prm, view, scene = c["params"], c["views"][0], c["scenes"][0]
+    P = gpu_pyramid(scene["grid"])
+    (out,), stats = gpu_trace([P], [view], prm)
+    rng = np.random.default_rng(99)
+    idx = np.sort(rng.choice(view["width"] * view["height"], 20000, replace=False))
+    O = oracle.build_mips(scene["grid"])
+    ref = oracle.trace(O, view, prm, idx=idx)
+    res = compare(out, ref, idx=idx, prm=prm)
+    print("1080p sampled errors:", {k: (v[0].max(), v[1].max()) for k, v in res.items()})
+    assert ref["margin"] > 1e-9
+    assert worst(res) <= FP32_BOUND, res
+    total = sum(stats["samples"])
+    assert total > 1e8
+    assert stats["cones"] == [9 * view["mask"].sum(), view["mask"].sum(), view["mask"].sum()]
+
+
+def test_fp16_storage_error_report():
+    """Same scene as the small config with the pyramid stored in binary16;
+    compositing stays float32.  No bound is set for this variant: the
+    measured error is reported and sanity-checked."""
+    c = vs.config_small_fp32()
+    prm = dict(c["params"], occ_enable=1)
+    view = c["views"][0]
+    P = gpu_pyramid(c["scenes"][0]["grid"], dtype="f16")
+    O = oracle.build_mips(c["scenes"][0]["grid"])
+    (out,), _ = gpu_trace([P], [view], prm)
+    ref = oracle.trace(O, view, prm)
+    res = compare(out, ref, prm=prm)
+    print("fp16 storage errors (max, mean):", {k: (v[0].tolist(), v[1].tolist()) for k, v in res.items()})
+    assert worst(res) < 5e-2
+    assert max(float(v[1].max()) for v in res.values()) < 5e-3
+
+
+def test_batched_views_over_several_pyramids():
+    scenes = [vs.box_scene(n, 6, 300 + n, room=True) for n in (16, 64, 32)]
+    rng = np.random.default_rng(5)
+    views = []
+    for i, (sc, (w, h)) in enumerate(zip(scenes * 2, [(37, 21), (64, 48), (17, 33),
+                                                       (80, 9), (5, 5), (41, 40)])):
+        v = vs.interior_view(sc, w, h, rng)
+        v["pyramid"] = i % 3
+        views.append(v)
+    prm = vs.params_room9(scenes[0]["light"])
+    pyrs = [gpu_pyramid(sc["grid"]) for sc in scenes]
+    outs, stats = gpu_trace(pyrs, views, prm)
+    for v, out in zip(views, outs):
+        O = oracle.build_mips(scenes[v["pyramid"]]["grid"])
+        ref = oracle.trace(O, v, prm)
+        res = compare(out, ref, prm=prm)
+        assert worst(res) <= FP32_BOUND, res
+
+
+def test_null_outputs_and_no_specular():
+    scene, view, prm = room_case(n=32, width=30, height=20)
+    prm = dict(prm, spec_enable=0)
+    P = gpu_pyramid(scene["grid"])
+    v = vct.View.from_host(view, outputs=False)
+    v.alloc_outputs(diffuse=True, specular=False, visibility=False)
+    vct.trace([P], [v], prm)
+    ref = oracle.trace(oracle.build_mips(scene["grid"]), view, prm)
+    D = v.out_diffuse.cpu().numpy()
+    assert report(D, ref["D"])[0].max() <= FP32_BOUND
+
+
+# ---------------------------------------------------------------------------
+# a7 + a8: the adjoint
+# ---------------------------------------------------------------------------
+def _diff_case(n=32, W=48, H=40, seed=61):
+    gt = vs.box_scene(n, 6, seed, room=True)
+    rng = np.random.default_rng(seed + 1)
+    views = [vs.interior_view(gt, W, H, rng, with_roughness=False) for _ in range(2)]
+    dirs, w = vs.cone_table_ring6()
+    prm = vs.trace_params(dirs, w, math.radians(60), spec_enable=True,
+                          spec_aperture_min=math.radians(10), occ_enable=True, occ_aperture=0.55,
+                          light=gt["light"])
+    learn = np.full((n, n, n, 4), 0.1, np.float32)
+    return gt, views, prm, learn
+
+
+def test_backward_matches_oracle_gradient():
+    gt, views, prm, learn = _diff_case()
+    O_gt = oracle.build_mips(gt["grid"])
+    targets = [oracle.trace(O_gt, v, prm) for v in views]
+    O = oracle.build_mips(learn)
+    grad_ref = np.zeros(learn.shape)
+    gpu_grads = []
+    for v, t in zip(views, targets):
+        r = oracle.trace(O, v, prm)
+        gD, gS, gV = r["D"] - t["D"], r["S"] - t["S"], r["Vis"] - t["Vis"]
+        grad_ref += oracle.trace_backward(O, v, prm, gD, gS, gV)
+        gpu_grads.append(tuple(torch.from_numpy(a.astype(np.float32)).cuda()
+                               for a in (gD, gS, gV)))
+    P = gpu_pyramid(learn)
+    gviews = [vct.View.from_host(v) for v in views]
+    grad = vct.trace_backward(P, gviews, gpu_grads, prm).cpu().numpy().astype(np.float64)
+    scale = np.abs(grad_ref).max()
+    err = np.abs(grad - grad_ref)
+    print("gradient: max abs err / max |grad| =", err.max() / scale)
+    assert err.max() <= 1e-4 * scale
+    assert np.linalg.norm(grad - grad_ref) <= 1e-5 * np.linalg.norm(grad_ref)
+
+
+def test_backward_central_differences():
+    """dL/dV on 64 seeded voxels x 4 channels: central differences
+    (eps = 1e-3) of the FP64 loss against the CUDA adjoint."""
+    gt, views, prm, learn = _diff_case(n=16, W=24, H=20, seed=71)
+    views = views[:1]
+    O_gt = oracle.build_mips(gt["grid"])
+    t = oracle.trace(O_gt, views[0], prm)
+
+    def loss(g):
+        r = oracle.trace(oracle.build_mips(g), views[0], prm)
+        return 0.5 * (np.sum((r["D"] - t["D"]) ** 2) + np.sum((r["S"] - t["S"]) ** 2)
+                      + np.sum((r["Vis"] - t["Vis"]) ** 2)), r
+
+    L0, r = loss(learn.astype(np.float64))
+    grads = [tuple(torch.from_numpy(a.astype(np.float32)).cuda()
+                   for a in (r["D"] - t["D"], r["S"] - t["S"], r["Vis"] - t["Vis"]))]
+    P = gpu_pyramid(learn)
+    grad = vct.trace_backward(P, [vct.View.from_host(views[0])], grads, prm).cpu().numpy()
+    rng = np.random.default_rng(3)
+    vox = rng.integers(0, 16, size=(64, 3))
+    eps = 1e-3
+    scale = np.abs(grad).max()
+    for (x, y, z) in vox:
+        for ch in range(4):
+            gp = learn.astype(np.float64).copy()
+            gm = gp.copy()
+            gp[z, y, x, ch] += eps
+            gm[z, y, x, ch] -= eps
+            fd = (loss(gp)[0] - loss(gm)[0]) / (2 * eps)
+            an = float(grad[z, y, x, ch])
+            assert abs(fd - an) <= 2e-3 * max(abs(fd), 0.05 * scale), (x, y, z, ch, fd, an)
+
+
+def test_autograd_render():
+    gt, views, prm, learn = _diff_case(n=16, W=20, H=12, seed=81)
+    v = vct.View.from_host(views[0])
+    g = torch.from_numpy(learn).cuda().requires_grad_(True)
+    D, S, V = vct.render(g, v, prm)
+    loss = D.square().sum() + S.square().sum() + V.square().sum()
+    loss.backward()
+    P = gpu_pyramid(learn)
+    ref = vct.trace_backward(P, [v], [(2 * D.detach(), 2 * S.detach(), 2 * V.detach())], prm)
+    assert torch.allclose(g.grad, ref, rtol=1e-5, atol=1e-7 * ref.abs().max().item())
+
+
+# ---------------------------------------------------------------------------
+# failure paths
+# ---------------------------------------------------------------------------
+def test_bounded_wait_gives_up_with_status():
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    import ctypes
+    st = vct.lib().vct_debug_wait_probe(ctypes.c_void_p(flag.data_ptr()), 5_000_000,
+                                        torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    torch.cuda.synchronize()
+    assert int(flag.item()) == 5  # VCT_ERR_TIMEOUT
+    # the context is still usable
+    assert float(torch.ones(4, device="cuda").sum().item()) == 4.0
+
+
+def test_invalid_arguments_rejected():
+    P = gpu_pyramid(np.zeros((8, 8, 8, 4), np.float32))
+    scene, view, prm = room_case(n=8, width=4, height=4, n_boxes=1)
+    bad = dict(prm, beta=-1.0)
+    with pytest.raises(vct.VctError):
+        vct.trace([P], [vct.View.from_host(view)], bad)
+    bad = dict(prm, spec_aperture_min=1e-7)
+    with pytest.raises(vct.VctError):
+        vct.trace([P], [vct.View.from_host(view)], bad)
+    P16 = gpu_pyramid(np.zeros((8, 8, 8, 4), np.float32), dtype="f16")
+    with pytest.raises(vct.VctError):
+        vct.trace_backward(P16, [vct.View.from_host(view)], [(None, None, None)], prm)
