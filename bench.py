@@ -45,8 +45,11 @@ def parse():
     ap.add_argument("--dtype", choices=["f32", "f16"], default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 4-scene batched extra")
     ap.add_argument("--profile", action="store_true",
                     help="only warm-up + timed frames (for ncu captures); no e2e/extras/baseline")
+    ap.add_argument("--profile-bwd", action="store_true",
+                    help="only fwd+bwd steps of a reduced learnable-grid case (for ncu captures)")
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     return ap.parse_args()
@@ -331,9 +334,130 @@ def run_e2e(torch, vct, dev, scene, hv, params, args, stream, steps=None):
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
 
 
+def _time(torch, fn, reps, warm=2):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def extra_fp16_single(torch, vct, dev):
+    """The same 1080p frame with the pyramid stored in binary16."""
+    cfg = make_workload()
+    scene, hv, prm = cfg["scenes"][0], cfg["views"][0], cfg["params"]
+    level0 = torch.from_numpy(scene["grid"]).to(dev)
+    view = vct.View.from_host(hv, device=dev)
+    P = vct.Pyramid(scene["n"], None, "f16", device=dev)
+    params = vct.make_params(prm)
+    ws = torch.zeros(256, dtype=torch.uint8, device=dev)
+    vct.build_mips(level0, out=P)
+    tr_ms = _time(torch, lambda: vct.trace([P], [view], params, workspace=ws), 10)
+    step_ms = _time(torch, lambda: (vct.build_mips(level0, out=P),
+                                    vct.trace([P], [view], params, workspace=ws)), 10)
+    samples = int(sum(vct.read_stats(ws)["samples"]))
+    return {"workload": "room256_1080p_f16", "trace_ms": tr_ms, "ms_per_step": step_ms,
+            "gsamples_per_s": samples / (step_ms / 1e3) / 1e9, "samples_per_frame": samples}
+
+
+def extra_fwd_bwd(torch, vct, dev, n=128, n_views=32, res=512):
+    """Learnable 128^3 grid at 0.1, 32 views of 512x512 of a ground-truth box
+    scene, L2 loss: forward (mips + trace) and forward + adjoint (trace
+    adjoint + mip adjoint) against the plain forward."""
+    import vct_synth as vs
+    cfg = vs.config_learnable(n=n, n_views=n_views, width=res, height=res)
+    gt = torch.from_numpy(cfg["scenes"][0]["grid"]).to(dev)
+    learn = torch.from_numpy(cfg["learnable"]).to(dev)
+    params = vct.make_params(cfg["params"])
+    views = [vct.View.from_host(v, device=dev) for v in cfg["views"]]
+    ws = torch.zeros(256, dtype=torch.uint8, device=dev)
+    Pgt = vct.build_mips(gt)
+    vct.trace([Pgt], views, params, workspace=ws)
+    targets = [(v.out_diffuse.clone(), v.out_specular.clone(), v.out_visibility.clone())
+               for v in views]
+    P = vct.Pyramid(n, None, "f32", device=dev)
+    bws = vct.backward_workspace(P)
+    grad = torch.zeros_like(learn)
+
+    def fwd():
+        vct.build_mips(learn, out=P)
+        vct.trace([P], views, params, workspace=ws)
+
+    def fwd_bwd():
+        fwd()
+        grads = [(v.out_diffuse - t[0], v.out_specular - t[1], v.out_visibility - t[2])
+                 for v, t in zip(views, targets)]
+        grad.zero_()
+        vct.trace_backward(P, views, grads, params, grad_level0=grad, workspace=bws)
+
+    f_ms = _time(torch, fwd, 5)
+    fb_ms = _time(torch, fwd_bwd, 5)
+    samples = int(sum(vct.read_stats(ws)["samples"]))
+    return {"workload": f"learnable{n}_{n_views}x{res}^2_f32", "fwd_ms": f_ms, "fwd_bwd_ms": fb_ms,
+            "fwd_bwd_over_fwd": fb_ms / f_ms, "samples_per_fwd": samples,
+            "fwd_gsamples_per_s": samples / (f_ms / 1e3) / 1e9}
+
+
+def extra_batched(torch, vct, dev, grids=(128, 256, 256, 512), views_per_scene=64):
+    """4 scenes x 64 interior views of uneven resolution, FP16 pyramids, one
+    persistent launch captured in a CUDA graph, launch shape autotuned."""
+    import vct_synth as vs
+    t0 = time.perf_counter()
+    cfg = vs.config_batched(grids=grids, views_per_scene=views_per_scene)
+    gen_s = time.perf_counter() - t0
+    params = vct.make_params(cfg["params"])
+    pyrs = []
+    for sc in cfg["scenes"]:
+        g = torch.from_numpy(sc["grid"]).to(dev)
+        pyrs.append(vct.build_mips(g, dtype="f16"))
+        del g
+    views = [vct.View.from_host(v, device=dev) for v in cfg["views"]]
+    npx = sum(v.width * v.height for v in views)
+    ws = torch.zeros(256, dtype=torch.uint8, device=dev)
+    # autotune on a probe: one reduced view per scene
+    probe_host = []
+    rng = np.random.default_rng(7)
+    for si, sc in enumerate(cfg["scenes"]):
+        pv = vs.interior_view(sc, 480, 270, rng)
+        pv["pyramid"] = si
+        probe_host.append(pv)
+    probe = [vct.View.from_host(v, device=dev) for v in probe_host]
+    best = vct.autotune(pyrs, probe, params, workspace=ws)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream(device=dev)
+    stream.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(stream):
+        vct.trace(pyrs, views, params, workspace=ws)  # warm (tuned shape)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        vct.trace(pyrs, views, params, workspace=ws)
+    ms = _time(torch, graph.replay, 3, warm=1)
+    samples = int(sum(vct.read_stats(ws)["samples"]))
+    return {"workload": f"batched_{len(grids)}scenes{list(grids)}_{len(views)}views_f16",
+            "pixels": npx, "trace_ms": ms, "samples": samples,
+            "gsamples_per_s": samples / (ms / 1e3) / 1e9,
+            "tuned": {"tile": [best.tile_w, best.tile_h], "lanes_per_pixel": best.lanes_per_pixel},
+            "launches_per_replay": 1, "graph": True, "gen_s": gen_s}
+
+
 def run_extras(torch, vct, dev, args):
-    """Secondary measurements: FP16 storage on the same frame."""
+    """Secondary measurements reported beside the main metric."""
     out = {}
+    for name, fn in (("fp16_single_view", extra_fp16_single), ("fwd_bwd", extra_fwd_bwd),
+                     ("batched_fp16", extra_batched)):
+        if name == "batched_fp16" and args.no_batched:
+            continue
+        try:
+            out[name] = fn(torch, vct, dev)
+        except Exception as e:  # report, keep the main line
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.empty_cache()
     return out
 
 
@@ -379,8 +503,38 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_profile_bwd(args):
+    import torch
+
+    import paper_2104_00618_gb300 as vct
+    import vct_synth as vs
+    dev = torch.device("cuda", 0)
+    cfg = vs.config_learnable(n=128, n_views=4, width=256, height=256)
+    learn = torch.from_numpy(cfg["learnable"]).to(dev)
+    gt = torch.from_numpy(cfg["scenes"][0]["grid"]).to(dev)
+    params = vct.make_params(cfg["params"])
+    views = [vct.View.from_host(v, device=dev) for v in cfg["views"]]
+    vct.trace([vct.build_mips(gt)], views, params)
+    targets = [(v.out_diffuse.clone(), v.out_specular.clone(), v.out_visibility.clone())
+               for v in views]
+    P = vct.Pyramid(128, None, "f32", device=dev)
+    bws = vct.backward_workspace(P)
+    grad = torch.zeros_like(learn)
+    for _ in range(args.warmup + args.steps):
+        vct.build_mips(learn, out=P)
+        vct.trace([P], views, params)
+        grads = [(v.out_diffuse - t[0], v.out_specular - t[1], v.out_visibility - t[2])
+                 for v, t in zip(views, targets)]
+        vct.trace_backward(P, views, grads, params, grad_level0=grad, workspace=bws)
+    torch.cuda.synchronize()
+    return {"profile_bwd": True, "steps": args.steps, "warmup": args.warmup}
+
+
 def main():
     args = parse()
+    if args.profile_bwd:
+        print(json.dumps(run_profile_bwd(args)))
+        return
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:
         print(json.dumps(line))

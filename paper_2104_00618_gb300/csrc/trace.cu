@@ -22,31 +22,33 @@ __device__ __forceinline__ int find_view(const Launch &L, int item) {
 }
 
 // One cone: returns (rgb, alpha) and, in `trans`, the transmittance
-// T = prod_k (1 - a_k).  The thesis's occlusion update alpha += (1 - alpha) a_s
-// is carried as T (alpha = 1 - T, the same recurrence) so that T, the colour
-// weights T_k a_k and the visibility keep their relative precision as alpha
-// approaches one; the loop runs while alpha = 1 - T < 1 in float32.
+// T = prod_k (1 - a_k).  The thesis's accumulation (Ch. 4.3.2) is evaluated as
+//   c += T_k a_k c_k,  alpha += T_k a_k,  T_{k+1} = T_k (1 - a_k)
+// (alpha_k = 1 - T_k: the same recurrence), which keeps alpha precise when it
+// is small and T precise when alpha is close to one; the loop runs while
+// alpha = 1 - T < 1 in float32 and t <= t_max.
 template <int DT>
 __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const float w[3],
                                         const ConeConst &cc, float T0, uint32_t &nsamp,
                                         float &trans) {
-  float cr = 0.f, cg = 0.f, cb = 0.f, tr = 1.f;
+  float cr = 0.f, cg = 0.f, cb = 0.f, al = 0.f, tr = 1.f;
   int k = 0;
   for (; k < cc.kmax; ++k) {
     if (!((1.0f - tr) < 1.0f)) break;
-    float T, lam;
+    float T, lam, om;
     step_at(cc, T0, k, T, lam);
     const float F[3] = {fmaf(T, w[0], A.Of[0]), fmaf(T, w[1], A.Of[1]), fmaf(T, w[2], A.Of[2])};
-    const float4 s = sample<DT>(P, A, F, lam);
+    const float4 s = sample<DT>(P, A, F, lam, om);
     const float wg = tr * s.w;  // front-to-back weight T_k a_s
     cr = fmaf(wg, s.x, cr);
     cg = fmaf(wg, s.y, cg);
     cb = fmaf(wg, s.z, cb);
-    tr *= 1.0f - s.w;
+    al += wg;
+    tr *= om;
   }
   nsamp += (uint32_t)k;
   trans = tr;
-  return make_float4(cr, cg, cb, 1.0f - tr);
+  return make_float4(cr, cg, cb, al);
 }
 
 // Each warp works independently: it takes a tile of pixels from the queue

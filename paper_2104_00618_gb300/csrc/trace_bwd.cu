@@ -18,68 +18,165 @@ namespace vct {
 
 namespace {
 
-__device__ __forceinline__ void scatter_level(float *glvl, const LevelStencil &s, float dc0,
-                                              float dc1, float dc2, float da) {
-  float4 *g = reinterpret_cast<float4 *>(glvl);
+// Levels with at most 16^3 texels are accumulated per CTA in shared memory
+// (every sample of a coarse level lands on a handful of texels, so global
+// atomics there would serialize) and added to global memory once per CTA.
+struct SmemGrad {
+  float *base;      // shared float[4 * texels of levels >= first]
+  int first;        // first level kept in shared memory
+  int off[VCT_MAX_LEVELS];  // texel offset of each such level
+};
+
+__device__ __forceinline__ float *grad_texel(const BwdLaunch &L, const SmemGrad &sg, int l,
+                                             uint32_t idx) {
+  return l >= sg.first ? sg.base + 4 * (sg.off[l] + idx)
+                       : reinterpret_cast<float *>(L.gpyr_lvl[l]) + 4 * (size_t)idx;
+}
+
+// Per-lane scatter of one level's 8 corners (lanes in different cells).
+__device__ __forceinline__ void scatter_lane(const BwdLaunch &L, const SmemGrad &sg, int l,
+                                             const LevelStencil &s, const float g[4]) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     if (!((s.valid >> c) & 1u)) continue;
     const float w = corner_weight(s, c);
     if (w == 0.0f) continue;
-    atomicAdd(g + corner_index(s, c), make_float4(w * dc0, w * dc1, w * dc2, w * da));
+    float *t = grad_texel(L, sg, l, corner_index(s, c));
+    if (l >= sg.first) {
+      atomicAdd(t + 0, w * g[0]);
+      atomicAdd(t + 1, w * g[1]);
+      atomicAdd(t + 2, w * g[2]);
+      atomicAdd(t + 3, w * g[3]);
+    } else {
+      atomicAdd(reinterpret_cast<float4 *>(t), make_float4(w * g[0], w * g[1], w * g[2], w * g[3]));
+    }
   }
 }
 
-__device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const Apex &A, const float w[3],
+// Scatter of one level for the whole warp (warp-uniform call).  When every
+// active lane uses the same level and the same 2x2x2 cell, the 32 values
+// (8 corners x 4 channels) are summed over the warp by recursive halving so
+// that lane j ends with the total of value j, and each lane issues one atomic
+// on a distinct address; otherwise each lane scatters its own corners.
+__device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const SmemGrad &sg, bool act,
+                                             int l, const LevelStencil &s, const float g[4]) {
+  const unsigned full = 0xffffffffu;
+  const unsigned actmask = __ballot_sync(full, act);
+  if (actmask == 0u) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(actmask) - 1;
+  const uint32_t key = s.sx[0] | s.sy[0] | s.sz[0];
+  const uint32_t lkey = __shfl_sync(full, key, leader);
+  const uint32_t lvalid = __shfl_sync(full, s.valid, leader);
+  const int ll = __shfl_sync(full, l, leader);
+  const bool uniform = __all_sync(full, !act || (key == lkey && l == ll && s.valid == lvalid));
+  if (!uniform) {
+    if (act) scatter_lane(L, sg, l, s, g);
+    return;
+  }
+  float v[32];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float w = act ? corner_weight(s, c) : 0.0f;
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) v[4 * c + ch] = w * g[ch];
+  }
+#pragma unroll
+  for (int half = 16; half >= 1; half >>= 1) {
+    const bool upper = (lane & half) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float send = upper ? v[i] : v[i + half];
+      const float keep = upper ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(full, send, half);
+    }
+  }
+  // Lane j holds the warp total of corner j / 4, channel j % 4.  The cell is
+  // the leader's: take its spread coordinates and form corner j / 4 here.
+  const int c = lane >> 2, ch = lane & 3;
+  // (A shuffle returns the source lane's value of the expression, so every
+  // per-corner choice is made here, after the shuffles.)
+  const uint32_t sx0 = __shfl_sync(full, s.sx[0], leader), sx1 = __shfl_sync(full, s.sx[1], leader);
+  const uint32_t sy0 = __shfl_sync(full, s.sy[0], leader), sy1 = __shfl_sync(full, s.sy[1], leader);
+  const uint32_t sz0 = __shfl_sync(full, s.sz[0], leader), sz1 = __shfl_sync(full, s.sz[1], leader);
+  const uint32_t idx = ((c & 1) ? sx1 : sx0) | (((c >> 1) & 1) ? sy1 : sy0) | ((c >> 2) ? sz1 : sz0);
+  if (((lvalid >> c) & 1u) && v[0] != 0.0f) atomicAdd(grad_texel(L, sg, ll, idx) + ch, v[0]);
+}
+
+// Adjoint of one cone for every lane of the warp (warp-uniform call; lanes
+// with active == false take no samples).
+__device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const SmemGrad &sg, bool active,
+                                             const Apex &A, const float w[3],
                                              const ConeConst &cc, float T0, float gc0, float gc1,
                                              float gc2, float ga) {
+  const unsigned full = 0xffffffffu;
   const DevPyr &P = L.pyr;
   float prod = 1.f, prod_last = 1.f;
   float tr_next = 0.f, R0 = 0.f, R1 = 0.f, R2 = 0.f, Q = 1.f;
-  int k = 0, K = 0;
-  bool rev = false;
+  int k = 0;                    // this lane's forward step
+  int K = active ? -1 : 0;      // this lane's sample count once known
+  bool rev = false;             // warp-uniform
+  int kr = 0;                   // warp-uniform backward step
   for (;;) {
     if (!rev) {
-      if (k >= cc.kmax || !((1.0f - prod) < 1.0f)) {
-        K = k;
+      if (K < 0 && !(k < cc.kmax && (1.0f - prod) < 1.0f)) K = k;
+      if (__all_sync(full, K >= 0)) {
         rev = true;
-        k = K - 1;
-        if (k < 0) break;
+        kr = (int)__reduce_max_sync(full, (unsigned)K) - 1;
       }
-    } else if (k < 0) {
-      break;
-    }
-    float T, lam;
-    step_at(cc, T0, k, T, lam);
-    const float F[3] = {fmaf(T, w[0], A.Of[0]), fmaf(T, w[1], A.Of[1]), fmaf(T, w[2], A.Of[2])};
-    const LodPick lp = pick_levels(lam, P.levels);
-    LevelStencil s0, s1;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    level_stencil(lp.l0, P.n >> lp.l0, 1.0f - lp.f, A, F, s0);
-    accumulate_level<VCT_F32>(P.lvl[lp.l0], s0, v);
-    if (lp.f > 0.0f) {
-      level_stencil(lp.l1, P.n >> lp.l1, lp.f, A, F, s1);
-      accumulate_level<VCT_F32>(P.lvl[lp.l1], s1, v);
-    }
-    const float om = 1.0f - v.w;
-    if (!rev) {
-      prod_last = prod;
-      prod *= om;
-      ++k;
     } else {
-      const float tr = (k == K - 1) ? prod_last : tr_next / om;
+      --kr;
+    }
+    if (rev && kr < 0) break;
+    const bool act = rev ? (kr < K) : (K < 0);
+    const int ks = rev ? kr : k;
+    LevelStencil s0, s1;
+    s0.valid = 0u;
+    s1.valid = 0u;
+    LodPick lp;
+    lp.l0 = lp.l1 = 0;
+    lp.f = 0.f;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    float om = 1.f;
+    if (act) {
+      float T, lam;
+      step_at(cc, T0, ks, T, lam);
+      const float F[3] = {fmaf(T, w[0], A.Of[0]), fmaf(T, w[1], A.Of[1]), fmaf(T, w[2], A.Of[2])};
+      lp = pick_levels(lam, P.levels);
+      om = 0.f;  // 1 - a_k, interpolated as in the forward kernel
+      level_stencil(lp.l0, P.n >> lp.l0, 1.0f - lp.f, A, F, s0);
+      accumulate_level<VCT_F32>(P.lvl[lp.l0], s0, v, om);
+      if (lp.f > 0.0f) {
+        level_stencil(lp.l1, P.n >> lp.l1, lp.f, A, F, s1);
+        accumulate_level<VCT_F32>(P.lvl[lp.l1], s1, v, om);
+      }
+      om = select_transparency(v.w, om);
+    }
+    if (!rev) {
+      if (act) {
+        prod_last = prod;
+        prod *= om;
+        ++k;
+      }
+      continue;
+    }
+    float g[4] = {0.f, 0.f, 0.f, 0.f};
+    if (act) {
+      const float tr = (kr == K - 1) ? prod_last : tr_next / om;
       const float ta = tr * v.w;  // same T_k as the forward's colour weight
-      const float dc0 = gc0 * ta, dc1 = gc1 * ta, dc2 = gc2 * ta;
-      const float da = tr * (gc0 * (v.x - R0) + gc1 * (v.y - R1) + gc2 * (v.z - R2) + ga * Q);
+      g[0] = gc0 * ta;
+      g[1] = gc1 * ta;
+      g[2] = gc2 * ta;
+      g[3] = tr * (gc0 * (v.x - R0) + gc1 * (v.y - R1) + gc2 * (v.z - R2) + ga * Q);
       R0 = fmaf(v.w, v.x, om * R0);
       R1 = fmaf(v.w, v.y, om * R1);
       R2 = fmaf(v.w, v.z, om * R2);
       Q *= om;
-      scatter_level(L.gpyr_lvl[lp.l0], s0, dc0, dc1, dc2, da);
-      if (lp.f > 0.0f) scatter_level(L.gpyr_lvl[lp.l1], s1, dc0, dc1, dc2, da);
       tr_next = tr;
-      --k;
     }
+    scatter_warp(L, sg, act, lp.l0, s0, g);
+    const bool two = act && lp.f > 0.0f;
+    if (__any_sync(full, two)) scatter_warp(L, sg, two, lp.l1, s1, g);
   }
 }
 
@@ -92,6 +189,18 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
   const int n_cones = L.n_diffuse + L.spec_enable + L.occ_enable;
   const float T0 = (float)L.t0_vox;
   const DevPyr &P = L.pyr;
+
+  extern __shared__ __align__(16) float s_grad[];
+  SmemGrad sg;
+  sg.base = s_grad;
+  sg.first = L.smem_first_level;
+  int smem_texels = 0;
+  for (int l = 0; l < VCT_MAX_LEVELS; ++l) {
+    sg.off[l] = smem_texels;
+    if (l >= sg.first && l < P.levels) smem_texels += (int)level_texels(P.n, l);
+  }
+  for (int i = threadIdx.x; i < 4 * smem_texels; i += blockDim.x) s_grad[i] = 0.f;
+  __syncthreads();
 
   for (;;) {
     const int item = next_item(L.queue);
@@ -116,31 +225,39 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
       const int px = tx0 + pi % L.tile_w;
       const int py = ty0 + pi / L.tile_w;
       const bool inimg = pi < tile_pix && px < V.W && py < V.H;
-      const int p = py * V.W + px;
-      if (!inimg || (V.mask != nullptr && V.mask[p] == 0)) continue;
-      float x[3], n[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        x[a] = V.pos[3 * p + a];
-        n[a] = V.nrm[3 * p + a];
-      }
+      const int p = inimg ? py * V.W + px : 0;
+      const bool pix_on = inimg && (V.mask == nullptr || V.mask[p] != 0);
+      float x[3] = {0.f, 0.f, 0.f}, n[3] = {0.f, 0.f, 1.f};
       float4 gD = make_float4(0.f, 0.f, 0.f, 0.f), gS = gD;
       float gV = 0.f;
-      if (BV.gD) gD = reinterpret_cast<const float4 *>(BV.gD)[p];
-      if (BV.gS) gS = reinterpret_cast<const float4 *>(BV.gS)[p];
-      if (BV.gV) gV = BV.gV[p];
+      if (pix_on) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          x[a] = V.pos[3 * p + a];
+          n[a] = V.nrm[3 * p + a];
+        }
+        if (BV.gD) gD = reinterpret_cast<const float4 *>(BV.gD)[p];
+        if (BV.gS) gS = reinterpret_cast<const float4 *>(BV.gS)[p];
+        if (BV.gV) gV = BV.gV[p];
+      }
       Apex A;
       make_apex(P, x, n, L.normal_offset, A);
       float Tf[3], Bf[3];
       tangent_frame(n, Tf, Bf);
-      for (int c = slot; c < n_cones; c += LPP) {
-        const ConeSel cs = select_cone(c, L.spec_enable, L.occ_enable);
-        float w[3];
-        ConeConst cc;
+      // The warp runs its lanes' cones together (the trip count is the same
+      // for every lane: warp-collective operations inside need it).
+      for (int c0 = 0; c0 < n_cones; c0 += LPP) {
+        const int c = c0 + slot;
+        const bool has_cone = c < n_cones;
+        const ConeSel cs = select_cone(has_cone ? c : 0, L.spec_enable, L.occ_enable);
+        float w[3] = {0.f, 0.f, 1.f};
+        ConeConst cc = P.diffuse;
         float g0, g1, g2, ga;
         if (cs.kind == kSpecular) {
-          reflect_dir(x, V.cam, n, w);
-          cc = spec_const(P, L.spec_gmin, L.spec_gmax, L.rough_min, L.beta, L.t0_vox, V.rough, p);
+          if (pix_on) reflect_dir(x, V.cam, n, w);
+          cc = pix_on ? spec_const(P, L.spec_gmin, L.spec_gmax, L.rough_min, L.beta, L.t0_vox,
+                                   V.rough, p)
+                      : P.spec_fixed;
           g0 = gS.x;
           g1 = gS.y;
           g2 = gS.z;
@@ -156,30 +273,45 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
           const float *d = L.diffuse_dir[cs.diffuse_index];
 #pragma unroll
           for (int a = 0; a < 3; ++a) w[a] = fmaf(Tf[a], d[0], fmaf(Bf[a], d[1], n[a] * d[2]));
-          cc = P.diffuse;
           const float wt = L.diffuse_weight[cs.diffuse_index];
           g0 = wt * gD.x;
           g1 = wt * gD.y;
           g2 = wt * gD.z;
           ga = wt * gD.w;
         }
-        if (g0 == 0.f && g1 == 0.f && g2 == 0.f && ga == 0.f) continue;
-        cone_adjoint(L, A, w, cc, T0, g0, g1, g2, ga);
+        const bool on = pix_on && has_cone && (g0 != 0.f || g1 != 0.f || g2 != 0.f || ga != 0.f);
+        if (__any_sync(0xffffffffu, on)) cone_adjoint(L, sg, on, A, w, cc, T0, g0, g1, g2, ga);
       }
+    }
+  }
+  // Add this CTA's coarse-level gradients to global memory.
+  __syncthreads();
+  for (int l = sg.first; l < P.levels; ++l) {
+    const int cnt = (int)level_texels(P.n, l);
+    float4 *g = reinterpret_cast<float4 *>(L.gpyr_lvl[l]);
+    const float4 *src = reinterpret_cast<const float4 *>(s_grad) + sg.off[l];
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const float4 v = src[i];
+      if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) atomicAdd(g + i, v);
     }
   }
 }
 
 template <int LPP>
-cudaError_t launch_b(const BwdLaunch &L, int grid, cudaStream_t s) {
-  trace_bwd_kernel<LPP><<<grid, kTraceThreads, 0, s>>>(L);
+cudaError_t launch_b(const BwdLaunch &L, int grid, size_t smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(trace_bwd_kernel<LPP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  trace_bwd_kernel<LPP><<<grid, kTraceThreads, smem, s>>>(L);
   return cudaGetLastError();
 }
 
 template <int LPP>
-int occ_b() {
+int occ_b(size_t smem) {
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_bwd_kernel<LPP>, kTraceThreads, 0);
+  cudaFuncSetAttribute(trace_bwd_kernel<LPP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_bwd_kernel<LPP>, kTraceThreads, smem);
   return b;
 }
 
@@ -187,22 +319,29 @@ int occ_b() {
 
 static_assert(sizeof(BwdLaunch) <= 32000, "adjoint launch parameters exceed the 32 KB limit");
 
+size_t bwd_smem_bytes(int n, int levels, int first) {
+  size_t t = 0;
+  for (int l = first; l < levels; ++l) t += level_texels(n, l);
+  return t * 16;
+}
+
 cudaError_t launch_trace_bwd(const BwdLaunch &L, int lpp, int grid, cudaStream_t s) {
+  const size_t smem = bwd_smem_bytes(L.pyr.n, L.pyr.levels, L.smem_first_level);
   switch (lpp) {
-    case 1: return launch_b<1>(L, grid, s);
-    case 2: return launch_b<2>(L, grid, s);
-    case 4: return launch_b<4>(L, grid, s);
-    case 8: return launch_b<8>(L, grid, s);
+    case 1: return launch_b<1>(L, grid, smem, s);
+    case 2: return launch_b<2>(L, grid, smem, s);
+    case 4: return launch_b<4>(L, grid, smem, s);
+    case 8: return launch_b<8>(L, grid, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-int trace_bwd_occupancy(int lpp) {
+int trace_bwd_occupancy(int lpp, size_t smem) {
   switch (lpp) {
-    case 1: return occ_b<1>();
-    case 2: return occ_b<2>();
-    case 4: return occ_b<4>();
-    case 8: return occ_b<8>();
+    case 1: return occ_b<1>(smem);
+    case 2: return occ_b<2>(smem);
+    case 4: return occ_b<4>(smem);
+    case 8: return occ_b<8>(smem);
     default: return 0;
   }
 }

@@ -147,9 +147,14 @@ __device__ __forceinline__ float corner_weight(const LevelStencil &s, int c) {
   return s.wx[c & 1] * s.wyz[c >> 1];
 }
 
+// Adds one level's weighted corners to acc = (r, g, b, a) and to `om`, the
+// interpolated transparency sum_c w_c (1 - a_c), formed corner by corner
+// (one rounding each) so that it is exactly 0 inside opaque regions and keeps
+// its relative precision when the sample is nearly opaque.  Corners outside
+// the grid are empty: they add w_c to `om` and nothing to acc.
 template <int DT>
 __device__ __forceinline__ void accumulate_level(const uint8_t *lvl, const LevelStencil &s,
-                                                 float4 &acc) {
+                                                 float4 &acc, float &om) {
   using T = typename TexOf<DT>::T;
   const T *base = reinterpret_cast<const T *>(lvl);
   float4 v[8];
@@ -170,6 +175,7 @@ __device__ __forceinline__ void accumulate_level(const uint8_t *lvl, const Level
     acc.y = fmaf(w, v[c].y, acc.y);
     acc.z = fmaf(w, v[c].z, acc.z);
     acc.w = fmaf(w, v[c].w, acc.w);
+    om += fmaf(-w, v[c].w, w);
   }
 }
 
@@ -187,19 +193,29 @@ __device__ __forceinline__ LodPick pick_levels(float lam, int levels) {
   return r;
 }
 
-// The full sample S(p, lambda) at apex-relative voxel coordinates F.
+// 1 - a_s: directly from a_s while the sample is at most half opaque (exact 1
+// for empty space), from the per-corner transparency sum otherwise (exact 0
+// for opaque space, full relative precision when nearly opaque).
+__device__ __forceinline__ float select_transparency(float a, float om_sum) {
+  return a <= 0.5f ? 1.0f - a : om_sum;
+}
+
+// The full sample S(p, lambda) at apex-relative voxel coordinates F;
+// `om` receives the sample's transparency 1 - a_s.
 template <int DT>
 __device__ __forceinline__ float4 sample(const DevPyr &P, const Apex &A, const float F[3],
-                                         float lam) {
+                                         float lam, float &om) {
   const LodPick lp = pick_levels(lam, P.levels);
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  om = 0.f;
   LevelStencil s;
   level_stencil(lp.l0, P.n >> lp.l0, 1.0f - lp.f, A, F, s);
-  accumulate_level<DT>(P.lvl[lp.l0], s, acc);
+  accumulate_level<DT>(P.lvl[lp.l0], s, acc, om);
   if (lp.f > 0.0f) {
     level_stencil(lp.l1, P.n >> lp.l1, lp.f, A, F, s);
-    accumulate_level<DT>(P.lvl[lp.l1], s, acc);
+    accumulate_level<DT>(P.lvl[lp.l1], s, acc, om);
   }
+  om = select_transparency(acc.w, om);
   return acc;
 }
 

@@ -228,7 +228,7 @@ TuneKey tune_key(const vct_pyramid *pyrs, const vct_view *views, const vct_trace
                  views[0].roughness != nullptr);
 }
 
-vct_launch_config default_cfg() { return vct_launch_config{8, 8, 1, 0}; }
+vct_launch_config default_cfg() { return vct_launch_config{8, 4, 1, 0}; }
 
 vct_launch_config pick_cfg(const vct_launch_config *cfg, const vct_pyramid *pyrs,
                            const vct_view *views, const vct_trace_params *P) {
@@ -493,10 +493,17 @@ vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
   L->queue = reinterpret_cast<unsigned *>(ws);
   L->tile_w = c.tile_w;
   L->tile_h = c.tile_h;
+  {
+    int first = 0;
+    while (first < pyr->levels && (pyr->n >> first) > kBwdSmemMaxEdge) ++first;
+    L->smem_first_level = first;
+  }
+  const size_t smem = bwd_smem_bytes(pyr->n, pyr->levels, L->smem_first_level);
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(ws, 0, gl.total, s);
   if (e != cudaSuccess) return cuda_fail(e, "vct_trace_backward workspace clear");
-  int per_sm = c.ctas_per_sm ? c.ctas_per_sm : std::max(1, trace_bwd_occupancy(c.lanes_per_pixel));
+  int per_sm =
+      c.ctas_per_sm ? c.ctas_per_sm : std::max(1, trace_bwd_occupancy(c.lanes_per_pixel, smem));
   const int sms = sm_count();
   for (int v0 = 0; v0 < n_views; v0 += kMaxBwdViewsPerLaunch) {
     const int nv = std::min(kMaxBwdViewsPerLaunch, n_views - v0);

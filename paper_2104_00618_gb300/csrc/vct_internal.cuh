@@ -13,10 +13,10 @@ namespace vct {
 constexpr int kHeaderBytes = 256;
 constexpr int kTraceThreads = 256;      // one CTA shape for every trace kernel
 #ifndef VCT_TRACE_MIN_BLOCKS
-#define VCT_TRACE_MIN_BLOCKS 3
+#define VCT_TRACE_MIN_BLOCKS 2
 #endif
 constexpr int kTraceMinBlocks = VCT_TRACE_MIN_BLOCKS;  // register budget: 65536 / (256 * this)
-constexpr int kMaxViewsPerLaunch = 224;  // keeps the forward launch under 32 KB
+constexpr int kMaxViewsPerLaunch = 256;  // keeps the forward launch under 32 KB
 constexpr int kMaxBwdViewsPerLaunch = 128;
 constexpr int kMaxSteps = 1 << 16;       // per-cone step cap (parameter check)
 
@@ -225,6 +225,8 @@ struct BwdLaunch {
   float normal_offset;
   double spec_gmin, spec_gmax, rough_min, beta, t0_vox;
   unsigned *queue;
+  int smem_first_level;             // levels >= this accumulate in shared memory
+  int pad1;
   float *gpyr_lvl[VCT_MAX_LEVELS];  // float32 gradient pyramid levels
   DevPyr pyr;
   BwdView views[kMaxBwdViewsPerLaunch];
@@ -262,6 +264,8 @@ cudaError_t launch_wait_probe(uint32_t *flag, uint64_t max_ns, cudaStream_t s);
 cudaError_t launch_trace(const TraceLaunch &L, int lpp, int dtype, int grid, cudaStream_t s);
 int trace_occupancy(int lpp, int dtype);
 cudaError_t launch_trace_bwd(const BwdLaunch &L, int lpp, int grid, cudaStream_t s);
-int trace_bwd_occupancy(int lpp);
+int trace_bwd_occupancy(int lpp, size_t smem);
+size_t bwd_smem_bytes(int n, int levels, int first);
+constexpr int kBwdSmemMaxEdge = 16;  // levels of at most 16^3 texels use shared memory
 
 }  // namespace vct

@@ -221,8 +221,10 @@ def _diff_case(n=32, W=48, H=40, seed=61):
     return gt, views, prm, learn
 
 
-def test_backward_matches_oracle_gradient():
+@pytest.mark.parametrize("lpp,occ", [(1, 1), (2, 0), (4, 1), (8, 0)])
+def test_backward_matches_oracle_gradient(lpp, occ):
     gt, views, prm, learn = _diff_case()
+    prm = dict(prm, occ_enable=occ)
     O_gt = oracle.build_mips(gt["grid"])
     targets = [oracle.trace(O_gt, v, prm) for v in views]
     O = oracle.build_mips(learn)
@@ -236,7 +238,8 @@ def test_backward_matches_oracle_gradient():
                                for a in (gD, gS, gV)))
     P = gpu_pyramid(learn)
     gviews = [vct.View.from_host(v) for v in views]
-    grad = vct.trace_backward(P, gviews, gpu_grads, prm).cpu().numpy().astype(np.float64)
+    grad = vct.trace_backward(P, gviews, gpu_grads, prm, cfg=vct.launch_config(8, 8, lpp))
+    grad = grad.cpu().numpy().astype(np.float64)
     scale = np.abs(grad_ref).max()
     err = np.abs(grad - grad_ref)
     print("gradient: max abs err / max |grad| =", err.max() / scale)
@@ -316,3 +319,61 @@ def test_invalid_arguments_rejected():
     P16 = gpu_pyramid(np.zeros((8, 8, 8, 4), np.float32), dtype="f16")
     with pytest.raises(vct.VctError):
         vct.trace_backward(P16, [vct.View.from_host(view)], [(None, None, None)], prm)
+
+
+# ---------------------------------------------------------------------------
+# batching: autotuned shape, CUDA-graph replay, FP16 pyramids
+# ---------------------------------------------------------------------------
+def _batch(dtype="f32"):
+    scenes = [vs.box_scene(n, 6, 400 + n, room=True) for n in (32, 64)]
+    rng = np.random.default_rng(9)
+    hv = []
+    for i, (w, h) in enumerate([(70, 33), (41, 64), (16, 16), (97, 11)]):
+        v = vs.interior_view(scenes[i % 2], w, h, rng)
+        v["pyramid"] = i % 2
+        hv.append(v)
+    prm = vs.params_room9(scenes[0]["light"])
+    pyrs = [gpu_pyramid(sc["grid"], dtype=dtype) for sc in scenes]
+    return scenes, hv, prm, pyrs
+
+
+def test_autotune_then_graph_replay_matches_direct_call():
+    scenes, hv, prm, pyrs = _batch()
+    views = [vct.View.from_host(v) for v in hv]
+    best = vct.autotune(pyrs, views, prm)
+    assert best.lanes_per_pixel in (1, 2, 4, 8) and best.tile_w * best.tile_h >= 32
+    ws = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    vct.trace(pyrs, views, prm, workspace=ws)
+    torch.cuda.synchronize()
+    direct = [(v.out_diffuse.clone(), v.out_specular.clone(), v.out_visibility.clone())
+              for v in views]
+    for v in views:
+        v.out_diffuse.fill_(-1)
+        v.out_specular.fill_(-1)
+        v.out_visibility.fill_(-1)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        vct.trace(pyrs, views, prm, workspace=ws)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for v, d in zip(views, direct):
+        assert torch.equal(v.out_diffuse, d[0]) and torch.equal(v.out_specular, d[1])
+        assert torch.equal(v.out_visibility, d[2])
+    # the replayed stats count one call (the workspace is cleared inside the graph)
+    st = vct.read_stats(ws)
+    assert st["cones"][1] == sum(int(v["mask"].sum()) for v in hv)
+
+
+def test_batched_fp16_pyramids_against_oracle():
+    scenes, hv, prm, pyrs = _batch("f16")
+    outs, _ = gpu_trace(pyrs, hv, prm)
+    worst_fp16 = 0.0
+    for v, out in zip(hv, outs):
+        ref = oracle.trace(oracle.build_mips(scenes[v["pyramid"]]["grid"]), v, prm)
+        res = compare(out, ref, prm=prm)
+        worst_fp16 = max(worst_fp16, worst(res))
+    print("batched fp16 worst floored rel error:", worst_fp16)
+    assert worst_fp16 < 5e-2
