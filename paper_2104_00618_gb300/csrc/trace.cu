@@ -29,8 +29,8 @@ __device__ __forceinline__ int find_view(const Launch &L, int item) {
 // alpha = 1 - T < 1 in float32 and t <= t_max.
 template <int DT>
 __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const float w[3],
-                                        const ConeConst &cc, float T0, uint32_t &nsamp,
-                                        float &trans) {
+                                        const ConeConst &cc, float T0, const uint32_t *lut,
+                                        uint32_t &nsamp, float &trans) {
   float cr = 0.f, cg = 0.f, cb = 0.f, al = 0.f, tr = 1.f;
   int k = 0;
   for (; k < cc.kmax; ++k) {
@@ -38,7 +38,8 @@ __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const fl
     float T, lam, om;
     step_at(cc, T0, k, T, lam);
     const float F[3] = {fmaf(T, w[0], A.Of[0]), fmaf(T, w[1], A.Of[1]), fmaf(T, w[2], A.Of[2])};
-    const float4 s = sample<DT>(P, A, F, lam, om);
+    LodPick lp;
+    const float4 s = sample<DT>(P, A, F, lam, lut, om, lp);
     const float wg = tr * s.w;  // front-to-back weight T_k a_s
     cr = fmaf(wg, s.x, cr);
     cg = fmaf(wg, s.y, cg);
@@ -63,6 +64,8 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
   const int pr = lane / LPP;
   const int n_cones = L.n_diffuse + L.spec_enable + L.occ_enable;
   const float T0 = (float)L.t0_vox;
+  __shared__ uint32_t s_lut[1024];
+  fill_spread_lut(s_lut);
 
   for (;;) {
     const int item = next_item(L.queue);
@@ -117,7 +120,7 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
             cc = P.diffuse;
           }
           float trans;
-          const float4 r = march<DT>(P, A, w, cc, T0, n_samp[cs.kind], trans);
+          const float4 r = march<DT>(P, A, w, cc, T0, s_lut, n_samp[cs.kind], trans);
           n_cone[cs.kind] += 1u;
           if (cs.kind == kDiffuse) {
             const float wt = L.diffuse_weight[cs.diffuse_index];

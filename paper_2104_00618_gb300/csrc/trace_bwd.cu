@@ -35,11 +35,11 @@ __device__ __forceinline__ float *grad_texel(const BwdLaunch &L, const SmemGrad 
 
 // Per-lane scatter of one level's 8 corners (lanes in different cells).
 __device__ __forceinline__ void scatter_lane(const BwdLaunch &L, const SmemGrad &sg, int l,
-                                             const LevelStencil &s, const float g[4]) {
+                                             const LevelStencil &s, float lw, const float g[4]) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     if (!((s.valid >> c) & 1u)) continue;
-    const float w = corner_weight(s, c);
+    const float w = corner_weight(s, lw, c);
     if (w == 0.0f) continue;
     float *t = grad_texel(L, sg, l, corner_index(s, c));
     if (l >= sg.first) {
@@ -59,7 +59,8 @@ __device__ __forceinline__ void scatter_lane(const BwdLaunch &L, const SmemGrad 
 // that lane j ends with the total of value j, and each lane issues one atomic
 // on a distinct address; otherwise each lane scatters its own corners.
 __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const SmemGrad &sg, bool act,
-                                             int l, const LevelStencil &s, const float g[4]) {
+                                             int l, const LevelStencil &s, float lw,
+                                             const float g[4]) {
   const unsigned full = 0xffffffffu;
   const unsigned actmask = __ballot_sync(full, act);
   if (actmask == 0u) return;
@@ -71,13 +72,13 @@ __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const SmemGrad 
   const int ll = __shfl_sync(full, l, leader);
   const bool uniform = __all_sync(full, !act || (key == lkey && l == ll && s.valid == lvalid));
   if (!uniform) {
-    if (act) scatter_lane(L, sg, l, s, g);
+    if (act) scatter_lane(L, sg, l, s, lw, g);
     return;
   }
   float v[32];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const float w = act ? corner_weight(s, c) : 0.0f;
+    const float w = act ? corner_weight(s, lw, c) : 0.0f;
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch) v[4 * c + ch] = w * g[ch];
   }
@@ -105,7 +106,8 @@ __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const SmemGrad 
 
 // Adjoint of one cone for every lane of the warp (warp-uniform call; lanes
 // with active == false take no samples).
-__device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const SmemGrad &sg, bool active,
+__device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const SmemGrad &sg,
+                                             const uint32_t *lut, bool active,
                                              const Apex &A, const float w[3],
                                              const ConeConst &cc, float T0, float gc0, float gc1,
                                              float gc2, float ga) {
@@ -130,9 +132,9 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const SmemGrad 
     if (rev && kr < 0) break;
     const bool act = rev ? (kr < K) : (K < 0);
     const int ks = rev ? kr : k;
-    LevelStencil s0, s1;
-    s0.valid = 0u;
-    s1.valid = 0u;
+    LevelStencil st[2];
+    st[0].valid = 0u;
+    st[1].valid = 0u;
     LodPick lp;
     lp.l0 = lp.l1 = 0;
     lp.f = 0.f;
@@ -142,15 +144,7 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const SmemGrad 
       float T, lam;
       step_at(cc, T0, ks, T, lam);
       const float F[3] = {fmaf(T, w[0], A.Of[0]), fmaf(T, w[1], A.Of[1]), fmaf(T, w[2], A.Of[2])};
-      lp = pick_levels(lam, P.levels);
-      om = 0.f;  // 1 - a_k, interpolated as in the forward kernel
-      level_stencil(lp.l0, P.n >> lp.l0, 1.0f - lp.f, A, F, s0);
-      accumulate_level<VCT_F32>(P.lvl[lp.l0], s0, v, om);
-      if (lp.f > 0.0f) {
-        level_stencil(lp.l1, P.n >> lp.l1, lp.f, A, F, s1);
-        accumulate_level<VCT_F32>(P.lvl[lp.l1], s1, v, om);
-      }
-      om = select_transparency(v.w, om);
+      v = sample<VCT_F32>(P, A, F, lam, lut, om, lp, st);
     }
     if (!rev) {
       if (act) {
@@ -174,9 +168,9 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const SmemGrad 
       Q *= om;
       tr_next = tr;
     }
-    scatter_warp(L, sg, act, lp.l0, s0, g);
+    scatter_warp(L, sg, act, lp.l0, st[0], 1.0f - lp.f, g);
     const bool two = act && lp.f > 0.0f;
-    if (__any_sync(full, two)) scatter_warp(L, sg, two, lp.l1, s1, g);
+    if (__any_sync(full, two)) scatter_warp(L, sg, two, lp.l1, st[1], lp.f, g);
   }
 }
 
@@ -200,7 +194,8 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
     if (l >= sg.first && l < P.levels) smem_texels += (int)level_texels(P.n, l);
   }
   for (int i = threadIdx.x; i < 4 * smem_texels; i += blockDim.x) s_grad[i] = 0.f;
-  __syncthreads();
+  __shared__ uint32_t s_lut[1024];
+  fill_spread_lut(s_lut);  // (its barrier also covers the zeroing above)
 
   for (;;) {
     const int item = next_item(L.queue);
@@ -280,7 +275,8 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
           ga = wt * gD.w;
         }
         const bool on = pix_on && has_cone && (g0 != 0.f || g1 != 0.f || g2 != 0.f || ga != 0.f);
-        if (__any_sync(0xffffffffu, on)) cone_adjoint(L, sg, on, A, w, cc, T0, g0, g1, g2, ga);
+        if (__any_sync(0xffffffffu, on))
+          cone_adjoint(L, sg, s_lut, on, A, w, cc, T0, g0, g1, g2, ga);
       }
     }
   }

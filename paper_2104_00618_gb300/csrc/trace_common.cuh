@@ -78,19 +78,63 @@ __device__ __forceinline__ void step_at(const ConeConst &cc, float T0, int k, fl
   lam = (cc.lam0_hi + p) + (q + cc.lam0_lo);
 }
 
-// One level of the quadrilinear lookup: the 2x2x2 stencil around the sample.
+// ---------------------------------------------------------------------------
+// packed float32 pairs (Blackwell f32x2 arithmetic): RGBA is carried as the
+// two pairs (r, g) and (b, a), halving the instruction count of the lerps.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 f2_pack(float a, float b) {
+  f32x2 d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(a), "f"(b));
+  return d;
+}
+__device__ __forceinline__ float2 f2_unpack(f32x2 v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// a + t (b - a), both lanes
+__device__ __forceinline__ f32x2 f2_lerp(f32x2 a, f32x2 b, f32x2 t) {
+  return f2_fma(t, f2_sub(b, a), a);
+}
+
+__device__ __forceinline__ void ld_texel2(const float4 *p, f32x2 &rg, f32x2 &ba) {
+  asm("ld.global.nc.v2.u64 {%0, %1}, [%2];" : "=l"(rg), "=l"(ba) : "l"(p));
+}
+__device__ __forceinline__ void ld_texel2(const uint2 *p, f32x2 &rg, f32x2 &ba) {
+  const uint2 u = __ldg(p);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+  rg = f2_pack(a.x, a.y);
+  ba = f2_pack(b.x, b.y);
+}
+
+// ---------------------------------------------------------------------------
+// one level of the quadrilinear lookup: the 2x2x2 cell around the sample
+// ---------------------------------------------------------------------------
 struct LevelStencil {
   uint32_t sx[2], sy[2], sz[2];  // spread Morton bits of the two corners per axis
-  float wx[2], wyz[4];           // x weights (times the level weight), y*z weights
+  float fr[3];                   // position inside the cell, per axis
   uint32_t valid;  // bit c set if corner c = dx | dy<<1 | dz<<2 is inside the level
 };
 
-__device__ __forceinline__ void level_stencil(int l, int Nl, float lw, const Apex &A,
-                                              const float F[3], LevelStencil &s) {
+// lut: spread3 of 0..1023 (shared memory).
+__device__ __forceinline__ void level_stencil(int l, int Nl, const Apex &A, const float F[3],
+                                              const uint32_t *lut, LevelStencil &s) {
   const float sc = __int_as_float((127 - l) << 23);  // 2^-l
   const int mask = (1 << l) - 1;
   int b[3];
-  float fr[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int ri = A.Xi[a] & mask;
@@ -98,26 +142,19 @@ __device__ __forceinline__ void level_stencil(int l, int Nl, float lw, const Ape
     // u = (Xi + F) / 2^l - 1/2, formed from small numbers only
     const float v = fmaf(F[a], sc, fmaf((float)ri, sc, -0.5f));
     const float fl = floorf(v);
-    fr[a] = v - fl;
+    s.fr[a] = v - fl;
     b[a] = qi + (int)fl;
   }
-  s.wx[0] = lw * (1.0f - fr[0]);
-  s.wx[1] = lw * fr[0];
-  const float wy0 = 1.0f - fr[1], wz0 = 1.0f - fr[2];
-  s.wyz[0] = wy0 * wz0;
-  s.wyz[1] = fr[1] * wz0;
-  s.wyz[2] = wy0 * fr[2];
-  s.wyz[3] = fr[1] * fr[2];
-  const uint32_t x0 = spread3((uint32_t)b[0]);
-  const uint32_t y0 = spread3((uint32_t)b[1]);
-  const uint32_t z0 = spread3((uint32_t)b[2]);
+  const uint32_t x0 = lut[(uint32_t)b[0] & 1023u];
+  const uint32_t y0 = lut[(uint32_t)b[1] & 1023u];
+  const uint32_t z0 = lut[(uint32_t)b[2] & 1023u];
   s.sx[0] = x0;
   s.sx[1] = spread3_inc(x0);
   s.sy[0] = y0 << 1;
   s.sy[1] = spread3_inc(y0) << 1;
   s.sz[0] = z0 << 2;
   s.sz[1] = spread3_inc(z0) << 2;
-  // Interior stencils (the common case) need no per-corner test.
+  // Interior cells (the common case) need no per-corner test.
   const uint32_t lim = (uint32_t)Nl - 1u;
   if ((uint32_t)b[0] < lim && (uint32_t)b[1] < lim && (uint32_t)b[2] < lim) {
     s.valid = 0xffu;
@@ -142,41 +179,46 @@ __device__ __forceinline__ void level_stencil(int l, int Nl, float lw, const Ape
 __device__ __forceinline__ uint32_t corner_index(const LevelStencil &s, int c) {
   return s.sx[c & 1] | s.sy[(c >> 1) & 1] | s.sz[c >> 2];
 }
-// Weight of corner c (level weight included).
-__device__ __forceinline__ float corner_weight(const LevelStencil &s, int c) {
-  return s.wx[c & 1] * s.wyz[c >> 1];
+// Trilinear weight of corner c times the level weight lw (adjoint scatter).
+__device__ __forceinline__ float corner_weight(const LevelStencil &s, float lw, int c) {
+  const float wx = (c & 1) ? s.fr[0] : 1.0f - s.fr[0];
+  const float wy = ((c >> 1) & 1) ? s.fr[1] : 1.0f - s.fr[1];
+  const float wz = (c >> 2) ? s.fr[2] : 1.0f - s.fr[2];
+  return lw * wx * wy * wz;
 }
 
-// Adds one level's weighted corners to acc = (r, g, b, a) and to `om`, the
-// interpolated transparency sum_c w_c (1 - a_c), formed corner by corner
-// (one rounding each) so that it is exactly 0 inside opaque regions and keeps
-// its relative precision when the sample is nearly opaque.  Corners outside
-// the grid are empty: they add w_c to `om` and nothing to acc.
+// Trilinear lookup of one level as seven packed lerps (x, then y, then z);
+// corners outside the grid read as zero.
 template <int DT>
-__device__ __forceinline__ void accumulate_level(const uint8_t *lvl, const LevelStencil &s,
-                                                 float4 &acc, float &om) {
+__device__ __forceinline__ void trilerp(const uint8_t *lvl, const LevelStencil &s, f32x2 &rg,
+                                        f32x2 &ba) {
   using T = typename TexOf<DT>::T;
   const T *base = reinterpret_cast<const T *>(lvl);
-  float4 v[8];
+  f32x2 c_rg[8], c_ba[8];
   if (s.valid == 0xffu) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) v[c] = ld_texel(base + corner_index(s, c));
+    for (int c = 0; c < 8; ++c) ld_texel2(base + corner_index(s, c), c_rg[c], c_ba[c]);
   } else {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      v[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if ((s.valid >> c) & 1u) v[c] = ld_texel(base + corner_index(s, c));
+      c_rg[c] = 0ull;
+      c_ba[c] = 0ull;
+      if ((s.valid >> c) & 1u) ld_texel2(base + corner_index(s, c), c_rg[c], c_ba[c]);
     }
   }
+  const f32x2 tx = f2_pack(s.fr[0], s.fr[0]);
+  const f32x2 ty = f2_pack(s.fr[1], s.fr[1]);
+  const f32x2 tz = f2_pack(s.fr[2], s.fr[2]);
+  f32x2 e_rg[4], e_ba[4];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const float w = corner_weight(s, c);
-    acc.x = fmaf(w, v[c].x, acc.x);
-    acc.y = fmaf(w, v[c].y, acc.y);
-    acc.z = fmaf(w, v[c].z, acc.z);
-    acc.w = fmaf(w, v[c].w, acc.w);
-    om += fmaf(-w, v[c].w, w);
+  for (int i = 0; i < 4; ++i) {
+    e_rg[i] = f2_lerp(c_rg[2 * i], c_rg[2 * i + 1], tx);
+    e_ba[i] = f2_lerp(c_ba[2 * i], c_ba[2 * i + 1], tx);
   }
+  const f32x2 g0_rg = f2_lerp(e_rg[0], e_rg[1], ty), g1_rg = f2_lerp(e_rg[2], e_rg[3], ty);
+  const f32x2 g0_ba = f2_lerp(e_ba[0], e_ba[1], ty), g1_ba = f2_lerp(e_ba[2], e_ba[3], ty);
+  rg = f2_lerp(g0_rg, g1_rg, tz);
+  ba = f2_lerp(g0_ba, g1_ba, tz);
 }
 
 // Level choice of Ch. 4.5 with the quadrilinear blend of Ch. 4.3.3.
@@ -193,30 +235,41 @@ __device__ __forceinline__ LodPick pick_levels(float lam, int levels) {
   return r;
 }
 
-// 1 - a_s: directly from a_s while the sample is at most half opaque (exact 1
-// for empty space), from the per-corner transparency sum otherwise (exact 0
-// for opaque space, full relative precision when nearly opaque).
-__device__ __forceinline__ float select_transparency(float a, float om_sum) {
-  return a <= 0.5f ? 1.0f - a : om_sum;
-}
+// 1 - a_s, clamped at zero: with texel opacities in [0, 1] the exact value is
+// >= 0, and rounding can put an all-opaque sample a hair above one.
+__device__ __forceinline__ float transparency(float a) { return fmaxf(1.0f - a, 0.0f); }
 
-// The full sample S(p, lambda) at apex-relative voxel coordinates F;
-// `om` receives the sample's transparency 1 - a_s.
+// The full sample S(p, lambda) at apex-relative voxel coordinates F (levels
+// floor(lambda) and floor(lambda)+1 blended linearly); `om` receives 1 - a_s.
+// When `st` is non-null the two stencils are kept for the adjoint.
 template <int DT>
 __device__ __forceinline__ float4 sample(const DevPyr &P, const Apex &A, const float F[3],
-                                         float lam, float &om) {
-  const LodPick lp = pick_levels(lam, P.levels);
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  om = 0.f;
+                                         float lam, const uint32_t *lut, float &om,
+                                         LodPick &lp, LevelStencil *st = nullptr) {
+  lp = pick_levels(lam, P.levels);
   LevelStencil s;
-  level_stencil(lp.l0, P.n >> lp.l0, 1.0f - lp.f, A, F, s);
-  accumulate_level<DT>(P.lvl[lp.l0], s, acc, om);
+  f32x2 rg, ba;
+  level_stencil(lp.l0, P.n >> lp.l0, A, F, lut, s);
+  trilerp<DT>(P.lvl[lp.l0], s, rg, ba);
+  if (st) st[0] = s;
   if (lp.f > 0.0f) {
-    level_stencil(lp.l1, P.n >> lp.l1, lp.f, A, F, s);
-    accumulate_level<DT>(P.lvl[lp.l1], s, acc, om);
+    level_stencil(lp.l1, P.n >> lp.l1, A, F, lut, s);
+    f32x2 rg1, ba1;
+    trilerp<DT>(P.lvl[lp.l1], s, rg1, ba1);
+    const f32x2 tf = f2_pack(lp.f, lp.f);
+    rg = f2_lerp(rg, rg1, tf);
+    ba = f2_lerp(ba, ba1, tf);
+    if (st) st[1] = s;
   }
-  om = select_transparency(acc.w, om);
-  return acc;
+  const float2 v0 = f2_unpack(rg), v1 = f2_unpack(ba);
+  om = transparency(v1.y);
+  return make_float4(v0.x, v0.y, v1.x, v1.y);
+}
+
+// Fills the Morton spread table (shared memory) of a CTA.
+__device__ __forceinline__ void fill_spread_lut(uint32_t *lut) {
+  for (int i = threadIdx.x; i < 1024; i += blockDim.x) lut[i] = spread3((uint32_t)i);
+  __syncthreads();
 }
 
 // Per-warp work queue: lane 0 takes the next item, the warp shares it.
