@@ -52,19 +52,63 @@ __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const fl
   return make_float4(cr, cg, cb, al);
 }
 
+// Estimated step count of the specular cone (sort key only; float32).
+__device__ __forceinline__ uint32_t spec_steps_estimate(const TraceLaunch &L, const DevPyr &P,
+                                                        const float *rough, int p) {
+  float g = (float)L.spec_gmin;
+  if (rough != nullptr) {
+    float f = (rough[p] - (float)L.rough_min) / (1.0f - (float)L.rough_min);
+    f = fminf(fmaxf(f, 0.0f), 1.0f);
+    g += f * (float)(L.spec_gmax - L.spec_gmin);
+  }
+  const float l2r = log1pf(2.0f * (float)L.beta * tanf(0.5f * g)) * 1.44269504f;
+  const float e = log2f((float)(P.tmax_vox / L.t0_vox)) / l2r;
+  return (uint32_t)fminf(fmaxf(e + 1.0f, 1.0f), 65535.0f);
+}
+
+// Bitonic sort (descending) of n = 2^k keys in shared memory by one warp.
+__device__ __forceinline__ void warp_sort_desc(uint32_t *keys, int n) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 2; k <= n; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < n; i += 32) {
+        const int q = i ^ j;
+        if (q > i) {
+          const uint32_t a = keys[i], b = keys[q];
+          const bool desc = (i & k) == 0;
+          if (desc ? (a < b) : (a > b)) {
+            keys[i] = b;
+            keys[q] = a;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // Each warp works independently: it takes a tile of pixels from the queue
 // and covers it in rounds of 32 / LPP pixels (LPP lanes share one pixel's
-// cones).  No block-wide barrier anywhere.
+// cones).  No block-wide barrier in the work loop.  With one lane per pixel
+// the specular cones of the tile are marched last, longest first: the
+// tile's estimated specular step counts are sorted so that the lanes of a
+// warp march cones of similar length together (the aperture, hence the
+// length, varies from pixel to pixel with the roughness).
 template <int LPP, int DT>
 __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(const __grid_constant__ TraceLaunch L) {
   constexpr int kPixPerRound = 32 / LPP;
+  constexpr bool kSortSpec = (LPP == 1);
   uint32_t n_samp[3] = {0u, 0u, 0u}, n_cone[3] = {0u, 0u, 0u};
   const int lane = threadIdx.x & 31;
   const int slot = lane % LPP;
   const int pr = lane / LPP;
+  const bool defer_spec = kSortSpec && L.spec_enable;
   const int n_cones = L.n_diffuse + L.spec_enable + L.occ_enable;
+  const int first_cone = defer_spec ? 1 : 0;  // the specular cone is cone 0
   const float T0 = (float)L.t0_vox;
   __shared__ uint32_t s_lut[1024];
+  __shared__ uint32_t s_keys[kTraceThreads / 32][kMaxSortPixels];
+  uint32_t *keys = s_keys[threadIdx.x >> 5];
   fill_spread_lut(s_lut);
 
   for (;;) {
@@ -100,7 +144,7 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
         make_apex(P, x, n, L.normal_offset, A);
         float Tf[3], Bf[3];
         tangent_frame(n, Tf, Bf);
-        for (int c = slot; c < n_cones; c += LPP) {
+        for (int c = first_cone + slot; c < n_cones; c += LPP) {
           const ConeSel cs = select_cone(c, L.spec_enable, L.occ_enable);
           float w[3];
           ConeConst cc;
@@ -152,10 +196,48 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
       }
       if (inimg && slot == 0) {
         if (V.outD) reinterpret_cast<float4 *>(V.outD)[p] = D;
-        if (V.outS) reinterpret_cast<float4 *>(V.outS)[p] = S;
+        if (V.outS && !(defer_spec && active)) reinterpret_cast<float4 *>(V.outS)[p] = S;
         if (V.outV) V.outV[p] = has_occ ? vis : 1.0f;
       }
+      if (defer_spec) {
+        // key: valid bit, estimated steps, pixel within the tile
+        keys[pi] = active ? (0x80000000u | (spec_steps_estimate(L, P, V.rough, p) << 8) |
+                             (uint32_t)pi)
+                          : 0u;
+      }
     }
+    if (!defer_spec) continue;
+
+    // Specular cones of the tile, longest first.
+    int nsort = 32;
+    while (nsort < tile_pix) nsort <<= 1;
+    for (int i = tile_pix + lane; i < nsort; i += 32) keys[i] = 0u;
+    __syncwarp();
+    warp_sort_desc(keys, nsort);
+    for (int base = 0; base < tile_pix; base += 32) {
+      const uint32_t key = keys[base + lane];
+      if (!(key & 0x80000000u)) continue;
+      const int pi = (int)(key & 0xffu);
+      const int px = tx0 + pi % L.tile_w;
+      const int py = ty0 + pi / L.tile_w;
+      const int p = py * V.W + px;
+      float x[3], n[3], w[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        x[a] = V.pos[3 * p + a];
+        n[a] = V.nrm[3 * p + a];
+      }
+      Apex A;
+      make_apex(P, x, n, L.normal_offset, A);
+      reflect_dir(x, V.cam, n, w);
+      const ConeConst cc =
+          spec_const(P, L.spec_gmin, L.spec_gmax, L.rough_min, L.beta, L.t0_vox, V.rough, p);
+      float trans;
+      const float4 r = march<DT>(P, A, w, cc, T0, s_lut, n_samp[kSpecular], trans);
+      n_cone[kSpecular] += 1u;
+      if (V.outS) reinterpret_cast<float4 *>(V.outS)[p] = r;
+    }
+    __syncwarp();
   }
   // Per-kind sample and cone counters: one atomic per warp.
 #pragma unroll

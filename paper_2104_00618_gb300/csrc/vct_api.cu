@@ -211,7 +211,7 @@ void fill_view(const vct_view &v, int tile_w, int tile_h, int &tile_cursor, DevV
 
 bool cfg_ok(const vct_launch_config &c) {
   const int lpp = c.lanes_per_pixel;
-  return c.tile_w >= 1 && c.tile_h >= 1 && c.tile_w * c.tile_h <= 4096 &&
+  return c.tile_w >= 1 && c.tile_h >= 1 && c.tile_w * c.tile_h <= kMaxSortPixels &&
          (lpp == 1 || lpp == 2 || lpp == 4 || lpp == 8) && c.ctas_per_sm >= 0 &&
          c.ctas_per_sm <= 32;
 }
@@ -228,7 +228,7 @@ TuneKey tune_key(const vct_pyramid *pyrs, const vct_view *views, const vct_trace
                  views[0].roughness != nullptr);
 }
 
-vct_launch_config default_cfg() { return vct_launch_config{8, 4, 1, 0}; }
+vct_launch_config default_cfg() { return vct_launch_config{16, 16, 1, 0}; }
 
 vct_launch_config pick_cfg(const vct_launch_config *cfg, const vct_pyramid *pyrs,
                            const vct_view *views, const vct_trace_params *P) {

@@ -17,6 +17,7 @@ constexpr int kTraceThreads = 256;      // one CTA shape for every trace kernel
 #endif
 constexpr int kTraceMinBlocks = VCT_TRACE_MIN_BLOCKS;  // register budget: 65536 / (256 * this)
 constexpr int kMaxViewsPerLaunch = 256;  // keeps the forward launch under 32 KB
+constexpr int kMaxSortPixels = 256;      // largest pixel tile of one work item
 constexpr int kMaxBwdViewsPerLaunch = 128;
 constexpr int kMaxSteps = 1 << 16;       // per-cone step cap (parameter check)
 
