@@ -264,6 +264,31 @@ vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
                               float *grad_level0_dense, void *workspace,
                               size_t workspace_bytes, vct_stream_t stream);
 
+/*
+ * vct_trace_backward without a workspace argument, for callers that cannot
+ * allocate device memory (a plugin handed only pre-sized buffers, a host
+ * application whose device heap is partitioned up front, code that must not
+ * touch an allocator it does not own).  The thesis has no counterpart: this
+ * is a packaging variant of the adjoint above, with the same arguments,
+ * results and errors except that the scratch comes from the library.
+ *   - Scratch: a 5 MiB array in the library's device memory, enough for the
+ *     gradient pyramid of any grid up to 64^3.  Every GPU that loads the
+ *     library holds it until the process exits.  Larger pyramids are
+ *     rejected with VCT_ERR_WORKSPACE (and a message naming the limit).
+ *   - Allocation: none (no cudaMalloc/cudaFree or allocating library call).
+ *   - Set-up: the first call on a device looks the array's device address up
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Sharing: every call uses the same array and leaves its contents behind;
+ *     each call clears what must start at zero.  Calls whose GPU work
+ *     overlaps (other streams, other host threads) race on the array.
+ */
+vct_status vct_trace_backward_noalloc(const vct_pyramid *pyr, const vct_view *views,
+                                      const vct_view_grad *grads, int32_t n_views,
+                                      const vct_trace_params *params,
+                                      const vct_launch_config *cfg,
+                                      float *grad_level0_dense, vct_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Diagnostics                                                              */
 /* ------------------------------------------------------------------------ */

@@ -75,6 +75,10 @@ EXPORTS = {
                                     ctypes.POINTER(VctTraceParams),
                                     ctypes.POINTER(VctLaunchConfig), _vp, _vp, ctypes.c_size_t,
                                     _vp]),
+    "vct_trace_backward_noalloc": (_c_i32, [ctypes.POINTER(VctPyramid), ctypes.POINTER(VctView),
+                                            ctypes.POINTER(VctViewGrad), _c_i32,
+                                            ctypes.POINTER(VctTraceParams),
+                                            ctypes.POINTER(VctLaunchConfig), _vp, _vp]),
     "vct_status_string": (ctypes.c_char_p, [_c_i32]),
     "vct_last_error": (ctypes.c_char_p, []),
     "vct_version": (_c_i32, []),

@@ -244,6 +244,18 @@ struct TraceStatsLayout {
 
 }  // namespace
 
+namespace vct {
+vct_status set_last_error(vct_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+}  // namespace vct
+
 extern "C" {
 
 const char *vct_status_string(vct_status s) {

@@ -255,6 +255,9 @@ __host__ __device__ inline ConeConst cone_const(double gamma, double beta, doubl
   return c;
 }
 
+// Records the thread-local message returned by vct_last_error(); returns st.
+vct_status set_last_error(vct_status st, const char *fmt, ...);
+
 // Host entry points implemented in the .cu files (internal linkage across TUs).
 cudaError_t launch_pack_mips(const float *level0, const vct_pyramid &pyr,
                              const CUtensorMap &map, cudaStream_t s);
