@@ -53,55 +53,61 @@ __device__ __forceinline__ void scatter_lane(const BwdLaunch &L, const SmemGrad 
   }
 }
 
-// Scatter of one level for the whole warp (warp-uniform call).  When every
-// active lane uses the same level and the same 2x2x2 cell, the 32 values
-// (8 corners x 4 channels) are summed over the warp by recursive halving so
-// that lane j ends with the total of value j, and each lane issues one atomic
-// on a distinct address; otherwise each lane scatters its own corners.
+// Scatter of one level for the whole warp (warp-uniform call).  Lanes are
+// grouped by (level, 2x2x2 cell).  A lane whose group has fewer than four
+// lanes scatters its own corners.  For each larger group the 32 values
+// (8 corners x 4 channels) are summed over the group by recursive halving,
+// so that lane j ends with the group total of value j, and each lane issues
+// one atomic on a distinct address: contending atomics (the same texel from
+// many lanes) are what makes a naive scatter slow at the coarse levels.
 __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const SmemGrad &sg, bool act,
                                              int l, const LevelStencil &s, float lw,
                                              const float g[4]) {
   const unsigned full = 0xffffffffu;
-  const unsigned actmask = __ballot_sync(full, act);
-  if (actmask == 0u) return;
+  if (__ballot_sync(full, act) == 0u) return;
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(actmask) - 1;
-  const uint32_t key = s.sx[0] | s.sy[0] | s.sz[0];
-  const uint32_t lkey = __shfl_sync(full, key, leader);
-  const uint32_t lvalid = __shfl_sync(full, s.valid, leader);
-  const int ll = __shfl_sync(full, l, leader);
-  const bool uniform = __all_sync(full, !act || (key == lkey && l == ll && s.valid == lvalid));
-  if (!uniform) {
-    if (act) scatter_lane(L, sg, l, s, lw, g);
-    return;
-  }
-  float v[32];
+  const unsigned long long key =
+      act ? ((unsigned long long)(uint32_t)l << 40) | ((unsigned long long)s.valid << 32) |
+                (s.sx[0] | s.sy[0] | s.sz[0])
+          : ~0ull;
+  const unsigned grp = __match_any_sync(full, key);
+  const bool big = act && __popc(grp) >= 4;
+  if (act && !big) scatter_lane(L, sg, l, s, lw, g);
+  unsigned pending = __ballot_sync(full, big);
+  while (pending) {
+    const int leader = __ffs(pending) - 1;
+    const unsigned lgrp = __shfl_sync(full, grp, leader);
+    const bool in = (lgrp >> lane) & 1u;
+    float v[32];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const float w = act ? corner_weight(s, lw, c) : 0.0f;
+    for (int c = 0; c < 8; ++c) {
+      const float w = in ? corner_weight(s, lw, c) : 0.0f;
 #pragma unroll
-    for (int ch = 0; ch < 4; ++ch) v[4 * c + ch] = w * g[ch];
-  }
-#pragma unroll
-  for (int half = 16; half >= 1; half >>= 1) {
-    const bool upper = (lane & half) != 0;
-#pragma unroll
-    for (int i = 0; i < half; ++i) {
-      const float send = upper ? v[i] : v[i + half];
-      const float keep = upper ? v[i + half] : v[i];
-      v[i] = keep + __shfl_xor_sync(full, send, half);
+      for (int ch = 0; ch < 4; ++ch) v[4 * c + ch] = w * g[ch];
     }
+#pragma unroll
+    for (int half = 16; half >= 1; half >>= 1) {
+      const bool upper = (lane & half) != 0;
+#pragma unroll
+      for (int i = 0; i < half; ++i) {
+        const float send = upper ? v[i] : v[i + half];
+        const float keep = upper ? v[i + half] : v[i];
+        v[i] = keep + __shfl_xor_sync(full, send, half);
+      }
+    }
+    // Lane j holds the group total of corner j / 4, channel j % 4.  The cell
+    // is the leader's: take its spread coordinates (a shuffle returns the
+    // source lane's value, so per-corner choices are made afterwards).
+    const int c = lane >> 2, ch = lane & 3;
+    const int ll = __shfl_sync(full, l, leader);
+    const uint32_t lvalid = __shfl_sync(full, s.valid, leader);
+    const uint32_t sx0 = __shfl_sync(full, s.sx[0], leader), sx1 = __shfl_sync(full, s.sx[1], leader);
+    const uint32_t sy0 = __shfl_sync(full, s.sy[0], leader), sy1 = __shfl_sync(full, s.sy[1], leader);
+    const uint32_t sz0 = __shfl_sync(full, s.sz[0], leader), sz1 = __shfl_sync(full, s.sz[1], leader);
+    const uint32_t idx = ((c & 1) ? sx1 : sx0) | (((c >> 1) & 1) ? sy1 : sy0) | ((c >> 2) ? sz1 : sz0);
+    if (((lvalid >> c) & 1u) && v[0] != 0.0f) atomicAdd(grad_texel(L, sg, ll, idx) + ch, v[0]);
+    pending &= ~lgrp;
   }
-  // Lane j holds the warp total of corner j / 4, channel j % 4.  The cell is
-  // the leader's: take its spread coordinates and form corner j / 4 here.
-  const int c = lane >> 2, ch = lane & 3;
-  // (A shuffle returns the source lane's value of the expression, so every
-  // per-corner choice is made here, after the shuffles.)
-  const uint32_t sx0 = __shfl_sync(full, s.sx[0], leader), sx1 = __shfl_sync(full, s.sx[1], leader);
-  const uint32_t sy0 = __shfl_sync(full, s.sy[0], leader), sy1 = __shfl_sync(full, s.sy[1], leader);
-  const uint32_t sz0 = __shfl_sync(full, s.sz[0], leader), sz1 = __shfl_sync(full, s.sz[1], leader);
-  const uint32_t idx = ((c & 1) ? sx1 : sx0) | (((c >> 1) & 1) ? sy1 : sy0) | ((c >> 2) ? sz1 : sz0);
-  if (((lvalid >> c) & 1u) && v[0] != 0.0f) atomicAdd(grad_texel(L, sg, ll, idx) + ch, v[0]);
 }
 
 // Adjoint of one cone for every lane of the warp (warp-uniform call; lanes
@@ -175,7 +181,7 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const SmemGrad 
 }
 
 template <int LPP>
-__global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __grid_constant__ BwdLaunch L) {
+__global__ void __launch_bounds__(kTraceThreads, 3) trace_bwd_kernel(const __grid_constant__ BwdLaunch L) {
   constexpr int kPixPerRound = 32 / LPP;
   const int lane = threadIdx.x & 31;
   const int slot = lane % LPP;
