@@ -28,7 +28,7 @@ class OrcParams(ctypes.Structure):
         ("n_diffuse", ctypes.c_int32),
         ("spec_enable", ctypes.c_int32),
         ("occ_enable", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
         ("diffuse_dir", (ctypes.c_double * 3) * MAX_DIFFUSE),
         ("diffuse_weight", ctypes.c_double * MAX_DIFFUSE),
         ("diffuse_aperture", ctypes.c_double),
@@ -41,7 +41,18 @@ class OrcParams(ctypes.Structure):
         ("t0_voxels", ctypes.c_double),
         ("normal_offset_voxels", ctypes.c_double),
         ("t_max", ctypes.c_double),
+        ("shadow_str", ctypes.c_double),
+        ("occ_max_dist", ctypes.c_double),
+        ("shininess", ctypes.c_double),
+        ("shininess_falloff", ctypes.c_double),
+        ("diffuse_str", ctypes.c_double),
+        ("specular_str", ctypes.c_double),
+        ("light_color", ctypes.c_double * 3),
     ]
+
+
+# variant flags (same bit values as the library's, an input convention)
+OCC_SMOOTH, SPEC_GRACE, DIFF_FIRST, SHADE, SHADE_IMPL = 1, 2, 4, 8, 16
 
 
 class OrcView(ctypes.Structure):
@@ -52,6 +63,7 @@ class OrcView(ctypes.Structure):
         ("normal", ctypes.c_void_p),
         ("roughness", ctypes.c_void_p),
         ("mask", ctypes.c_void_p),
+        ("albedo", ctypes.c_void_p),
         ("camera", ctypes.c_double * 3),
     ]
 
@@ -98,12 +110,14 @@ def load_library(path: str):
     lib.orc_mip_adjoint.argtypes = [vp, i32, i32, vp]
     lib.orc_sample.argtypes = [vp, i32, i32, vp, dbl, vp, dbl, vp]
     lib.orc_sample_lod.argtypes = [vp, i32, i32, vp, dbl, vp]
-    lib.orc_trace_cone.argtypes = [vp, i32, i32, vp, dbl, vp, vp, dbl, vp, vp, vp]
+    lib.orc_trace_cone.argtypes = [vp, i32, i32, vp, dbl, vp, vp, dbl, vp, i32, vp, vp]
+    lib.orc_spec_grace.argtypes = [vp, vp]
+    lib.orc_spec_grace.restype = dbl
     lib.orc_tangent_frame.argtypes = [vp, vp, vp]
     lib.orc_cone_set.argtypes = [vp, dbl, i32, vp, i64, vp, vp, vp, vp, vp, vp]
     lib.orc_cone_set.restype = i32
     lib.orc_trace.argtypes = [vp, i32, i32, vp, dbl, vp, vp, vp, i64, vp, vp,
-                              vp, vp, vp, vp]
+                              vp, vp, vp, vp, vp, vp]
     lib.orc_trace_backward.argtypes = [vp, i32, i32, vp, dbl, vp, vp, vp, i64,
                                        vp, vp, vp, vp, vp]
     for f in ("orc_build_mips", "orc_mip_adjoint", "orc_sample", "orc_sample_lod",
@@ -238,19 +252,36 @@ def params_struct(prm: dict) -> OrcParams:
     P.t0_voxels = float(prm["t0_voxels"])
     P.normal_offset_voxels = float(prm["normal_offset_voxels"])
     P.t_max = float(prm["t_max"])
+    P.flags = int(prm.get("flags", 0))
+    P.shadow_str = float(prm.get("shadow_str", 1.0))
+    P.occ_max_dist = float(prm.get("occ_max_dist", 1.0))
+    P.shininess = float(prm.get("shininess", 32.0))
+    P.shininess_falloff = float(prm.get("shininess_falloff", 1.0))
+    P.diffuse_str = float(prm.get("diffuse_str", 1.0))
+    P.specular_str = float(prm.get("specular_str", 1.0))
+    lc = np.asarray(prm.get("light_color", (1.0, 1.0, 1.0)), dtype=np.float64).reshape(3)
+    for a in range(3):
+        P.light_color[a] = float(lc[a])
     return P
 
 
-def trace_cone(pyr: Pyramid, apex, direction, aperture: float, prm: dict):
-    """One cone; returns (rgba, number of samples)."""
+def trace_cone(pyr: Pyramid, apex, direction, aperture: float, prm: dict, kind: int = -1):
+    """One cone; returns (rgba, number of samples).  kind (0 diffuse, 1
+    specular, 2 occlusion) selects the variant enabled by prm["flags"]."""
     P = params_struct(prm)
     out = np.zeros(4)
     steps = np.zeros(1, dtype=np.int64)
     apex, direction = _f64(apex), _f64(direction)
     _lib().orc_trace_cone(_p(pyr.data), pyr.n, pyr.levels, _p(pyr.origin), pyr.size,
                           _p(apex), _p(direction), float(aperture),
-                          ctypes.byref(P), _p(out), _p(steps))
+                          ctypes.byref(P), int(kind), _p(out), _p(steps))
     return out, int(steps[0])
+
+
+def spec_grace(direction, prm: dict) -> float:
+    P = params_struct(prm)
+    d = _f64(direction)
+    return float(_lib().orc_spec_grace(_p(d), ctypes.byref(P)))
 
 
 def tangent_frame(nrm):
@@ -289,9 +320,12 @@ def _view_struct(view: dict, keep: list) -> OrcView:
                          np.ascontiguousarray(view["roughness"], dtype=np.float32))
     arrs["mask"] = (None if view.get("mask") is None else
                     np.ascontiguousarray(view["mask"], dtype=np.uint8))
+    arrs["albedo"] = (None if view.get("albedo") is None else
+                      np.ascontiguousarray(view["albedo"], dtype=np.float32))
     keep.extend(a for a in arrs.values() if a is not None)
     V.position, V.normal = _p(arrs["position"]), _p(arrs["normal"])
     V.roughness, V.mask = _p(arrs["roughness"]), _p(arrs["mask"])
+    V.albedo = _p(arrs["albedo"])
     for a in range(3):
         V.camera[a] = float(np.asarray(view["camera"], dtype=np.float64)[a])
     return V
@@ -313,14 +347,20 @@ def trace(pyr: Pyramid, view: dict, prm: dict, idx=None):
     D = np.zeros((count, 4))
     S = np.zeros((count, 4))
     Vis = np.zeros(count)
+    L = np.zeros((count, 4))
     steps = np.zeros(3, dtype=np.int64)
     cones = np.zeros(3, dtype=np.int64)
     margin = np.array([np.inf])
+    hit_margin = np.array([np.inf])
     _lib().orc_trace(_p(pyr.data), pyr.n, pyr.levels, _p(pyr.origin), pyr.size,
                      ctypes.byref(V), ctypes.byref(P), _p(idx_arr), count, _p(D),
-                     _p(S), _p(Vis), _p(steps), _p(cones), _p(margin))
-    return {"D": D, "S": S, "Vis": Vis, "steps": steps, "cones": cones,
-            "margin": float(margin[0])}
+                     _p(S), _p(Vis), _p(L), _p(steps), _p(cones), _p(margin),
+                     _p(hit_margin))
+    out = {"D": D, "S": S, "Vis": Vis, "steps": steps, "cones": cones,
+           "margin": float(margin[0]), "hit_margin": float(hit_margin[0])}
+    if P.flags & SHADE:
+        out["L"] = L
+    return out
 
 
 def trace_backward(pyr: Pyramid, view: dict, prm: dict, gD, gS, gV, idx=None):

@@ -56,11 +56,19 @@
 
 #define ORC_MAX_DIFFUSE 32
 
+/* Variant flags (Ch. 5.4.4, the thesis's modified cones; and the shading
+ * composition of Ch. 4.2.2 / Ch. 5.4.4). */
+#define ORC_OCC_SMOOTH 1   /* occlusion: a_s * smoothstep(0, max_dist, sqrt(t) shadow_str) */
+#define ORC_SPEC_GRACE 2   /* specular: colour * (1 - max(0, acos(w.l) - p)/pi)^q          */
+#define ORC_DIFF_FIRST 4   /* diffuse: colour of the first sample with opacity > 1/100     */
+#define ORC_SHADE 8        /* write the radiance L_vxct                                     */
+#define ORC_SHADE_IMPL 16  /* ... composed as L_impl instead                                */
+
 typedef struct {
   int32_t n_diffuse;
   int32_t spec_enable;
   int32_t occ_enable;
-  int32_t pad;
+  int32_t flags;
   double diffuse_dir[ORC_MAX_DIFFUSE][3];
   double diffuse_weight[ORC_MAX_DIFFUSE];
   double diffuse_aperture;
@@ -68,6 +76,10 @@ typedef struct {
   double occ_aperture;
   double light_dir[3];
   double beta, t0_voxels, normal_offset_voxels, t_max;
+  double shadow_str, occ_max_dist;       /* modified occlusion cone          */
+  double shininess, shininess_falloff;   /* Phong alpha; angular-grace q     */
+  double diffuse_str, specular_str;      /* material ratios c_d, c_s scales  */
+  double light_color[3];                 /* i_{s,d} = i_{s,g} (RGB)          */
 } orc_params;
 
 /* A pyramid: `levels` dense arrays [z][y][x][4] of doubles, level l has
@@ -86,6 +98,7 @@ typedef struct {
   const float *normal;   /* [H*W*3] */
   const float *roughness; /* [H*W] or NULL */
   const uint8_t *mask;    /* [H*W] or NULL */
+  const float *albedo;    /* [H*W*3] material colour, or NULL (white) */
   double camera[3];
 } orc_view;
 
@@ -255,14 +268,38 @@ typedef struct {
 typedef struct {
   double c[3], alpha;
   int64_t steps;
-  double margin; /* min |t - t_max| / t_max over the tested t values      */
+  double margin;     /* min |t - t_max| / t_max over the tested t values  */
+  double hit_margin; /* min |a_s - 1/100| over first-hit tests (variant)  */
 } orc_cone_result;
 
 /* Marches one cone.  If `rec` is non-NULL the per-step state is stored
  * there (capacity `cap`) for the adjoint. */
+/* GLSL smoothstep: Hermite interpolation between two edges. */
+static double smoothstep(double e0, double e1, double x) {
+  double t = (x - e0) / (e1 - e0);
+  if (t < 0.0) t = 0.0;
+  if (t > 1.0) t = 1.0;
+  return t * t * (3.0 - 2.0 * t);
+}
+
+/* kind: 0 diffuse, 1 specular, 2 occlusion (selects the Ch. 5.4.4 variants
+ * enabled in P->flags). */
+static void march_kind(const orc_grid *g, const double o[3], const double w[3],
+                       double aperture, const orc_params *P, int kind,
+                       orc_cone_result *res, orc_step *rec, int64_t cap);
+
 static void march(const orc_grid *g, const double o[3], const double w[3],
                   double aperture, const orc_params *P, orc_cone_result *res,
                   orc_step *rec, int64_t cap) {
+  march_kind(g, o, w, aperture, P, -1, res, rec, cap);
+}
+
+static void march_kind(const orc_grid *g, const double o[3], const double w[3],
+                       double aperture, const orc_params *P, int kind,
+                       orc_cone_result *res, orc_step *rec, int64_t cap) {
+  const int occ_smooth = kind == 2 && (P->flags & ORC_OCC_SMOOTH);
+  const int first_hit = kind == 0 && (P->flags & ORC_DIFF_FIRST);
+  double hit_margin = INFINITY;
   double h0 = g->size / g->n;
   double tan_half = tan(0.5 * aperture);
   double t = P->t0_voxels * h0;
@@ -281,6 +318,22 @@ static void march(const orc_grid *g, const double o[3], const double w[3],
     stencil(g->n, g->levels, q, log2(d / h0), &st);
     double v[4];
     apply_stencil(g, &st, v);
+    if (first_hit) {
+      /* Ch. 5.4.4 diffuse cone: the first sample whose opacity exceeds
+       * 1/100 ends the trace and its colour is returned. */
+      if (fabs(v[3] - 0.01) < hit_margin) hit_margin = fabs(v[3] - 0.01);
+      if (v[3] > 0.01) {
+        for (int ch = 0; ch < 3; ++ch) c[ch] = v[ch];
+        alpha = 1.0;
+        ++k;
+        break;
+      }
+      t += P->beta * d;
+      ++k;
+      continue;
+    }
+    if (occ_smooth) /* Ch. 5.4.4 occlusion cone: fade near the apex */
+      v[3] *= smoothstep(0.0, P->occ_max_dist, sqrt(t) * P->shadow_str);
     if (rec && k < cap) {
       rec[k].t = t;
       rec[k].a = v[3];
@@ -300,16 +353,18 @@ static void march(const orc_grid *g, const double o[3], const double w[3],
   res->alpha = alpha;
   res->steps = k;
   res->margin = margin;
+  res->hit_margin = hit_margin;
 }
 
-/* Public single-cone entry (scene units). */
+/* Public single-cone entry (scene units); kind selects the Ch. 5.4.4
+ * variant enabled in P->flags (0 diffuse, 1 specular, 2 occlusion, -1 none). */
 void orc_trace_cone(const double *pyr, int n, int levels, const double *origin,
                     double size, const double *apex, const double *dir,
-                    double aperture, const orc_params *P, double *out_rgba,
+                    double aperture, const orc_params *P, int kind, double *out_rgba,
                     int64_t *steps) {
   orc_grid g = {pyr, n, levels, {origin[0], origin[1], origin[2]}, size};
   orc_cone_result r;
-  march(&g, apex, dir, aperture, P, &r, NULL, 0);
+  march_kind(&g, apex, dir, aperture, P, kind, &r, NULL, 0);
   out_rgba[0] = r.c[0];
   out_rgba[1] = r.c[1];
   out_rgba[2] = r.c[2];
@@ -426,17 +481,73 @@ int orc_cone_set(const double *origin, double size, int n, const orc_view *v,
  * steps[3] accumulates the number of samples per cone kind, cones[3] the
  * number of cones, margin receives min |t - t_max| / t_max.
  */
+/* Ch. 5.4.4 specular BRDF with angular grace p = 0.008 pi shininess:
+ * (1 - max(0, acos(w . l) - p) / pi)^q, q = shininess_falloff, w the cone
+ * axis (mirror direction) and l the direction towards the light. */
+static double spec_grace(const double w[3], const orc_params *P) {
+  double wl = w[0] * P->light_dir[0] + w[1] * P->light_dir[1] + w[2] * P->light_dir[2];
+  double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  double ln = sqrt(P->light_dir[0] * P->light_dir[0] + P->light_dir[1] * P->light_dir[1] +
+                   P->light_dir[2] * P->light_dir[2]);
+  double cosg = wl / (wn * ln);
+  if (cosg > 1.0) cosg = 1.0;
+  if (cosg < -1.0) cosg = -1.0;
+  const double pi = 3.14159265358979323846;
+  double gn = acos(cosg) - 0.008 * pi * P->shininess;
+  if (gn < 0.0) gn = 0.0;
+  return pow(1.0 - gn / pi, P->shininess_falloff);
+}
+
+double orc_spec_grace(const double *w, const orc_params *P) { return spec_grace(w, P); }
+
+/* Shading epilogue.  Direct light of the Phong model as in the thesis's
+ * GLSL listing (Ch. 3.3) for one directional light: diffuse max(n.l, 0),
+ * glossy max(w.R, 0)^shininess with R = reflect(-l, n) and w towards the
+ * viewer, both times the light colour and the material colour.  L_vxct
+ * (Ch. 4.2.2) replaces the ambient term by the indirect light:
+ *   L = albedo (c_d D + c_s S) + Vis direct;
+ * L_impl (Ch. 5.4.4): L = o_min D + S + Vis direct (o_min = Vis, one light). */
+static void shade(const orc_view *v, size_t px, const orc_params *P, const double *D,
+                  const double *S, double vis, double *out) {
+  double x[3], n[3], alb[3] = {1.0, 1.0, 1.0};
+  for (int a = 0; a < 3; ++a) {
+    x[a] = v->position[3 * px + a];
+    n[a] = v->normal[3 * px + a];
+    if (v->albedo) alb[a] = v->albedo[3 * px + a];
+  }
+  const double *l = P->light_dir;
+  double nl = n[0] * l[0] + n[1] * l[1] + n[2] * l[2];
+  double R[3], w[3];
+  for (int a = 0; a < 3; ++a) {
+    R[a] = -l[a] + 2.0 * nl * n[a];
+    w[a] = v->camera[a] - x[a];
+  }
+  normalize3(w);
+  double wr = w[0] * R[0] + w[1] * R[1] + w[2] * R[2];
+  double diff = nl > 0.0 ? nl : 0.0;
+  double gloss = pow(wr > 0.0 ? wr : 0.0, P->shininess);
+  for (int ch = 0; ch < 3; ++ch) {
+    double direct = P->light_color[ch] * alb[ch] * (P->diffuse_str * diff + P->specular_str * gloss);
+    if (P->flags & ORC_SHADE_IMPL)
+      out[ch] = vis * D[ch] + S[ch] + vis * direct;
+    else
+      out[ch] = alb[ch] * (P->diffuse_str * D[ch] + P->specular_str * S[ch]) + vis * direct;
+  }
+  out[3] = 1.0;
+}
+
 void orc_trace(const double *pyr, int n, int levels, const double *origin,
                double size, const orc_view *v, const orc_params *P,
                const int64_t *idx, int64_t count, double *D, double *S,
-               double *Vis, int64_t *steps, int64_t *cones, double *margin) {
+               double *Vis, double *L, int64_t *steps, int64_t *cones, double *margin,
+               double *hit_margin) {
   orc_grid g = {pyr, n, levels, {origin[0], origin[1], origin[2]}, size};
   int64_t st[3] = {0, 0, 0}, cn[3] = {0, 0, 0};
-  double mg = INFINITY;
+  double mg = INFINITY, hm = INFINITY;
 #pragma omp parallel
   {
     int64_t lst[3] = {0, 0, 0}, lcn[3] = {0, 0, 0};
-    double lmg = INFINITY;
+    double lmg = INFINITY, lhm = INFINITY;
 #pragma omp for schedule(dynamic, 64)
     for (int64_t i = 0; i < count; ++i) {
       size_t px = idx ? (size_t)idx[i] : (size_t)i;
@@ -444,25 +555,30 @@ void orc_trace(const double *pyr, int n, int levels, const double *origin,
       d[0] = d[1] = d[2] = d[3] = 0.0;
       s[0] = s[1] = s[2] = s[3] = 0.0;
       Vis[i] = 1.0;
+      if (L) L[4 * i] = L[4 * i + 1] = L[4 * i + 2] = L[4 * i + 3] = 0.0;
       if (v->mask && !v->mask[px]) continue;
       orc_coneset cs;
       cone_set(&g, v, px, P, &cs);
       for (int c = 0; c < cs.count; ++c) {
         orc_cone_result r;
-        march(&g, cs.apex, cs.dir[c], cs.aperture[c], P, &r, NULL, 0);
+        march_kind(&g, cs.apex, cs.dir[c], cs.aperture[c], P, cs.kind[c], &r, NULL, 0);
         lst[cs.kind[c]] += r.steps;
         lcn[cs.kind[c]] += 1;
         if (r.margin < lmg) lmg = r.margin;
+        if (r.hit_margin < lhm) lhm = r.hit_margin;
         if (cs.kind[c] == 0) {
           for (int ch = 0; ch < 3; ++ch) d[ch] += cs.weight[c] * r.c[ch];
           d[3] += cs.weight[c] * r.alpha;
         } else if (cs.kind[c] == 1) {
-          for (int ch = 0; ch < 3; ++ch) s[ch] = r.c[ch];
+          double f = 1.0;
+          if (P->flags & ORC_SPEC_GRACE) f = spec_grace(cs.dir[c], P);
+          for (int ch = 0; ch < 3; ++ch) s[ch] = f * r.c[ch];
           s[3] = r.alpha;
         } else {
           Vis[i] = 1.0 - r.alpha;
         }
       }
+      if (L && (P->flags & ORC_SHADE)) shade(v, px, P, d, s, Vis[i], L + 4 * i);
     }
 #pragma omp critical
     {
@@ -471,8 +587,10 @@ void orc_trace(const double *pyr, int n, int levels, const double *origin,
         cn[k] += lcn[k];
       }
       if (lmg < mg) mg = lmg;
+      if (lhm < hm) hm = lhm;
     }
   }
+  if (hit_margin && hm < *hit_margin) *hit_margin = hm;
   if (steps)
     for (int k = 0; k < 3; ++k) steps[k] += st[k];
   if (cones)

@@ -7,13 +7,14 @@ namespace vct {
 
 namespace {
 
-// Finds the view whose tile range holds `item` (views sorted by tile_begin).
-template <typename Launch>
-__device__ __forceinline__ int find_view(const Launch &L, int item) {
+// Finds the view whose big-tile (small = false) or small-tile range holds
+// `item` (both ranges increase with the view index).
+__device__ __forceinline__ int find_view(const TraceLaunch &L, int item, bool small) {
   int lo = 0, hi = L.n_views - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (L.views[mid].tile_begin <= item)
+    const int begin = small ? L.views[mid].small_begin : L.views[mid].tile_begin;
+    if (begin <= item)
       lo = mid;
     else
       hi = mid - 1;
@@ -114,18 +115,29 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
   for (;;) {
     const int item = next_item(L.queue);
     if (item >= L.total_tiles) break;
-    const int vi = find_view(L, item);
+    const bool small = item >= L.n_big;
+    const int vi = find_view(L, item, small);
     const DevView &V = L.views[vi];
     const DevPyr &P = L.pyr[V.pyr];
-    const int t = item - V.tile_begin;
-    const int tx0 = (t % V.tiles_x) * L.tile_w;
-    const int ty0 = (t / V.tiles_x) * L.tile_h;
-    const int tile_pix = L.tile_w * L.tile_h;
+    int tile_w, tx0, ty0, tile_pix;
+    if (!small) {
+      const int t = item - V.tile_begin;
+      tile_w = L.tile_w;
+      tx0 = (t % V.tiles_x) * L.tile_w;
+      ty0 = (t / V.tiles_x) * L.tile_h;
+      tile_pix = L.tile_w * L.tile_h;
+    } else {
+      const int t = item - V.small_begin;
+      tile_w = kSmallTileW;
+      tx0 = (t % V.small_tiles_x) * kSmallTileW;
+      ty0 = V.y_split + (t / V.small_tiles_x) * kSmallTileH;
+      tile_pix = kSmallTileW * kSmallTileH;
+    }
 
     for (int base = 0; base < tile_pix; base += kPixPerRound) {
       const int pi = base + pr;
-      const int px = tx0 + pi % L.tile_w;
-      const int py = ty0 + pi / L.tile_w;
+      const int px = tx0 + pi % tile_w;
+      const int py = ty0 + pi / tile_w;
       const bool inimg = pi < tile_pix && px < V.W && py < V.H;
       const int p = py * V.W + px;
       bool active = inimg && (V.mask == nullptr || V.mask[p] != 0);
@@ -218,8 +230,8 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
       const uint32_t key = keys[base + lane];
       if (!(key & 0x80000000u)) continue;
       const int pi = (int)(key & 0xffu);
-      const int px = tx0 + pi % L.tile_w;
-      const int py = ty0 + pi / L.tile_w;
+      const int px = tx0 + pi % tile_w;
+      const int py = ty0 + pi / tile_w;
       const int p = py * V.W + px;
       float x[3], n[3], w[3];
 #pragma unroll

@@ -207,6 +207,35 @@ void fill_view(const vct_view &v, int tile_w, int tile_h, int &tile_cursor, DevV
   d.tiles_x = (v.width + tile_w - 1) / tile_w;
   d.tile_begin = tile_cursor;
   tile_cursor += d.tiles_x * ((v.height + tile_h - 1) / tile_h);
+  d.y_split = v.height;
+  d.small_tiles_x = (v.width + kSmallTileW - 1) / kSmallTileW;
+  d.small_begin = 0;
+}
+
+// Splits the work of a launch into big tiles followed by small tail tiles:
+// the bottom big-tile rows of the last views, about `tail_px` pixels, are
+// re-tiled with kSmallTileW x kSmallTileH tiles.  Returns the item count;
+// big items come first (view by view), then the small ones.
+int assign_tail_tiles(DevView *v, int nv, int tile_w, int tile_h, int64_t tail_px, int &n_big) {
+  for (int i = nv - 1; i >= 0 && tail_px > 0; --i) {
+    const int rows = (v[i].H + tile_h - 1) / tile_h;
+    const int64_t row_px = (int64_t)tile_h * v[i].W;
+    int take = (int)std::min<int64_t>(rows, (tail_px + row_px - 1) / row_px);
+    v[i].y_split = (rows - take) * tile_h;
+    tail_px -= (int64_t)take * row_px;
+  }
+  int cursor = 0;
+  for (int i = 0; i < nv; ++i) {
+    v[i].tile_begin = cursor;
+    cursor += v[i].tiles_x * (v[i].y_split / tile_h);
+  }
+  n_big = cursor;
+  for (int i = 0; i < nv; ++i) {
+    v[i].small_begin = cursor;
+    if (v[i].y_split < v[i].H)
+      cursor += v[i].small_tiles_x * ((v[i].H - v[i].y_split + kSmallTileH - 1) / kSmallTileH);
+  }
+  return cursor;
 }
 
 bool cfg_ok(const vct_launch_config &c) {
@@ -369,10 +398,12 @@ static vct_status trace_impl(const vct_pyramid *pyrs, int32_t n_pyr, const vct_v
     if (mixed)
       return fail(VCT_ERR_UNSUPPORTED, "vct_trace: views of one call must use pyramids of one dtype");
     L->n_views = nv;
-    L->total_tiles = cursor;
+    const int grid = std::max(1, std::min(cursor, per_sm * sms));
+    // about two waves of the launch's warps, in small tiles, at the end
+    const int64_t tail_px = (int64_t)2 * grid * (kTraceThreads / 32) * kSmallTileW * kSmallTileH;
+    L->total_tiles = assign_tail_tiles(L->views, nv, cfg.tile_w, cfg.tile_h, tail_px, L->n_big);
     if (v0 > 0 && (e = cudaMemsetAsync(L->queue, 0, 4, stream)) != cudaSuccess)
       return cuda_fail(e, "vct_trace queue clear");
-    const int grid = std::max(1, std::min(cursor, per_sm * sms));
     e = launch_trace(*L, cfg.lanes_per_pixel, pyrs[views[v0].pyramid].dtype, grid, stream);
     if (e != cudaSuccess) return cuda_fail(e, "vct_trace launch");
   }

@@ -195,11 +195,17 @@ struct DevView {
   const uint8_t *mask;
   float *outD, *outS, *outV;
   float cam[3];
-  int W, H, pyr, tiles_x, tile_begin;
+  int W, H, pyr, tiles_x, tile_begin;  // big tiles cover rows [0, y_split)
+  int y_split, small_tiles_x, small_begin;  // small tiles cover rows [y_split, H)
 };
+
+// Tail tiles: the last pixels of a launch are handed out in small tiles so
+// that warps finish together (forward trace only).
+constexpr int kSmallTileW = 8, kSmallTileH = 4;
 
 struct TraceLaunch {
   int n_views, total_tiles, tile_w, tile_h;
+  int n_big, pad_big;  // items [0, n_big) are big tiles, the rest small tiles
   int n_diffuse, spec_enable, occ_enable, pad0;
   float diffuse_dir[VCT_MAX_DIFFUSE][3];
   float diffuse_weight[VCT_MAX_DIFFUSE];

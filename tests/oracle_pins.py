@@ -462,3 +462,118 @@ def check_gradient_fd():
         an = grad.reshape(-1)[flat]
         assert abs(fd - an) <= 1e-7 * max(1e-3, abs(an)), (flat, fd, an)
     assert np.abs(grad).max() > 1e-3
+
+
+# --------------------------------------------------------------------------
+# the thesis's modified cones (Ch. 5.4.4) and the shading epilogue
+# --------------------------------------------------------------------------
+
+
+def glsl_smoothstep(e0, e1, x):
+    t = min(max((x - e0) / (e1 - e0), 0.0), 1.0)
+    return t * t * (3.0 - 2.0 * t)
+
+
+def check_first_hit_diffuse():
+    """The modified diffuse cone returns the colour of the first sample whose
+    opacity exceeds 1/100 (brute-force sampler on a slab), alpha 1."""
+    n = 16
+    g = np.zeros((n, n, n, 4))
+    g[:, :, 11:, :3] = (0.2, 0.5, 0.7)
+    g[:, :, 11:, 3] = 1.0
+    P = oracle.build_mips(g)
+    lv = bf_levels(g, P.levels)
+    h0 = 1.0 / n
+    prm = base_params(flags=oracle.DIFF_FIRST, beta=0.5, t_max=1.0)
+    apex, w, ap = np.array([0.25, 0.52, 0.47]), np.array([1.0, 0.0, 0.0]), 0.4
+    got, k = oracle.trace_cone(P, apex, w, ap, prm, kind=0)
+    r = 1.0 + 2.0 * 0.5 * math.tan(ap / 2)
+    for kk in range(200):
+        t = h0 * r ** kk
+        v = bf_sample(lv, apex + t * w, math.log2(2 * t * math.tan(ap / 2) / h0))
+        if v[3] > 0.01:
+            break
+    assert k == kk + 1, (k, kk)
+    assert np.allclose(got, [*v[:3], 1.0], rtol=1e-12, atol=1e-15), (got, v)
+    # below the threshold everywhere: nothing is returned
+    g2 = np.full((n, n, n, 4), 0.005)
+    out, _ = oracle.trace_cone(oracle.build_mips(g2), apex, w, ap, prm, kind=0)
+    assert np.all(out == 0.0)
+
+
+def check_smoothstep_occlusion():
+    """Homogeneous medium: alpha = 1 - prod_k (1 - a s(t_k)) with
+    s(t) = smoothstep(0, max_dist, sqrt(t) shadow_str) and t_k = t0 r^k."""
+    n = 64
+    a, ap, beta, t_max, md, st = 0.3, math.radians(25), 0.5, 0.25, 0.8, 1.7
+    g = np.empty((n, n, n, 4))
+    g[..., :3], g[..., 3] = 0.5, a
+    P = oracle.build_mips(g)
+    prm = base_params(flags=oracle.OCC_SMOOTH, beta=beta, t_max=t_max, occ_max_dist=md,
+                      shadow_str=st)
+    out, k = oracle.trace_cone(P, [0.5, 0.5, 0.5], [0.0, 0.6, 0.8], ap, prm, kind=2)
+    r = 1.0 + 2.0 * beta * math.tan(ap / 2)
+    T, kk = 1.0, 0
+    while (1.0 / n) * r ** kk <= t_max:
+        T *= 1.0 - a * glsl_smoothstep(0.0, md, math.sqrt((1.0 / n) * r ** kk) * st)
+        kk += 1
+    assert k == kk
+    assert rel(out[3], 1.0 - T) < 1e-12
+    # the variant is off for the other kinds
+    plain, _ = oracle.trace_cone(P, [0.5, 0.5, 0.5], [0.0, 0.6, 0.8], ap, prm, kind=0)
+    assert rel(plain[3], 1.0 - (1.0 - a) ** kk) < 1e-12
+
+
+def check_spec_grace():
+    """f = (1 - max(0, acos(w.l) - 0.008 pi shininess) / pi)^q."""
+    for theta_deg, shin, q in ((40.0, 10.0, 5.0), (3.0, 20.0, 8.0), (170.0, 0.0, 2.0)):
+        th = math.radians(theta_deg)
+        w = np.array([math.sin(th), math.cos(th), 0.0])
+        prm = base_params(light_dir=np.array([0.0, 1.0, 0.0]), shininess=shin,
+                          shininess_falloff=q)
+        want = (1.0 - max(0.0, th - 0.008 * math.pi * shin) / math.pi) ** q
+        assert abs(oracle.spec_grace(w, prm) - want) < 1e-13
+
+
+def _shade_view(x, nrm, cam, albedo):
+    return {"width": 1, "height": 1, "position": np.asarray(x, np.float32),
+            "normal": np.asarray(nrm, np.float32), "mask": None, "roughness": None,
+            "albedo": np.asarray(albedo, np.float32), "camera": np.asarray(cam, np.float32)}
+
+
+def check_shading_epilogue():
+    """L_vxct and L_impl at one pixel against the Phong terms written out
+    (light (0.6, 0.8, 0): n.l = 0.8, mirror direction (-0.6, 0.8, 0))."""
+    import vct_synth as vs
+    n = 16
+    g = np.zeros((n, n, n, 4))
+    g[:, 12:, :, :3], g[:, 12:, :, 3] = (0.9, 0.4, 0.1), 1.0
+    P = oracle.build_mips(g)
+    dirs, w = vs.cone_table_ring6()
+    x, nrm = np.array([0.5, 0.25, 0.5]), np.array([0.0, 1.0, 0.0])
+    cam = x + 0.3 * np.array([-0.6, 0.8, 0.0]) + np.array([0.0, 0.0, 0.05])
+    alb = np.array([0.3, 0.6, 0.9])
+    light = np.array([0.6, 0.8, 0.0])
+    base = vs.trace_params(dirs, w, math.radians(60), spec_enable=True,
+                           spec_aperture_min=math.radians(15), occ_enable=True, light=light)
+    base.update(diffuse_str=0.7, specular_str=0.4, shininess=12.0,
+                light_color=np.array([1.0, 0.9, 0.8]))
+    view = _shade_view(x, nrm, cam.astype(np.float32), alb)
+    x32 = np.asarray(view["position"], np.float64)
+    c64 = np.asarray(view["camera"], np.float64)
+    l64 = np.asarray(base["light_dir"], np.float64)
+    alb = np.asarray(view["albedo"], np.float64)
+    wv = (c64 - x32) / np.linalg.norm(c64 - x32)
+    R = -l64 + 2.0 * (l64 @ nrm) * nrm
+    gloss = max(wv @ R, 0.0) ** 12.0
+    for flags in (oracle.SHADE, oracle.SHADE | oracle.SHADE_IMPL):
+        prm = dict(base, flags=flags)
+        r = oracle.trace(P, view, prm)
+        D, S, V = r["D"][0], r["S"][0], r["Vis"][0]
+        assert 0.0 < V < 1.0 and S[:3].max() > 0.0
+        direct = np.array([1.0, 0.9, 0.8]) * alb * (0.7 * max(l64 @ nrm, 0.0) + 0.4 * gloss)
+        if flags & oracle.SHADE_IMPL:
+            want = V * D[:3] + S[:3] + V * direct
+        else:
+            want = alb * (0.7 * D[:3] + 0.4 * S[:3]) + V * direct
+        assert np.allclose(r["L"][0, :3], want, rtol=1e-12, atol=1e-15), (flags, r["L"][0], want)

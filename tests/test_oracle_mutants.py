@@ -26,7 +26,7 @@ MUTANTS = {
         "stencil(g->n, g->levels, q, log2(d / g->size), &st);"),
     "reflection sign": ("cs->dir[c][a] = view[a] - 2.0 * vn * nrm[a];",
                         "cs->dir[c][a] = view[a] + 2.0 * vn * nrm[a];"),
-    "step ignores beta": ("t += P->beta * d;", "t += d;"),
+    "step ignores beta": ("alpha += wgt;\n    t += P->beta * d;", "alpha += wgt;\n    t += d;"),
     "mip divides by 4": ("dst[(((size_t)z * np + y) * np + x) * 4 + c] = s / 8.0;",
                          "dst[(((size_t)z * np + y) * np + x) * 4 + c] = s / 4.0;"),
     "level blend swapped": ("s->level_w[0] = 1.0 - f;\n  s->level_w[1] = f;",
@@ -47,6 +47,15 @@ MUTANTS = {
                            "gp[(((size_t)(z / 2) * np + y / 2) * np + x / 2) * 4 + c] / 4.0;"),
     "diffuse weight dropped": ("d[ch] += cs.weight[c] * r.c[ch];", "d[ch] += r.c[ch];"),
     "transmittance not stored": ("rec[k].trans = 1.0 - alpha;", "rec[k].trans = 1.0;"),
+    "first-hit threshold": ("if (v[3] > 0.01) {", "if (v[3] > 0.001) {"),
+    "smoothstep as a ramp": ("return t * t * (3.0 - 2.0 * t);", "return t;"),
+    "angular grace without pi": ("double gn = acos(cosg) - 0.008 * pi * P->shininess;",
+                                 "double gn = acos(cosg) - 0.008 * P->shininess;"),
+    "light reflected the wrong way": ("R[a] = -l[a] + 2.0 * nl * n[a];",
+                                      "R[a] = l[a] - 2.0 * nl * n[a];"),
+    "direct light not occluded": (
+        "out[ch] = alb[ch] * (P->diffuse_str * D[ch] + P->specular_str * S[ch]) + vis * direct;",
+        "out[ch] = alb[ch] * (P->diffuse_str * D[ch] + P->specular_str * S[ch]) + direct;"),
 }
 
 CHECKS = [name for name in dir(pins) if name.startswith("check_")]
