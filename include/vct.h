@@ -131,6 +131,36 @@ vct_status vct_pyramid_status(const vct_pyramid *pyr, vct_stream_t stream);
 /* Cone tracing                                                             */
 /* ------------------------------------------------------------------------ */
 /*
+ * Variant flags (vct_trace_params.flags).  The first three are the thesis's
+ * modified cones (Ch. 5.4.4); the last two add the shading epilogue.
+ *   VCT_FLAG_OCC_SMOOTH       occlusion cone: every sample opacity is scaled
+ *                             by smoothstep(0, occ_max_dist, sqrt(t) *
+ *                             shadow_str), t the distance travelled
+ *   VCT_FLAG_SPEC_GRACE       specular colour times the angular-grace BRDF
+ *                             (1 - max(0, acos(w.l) - p) / pi)^q with
+ *                             p = 0.008 pi shininess, q = shininess_falloff,
+ *                             w the cone axis, l = light_dir
+ *   VCT_FLAG_DIFFUSE_FIRST_HIT diffuse cones stop at the first sample whose
+ *                             opacity exceeds 1/100 and return its colour
+ *                             with alpha 1 (zero if there is none)
+ *   VCT_FLAG_SHADE            write out_radiance: with Phong direct light
+ *                             direct = light_color * albedo * (diffuse_str *
+ *                             max(n.l, 0) + specular_str * max(v.R, 0)^shininess),
+ *                             R = reflect(-l, n), v towards the camera
+ *                             (Ch. 3.3), L = albedo * (diffuse_str * D +
+ *                             specular_str * S) + Vis * direct (Ch. 4.2.2)
+ *   VCT_FLAG_SHADE_IMPL       with VCT_FLAG_SHADE: L = Vis * D + S + Vis *
+ *                             direct instead (the thesis's L_impl, Ch. 5.4.4)
+ * vct_trace_backward accepts only the two shading flags (the adjoint covers
+ * D, S and Vis of the unmodified cones).
+ */
+#define VCT_FLAG_OCC_SMOOTH 1
+#define VCT_FLAG_SPEC_GRACE 2
+#define VCT_FLAG_DIFFUSE_FIRST_HIT 4
+#define VCT_FLAG_SHADE 8
+#define VCT_FLAG_SHADE_IMPL 16
+
+/*
  * Cone set and march parameters (the thesis's VoxSettings, Ch. 5.4.4).
  * Angles are full aperture angles in radians (Ch. 4.2.2, gamma).
  */
@@ -138,7 +168,7 @@ typedef struct {
   int32_t n_diffuse;   /* number of diffuse cones, 0 .. VCT_MAX_DIFFUSE    */
   int32_t spec_enable; /* 1: trace the specular cone                        */
   int32_t occ_enable;  /* 1: trace the occlusion cone towards light_dir     */
-  int32_t flags;       /* reserved, must be 0                               */
+  int32_t flags;       /* VCT_FLAG_* bits                                   */
   /* Diffuse axes in the pixel's tangent frame (T, B, N): the scene
    * direction is T*d[0] + B*d[1] + N*d[2] with N the pixel normal,
    * T = normalize(a x N), B = N x T, a = (1,0,0) if |N.x| < 0.9 else
@@ -156,6 +186,12 @@ typedef struct {
   float t0_voxels;       /* first sample at t0 = t0_voxels * h0, > 0         */
   float normal_offset_voxels; /* apex = x + normal_offset_voxels * h0 * N    */
   float t_max;           /* the march stops once t > t_max (scene units)     */
+  float shadow_str;      /* VCT_FLAG_OCC_SMOOTH strength                     */
+  float occ_max_dist;    /* VCT_FLAG_OCC_SMOOTH upper edge (scene units), > 0 */
+  float shininess;       /* Phong exponent; angular grace p = 0.008 pi this  */
+  float shininess_falloff; /* exponent q of the angular-grace BRDF           */
+  float diffuse_str, specular_str; /* material ratios of the shading        */
+  float light_color[3];  /* RGB intensity of the directional light           */
 } vct_trace_params;
 
 /*
@@ -164,7 +200,7 @@ typedef struct {
  * and Vis = 1.
  */
 typedef struct {
-  int32_t width, height; /* >= 1                                             */
+  int32_t width, height; /* 1 .. 65535                                       */
   int32_t pyramid;       /* index into the pyramids passed with the views    */
   int32_t reserved;      /* must be 0                                        */
   const float *position; /* [H*W*3] surface position, scene units            */
@@ -176,6 +212,8 @@ typedef struct {
   float *out_diffuse;    /* [H*W*4] D = sum_k w_k (rgb_k, alpha_k), or NULL   */
   float *out_specular;   /* [H*W*4] S = (rgb, alpha) of the specular cone     */
   float *out_visibility; /* [H*W] Vis = 1 - alpha of the occlusion cone       */
+  const float *albedo;   /* [H*W*3] material colour for the shading, or NULL (1) */
+  float *out_radiance;   /* [H*W*4] shaded colour (VCT_FLAG_SHADE), or NULL  */
 } vct_view;
 
 /* Launch shape of the trace kernels (see vct_autotune_trace). */

@@ -20,12 +20,14 @@ from dataclasses import dataclass, field
 import torch
 
 from . import _abi
-from ._abi import (VCT_F16, VCT_F32, VctError, VctLaunchConfig, VctPyramid, VctTraceParams,
-                   VctTraceStats, VctView, VctViewGrad, check, load)
+from ._abi import (FLAG_DIFFUSE_FIRST_HIT, FLAG_OCC_SMOOTH, FLAG_SHADE, FLAG_SHADE_IMPL,
+                   FLAG_SPEC_GRACE, VCT_F16, VCT_F32, VctError, VctLaunchConfig, VctPyramid,
+                   VctTraceParams, VctTraceStats, VctView, VctViewGrad, check, load)
 
 __all__ = ["Pyramid", "build_mips", "read_level", "pyramid_status", "make_params", "trace",
            "trace_backward", "autotune", "read_stats", "TraceFn", "render", "VctError",
-           "launch_config", "num_levels", "lib"]
+           "launch_config", "num_levels", "lib", "FLAG_OCC_SMOOTH", "FLAG_SPEC_GRACE",
+           "FLAG_DIFFUSE_FIRST_HIT", "FLAG_SHADE", "FLAG_SHADE_IMPL"]
 
 DTYPES = {"f32": VCT_F32, "f16": VCT_F16, VCT_F32: VCT_F32, VCT_F16: VCT_F16}
 
@@ -137,6 +139,15 @@ def make_params(prm: dict) -> VctTraceParams:
     P.t0_voxels = float(prm["t0_voxels"])
     P.normal_offset_voxels = float(prm["normal_offset_voxels"])
     P.t_max = float(prm["t_max"])
+    P.shadow_str = float(prm.get("shadow_str", 1.0))
+    P.occ_max_dist = float(prm.get("occ_max_dist", 1.0))
+    P.shininess = float(prm.get("shininess", 32.0))
+    P.shininess_falloff = float(prm.get("shininess_falloff", 1.0))
+    P.diffuse_str = float(prm.get("diffuse_str", 1.0))
+    P.specular_str = float(prm.get("specular_str", 1.0))
+    lc = torch.as_tensor(prm.get("light_color", (1.0, 1.0, 1.0)), dtype=torch.float32).reshape(3)
+    for a in range(3):
+        P.light_color[a] = float(lc[a])
     return P
 
 
@@ -154,6 +165,8 @@ class View:
     out_diffuse: torch.Tensor | None = None
     out_specular: torch.Tensor | None = None
     out_visibility: torch.Tensor | None = None
+    albedo: torch.Tensor | None = None
+    out_radiance: torch.Tensor | None = None
     keep: list = field(default_factory=list)
 
     @staticmethod
@@ -169,23 +182,26 @@ class View:
                     tuple(float(c) for c in v["camera"]),
                     dev(v.get("roughness"), torch.float32), dev(v.get("mask"), torch.uint8),
                     int(v.get("pyramid", 0)))
+        view.albedo = dev(v.get("albedo"), torch.float32)
         if outputs:
             view.alloc_outputs()
         return view
 
-    def alloc_outputs(self, diffuse=True, specular=True, visibility=True):
+    def alloc_outputs(self, diffuse=True, specular=True, visibility=True, radiance=False):
         dev = self.position.device
         npx = self.width * self.height
         self.out_diffuse = torch.empty((npx, 4), device=dev) if diffuse else None
         self.out_specular = torch.empty((npx, 4), device=dev) if specular else None
         self.out_visibility = torch.empty((npx,), device=dev) if visibility else None
+        self.out_radiance = torch.empty((npx, 4), device=dev) if radiance else None
         return self
 
     def struct(self) -> VctView:
         return VctView(self.width, self.height, self.pyramid, 0, _ptr(self.position),
                        _ptr(self.normal), _ptr(self.roughness), _ptr(self.mask),
                        (ctypes.c_float * 3)(*self.camera), 0.0, _ptr(self.out_diffuse),
-                       _ptr(self.out_specular), _ptr(self.out_visibility))
+                       _ptr(self.out_specular), _ptr(self.out_visibility), _ptr(self.albedo),
+                       _ptr(self.out_radiance))
 
 
 def _workspace(nbytes: int, device) -> torch.Tensor:
@@ -273,7 +289,7 @@ class TraceFn(torch.autograd.Function):
     def forward(ctx, level0, view: View, params, levels, origin, size):
         pyr = build_mips(level0.detach().contiguous(), levels, "f32", origin, size)
         v = dataclasses.replace(view, keep=[])
-        v.alloc_outputs()
+        v.alloc_outputs()  # no radiance output: the adjoint covers D, S and Vis
         trace(pyr, [v], params)
         ctx.pyr, ctx.view, ctx.params = pyr, v, params
         return v.out_diffuse, v.out_specular, v.out_visibility

@@ -14,6 +14,8 @@ MAX_LEVELS = 11
 VCT_OK, VCT_ERR_INVALID_ARG, VCT_ERR_CUDA, VCT_ERR_WORKSPACE, VCT_ERR_UNSUPPORTED, \
     VCT_ERR_TIMEOUT = range(6)
 VCT_F32, VCT_F16 = 0, 1
+FLAG_OCC_SMOOTH, FLAG_SPEC_GRACE, FLAG_DIFFUSE_FIRST_HIT, FLAG_SHADE, FLAG_SHADE_IMPL = \
+    1, 2, 4, 8, 16
 
 _c_i32, _c_u64, _c_f32, _vp = ctypes.c_int32, ctypes.c_uint64, ctypes.c_float, ctypes.c_void_p
 
@@ -32,14 +34,18 @@ class VctTraceParams(ctypes.Structure):
                 ("spec_aperture_min", _c_f32), ("spec_aperture_max", _c_f32),
                 ("roughness_min", _c_f32), ("occ_aperture", _c_f32),
                 ("light_dir", _c_f32 * 3), ("beta", _c_f32), ("t0_voxels", _c_f32),
-                ("normal_offset_voxels", _c_f32), ("t_max", _c_f32)]
+                ("normal_offset_voxels", _c_f32), ("t_max", _c_f32),
+                ("shadow_str", _c_f32), ("occ_max_dist", _c_f32), ("shininess", _c_f32),
+                ("shininess_falloff", _c_f32), ("diffuse_str", _c_f32),
+                ("specular_str", _c_f32), ("light_color", _c_f32 * 3)]
 
 
 class VctView(ctypes.Structure):
     _fields_ = [("width", _c_i32), ("height", _c_i32), ("pyramid", _c_i32), ("reserved", _c_i32),
                 ("position", _vp), ("normal", _vp), ("roughness", _vp), ("mask", _vp),
                 ("camera", _c_f32 * 3), ("pad", _c_f32),
-                ("out_diffuse", _vp), ("out_specular", _vp), ("out_visibility", _vp)]
+                ("out_diffuse", _vp), ("out_specular", _vp), ("out_visibility", _vp),
+                ("albedo", _vp), ("out_radiance", _vp)]
 
 
 class VctLaunchConfig(ctypes.Structure):

@@ -22,16 +22,29 @@ __device__ __forceinline__ int find_view(const TraceLaunch &L, int item, bool sm
   return lo;
 }
 
+// Cone march variants (Ch. 5.4.4): the plain march, the occlusion cone that
+// fades its samples near the apex, and the diffuse cone that stops at the
+// first sample with opacity above 1/100.
+enum MarchMode { kPlain = 0, kOccSmooth = 1, kFirstHit = 2 };
+
+// GLSL smoothstep(0, e1, x).
+__device__ __forceinline__ float smoothstep0(float e1, float x) {
+  const float u = fminf(fmaxf(x / e1, 0.0f), 1.0f);
+  return u * u * (3.0f - 2.0f * u);
+}
+
 // One cone: returns (rgb, alpha) and, in `trans`, the transmittance
 // T = prod_k (1 - a_k).  The thesis's accumulation (Ch. 4.3.2) is evaluated as
 //   c += T_k a_k c_k,  alpha += T_k a_k,  T_{k+1} = T_k (1 - a_k)
 // (alpha_k = 1 - T_k: the same recurrence), which keeps alpha precise when it
 // is small and T precise when alpha is close to one; the loop runs while
-// alpha = 1 - T < 1 in float32 and t <= t_max.
-template <int DT>
+// alpha = 1 - T < 1 in float32 and t <= t_max.  kVar instances also take the
+// Ch. 5.4.4 variants selected by `mode`.
+template <int DT, bool kVar>
 __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const float w[3],
                                         const ConeConst &cc, float T0, const uint32_t *lut,
-                                        uint32_t &nsamp, float &trans) {
+                                        uint32_t &nsamp, float &trans, int mode = kPlain,
+                                        const Variants *var = nullptr) {
   float cr = 0.f, cg = 0.f, cb = 0.f, al = 0.f, tr = 1.f;
   int k = 0;
   for (; k < cc.kmax; ++k) {
@@ -40,7 +53,22 @@ __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const fl
     step_at(cc, T0, k, T, lam);
     const float F[3] = {fmaf(T, w[0], A.Of[0]), fmaf(T, w[1], A.Of[1]), fmaf(T, w[2], A.Of[2])};
     LodPick lp;
-    const float4 s = sample<DT>(P, A, F, lam, lut, om, lp);
+    float4 s = sample<DT>(P, A, F, lam, lut, om, lp);
+    if constexpr (kVar) {
+      if (mode == kFirstHit) {
+        if (s.w > 0.01f) {
+          nsamp += (uint32_t)(k + 1);
+          trans = 0.0f;
+          return make_float4(s.x, s.y, s.z, 1.0f);
+        }
+        continue;
+      }
+      if (mode == kOccSmooth) {
+        // t = T h0 in scene units
+        s.w *= smoothstep0(var->occ_max_dist, sqrtf(T * P.h0) * var->shadow_str);
+        om = transparency(s.w);
+      }
+    }
     const float wg = tr * s.w;  // front-to-back weight T_k a_s
     cr = fmaf(wg, s.x, cr);
     cg = fmaf(wg, s.y, cg);
@@ -51,6 +79,74 @@ __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const fl
   nsamp += (uint32_t)k;
   trans = tr;
   return make_float4(cr, cg, cb, al);
+}
+
+// Angular-grace specular BRDF (Ch. 5.4.4): (1 - max(0, g - p) / pi)^q with g
+// the angle between the cone axis w and the light direction, taken as
+// atan2(|w x l|, w . l) (well conditioned at every angle).
+__device__ __forceinline__ float spec_grace(const Variants &v, const float w[3]) {
+  const float *l = v.light_dir;
+  const float cx = w[1] * l[2] - w[2] * l[1];
+  const float cy = w[2] * l[0] - w[0] * l[2];
+  const float cz = w[0] * l[1] - w[1] * l[0];
+  const float d = w[0] * l[0] + w[1] * l[1] + w[2] * l[2];
+  const float g = atan2f(sqrtf(cx * cx + cy * cy + cz * cz), d);
+  const float e = fmaxf(g - v.grace, 0.0f);
+  return powf(1.0f - e * 0.318309886f, v.falloff);
+}
+
+// Shading epilogue, split in the part without the specular cone (`first`)
+// and its specular term (`spec`), so that a deferred specular cone adds its
+// term later.  Direct light: Phong with one directional light (Ch. 3.3)
+//   direct = light_color * albedo * (kd max(n.l, 0) + ks max(v.R, 0)^shininess)
+// L_vxct (Ch. 4.2.2): L = albedo (kd D + ks S) + Vis direct
+// L_impl (Ch. 5.4.4): L = Vis D + S + Vis direct.
+__device__ __forceinline__ float4 shade_first(const Variants &v, const DevView &V, int p,
+                                              const float4 &D, float vis) {
+  float x[3], n[3], alb[3] = {1.0f, 1.0f, 1.0f};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    x[a] = V.pos[3 * p + a];
+    n[a] = V.nrm[3 * p + a];
+    if (V.albedo) alb[a] = V.albedo[3 * p + a];
+  }
+  const float *l = v.light_dir;
+  const float nl = n[0] * l[0] + n[1] * l[1] + n[2] * l[2];
+  float R[3], e[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R[a] = fmaf(2.0f * nl, n[a], -l[a]);
+    e[a] = V.cam[a] - x[a];
+  }
+  const float inv = rsqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+  const float wr = (e[0] * R[0] + e[1] * R[1] + e[2] * R[2]) * inv;
+  const float lobe = v.kd * fmaxf(nl, 0.0f) + v.ks * powf(fmaxf(wr, 0.0f), v.shininess);
+  const bool impl = (v.flags & VCT_FLAG_SHADE_IMPL) != 0;
+  const float Dc[3] = {D.x, D.y, D.z};
+  float o[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float direct = v.light_color[a] * alb[a] * lobe;
+    o[a] = impl ? vis * (Dc[a] + direct) : fmaf(alb[a] * v.kd, Dc[a], vis * direct);
+  }
+  return make_float4(o[0], o[1], o[2], 1.0f);
+}
+
+__device__ __forceinline__ float4 shade_spec(const Variants &v, const DevView &V, int p,
+                                             const float4 &S, float4 L) {
+  if (v.flags & VCT_FLAG_SHADE_IMPL) {
+    L.x += S.x;
+    L.y += S.y;
+    L.z += S.z;
+  } else {
+    const float a0 = V.albedo ? V.albedo[3 * p] : 1.0f;
+    const float a1 = V.albedo ? V.albedo[3 * p + 1] : 1.0f;
+    const float a2 = V.albedo ? V.albedo[3 * p + 2] : 1.0f;
+    L.x = fmaf(a0 * v.ks, S.x, L.x);
+    L.y = fmaf(a1 * v.ks, S.y, L.y);
+    L.z = fmaf(a2 * v.ks, S.z, L.z);
+  }
+  return L;
 }
 
 // Estimated step count of the specular cone (sort key only; float32).
@@ -95,7 +191,9 @@ __device__ __forceinline__ void warp_sort_desc(uint32_t *keys, int n) {
 // tile's estimated specular step counts are sorted so that the lanes of a
 // warp march cones of similar length together (the aperture, hence the
 // length, varies from pixel to pixel with the roughness).
-template <int LPP, int DT>
+// kVar instances add the Ch. 5.4.4 cone variants and the shading epilogue
+// (any VCT_FLAG_* set); the plain instances carry none of that code.
+template <int LPP, int DT, bool kVar>
 __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(const __grid_constant__ TraceLaunch L) {
   constexpr int kPixPerRound = 32 / LPP;
   constexpr bool kSortSpec = (LPP == 1);
@@ -176,8 +274,21 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
             cc = P.diffuse;
           }
           float trans;
-          const float4 r = march<DT>(P, A, w, cc, T0, s_lut, n_samp[cs.kind], trans);
+          int mode = kPlain;
+          if constexpr (kVar) {
+            if (cs.kind == kOcclusion && (L.var.flags & VCT_FLAG_OCC_SMOOTH)) mode = kOccSmooth;
+            if (cs.kind == kDiffuse && (L.var.flags & VCT_FLAG_DIFFUSE_FIRST_HIT)) mode = kFirstHit;
+          }
+          float4 r = march<DT, kVar>(P, A, w, cc, T0, s_lut, n_samp[cs.kind], trans, mode, &L.var);
           n_cone[cs.kind] += 1u;
+          if constexpr (kVar) {
+            if (cs.kind == kSpecular && (L.var.flags & VCT_FLAG_SPEC_GRACE)) {
+              const float f = spec_grace(L.var, w);
+              r.x *= f;
+              r.y *= f;
+              r.z *= f;
+            }
+          }
           if (cs.kind == kDiffuse) {
             const float wt = L.diffuse_weight[cs.diffuse_index];
             D.x = fmaf(wt, r.x, D.x);
@@ -210,6 +321,16 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
         if (V.outD) reinterpret_cast<float4 *>(V.outD)[p] = D;
         if (V.outS && !(defer_spec && active)) reinterpret_cast<float4 *>(V.outS)[p] = S;
         if (V.outV) V.outV[p] = has_occ ? vis : 1.0f;
+        if constexpr (kVar) {
+          if (V.outL) {
+            float4 Lp = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (active) {
+              Lp = shade_first(L.var, V, p, D, has_occ ? vis : 1.0f);
+              if (!defer_spec) Lp = shade_spec(L.var, V, p, S, Lp);
+            }
+            reinterpret_cast<float4 *>(V.outL)[p] = Lp;
+          }
+        }
       }
       if (defer_spec) {
         // key: valid bit, estimated steps, pixel within the tile
@@ -245,8 +366,22 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
       const ConeConst cc =
           spec_const(P, L.spec_gmin, L.spec_gmax, L.rough_min, L.beta, L.t0_vox, V.rough, p);
       float trans;
-      const float4 r = march<DT>(P, A, w, cc, T0, s_lut, n_samp[kSpecular], trans);
+      float4 r = march<DT, false>(P, A, w, cc, T0, s_lut, n_samp[kSpecular], trans);
       n_cone[kSpecular] += 1u;
+      if constexpr (kVar) {
+        if (L.var.flags & VCT_FLAG_SPEC_GRACE) {
+          const float f = spec_grace(L.var, w);
+          r.x *= f;
+          r.y *= f;
+          r.z *= f;
+        }
+        // The first part of the pixel's radiance was written by another lane
+        // of this warp before the __syncwarp that precedes the sort.
+        if (V.outL) {
+          float4 *q = reinterpret_cast<float4 *>(V.outL) + p;
+          *q = shade_spec(L.var, V, p, r, *q);
+        }
+      }
       if (V.outS) reinterpret_cast<float4 *>(V.outS)[p] = r;
     }
     __syncwarp();
@@ -265,14 +400,22 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
 
 template <int LPP, int DT>
 cudaError_t launch_t(const TraceLaunch &L, int grid, cudaStream_t s) {
-  trace_kernel<LPP, DT><<<grid, kTraceThreads, 0, s>>>(L);
+  if (L.var.flags)
+    trace_kernel<LPP, DT, true><<<grid, kTraceThreads, 0, s>>>(L);
+  else
+    trace_kernel<LPP, DT, false><<<grid, kTraceThreads, 0, s>>>(L);
   return cudaGetLastError();
 }
 
 template <int LPP, int DT>
-int occ_t() {
+int occ_t(bool var) {
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<LPP, DT>, kTraceThreads, 0);
+  if (var)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<LPP, DT, true>, kTraceThreads,
+                                                  0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<LPP, DT, false>, kTraceThreads,
+                                                  0);
   return b;
 }
 
@@ -291,13 +434,13 @@ cudaError_t launch_trace(const TraceLaunch &L, int lpp, int dtype, int grid, cud
   }
 }
 
-int trace_occupancy(int lpp, int dtype) {
+int trace_occupancy(int lpp, int dtype, bool var) {
   const bool h = dtype == VCT_F16;
   switch (lpp) {
-    case 1: return h ? occ_t<1, VCT_F16>() : occ_t<1, VCT_F32>();
-    case 2: return h ? occ_t<2, VCT_F16>() : occ_t<2, VCT_F32>();
-    case 4: return h ? occ_t<4, VCT_F16>() : occ_t<4, VCT_F32>();
-    case 8: return h ? occ_t<8, VCT_F16>() : occ_t<8, VCT_F32>();
+    case 1: return h ? occ_t<1, VCT_F16>(var) : occ_t<1, VCT_F32>(var);
+    case 2: return h ? occ_t<2, VCT_F16>(var) : occ_t<2, VCT_F32>(var);
+    case 4: return h ? occ_t<4, VCT_F16>(var) : occ_t<4, VCT_F32>(var);
+    case 8: return h ? occ_t<8, VCT_F16>(var) : occ_t<8, VCT_F32>(var);
     default: return 0;
   }
 }

@@ -92,14 +92,44 @@ constexpr double kPi = 3.14159265358979323846;
 
 bool aperture_ok(float g) { return finite(g) && g > 0.0f && g < (float)kPi; }
 
-vct_status check_params(const vct_trace_params *P) {
+constexpr int kFlagsAll = VCT_FLAG_OCC_SMOOTH | VCT_FLAG_SPEC_GRACE | VCT_FLAG_DIFFUSE_FIRST_HIT |
+                          VCT_FLAG_SHADE | VCT_FLAG_SHADE_IMPL;
+constexpr int kFlagsCone = VCT_FLAG_OCC_SMOOTH | VCT_FLAG_SPEC_GRACE | VCT_FLAG_DIFFUSE_FIRST_HIT;
+
+// `backward`: the adjoint covers the unmodified cones only.
+vct_status check_params(const vct_trace_params *P, bool backward) {
   if (!P) return fail(VCT_ERR_INVALID_ARG, "params: NULL");
   if (P->n_diffuse < 0 || P->n_diffuse > VCT_MAX_DIFFUSE)
     return fail(VCT_ERR_INVALID_ARG, "params: n_diffuse %d out of [0, %d]", P->n_diffuse,
                 VCT_MAX_DIFFUSE);
   if ((P->spec_enable != 0 && P->spec_enable != 1) || (P->occ_enable != 0 && P->occ_enable != 1))
     return fail(VCT_ERR_INVALID_ARG, "params: spec_enable/occ_enable must be 0 or 1");
-  if (P->flags != 0) return fail(VCT_ERR_UNSUPPORTED, "params: flags %d not supported", P->flags);
+  if (P->flags & ~kFlagsAll) return fail(VCT_ERR_INVALID_ARG, "params: unknown flags 0x%x", P->flags);
+  if ((P->flags & VCT_FLAG_SHADE_IMPL) && !(P->flags & VCT_FLAG_SHADE))
+    return fail(VCT_ERR_INVALID_ARG, "params: VCT_FLAG_SHADE_IMPL needs VCT_FLAG_SHADE");
+  if (backward && (P->flags & kFlagsCone))
+    return fail(VCT_ERR_UNSUPPORTED,
+                "params: the adjoint does not cover the modified cones (flags 0x%x)",
+                P->flags & kFlagsCone);
+  if ((P->flags & VCT_FLAG_OCC_SMOOTH) &&
+      (!finite(P->shadow_str) || !(P->occ_max_dist > 0.0f) || !finite(P->occ_max_dist)))
+    return fail(VCT_ERR_INVALID_ARG, "params: shadow_str must be finite and occ_max_dist > 0");
+  if ((P->flags & (VCT_FLAG_SPEC_GRACE | VCT_FLAG_SHADE)) &&
+      (!finite(P->shininess) || P->shininess < 0.0f))
+    return fail(VCT_ERR_INVALID_ARG, "params: shininess must be finite and >= 0");
+  if ((P->flags & VCT_FLAG_SPEC_GRACE) &&
+      (!finite(P->shininess_falloff) || P->shininess_falloff < 0.0f))
+    return fail(VCT_ERR_INVALID_ARG, "params: shininess_falloff must be finite and >= 0");
+  if ((P->flags & VCT_FLAG_SHADE) &&
+      (!finite(P->diffuse_str) || !finite(P->specular_str) || !finite(P->light_color[0]) ||
+       !finite(P->light_color[1]) || !finite(P->light_color[2])))
+    return fail(VCT_ERR_INVALID_ARG, "params: shading strengths and light_color must be finite");
+  if (P->flags & (VCT_FLAG_SPEC_GRACE | VCT_FLAG_SHADE)) {
+    const float l2 = P->light_dir[0] * P->light_dir[0] + P->light_dir[1] * P->light_dir[1] +
+                     P->light_dir[2] * P->light_dir[2];
+    if (!finite(l2) || !(l2 > 0.0f))
+      return fail(VCT_ERR_INVALID_ARG, "params: light_dir must be finite and non-zero");
+  }
   if (P->n_diffuse > 0 && !aperture_ok(P->diffuse_aperture))
     return fail(VCT_ERR_INVALID_ARG, "params: diffuse_aperture must be in (0, pi)");
   for (int k = 0; k < P->n_diffuse; ++k)
@@ -135,6 +165,7 @@ vct_status fill_pyr(const vct_pyramid &p, const vct_trace_params &P, DevPyr &d) 
   d.n = p.n;
   d.levels = p.levels;
   d.dtype = p.dtype;
+  d.h0 = (float)((double)p.size / (double)p.n);
   const double beta = P.beta, t0 = P.t0_voxels;
   auto mk = [&](float g, ConeConst &c, const char *name) -> vct_status {
     c = cone_const((double)g, beta, t0, d.tmax_vox);
@@ -172,8 +203,27 @@ void fill_common(const vct_trace_params &P, LaunchT &L) {
   L.t0_vox = P.t0_voxels;
 }
 
-vct_status check_view(const vct_view &v, int i, int n_pyr, bool need_outputs) {
-  if (v.width < 1 || v.height < 1 || (int64_t)v.width * v.height > (int64_t)1 << 29)
+void fill_variants(const vct_trace_params &P, Variants &v) {
+  v.flags = P.flags;
+  v.shadow_str = P.shadow_str;
+  v.occ_max_dist = P.occ_max_dist;
+  v.grace = (float)(0.008 * kPi * (double)P.shininess);
+  v.falloff = P.shininess_falloff;
+  v.shininess = P.shininess;
+  v.kd = P.diffuse_str;
+  v.ks = P.specular_str;
+  for (int a = 0; a < 3; ++a) {
+    v.light_color[a] = P.light_color[a];
+    v.light_dir[a] = P.light_dir[a];
+  }
+}
+
+// `flags`: the VCT_FLAG_* bits of the call (forward), or -1 for the adjoint
+// (which reads no albedo and writes no radiance).
+vct_status check_view(const vct_view &v, int i, int n_pyr, int flags) {
+  const bool need_outputs = flags >= 0;
+  if (v.width < 1 || v.height < 1 || v.width > 65535 || v.height > 65535 ||
+      (int64_t)v.width * v.height > (int64_t)1 << 29)
     return fail(VCT_ERR_INVALID_ARG, "view %d: bad size %dx%d", i, v.width, v.height);
   if (v.pyramid < 0 || v.pyramid >= n_pyr || v.reserved != 0)
     return fail(VCT_ERR_INVALID_ARG, "view %d: pyramid index %d out of range", i, v.pyramid);
@@ -185,7 +235,11 @@ vct_status check_view(const vct_view &v, int i, int n_pyr, bool need_outputs) {
       (v.out_specular && !aligned(v.out_specular, 16)) ||
       (v.out_visibility && !aligned(v.out_visibility, 4)))
     return fail(VCT_ERR_INVALID_ARG, "view %d: outputs must be 16-byte aligned", i);
-  if (need_outputs && !v.out_diffuse && !v.out_specular && !v.out_visibility)
+  if ((v.albedo && !aligned(v.albedo, 4)) || (v.out_radiance && !aligned(v.out_radiance, 16)))
+    return fail(VCT_ERR_INVALID_ARG, "view %d: albedo/out_radiance misaligned", i);
+  if (need_outputs && v.out_radiance && !(flags & VCT_FLAG_SHADE))
+    return fail(VCT_ERR_INVALID_ARG, "view %d: out_radiance needs VCT_FLAG_SHADE", i);
+  if (need_outputs && !v.out_diffuse && !v.out_specular && !v.out_visibility && !v.out_radiance)
     return fail(VCT_ERR_INVALID_ARG, "view %d: no output buffer", i);
   if (!finite(v.camera[0]) || !finite(v.camera[1]) || !finite(v.camera[2]))
     return fail(VCT_ERR_INVALID_ARG, "view %d: camera not finite", i);
@@ -200,15 +254,17 @@ void fill_view(const vct_view &v, int tile_w, int tile_h, int &tile_cursor, DevV
   d.outD = v.out_diffuse;
   d.outS = v.out_specular;
   d.outV = v.out_visibility;
+  d.albedo = v.albedo;
+  d.outL = v.out_radiance;
   for (int a = 0; a < 3; ++a) d.cam[a] = v.camera[a];
-  d.W = v.width;
-  d.H = v.height;
-  d.pyr = v.pyramid;
-  d.tiles_x = (v.width + tile_w - 1) / tile_w;
+  d.W = (uint16_t)v.width;
+  d.H = (uint16_t)v.height;
+  d.pyr = (uint16_t)v.pyramid;
+  d.tiles_x = (uint16_t)((v.width + tile_w - 1) / tile_w);
   d.tile_begin = tile_cursor;
   tile_cursor += d.tiles_x * ((v.height + tile_h - 1) / tile_h);
-  d.y_split = v.height;
-  d.small_tiles_x = (v.width + kSmallTileW - 1) / kSmallTileW;
+  d.y_split = (uint16_t)v.height;
+  d.small_tiles_x = (uint16_t)((v.width + kSmallTileW - 1) / kSmallTileW);
   d.small_begin = 0;
 }
 
@@ -221,7 +277,7 @@ int assign_tail_tiles(DevView *v, int nv, int tile_w, int tile_h, int64_t tail_p
     const int rows = (v[i].H + tile_h - 1) / tile_h;
     const int64_t row_px = (int64_t)tile_h * v[i].W;
     int take = (int)std::min<int64_t>(rows, (tail_px + row_px - 1) / row_px);
-    v[i].y_split = (rows - take) * tile_h;
+    v[i].y_split = (uint16_t)((rows - take) * tile_h);
     tail_px -= (int64_t)take * row_px;
   }
   int cursor = 0;
@@ -246,7 +302,7 @@ bool cfg_ok(const vct_launch_config &c) {
 }
 
 // Launch-shape cache filled by vct_autotune_trace.
-using TuneKey = std::tuple<int, int, int, int, int, int>;
+using TuneKey = std::tuple<int, int, int, int, int, int, int>;
 std::mutex g_tune_mu;
 std::map<TuneKey, vct_launch_config> g_tuned;
 
@@ -254,7 +310,7 @@ TuneKey tune_key(const vct_pyramid *pyrs, const vct_view *views, const vct_trace
   int dev = 0;
   cudaGetDevice(&dev);
   return TuneKey(dev, pyrs[0].dtype, pyrs[0].n, P->spec_enable, P->occ_enable,
-                 views[0].roughness != nullptr);
+                 views[0].roughness != nullptr, P->flags);
 }
 
 vct_launch_config default_cfg() { return vct_launch_config{16, 16, 1, 0}; }
@@ -372,6 +428,7 @@ static vct_status trace_impl(const vct_pyramid *pyrs, int32_t n_pyr, const vct_v
   auto L = std::make_unique<TraceLaunch>();
   memset(L.get(), 0, sizeof(TraceLaunch));
   fill_common(*params, *L);
+  fill_variants(*params, L->var);
   for (int i = 0; i < n_pyr; ++i) {
     vct_status st = fill_pyr(pyrs[i], *params, L->pyr[i]);
     if (st != VCT_OK) return st;
@@ -385,7 +442,8 @@ static vct_status trace_impl(const vct_pyramid *pyrs, int32_t n_pyr, const vct_v
   if (zero_stats && (e = cudaMemsetAsync(ws, 0, sizeof(vct_trace_stats), stream)) != cudaSuccess)
     return cuda_fail(e, "vct_trace workspace clear");
   int per_sm = cfg.ctas_per_sm;
-  if (per_sm == 0) per_sm = std::max(1, trace_occupancy(cfg.lanes_per_pixel, pyrs[0].dtype));
+  if (per_sm == 0)
+    per_sm = std::max(1, trace_occupancy(cfg.lanes_per_pixel, pyrs[0].dtype, params->flags != 0));
   const int sms = sm_count();
   for (int v0 = 0; v0 < n_views; v0 += kMaxViewsPerLaunch) {
     const int nv = std::min(kMaxViewsPerLaunch, n_views - v0);
@@ -420,10 +478,10 @@ static vct_status trace_checks(const vct_pyramid *pyrs, int32_t n_pyr, const vct
     if (st != VCT_OK) return st;
   }
   if (!views || n_views < 1) return fail(VCT_ERR_INVALID_ARG, "vct_trace: no views");
-  vct_status st = check_params(params);
+  vct_status st = check_params(params, false);
   if (st != VCT_OK) return st;
   for (int i = 0; i < n_views; ++i)
-    if ((st = check_view(views[i], i, n_pyr, true)) != VCT_OK) return st;
+    if ((st = check_view(views[i], i, n_pyr, params->flags)) != VCT_OK) return st;
   if (!workspace || workspace_bytes < vct_trace_workspace_bytes() || !aligned(workspace, 8))
     return fail(VCT_ERR_WORKSPACE, "vct_trace: workspace needs %zu bytes, 8-byte aligned",
                 vct_trace_workspace_bytes());
@@ -509,9 +567,9 @@ vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
     return fail(VCT_ERR_UNSUPPORTED, "vct_trace_backward: only VCT_F32 pyramids are supported");
   if (!views || !grads || n_views < 1)
     return fail(VCT_ERR_INVALID_ARG, "vct_trace_backward: no views");
-  if ((st = check_params(params)) != VCT_OK) return st;
+  if ((st = check_params(params, true)) != VCT_OK) return st;
   for (int i = 0; i < n_views; ++i) {
-    if ((st = check_view(views[i], i, 1, false)) != VCT_OK) return st;
+    if ((st = check_view(views[i], i, 1, -1)) != VCT_OK) return st;
     const vct_view_grad &g = grads[i];
     if ((g.grad_diffuse && !aligned(g.grad_diffuse, 16)) ||
         (g.grad_specular && !aligned(g.grad_specular, 16)) ||

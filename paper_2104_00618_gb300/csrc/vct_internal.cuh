@@ -186,17 +186,37 @@ struct DevPyr {
   double origin[3];
   double scale;  // n / size: scene units -> level-0 voxel units
   double tmax_vox;  // t_max in level-0 voxel units
-  int n, levels, dtype, pad;
+  int n, levels, dtype;
+  float h0;  // level-0 voxel edge in scene units
   ConeConst diffuse, occ, spec_fixed;
 };
 
+// One view of a launch.  Sizes are 16-bit (width, height <= 65535) so that
+// 256 views fit the 32 KB kernel-parameter space.
 struct DevView {
   const float *pos, *nrm, *rough;
   const uint8_t *mask;
   float *outD, *outS, *outV;
+  const float *albedo;
+  float *outL;
   float cam[3];
-  int W, H, pyr, tiles_x, tile_begin;  // big tiles cover rows [0, y_split)
-  int y_split, small_tiles_x, small_begin;  // small tiles cover rows [y_split, H)
+  int tile_begin, small_begin;  // first big / small tile item of the view
+  uint16_t W, H, pyr, tiles_x;  // big tiles cover rows [0, y_split)
+  uint16_t y_split, small_tiles_x;  // small tiles cover rows [y_split, H)
+};
+
+// Variant switches and shading constants of a forward launch (Ch. 5.4.4,
+// Ch. 3.3, Ch. 4.2.2).
+struct Variants {
+  int flags;            // VCT_FLAG_* bits
+  float shadow_str;     // occlusion fade: smoothstep(0, occ_max_dist, sqrt(t) shadow_str)
+  float occ_max_dist;
+  float grace;          // angular grace 0.008 pi shininess (radians)
+  float falloff;        // exponent of the angular-grace BRDF
+  float shininess;      // Phong exponent of the direct light
+  float kd, ks;         // material ratios
+  float light_color[3];
+  float light_dir[3];   // as given (not normalised), like the occlusion cone axis
 };
 
 // Tail tiles: the last pixels of a launch are handed out in small tiles so
@@ -207,6 +227,7 @@ struct TraceLaunch {
   int n_views, total_tiles, tile_w, tile_h;
   int n_big, pad_big;  // items [0, n_big) are big tiles, the rest small tiles
   int n_diffuse, spec_enable, occ_enable, pad0;
+  Variants var;
   float diffuse_dir[VCT_MAX_DIFFUSE][3];
   float diffuse_weight[VCT_MAX_DIFFUSE];
   float light[3];
@@ -272,7 +293,7 @@ cudaError_t launch_mip_adjoint(const float *gpyr_base, const Layout &gl, int n, 
                                float *grad0, cudaStream_t s);
 cudaError_t launch_wait_probe(uint32_t *flag, uint64_t max_ns, cudaStream_t s);
 cudaError_t launch_trace(const TraceLaunch &L, int lpp, int dtype, int grid, cudaStream_t s);
-int trace_occupancy(int lpp, int dtype);
+int trace_occupancy(int lpp, int dtype, bool variants);
 cudaError_t launch_trace_bwd(const BwdLaunch &L, int lpp, int grid, cudaStream_t s);
 int trace_bwd_occupancy(int lpp, size_t smem);
 size_t bwd_smem_bytes(int n, int levels, int first);

@@ -34,10 +34,10 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(_abi.VctPyramid) == 48
-    assert ctypes.sizeof(_abi.VctView) == 88
+    assert ctypes.sizeof(_abi.VctView) == 104
     assert ctypes.sizeof(_abi.VctLaunchConfig) == 16
     assert ctypes.sizeof(_abi.VctTraceStats) == 56
-    assert ctypes.sizeof(_abi.VctTraceParams) == 16 + 32 * 12 + 32 * 4 + 4 * 5 + 12 + 16
+    assert ctypes.sizeof(_abi.VctTraceParams) == 16 + 32 * 12 + 32 * 4 + 4 * 5 + 12 + 16 + 4 * 9
 
 
 def test_pyramid_layout(lib):
@@ -96,3 +96,54 @@ def test_validation_without_gpu(lib):
                                 ctypes.byref(prm), None, None, None, 0, None)
     assert st == _abi.VCT_ERR_UNSUPPORTED
     assert lib.vct_debug_wait_probe(None, 10, None) == _abi.VCT_ERR_INVALID_ARG
+
+
+def test_variant_flag_validation_without_gpu(lib):
+    """Flag combinations the library refuses before any CUDA call."""
+    base = {"n_diffuse": 1, "diffuse_dir": [[0, 0, 1]], "diffuse_weight": [1],
+            "diffuse_aperture": 0.5, "spec_enable": 1, "occ_enable": 1,
+            "spec_aperture_min": 0.1, "spec_aperture_max": 0.3, "roughness_min": 0.05,
+            "occ_aperture": 0.5, "light_dir": [0, 1, 0], "beta": 0.5, "t0_voxels": 1.0,
+            "normal_offset_voxels": 1.0, "t_max": 1.0}
+    p = _abi.VctPyramid(64, 7, 0, 0, (ctypes.c_float * 3)(0, 0, 0), 1.0, 256,
+                        lib.vct_pyramid_bytes(64, 7, 0))
+    v = _abi.VctView()
+    v.width, v.height, v.position, v.normal, v.out_diffuse = 4, 4, 1024, 2048, 4096
+
+    def run(flags, view=v, **kw):
+        prm = vct.make_params(dict(base, flags=flags, **kw))
+        return lib.vct_trace(ctypes.byref(p), 1, ctypes.byref(view), 1, ctypes.byref(prm),
+                             None, None, 0, None)
+
+    assert run(32) == _abi.VCT_ERR_INVALID_ARG and b"unknown flags" in lib.vct_last_error()
+    assert run(_abi.FLAG_SHADE_IMPL) == _abi.VCT_ERR_INVALID_ARG
+    assert run(_abi.FLAG_OCC_SMOOTH, occ_max_dist=0.0) == _abi.VCT_ERR_INVALID_ARG
+    assert run(_abi.FLAG_SPEC_GRACE, shininess=-1.0) == _abi.VCT_ERR_INVALID_ARG
+    assert run(_abi.FLAG_SHADE, light_dir=[0, 0, 0]) == _abi.VCT_ERR_INVALID_ARG
+    assert run(_abi.FLAG_SHADE, light_color=[1, float("nan"), 1]) == _abi.VCT_ERR_INVALID_ARG
+    # radiance output only with the shading flag; width/height are 16-bit
+    vr = _abi.VctView.from_buffer_copy(v)
+    vr.out_radiance = 8192
+    assert run(0, view=vr) == _abi.VCT_ERR_INVALID_ARG and b"out_radiance" in lib.vct_last_error()
+    vr.out_radiance = 8200
+    assert run(_abi.FLAG_SHADE, view=vr) == _abi.VCT_ERR_INVALID_ARG  # misaligned
+    vw = _abi.VctView.from_buffer_copy(v)
+    vw.width = 65536
+    assert run(0, view=vw) == _abi.VCT_ERR_INVALID_ARG
+    # every valid combination passes validation (and stops at the workspace)
+    vr.out_radiance = 8192
+    for flags in range(32):
+        if flags & _abi.FLAG_SHADE_IMPL and not flags & _abi.FLAG_SHADE:
+            continue
+        view = vr if flags & _abi.FLAG_SHADE else v
+        assert run(flags, view=view) == _abi.VCT_ERR_WORKSPACE, (flags, lib.vct_last_error())
+    # the adjoint takes the shading flags but not the modified cones
+    g = _abi.VctViewGrad()
+    for flags, want in [(_abi.FLAG_OCC_SMOOTH, _abi.VCT_ERR_UNSUPPORTED),
+                        (_abi.FLAG_DIFFUSE_FIRST_HIT, _abi.VCT_ERR_UNSUPPORTED),
+                        (_abi.FLAG_SPEC_GRACE, _abi.VCT_ERR_UNSUPPORTED),
+                        (_abi.FLAG_SHADE, _abi.VCT_ERR_INVALID_ARG)]:
+        prm = vct.make_params(dict(base, flags=flags))
+        st = lib.vct_trace_backward(ctypes.byref(p), ctypes.byref(v), ctypes.byref(g), 1,
+                                    ctypes.byref(prm), None, None, None, 0, None)
+        assert st == want, (flags, lib.vct_last_error())
