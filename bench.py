@@ -365,6 +365,35 @@ def extra_fp16_single(torch, vct, dev):
             "gsamples_per_s": samples / (step_ms / 1e3) / 1e9, "samples_per_frame": samples}
 
 
+def extra_variants(torch, vct, dev):
+    """The same 1080p frame (FP32) with the thesis's modified cones (occlusion
+    fade-in, angular-grace specular, first-hit diffuse) and L_vxct shading
+    into a radiance buffer, beside the plain trace."""
+    import vct_synth as vs
+    cfg = make_workload()
+    scene, hv, prm = cfg["scenes"][0], dict(cfg["views"][0]), cfg["params"]
+    hv["albedo"] = vs.albedo(hv["width"], hv["height"], 11)
+    flags = (vct.FLAG_OCC_SMOOTH | vct.FLAG_SPEC_GRACE | vct.FLAG_DIFFUSE_FIRST_HIT
+             | vct.FLAG_SHADE)
+    level0 = torch.from_numpy(scene["grid"]).to(dev)
+    view = vct.View.from_host(hv, device=dev, outputs=False)
+    view.alloc_outputs(radiance=True)
+    P = vct.build_mips(level0)
+    ws = torch.zeros(256, dtype=torch.uint8, device=dev)
+    out = {"workload": "room256_1080p_f32_variants_shaded", "flags": flags}
+    for name, p in (("plain", vct.make_params(prm)),
+                    ("variants", vct.make_params(vs.variant_params(prm, flags)))):
+        if name == "plain":
+            view.out_radiance = None
+        else:
+            view.alloc_outputs(radiance=True)
+        ms = _time(torch, lambda: vct.trace([P], [view], p, workspace=ws), 10)
+        samples = int(sum(vct.read_stats(ws)["samples"]))
+        out[name] = {"trace_ms": ms, "samples_per_frame": samples,
+                     "gsamples_per_s": samples / (ms / 1e3) / 1e9}
+    return out
+
+
 def extra_fwd_bwd(torch, vct, dev, n=128, n_views=32, res=512):
     """Learnable 128^3 grid at 0.1, 32 views of 512x512 of a ground-truth box
     scene, L2 loss: forward (mips + trace) and forward + adjoint (trace
@@ -449,8 +478,8 @@ def extra_batched(torch, vct, dev, grids=(128, 256, 256, 512), views_per_scene=6
 def run_extras(torch, vct, dev, args):
     """Secondary measurements reported beside the main metric."""
     out = {}
-    for name, fn in (("fp16_single_view", extra_fp16_single), ("fwd_bwd", extra_fwd_bwd),
-                     ("batched_fp16", extra_batched)):
+    for name, fn in (("fp16_single_view", extra_fp16_single), ("variants", extra_variants),
+                     ("fwd_bwd", extra_fwd_bwd), ("batched_fp16", extra_batched)):
         if name == "batched_fp16" and args.no_batched:
             continue
         try:

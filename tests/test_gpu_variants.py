@@ -26,18 +26,11 @@ def _cuda():
 
 
 def variant_params(prm, flags):
-    """Room parameters with the Ch. 5.4.4 settings: a fade-in over the first
-    0.3 scene units of the occlusion cone, Phong exponent 32 (angular grace
-    0.256 pi) with falloff 2, and unequal material ratios and light colour."""
-    return dict(prm, flags=flags, shadow_str=1.0, occ_max_dist=0.3, shininess=32.0,
-                shininess_falloff=2.0, diffuse_str=0.8, specular_str=0.6,
-                light_color=(1.0, 0.9, 0.7))
+    return vs.variant_params(prm, flags)
 
 
 def with_albedo(view, seed):
-    rng = np.random.default_rng(seed)
-    npx = view["width"] * view["height"]
-    return dict(view, albedo=(0.2 + 0.8 * rng.random((npx, 3))).astype(np.float32))
+    return dict(view, albedo=vs.albedo(view["width"], view["height"], seed))
 
 
 def run_gpu(pyr, view_host, prm, cfg=None):

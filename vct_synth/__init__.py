@@ -339,6 +339,22 @@ def interior_view(scene, width, height, rng, with_roughness=True):
     return view_dict(pos, nrm, mask, width, height, cam, roughness=rough)
 
 
+def albedo(width, height, seed):
+    """Per-pixel material colour in [0.2, 1] (float32 [H*W, 3])."""
+    rng = np.random.default_rng(seed)
+    return (0.2 + 0.8 * rng.random((width * height, 3))).astype(np.float32)
+
+
+def variant_params(prm, flags):
+    """Parameters of the thesis's modified cones and shading (Ch. 5.4.4):
+    occlusion fade-in over the first 0.3 scene units (shadow strength 1),
+    Phong exponent 32 (angular grace 0.256 pi) with falloff 2, material
+    ratios 0.8 / 0.6 and a warm light colour."""
+    return dict(prm, flags=flags, shadow_str=1.0, occ_max_dist=0.3, shininess=32.0,
+                shininess_falloff=2.0, diffuse_str=0.8, specular_str=0.6,
+                light_color=(1.0, 0.9, 0.7))
+
+
 def params_room9(light):
     dirs, w = cone_table_thesis9()
     return trace_params(dirs, w, 0.55, spec_enable=True,
