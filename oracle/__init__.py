@@ -69,7 +69,7 @@ class OrcView(ctypes.Structure):
 
 
 def _source_files():
-    return [os.path.join(_HERE, "vct_oracle.c")]
+    return [os.path.join(_HERE, "vct_oracle.c"), os.path.join(_HERE, "vct_voxelize.c")]
 
 
 def compile_source(sources, out_dir=None, tag=None) -> str:
@@ -120,6 +120,9 @@ def load_library(path: str):
                               vp, vp, vp, vp, vp, vp]
     lib.orc_trace_backward.argtypes = [vp, i32, i32, vp, dbl, vp, vp, vp, i64,
                                        vp, vp, vp, vp, vp]
+    lib.orc_voxelize.argtypes = [vp, i64, vp, i64, vp, i32, vp, ctypes.c_float, vp, vp, dbl,
+                                 dbl, vp, vp, vp]
+    lib.orc_voxelize.restype = None
     for f in ("orc_build_mips", "orc_mip_adjoint", "orc_sample", "orc_sample_lod",
               "orc_trace_cone", "orc_tangent_frame", "orc_trace",
               "orc_trace_backward"):
@@ -382,3 +385,28 @@ def trace_backward(pyr: Pyramid, view: dict, prm: dict, gD, gS, gV, idx=None):
                               ctypes.byref(V), ctypes.byref(P), _p(idx_arr), count,
                               _p(gD), _p(gS), _p(gV), _p(scratch), _p(grad0))
     return grad0.reshape(n, n, n, 4)
+
+
+def voxelize(mesh: dict, n: int, origin=(0.0, 0.0, 0.0), size: float = 1.0,
+             light: dict | None = None):
+    """Voxelizes a triangle mesh (dict: vertices [V,3], indices [T,3], colors
+    [T,3]; float32 / int32) into an n^3 grid.  light: dict(light_dir,
+    light_color, ambient, diffuse_str).  Returns (grid [n,n,n,4] float64,
+    owner [n,n,n] int32 (triangle index + 1, 0 empty), stats dict)."""
+    light = light or {}
+    verts = np.ascontiguousarray(mesh["vertices"], dtype=np.float32).reshape(-1, 3)
+    idx = np.ascontiguousarray(mesh["indices"], dtype=np.int32).reshape(-1, 3)
+    cols = np.ascontiguousarray(mesh["colors"], dtype=np.float32).reshape(-1, 3)
+    assert cols.shape[0] == idx.shape[0]
+    org = np.ascontiguousarray(origin, dtype=np.float32).reshape(3)
+    ldir = _f64(light.get("light_dir", (0.0, 1.0, 0.0))).reshape(3)
+    lcol = _f64(light.get("light_color", (1.0, 1.0, 1.0))).reshape(3)
+    grid = np.empty((n, n, n, 4), dtype=np.float64)
+    owner = np.empty((n, n, n), dtype=np.int32)
+    stats = np.zeros(3, dtype=np.int64)
+    _lib().orc_voxelize(_p(verts), verts.shape[0], _p(idx), idx.shape[0], _p(cols), int(n),
+                        _p(org), float(np.float32(size)), _p(ldir), _p(lcol),
+                        float(light.get("ambient", 0.0)), float(light.get("diffuse_str", 1.0)),
+                        _p(grid), _p(owner), _p(stats))
+    return grid, owner, {"fragments": int(stats[0]), "skipped": int(stats[1]),
+                         "degenerate": int(stats[2])}

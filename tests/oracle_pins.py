@@ -577,3 +577,239 @@ def check_shading_epilogue():
         else:
             want = alb * (0.7 * D[:3] + 0.4 * S[:3]) + V * direct
         assert np.allclose(r["L"][0, :3], want, rtol=1e-12, atol=1e-15), (flags, r["L"][0], want)
+
+
+# --------------------------------------------------------------------------
+# voxelization (Ch. 4.4): brute force with exact rationals
+# --------------------------------------------------------------------------
+from fractions import Fraction  # noqa: E402
+
+_SWIZZLE = {0: (2, 1), 1: (0, 2), 2: (0, 1)}  # raster axes (u, v) per dominant axis
+
+
+def bf_snap(verts, origin, size, n):
+    """Fixed-point vertex coordinates (1/256 voxel) by float32 arithmetic."""
+    s = np.float32(256.0 * n / np.float64(np.float32(size)))
+    a = np.asarray(verts, np.float32) - np.asarray(origin, np.float32)
+    return np.rint(a * s).astype(np.int64)
+
+
+def bf_voxelize(mesh, n, origin=(0.0, 0.0, 0.0), size=1.0, light=None):
+    """Serial voxelization from the definition: every pixel centre of the
+    dominant-axis projection, tested by exact barycentric coordinates (a
+    centre on an edge counts for top and left edges of the counter-clockwise
+    projection), depth = barycentric blend of the vertex depths, floor."""
+    light = light or {}
+    l = np.asarray(light.get("light_dir", (0.0, 1.0, 0.0)), np.float64)
+    lc = np.asarray(light.get("light_color", (1.0, 1.0, 1.0)), np.float64)
+    amb, kd = float(light.get("ambient", 0.0)), float(light.get("diffuse_str", 1.0))
+    verts = np.asarray(mesh["vertices"], np.float32).reshape(-1, 3)
+    X = bf_snap(verts, origin, size, n)
+    owner = np.zeros((n, n, n), np.int32)
+    grid = np.zeros((n, n, n, 4))
+    frags = 0
+    for t, tri in enumerate(np.asarray(mesh["indices"]).reshape(-1, 3)):
+        V = [tuple(int(c) for c in X[k]) for k in tri]
+        nrm = np.cross(np.subtract(V[1], V[0]), np.subtract(V[2], V[0]))
+        if not nrm.any():
+            continue
+        dom = int(np.argmax(np.abs(nrm)))  # first maximum on ties
+        u, v = _SWIZZLE[dom]
+        P = [(Fraction(p[u]), Fraction(p[v])) for p in V]
+        A = (P[1][0] - P[0][0]) * (P[2][1] - P[0][1]) - (P[1][1] - P[0][1]) * (P[2][0] - P[0][0])
+        if A < 0:
+            P = [P[0], P[2], P[1]]
+            V = [V[0], V[2], V[1]]
+            A = -A
+        f = np.asarray(verts[tri], np.float64)
+        g = np.cross(f[1] - f[0], f[2] - f[0])
+        lam = max(float(g @ l) / np.linalg.norm(g), 0.0) if np.linalg.norm(g) > 0 else 0.0
+        rgb = np.asarray(mesh["colors"], np.float64).reshape(-1, 3)[t] * lc * (amb + kd * lam)
+        for j in range(n):
+            for i in range(n):
+                c = (Fraction(256 * i + 128), Fraction(256 * j + 128))
+                bary, ok = [], True
+                for k in range(3):  # weight of vertex k: area opposite to it
+                    a, b = P[(k + 1) % 3], P[(k + 2) % 3]
+                    w = (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0])
+                    if w == 0:  # on the edge a -> b: top (horizontal, heading -u) or left (heading -v)
+                        ok = (b[1] - a[1] < 0) or (b[1] == a[1] and b[0] - a[0] < 0)
+                    elif w < 0:
+                        ok = False
+                    if not ok:
+                        break
+                    bary.append(w / A)
+                if not ok:
+                    continue
+                depth = sum(bary[k] * V[k][dom] for k in range(3))
+                kk = math.floor(depth / 256)
+                if not 0 <= kk < n:
+                    continue
+                cell = [0, 0, 0]
+                cell[u], cell[v], cell[dom] = i, j, kk
+                frags += 1
+                owner[cell[2], cell[1], cell[0]] = t + 1
+                grid[cell[2], cell[1], cell[0]] = (*rgb, 1.0)
+    return grid, owner, frags
+
+
+def _random_mesh(rng, n, count, snap_half=True):
+    """Small random triangles; with snap_half, coordinates on the half-voxel
+    lattice so that edges run through pixel centres (tie cases)."""
+    verts, idx = [], []
+    for t in range(count):
+        c = rng.uniform(0.5, n - 0.5, size=3)
+        tri = c + rng.uniform(-3.0, 3.0, size=(3, 3))
+        if snap_half and t % 2 == 0:
+            tri = np.round(tri * 2.0) / 2.0
+        if t % 5 == 1:
+            tri[:, t % 3] = np.round(tri[0, t % 3]) + 0.5  # axis-aligned plane through voxel centres
+        verts.extend(tri / n)
+        idx.append([3 * t, 3 * t + 1, 3 * t + 2])
+    cols = rng.uniform(0.1, 1.0, size=(count, 3))
+    return {"vertices": np.asarray(verts, np.float32), "indices": np.asarray(idx, np.int32),
+            "colors": np.asarray(cols, np.float32)}
+
+
+def check_voxelize_bruteforce():
+    rng = np.random.default_rng(2104)
+    n = 10
+    mesh = _random_mesh(rng, n, 40)
+    light = {"light_dir": (0.3, 0.8, 0.52), "light_color": (1.0, 0.8, 0.6), "ambient": 0.1,
+             "diffuse_str": 0.9}
+    g, o, st = oracle.voxelize(mesh, n, light=light)
+    bg, bo, bf = bf_voxelize(mesh, n, light=light)
+    assert st["fragments"] == bf, (st, bf)
+    assert np.array_equal(o, bo), int((o != bo).sum())
+    assert np.allclose(g, bg, rtol=1e-12, atol=1e-15)
+    # the same scene in a grid of edge 2.5 at another origin
+    origin, size = np.array([-0.75, 0.5, 0.125]), 2.5
+    moved = dict(mesh, vertices=(origin + size * mesh["vertices"].astype(np.float64))
+                 .astype(np.float32))
+    g, o, st = oracle.voxelize(moved, n, origin=origin, size=size, light=light)
+    bg, bo, bf = bf_voxelize(moved, n, origin=origin, size=size, light=light)
+    assert st["fragments"] == bf and np.array_equal(o, bo), (st, bf)
+    assert np.allclose(g, bg, rtol=1e-12, atol=1e-15)
+    assert bf > 50
+
+
+def check_voxelize_shared_edges_cover_once():
+    """A planar grid of triangles whose vertices sit on pixel centres: every
+    centre inside the region is covered by exactly one triangle."""
+    n = 16
+    verts, idx = [], []
+    xs = [2.5, 4.5, 7.5, 8.5, 12.5]
+    ys = [1.5, 3.5, 6.5, 11.5]
+    z = 5.5
+    vid = {}
+    for a, x in enumerate(xs):
+        for b, y in enumerate(ys):
+            vid[a, b] = len(verts)
+            verts.append((x / n, y / n, z / n))
+    for a in range(len(xs) - 1):
+        for b in range(len(ys) - 1):
+            q = (vid[a, b], vid[a + 1, b], vid[a + 1, b + 1], vid[a, b + 1])
+            if (a + b) % 2:
+                idx += [[q[0], q[1], q[2]], [q[0], q[2], q[3]]]
+            else:
+                idx += [[q[0], q[1], q[3]], [q[3], q[1], q[2]]]
+    mesh = {"vertices": np.asarray(verts, np.float32), "indices": np.asarray(idx, np.int32),
+            "colors": np.ones((len(idx), 3), np.float32)}
+    g, o, st = oracle.voxelize(mesh, n)
+    # centres (i + 1/2) with 2.5 <= i + 1/2 <= 12.5 and 1.5 <= j + 1/2 <= 11.5, on the
+    # region's boundary only its left and top sides count: i in [2, 12), j in (1, 11]
+    want = (12 - 2) * (11 - 1)
+    assert st["fragments"] == want and int((o > 0).sum()) == want, (st, int((o > 0).sum()))
+    assert np.all(o[5][o[5] > 0] > 0) and int((o[:5] > 0).sum() + (o[6:] > 0).sum()) == 0
+
+
+def check_voxelize_box_shell():
+    """A box whose faces run through voxel centres, in-plane inset by 1/4
+    voxel: its voxelization is exactly the box's one-voxel shell, each face
+    with its Lambert colour."""
+    n = 16
+    lo, hi = np.array([3, 5, 2]), np.array([11, 9, 14])  # voxels lo .. hi-1
+    a, b = lo + 0.5, hi - 0.5
+    e = 0.25
+    verts, idx, cols = [], [], []
+    light = {"light_dir": (0.48, 0.6, 0.64), "light_color": (1.0, 1.0, 1.0), "ambient": 0.05}
+    normals = []
+    for axis in range(3):
+        for side, pos in ((-1, a[axis]), (+1, b[axis])):
+            u, v = [x for x in range(3) if x != axis]
+            corners = []
+            for cu, cv in ((a[u] - e, a[v] - e), (b[u] + e, a[v] - e), (b[u] + e, b[v] + e),
+                           (a[u] - e, b[v] + e)):
+                p = np.zeros(3)
+                p[axis], p[u], p[v] = pos, cu, cv
+                corners.append(p / n)
+            base = len(verts)
+            verts += corners
+            nrm = np.zeros(3)
+            nrm[axis] = side
+            tri = [[0, 1, 2], [0, 2, 3]]
+            g = np.cross(corners[1] - corners[0], corners[2] - corners[0])
+            if g @ nrm < 0:
+                tri = [[0, 2, 1], [0, 3, 2]]
+            for t in tri:
+                idx.append([base + t[0], base + t[1], base + t[2]])
+                cols.append((0.8, 0.5, 0.3))
+                normals.append(nrm)
+    mesh = {"vertices": np.asarray(verts, np.float32), "indices": np.asarray(idx, np.int32),
+            "colors": np.asarray(cols, np.float32)}
+    g, o, st = oracle.voxelize(mesh, n, light=light)
+    zz, yy, xx = np.meshgrid(range(n), range(n), range(n), indexing="ij")
+    inside = ((xx >= lo[0]) & (xx < hi[0]) & (yy >= lo[1]) & (yy < hi[1]) &
+              (zz >= lo[2]) & (zz < hi[2]))
+    core = ((xx > lo[0]) & (xx < hi[0] - 1) & (yy > lo[1]) & (yy < hi[1] - 1) &
+            (zz > lo[2]) & (zz < hi[2] - 1))
+    shell = inside & ~core
+    assert np.array_equal(o > 0, shell)
+    assert np.array_equal(g[..., 3], shell.astype(np.float64))
+    ldir = np.asarray(light["light_dir"])
+    for t in np.unique(o[o > 0]):
+        lam = max(float(normals[t - 1] @ ldir), 0.0)
+        want = np.array([0.8, 0.5, 0.3], np.float32).astype(np.float64) * (0.05 + lam)
+        assert np.allclose(g[o == t][:, :3], want, rtol=1e-6), (t, g[o == t][0], want)
+
+
+def check_voxelize_draw_order_and_skips():
+    n = 8
+    tri = np.array([[0.1, 0.1, 0.55], [0.9, 0.1, 0.55], [0.1, 0.9, 0.55]], np.float32)
+    bad = np.array([[0.1, 0.1, 0.3], [1e7, 0.5, 0.3], [0.5, 0.9, 0.3]], np.float32)
+    line = np.array([[0.1, 0.1, 0.2], [0.5, 0.5, 0.2], [0.9, 0.9, 0.2]], np.float32)
+    verts = np.concatenate([tri, tri, bad, line])
+    mesh = {"vertices": verts,
+            "indices": np.array([[0, 1, 2], [3, 4, 5], [6, 7, 8], [9, 10, 11], [0, 1, 99]],
+                                np.int32),
+            "colors": np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1], [1, 1, 1]],
+                               np.float32)}
+    light = {"light_dir": (0.0, 0.0, 1.0)}
+    g, o, st = oracle.voxelize(mesh, n, light=light)
+    assert st["skipped"] == 2 and st["degenerate"] == 1, st
+    assert np.all(o[o > 0] == 2) and np.all(g[o > 0][:, :3] == (0.0, 1.0, 0.0))
+    assert st["fragments"] == 2 * int((o > 0).sum())
+    mesh["indices"], mesh["colors"] = mesh["indices"][[1, 0]], mesh["colors"][[1, 0]]
+    g, o, st = oracle.voxelize(mesh, n, light=light)
+    assert np.all(g[o > 0][:, :3] == (1.0, 0.0, 0.0))
+
+
+def check_voxelize_area_and_clip():
+    """Fragment count of a large triangle is its projected area up to the
+    boundary pixels; a triangle reaching outside the grid keeps only the
+    fragments inside."""
+    n = 64
+    p = np.array([[0.05, 0.1, 0.4], [0.93, 0.2, 0.45], [0.3, 0.97, 0.5]], np.float32)
+    mesh = {"vertices": p, "indices": np.array([[0, 1, 2]], np.int32),
+            "colors": np.ones((1, 3), np.float32)}
+    _, o, st = oracle.voxelize(mesh, n)
+    q = p.astype(np.float64) * n
+    area = 0.5 * abs(np.cross(q[1] - q[0], q[2] - q[0])[2])
+    perim = sum(np.linalg.norm((q[(k + 1) % 3] - q[k])[:2]) for k in range(3))
+    assert abs(st["fragments"] - area) <= perim + 1, (st, area, perim)
+    big = np.array([[-0.5, -0.5, 0.5], [1.5, -0.5, 0.5], [-0.5, 1.5, 0.5]], np.float32)
+    mesh["vertices"] = big
+    _, o, st = oracle.voxelize(mesh, n)
+    i, j = np.meshgrid(np.arange(n) + 0.5, np.arange(n) + 0.5, indexing="ij")
+    want = int(((i + j) < n).sum())  # the hypotenuse u + v = n passes no centre
+    assert st["fragments"] == want and int((o > 0).sum()) == want

@@ -11,7 +11,8 @@ import pytest
 import oracle
 import oracle_pins as pins
 
-SRC = os.path.join(os.path.dirname(oracle.__file__), "vct_oracle.c")
+ORACLE_DIR = os.path.dirname(oracle.__file__)
+SOURCES = ["vct_oracle.c", "vct_voxelize.c"]
 
 MUTANTS = {
     "texel centre dropped": ("double u = q[a] * nl - 0.5;", "double u = q[a] * nl;"),
@@ -56,6 +57,20 @@ MUTANTS = {
     "direct light not occluded": (
         "out[ch] = alb[ch] * (P->diffuse_str * D[ch] + P->specular_str * S[ch]) + vis * direct;",
         "out[ch] = alb[ch] * (P->diffuse_str * D[ch] + P->specular_str * S[ch]) + direct;"),
+    "top-left rule inverted": ("return ev < 0 || (ev == 0 && eu < 0);",
+                               "return ev > 0 || (ev == 0 && eu > 0);"),
+    "centre at the pixel corner": ("int64_t p[2] = {SUB * i + SUB / 2, SUB * j + SUB / 2};",
+                                   "int64_t p[2] = {SUB * i, SUB * j};"),
+    "depth rounded, not floored": ("int64_t k = floor_div(depth, SUB);",
+                                   "int64_t k = floor_div(depth + SUB / 2, SUB);"),
+    "dominant axis = smallest component": ("if (ax >= ay && ax >= az)",
+                                           "if (ax <= ay && ax <= az)"),
+    "first writer wins": ("stats[0] += 1;\n        owner_out[vox]",
+                          "stats[0] += 1;\n        if (owner_out[vox]) continue;\n"
+                          "        owner_out[vox]"),
+    "back-facing light not clamped": ("if (lam < 0.0) lam = 0.0;", ""),
+    "x-dominant swizzle transposed": ("au = 2;\n      av = 1;", "au = 1;\n      av = 2;"),
+    "snap without the origin": ("float a = v - origin;", "float a = v;"),
 }
 
 CHECKS = [name for name in dir(pins) if name.startswith("check_")]
@@ -64,13 +79,16 @@ CHECKS = [name for name in dir(pins) if name.startswith("check_")]
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_mutant_is_caught(name, tmp_path):
     old, new = MUTANTS[name]
-    with open(SRC) as f:
-        text = f.read()
-    assert text.count(old) == 1, f"mutation anchor not unique/found: {old!r}"
-    src = tmp_path / "vct_oracle_mutant.c"
-    src.write_text(text.replace(old, new))
-    lib = oracle.load_library(oracle.compile_source([str(src)], out_dir=str(tmp_path),
-                                                    tag="mutant"))
+    srcs, hits = [], 0
+    for fname in SOURCES:
+        with open(os.path.join(ORACLE_DIR, fname)) as f:
+            text = f.read()
+        hits += text.count(old)
+        src = tmp_path / fname
+        src.write_text(text.replace(old, new))
+        srcs.append(str(src))
+    assert hits == 1, f"mutation anchor not unique/found: {old!r}"
+    lib = oracle.load_library(oracle.compile_source(srcs, out_dir=str(tmp_path), tag="mutant"))
     caught = []
     with oracle.using(lib):
         for check in CHECKS:
