@@ -394,6 +394,44 @@ def extra_variants(torch, vct, dev):
     return out
 
 
+def extra_revoxelize(torch, vct, dev):
+    """The 1080p room frame with the scene revoxelized every frame (the
+    thesis's continuous-revoxelization measurement, Ch. 6.3.2): the room as a
+    mesh of about 244K triangles -> vct_voxelize -> vct_build_mips ->
+    vct_trace, FP32."""
+    import vct_synth as vs
+    c = vs.config_room_mesh()
+    mesh = vct.Mesh.from_host(c["mesh"], device=dev)
+    n, light = c["scenes"][0]["n"], c["light"]
+    view = vct.View.from_host(c["views"][0], device=dev)
+    params = vct.make_params(c["params"])
+    vws = vct.voxelize_workspace(n, mesh.indices.shape[0], dev)
+    grid = torch.empty((n, n, n, 4), dtype=torch.float32, device=dev)
+    P = vct.Pyramid(n, None, "f32", device=dev)
+    ws = torch.zeros(256, dtype=torch.uint8, device=dev)
+
+    def vox():
+        vct.voxelize(mesh, n, light=light, out=grid, workspace=vws)
+
+    def vox_mips():
+        vox()
+        vct.build_mips(grid, out=P)
+
+    def frame():
+        vox_mips()
+        vct.trace([P], [view], params, workspace=ws)
+
+    v_ms = _time(torch, vox, 10)
+    vm_ms = _time(torch, vox_mips, 10)
+    f_ms = _time(torch, frame, 10)
+    st = vct.read_voxelize_stats(vws)
+    samples = int(sum(vct.read_stats(ws)["samples"]))
+    return {"workload": f"room{n}_1080p_f32_revoxelized", "triangles": int(mesh.indices.shape[0]),
+            "fragments": st["fragments"], "voxelize_ms": v_ms, "voxelize_mips_ms": vm_ms,
+            "frame_ms": f_ms, "mtriangles_per_s": mesh.indices.shape[0] / (v_ms / 1e3) / 1e6,
+            "gsamples_per_s": samples / (f_ms / 1e3) / 1e9}
+
+
 def extra_fwd_bwd(torch, vct, dev, n=128, n_views=32, res=512):
     """Learnable 128^3 grid at 0.1, 32 views of 512x512 of a ground-truth box
     scene, L2 loss: forward (mips + trace) and forward + adjoint (trace
@@ -479,7 +517,8 @@ def run_extras(torch, vct, dev, args):
     """Secondary measurements reported beside the main metric."""
     out = {}
     for name, fn in (("fp16_single_view", extra_fp16_single), ("variants", extra_variants),
-                     ("fwd_bwd", extra_fwd_bwd), ("batched_fp16", extra_batched)):
+                     ("revoxelize", extra_revoxelize), ("fwd_bwd", extra_fwd_bwd),
+                     ("batched_fp16", extra_batched)):
         if name == "batched_fp16" and args.no_batched:
             continue
         try:

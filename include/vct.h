@@ -328,6 +328,78 @@ vct_status vct_trace_backward_noalloc(const vct_pyramid *pyr, const vct_view *vi
                                       float *grad_level0_dense, vct_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Voxelization (Ch. 4.4, Ch. 5.4.4 voxelize())                             */
+/* ------------------------------------------------------------------------ */
+/*
+ * A triangle mesh in device memory.  Triangles are double sided; their
+ * geometric normal (v2 - v1) x (v3 - v1) lights them.
+ */
+typedef struct {
+  const float *vertices;  /* [n_vertices][3] scene units, 4-byte aligned      */
+  const int32_t *indices; /* [n_triangles][3] vertex indices                  */
+  const float *colors;    /* [n_triangles][3] material colour per triangle    */
+  int32_t n_vertices;     /* >= 0                                             */
+  int32_t n_triangles;    /* 0 .. 2^30                                        */
+} vct_mesh;
+
+/* The directional light whose direct diffuse light the voxels store. */
+typedef struct {
+  float light_dir[3];   /* towards the light, as given (not normalised)        */
+  float light_color[3]; /* RGB intensity                                       */
+  float ambient;        /* ambient strength of the Phong model                 */
+  float diffuse_str;    /* diffuse strength of the Phong model                 */
+} vct_voxel_light;
+
+/* Counters at the start of the voxelization workspace after a call. */
+typedef struct {
+  uint64_t fragments;       /* fragments that landed inside the grid           */
+  uint64_t large_items;     /* work items of the triangles rasterised by warps */
+  uint64_t item_cursor;     /* internal                                        */
+  uint32_t skipped;         /* triangles with a bad index or a vertex out of range */
+  uint32_t degenerate;      /* triangles of zero area after snapping           */
+  uint32_t large_triangles; /* triangles whose bounding box exceeds 64 pixels  */
+  uint32_t reserved;
+} vct_voxelize_stats;
+
+/* Device workspace vct_voxelize needs for an n^3 grid and a mesh of
+ * n_triangles; 0 for invalid arguments.  Layout: a vct_voxelize_stats
+ * padded to 256 bytes; the owner grid, n^3 uint32 in the level-0 layout
+ * (triangle index + 1 of the voxel's fragment, 0 = empty); then 32 bytes
+ * per triangle of internal tables (256-byte aligned). */
+size_t vct_voxelize_workspace_bytes(int32_t n, int32_t n_triangles);
+
+/*
+ * Voxelizes `mesh` into the dense level-0 grid [n][n][n][4] float32 (z, y,
+ * x, rgba) that vct_build_mips takes, covering the cube [origin, origin +
+ * size)^3 (Ch. 4.4; Ch. 5.4.4 voxelize()).  The grid is cleared first.
+ * Every triangle is rasterised once, orthographically along its dominant
+ * axis (the largest component of |(v2 - v1) x (v3 - v1)|, the first on ties;
+ * Ch. 4.4.2) on an n x n viewport; each pixel whose centre it covers gives a
+ * fragment at the triangle's depth there, stored in its voxel as
+ *   (colour * light_color * (ambient + diffuse_str * max(N . l, 0)), 1)
+ * (Ch. 4.4.3: the Phong model without its glossy term; N the normalised
+ * geometric normal).  Rules the thesis leaves to the OpenGL rasteriser:
+ *   - vertices snap to 1/256 voxel: X = rint(float32(float32(v - origin) * s))
+ *     with s = float32(256 n / size); a triangle with a snapped coordinate of
+ *     magnitude >= 2^19 or a bad index is skipped, one of zero snapped area
+ *     is degenerate (both counted in the stats);
+ *   - pixel centres at (i + 1/2) voxels; a centre on an edge counts for top
+ *     and left edges of the counter-clockwise projection only (adjacent
+ *     triangles cover it once); the depth cell is the floor of the exact
+ *     plane depth; fragments outside the grid are dropped;
+ *   - where several triangles reach a voxel, the highest triangle index wins
+ *     (serial draw order), so the result does not depend on scheduling.
+ * The coverage, depth and winner decisions are exact integer arithmetic;
+ * only the colour is float32.  level0_dense: n^3 * 16 bytes, 16-byte
+ * aligned.  workspace: vct_voxelize_workspace_bytes(n, n_triangles) bytes,
+ * 256-byte aligned; on return (stream order) it holds the stats and the
+ * owner grid.  n is a power of two in [2, 1024]; size > 0.
+ */
+vct_status vct_voxelize(const vct_mesh *mesh, int32_t n, const float origin[3], float size,
+                        const vct_voxel_light *light, float *level0_dense, void *workspace,
+                        size_t workspace_bytes, vct_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Diagnostics                                                              */
 /* ------------------------------------------------------------------------ */
 const char *vct_status_string(vct_status status);

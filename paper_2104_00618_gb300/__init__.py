@@ -9,6 +9,7 @@ Main entry points
     build_mips(level0, ...)          -> Pyramid            (rows a1 + a2)
     trace(pyramids, views, params)   -> per-view outputs   (rows a3 .. a6)
     trace_backward(...)              -> dL/d level-0 grid   (rows a7 + a8)
+    voxelize(mesh, n, ...)           -> dense level-0 grid  (row f2)
     TraceFn / render(...)            -> torch.autograd wrapper
 """
 from __future__ import annotations
@@ -21,13 +22,15 @@ import torch
 
 from . import _abi
 from ._abi import (FLAG_DIFFUSE_FIRST_HIT, FLAG_OCC_SMOOTH, FLAG_SHADE, FLAG_SHADE_IMPL,
-                   FLAG_SPEC_GRACE, VCT_F16, VCT_F32, VctError, VctLaunchConfig, VctPyramid,
-                   VctTraceParams, VctTraceStats, VctView, VctViewGrad, check, load)
+                   FLAG_SPEC_GRACE, VCT_F16, VCT_F32, VctError, VctLaunchConfig, VctMesh,
+                   VctPyramid, VctTraceParams, VctTraceStats, VctView, VctViewGrad,
+                   VctVoxelizeStats, VctVoxelLight, check, load)
 
 __all__ = ["Pyramid", "build_mips", "read_level", "pyramid_status", "make_params", "trace",
            "trace_backward", "autotune", "read_stats", "TraceFn", "render", "VctError",
            "launch_config", "num_levels", "lib", "FLAG_OCC_SMOOTH", "FLAG_SPEC_GRACE",
-           "FLAG_DIFFUSE_FIRST_HIT", "FLAG_SHADE", "FLAG_SHADE_IMPL"]
+           "FLAG_DIFFUSE_FIRST_HIT", "FLAG_SHADE", "FLAG_SHADE_IMPL", "Mesh", "voxelize",
+           "voxelize_workspace", "read_voxelize_stats", "voxel_owner"]
 
 DTYPES = {"f32": VCT_F32, "f16": VCT_F16, VCT_F32: VCT_F32, VCT_F16: VCT_F16}
 
@@ -305,3 +308,72 @@ def render(level0: torch.Tensor, view: View, params, levels=None, origin=(0.0, 0
     """Differentiable (D, S, Vis) of one view from a level-0 grid."""
     P = params if isinstance(params, VctTraceParams) else make_params(params)
     return TraceFn.apply(level0, view, P, levels, origin, size)
+
+
+# ---------------------------------------------------------------------------
+# voxelization
+# ---------------------------------------------------------------------------
+@dataclass
+class Mesh:
+    """Triangle mesh on the device: vertices [V,3] float32, indices [T,3]
+    int32, colors [T,3] float32 (material colour per triangle)."""
+    vertices: torch.Tensor
+    indices: torch.Tensor
+    colors: torch.Tensor
+
+    @staticmethod
+    def from_host(m: dict, device="cuda") -> "Mesh":
+        def dev(a, dt):
+            return torch.as_tensor(a).to(device=device, dtype=dt).contiguous()
+        return Mesh(dev(m["vertices"], torch.float32).reshape(-1, 3),
+                    dev(m["indices"], torch.int32).reshape(-1, 3),
+                    dev(m["colors"], torch.float32).reshape(-1, 3))
+
+    def struct(self) -> VctMesh:
+        return VctMesh(_ptr(self.vertices), _ptr(self.indices), _ptr(self.colors),
+                       self.vertices.shape[0], self.indices.shape[0])
+
+
+def voxelize_workspace(n: int, n_triangles: int, device="cuda") -> torch.Tensor:
+    nbytes = lib().vct_voxelize_workspace_bytes(int(n), int(n_triangles))
+    if nbytes == 0:
+        raise VctError(_abi.VCT_ERR_INVALID_ARG, f"invalid voxelize size n={n}")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def voxelize(mesh: Mesh, n: int, origin=(0.0, 0.0, 0.0), size: float = 1.0,
+             light: dict | None = None, out: torch.Tensor | None = None,
+             workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Voxelizes the mesh into a dense float32 [n,n,n,4] grid (z,y,x,rgba).
+    light: dict(light_dir, light_color, ambient, diffuse_str)."""
+    light = light or {}
+    L = VctVoxelLight()
+    ld = [float(v) for v in light.get("light_dir", (0.0, 1.0, 0.0))]
+    lc = [float(v) for v in light.get("light_color", (1.0, 1.0, 1.0))]
+    for a in range(3):
+        L.light_dir[a], L.light_color[a] = ld[a], lc[a]
+    L.ambient = float(light.get("ambient", 0.0))
+    L.diffuse_str = float(light.get("diffuse_str", 1.0))
+    dev = mesh.vertices.device
+    if out is None:
+        out = torch.empty((n, n, n, 4), dtype=torch.float32, device=dev)
+    ws = workspace if workspace is not None else voxelize_workspace(n, mesh.indices.shape[0], dev)
+    m = mesh.struct()
+    org = (ctypes.c_float * 3)(*[float(v) for v in origin])
+    check(lib().vct_voxelize(ctypes.byref(m), int(n), org, float(size), ctypes.byref(L),
+                             _ptr(out), _ptr(ws), ws.numel(), _stream(stream)), "vct_voxelize")
+    return out
+
+
+def read_voxelize_stats(workspace: torch.Tensor) -> dict:
+    raw = workspace[:ctypes.sizeof(VctVoxelizeStats)].cpu().numpy().tobytes()
+    st = VctVoxelizeStats.from_buffer_copy(raw)
+    return {"fragments": int(st.fragments), "skipped": int(st.skipped),
+            "degenerate": int(st.degenerate), "large_triangles": int(st.large_triangles),
+            "large_items": int(st.large_items)}
+
+
+def voxel_owner(workspace: torch.Tensor, n: int) -> torch.Tensor:
+    """The owner grid of the last vct_voxelize on this workspace: [n,n,n]
+    int32, triangle index + 1 per voxel (0 = empty)."""
+    return workspace[256:256 + 4 * n * n * n].view(torch.int32).reshape(n, n, n)

@@ -62,6 +62,23 @@ class VctViewGrad(ctypes.Structure):
     _fields_ = [("grad_diffuse", _vp), ("grad_specular", _vp), ("grad_visibility", _vp)]
 
 
+class VctMesh(ctypes.Structure):
+    _fields_ = [("vertices", _vp), ("indices", _vp), ("colors", _vp), ("n_vertices", _c_i32),
+                ("n_triangles", _c_i32)]
+
+
+class VctVoxelLight(ctypes.Structure):
+    _fields_ = [("light_dir", _c_f32 * 3), ("light_color", _c_f32 * 3), ("ambient", _c_f32),
+                ("diffuse_str", _c_f32)]
+
+
+class VctVoxelizeStats(ctypes.Structure):
+    _fields_ = [("fragments", ctypes.c_uint64), ("large_items", ctypes.c_uint64),
+                ("item_cursor", ctypes.c_uint64), ("skipped", ctypes.c_uint32),
+                ("degenerate", ctypes.c_uint32), ("large_triangles", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
 EXPORTS = {
     "vct_pyramid_bytes": (ctypes.c_size_t, [_c_i32, _c_i32, _c_i32]),
     "vct_pyramid_level_offset": (_c_u64, [_c_i32, _c_i32, _c_i32, _c_i32]),
@@ -85,6 +102,9 @@ EXPORTS = {
                                             ctypes.POINTER(VctViewGrad), _c_i32,
                                             ctypes.POINTER(VctTraceParams),
                                             ctypes.POINTER(VctLaunchConfig), _vp, _vp]),
+    "vct_voxelize_workspace_bytes": (ctypes.c_size_t, [_c_i32, _c_i32]),
+    "vct_voxelize": (_c_i32, [ctypes.POINTER(VctMesh), _c_i32, ctypes.POINTER(_c_f32), _c_f32,
+                              ctypes.POINTER(VctVoxelLight), _vp, _vp, ctypes.c_size_t, _vp]),
     "vct_status_string": (ctypes.c_char_p, [_c_i32]),
     "vct_last_error": (ctypes.c_char_p, []),
     "vct_version": (_c_i32, []),

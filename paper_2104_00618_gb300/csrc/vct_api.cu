@@ -15,7 +15,7 @@
 #include <tuple>
 #include <vector>
 
-#include "vct_internal.cuh"
+#include "voxelize.cuh"
 
 using namespace vct;
 
@@ -627,6 +627,45 @@ vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
   e = launch_mip_adjoint(reinterpret_cast<const float *>(ws), gl, pyr->n, pyr->levels,
                          grad_level0_dense, s);
   if (e != cudaSuccess) return cuda_fail(e, "vct_trace_backward mip adjoint launch");
+  return VCT_OK;
+}
+
+size_t vct_voxelize_workspace_bytes(int32_t n, int32_t n_triangles) {
+  if (!is_pow2(n) || n < 2 || n > 1024 || n_triangles < 0 || n_triangles > (1 << 30)) return 0;
+  return voxelize_workspace_bytes(n, n_triangles);
+}
+
+vct_status vct_voxelize(const vct_mesh *mesh, int32_t n, const float origin[3], float size,
+                        const vct_voxel_light *light, float *level0_dense, void *workspace,
+                        size_t workspace_bytes, vct_stream_t stream) {
+  if (!mesh || !light || !origin) return fail(VCT_ERR_INVALID_ARG, "vct_voxelize: NULL argument");
+  if (!is_pow2(n) || n < 2 || n > 1024)
+    return fail(VCT_ERR_INVALID_ARG, "vct_voxelize: n=%d must be a power of two in [2, 1024]", n);
+  if (!(size > 0.0f) || !finite(size) || !finite(origin[0]) || !finite(origin[1]) ||
+      !finite(origin[2]))
+    return fail(VCT_ERR_INVALID_ARG, "vct_voxelize: bad origin/size");
+  if (mesh->n_vertices < 0 || mesh->n_triangles < 0 || mesh->n_triangles > (1 << 30))
+    return fail(VCT_ERR_INVALID_ARG, "vct_voxelize: bad mesh counts (%d vertices, %d triangles)",
+                mesh->n_vertices, mesh->n_triangles);
+  if (mesh->n_triangles > 0 &&
+      (!mesh->indices || !mesh->colors || !aligned(mesh->indices, 4) || !aligned(mesh->colors, 4)))
+    return fail(VCT_ERR_INVALID_ARG, "vct_voxelize: indices/colors NULL or misaligned");
+  if (mesh->n_vertices > 0 && (!mesh->vertices || !aligned(mesh->vertices, 4)))
+    return fail(VCT_ERR_INVALID_ARG, "vct_voxelize: vertices NULL or misaligned");
+  for (int a = 0; a < 3; ++a)
+    if (!finite(light->light_dir[a]) || !finite(light->light_color[a]))
+      return fail(VCT_ERR_INVALID_ARG, "vct_voxelize: light not finite");
+  if (!finite(light->ambient) || !finite(light->diffuse_str))
+    return fail(VCT_ERR_INVALID_ARG, "vct_voxelize: light strengths not finite");
+  if (!level0_dense || !aligned(level0_dense, 16))
+    return fail(VCT_ERR_INVALID_ARG, "vct_voxelize: output NULL or not 16-byte aligned");
+  const size_t need = voxelize_workspace_bytes(n, mesh->n_triangles);
+  if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
+    return fail(VCT_ERR_WORKSPACE, "vct_voxelize: workspace needs %zu bytes, 256-byte aligned",
+                need);
+  cudaError_t e = launch_voxelize(*mesh, n, origin, size, *light, level0_dense, workspace,
+                                  sm_count(), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "vct_voxelize launch");
   return VCT_OK;
 }
 

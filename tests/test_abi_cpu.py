@@ -147,3 +147,34 @@ def test_variant_flag_validation_without_gpu(lib):
         st = lib.vct_trace_backward(ctypes.byref(p), ctypes.byref(v), ctypes.byref(g), 1,
                                     ctypes.byref(prm), None, None, None, 0, None)
         assert st == want, (flags, lib.vct_last_error())
+
+
+def test_voxelize_structs_and_validation(lib):
+    assert ctypes.sizeof(_abi.VctMesh) == 32
+    assert ctypes.sizeof(_abi.VctVoxelLight) == 32
+    assert ctypes.sizeof(_abi.VctVoxelizeStats) == 40
+    n = 64
+    assert lib.vct_voxelize_workspace_bytes(n, 0) == 256 + 4 * n ** 3
+    assert lib.vct_voxelize_workspace_bytes(n, 1000) == 256 + 4 * n ** 3 + 16128 + 2 * 8192
+    assert lib.vct_voxelize_workspace_bytes(48, 10) == 0
+    assert lib.vct_voxelize_workspace_bytes(2048, 10) == 0
+    m = _abi.VctMesh(1024, 2048, 4096, 3, 1)
+    L = _abi.VctVoxelLight((ctypes.c_float * 3)(0, 1, 0), (ctypes.c_float * 3)(1, 1, 1), 0.0, 1.0)
+    org = (ctypes.c_float * 3)(0, 0, 0)
+    ws_need = lib.vct_voxelize_workspace_bytes(n, 1)
+
+    def run(mesh=m, nn=n, size=1.0, out=8192, ws=1 << 20, ws_bytes=ws_need):
+        return lib.vct_voxelize(ctypes.byref(mesh), nn, org, size, ctypes.byref(L), out, ws,
+                                ws_bytes, None)
+
+    assert run(nn=48) == _abi.VCT_ERR_INVALID_ARG
+    assert run(size=0.0) == _abi.VCT_ERR_INVALID_ARG
+    assert run(out=8200) == _abi.VCT_ERR_INVALID_ARG
+    assert run(ws_bytes=ws_need - 1) == _abi.VCT_ERR_WORKSPACE
+    assert run(ws=(1 << 20) + 8) == _abi.VCT_ERR_WORKSPACE
+    bad = _abi.VctMesh(1024, 0, 4096, 3, 1)
+    assert run(mesh=bad) == _abi.VCT_ERR_INVALID_ARG
+    neg = _abi.VctMesh(1024, 2048, 4096, -1, 1)
+    assert run(mesh=neg) == _abi.VCT_ERR_INVALID_ARG
+    L.light_dir[1] = float("inf")
+    assert run() == _abi.VCT_ERR_INVALID_ARG

@@ -339,6 +339,97 @@ def interior_view(scene, width, height, rng, with_roughness=True):
     return view_dict(pos, nrm, mask, width, height, cam, roughness=rough)
 
 
+# --------------------------------------------------------------------------
+# triangle meshes (input of the voxelizer)
+# --------------------------------------------------------------------------
+def _quad_grid(c0, c1, c2, c3, tess):
+    """tess x tess grid of quads over the bilinear patch c0 c1 c2 c3 (counter-
+    clockwise seen from the side the face looks at): vertices, triangles."""
+    t = np.linspace(0.0, 1.0, tess + 1)
+    u, v = np.meshgrid(t, t, indexing="xy")
+    u, v = u[..., None], v[..., None]
+    p = ((1 - u) * (1 - v) * c0 + u * (1 - v) * c1 + u * v * c2 + (1 - u) * v * c3)
+    verts = p.reshape(-1, 3)
+    a, b = np.meshgrid(np.arange(tess), np.arange(tess), indexing="xy")
+    i00 = (b * (tess + 1) + a).ravel()
+    i10, i01 = i00 + 1, i00 + tess + 1
+    i11 = i01 + 1
+    tris = np.concatenate([np.stack([i00, i10, i11], 1), np.stack([i00, i11, i01], 1)])
+    return verts, tris
+
+
+def _box_faces(a, b, e, outward):
+    """Six faces of the box with planes through a and b (voxel units), each
+    extended in-plane to [a - e, b + e]; normals outward or inward."""
+    faces = []
+    for axis in range(3):
+        u, v = [x for x in range(3) if x != axis]
+        for side, pos in ((-1.0, a[axis]), (1.0, b[axis])):
+            cs = []
+            for cu, cv in ((a[u] - e, a[v] - e), (b[u] + e, a[v] - e), (b[u] + e, b[v] + e),
+                           (a[u] - e, b[v] + e)):
+                p = np.zeros(3)
+                p[axis], p[u], p[v] = pos, cu, cv
+                cs.append(p)
+            nrm = np.zeros(3)
+            nrm[axis] = side if outward else -side
+            if np.cross(cs[1] - cs[0], cs[2] - cs[0]) @ nrm < 0:
+                cs = [cs[0], cs[3], cs[2], cs[1]]
+            faces.append((cs, axis, side))
+    return faces
+
+
+def _uv_sphere(c, r, stacks, slices):
+    th = np.linspace(0.0, math.pi, stacks + 1)
+    ph = np.linspace(0.0, 2.0 * math.pi, slices + 1)
+    T, Ph = np.meshgrid(th, ph, indexing="ij")
+    p = np.stack([np.sin(T) * np.cos(Ph), np.cos(T), np.sin(T) * np.sin(Ph)], -1)
+    verts = (c + r * p).reshape(-1, 3)
+    a, b = np.meshgrid(np.arange(slices), np.arange(stacks), indexing="xy")
+    i00 = (b * (slices + 1) + a).ravel()
+    i10, i01 = i00 + 1, i00 + slices + 1
+    i11 = i01 + 1
+    # outward: (p10 - p00) x (p11 - p00) points away from the centre
+    tris = np.concatenate([np.stack([i00, i11, i10], 1), np.stack([i00, i01, i11], 1)])
+    return verts, tris
+
+
+def scene_mesh(scene, tess=1, n_spheres=0, sphere_res=(32, 64), seed=0):
+    """Triangle mesh of a box scene: every box as six faces whose planes run
+    through the centres of its outermost voxel layers (in-plane inset 1/4
+    voxel), the room as six inward walls through the centres of the wall
+    voxels, each face a tess x tess grid of quads; plus n_spheres UV spheres
+    (random centre, radius n/24 .. n/10, random colour).  Scene units: the
+    grid spans [0, 1]^3.  Returns dict(vertices float32 [V,3], indices int32
+    [T,3], colors float32 [T,3])."""
+    n = scene["n"]
+    V, I, C = [], [], []
+    count = 0
+
+    def add(verts, tris, colour):
+        nonlocal count
+        V.append(verts)
+        I.append(tris + count)
+        C.append(np.broadcast_to(np.asarray(colour, np.float64), (len(tris), 3)))
+        count += len(verts)
+
+    if scene.get("room"):
+        walls = {(0, -1.0): RED, (0, 1.0): GREEN}
+        for cs, axis, side in _box_faces(np.full(3, 0.5), np.full(3, n - 0.5), 0.25, False):
+            add(*_quad_grid(*cs, tess), walls.get((axis, side), GREY))
+    for lo, hi, col in scene["boxes"]:
+        for cs, _, _ in _box_faces(np.asarray(lo) + 0.5, np.asarray(hi) - 0.5, 0.25, True):
+            add(*_quad_grid(*cs, tess), col)
+    rng = np.random.default_rng(seed)
+    for _ in range(n_spheres):
+        r = rng.uniform(n / 24.0, n / 10.0)
+        c = rng.uniform(r + 1.0, n - r - 1.0, size=3)
+        add(*_uv_sphere(c, r, *sphere_res), rng.random(3))
+    verts = np.concatenate(V) / n
+    return {"vertices": verts.astype(np.float32), "indices": np.concatenate(I).astype(np.int32),
+            "colors": np.concatenate(C).astype(np.float32)}
+
+
 def albedo(width, height, seed):
     """Per-pixel material colour in [0.2, 1] (float32 [H*W, 3])."""
     rng = np.random.default_rng(seed)
@@ -373,6 +464,20 @@ def config_room_1080p(n=256, n_boxes=32, width=1920, height=1080, seed=2):
     return {"name": f"{n}^3 room + {n_boxes} boxes, {width}x{height}, 9 diffuse + "
                     "1 specular + 1 occlusion cone",
             "scenes": [scene], "views": [view], "params": params_room9(scene["light"])}
+
+
+def config_room_mesh(n=256, n_boxes=32, seed=2, tess=24, n_spheres=4, width=1920,
+                     height=1080):
+    """The 256^3 room of config_room_1080p as a triangle mesh for per-frame
+    revoxelization: tess 24 quads per face edge and four UV spheres, about
+    244K triangles (a high-polygon scene), plus the 1080p view of the room."""
+    c = config_room_1080p(n=n, n_boxes=n_boxes, width=width, height=height, seed=seed)
+    scene = c["scenes"][0]
+    c["mesh"] = scene_mesh(scene, tess=tess, n_spheres=n_spheres, seed=seed + 100)
+    c["light"] = {"light_dir": np.asarray(scene["light"], np.float64),
+                  "light_color": (1.0, 1.0, 1.0), "ambient": 0.0, "diffuse_str": 1.0}
+    c["name"] += f", mesh of {len(c['mesh']['indices'])} triangles"
+    return c
 
 
 def config_batched(grids=(128, 256, 256, 512), views_per_scene=64, n_boxes=32,
