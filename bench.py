@@ -432,6 +432,39 @@ def extra_revoxelize(torch, vct, dev):
             "gsamples_per_s": samples / (f_ms / 1e3) / 1e9}
 
 
+def extra_bricks(torch, vct, dev, n=512):
+    """Brick storage at 512^3: the room voxelized from its mesh (surface
+    shells), pyramid bytes dense vs bricks, mip build and 1080p trace time in
+    both layouts (same frame, identical outputs)."""
+    import vct_synth as vs
+    scene = vs.box_scene(n, 32, 2, room=True)
+    mesh = vct.Mesh.from_host(vs.scene_mesh(scene, tess=24, n_spheres=4, seed=102), device=dev)
+    rng = np.random.default_rng(2)
+    hv = vs.interior_view(scene, 1920, 1080, rng)
+    params = vct.make_params(vs.params_room9(scene["light"]))
+    del scene
+    level0 = vct.voxelize(mesh, n, light={"light_dir": (0.36, 0.8, 0.48)})
+    view = vct.View.from_host(hv, device=dev)
+    ws = torch.zeros(256, dtype=torch.uint8, device=dev)
+    out = {"workload": f"room{n}_mesh_1080p_f32", "triangles": int(mesh.indices.shape[0])}
+    t0 = time.perf_counter()
+    occ, _ = vct.plan_bricks(level0)
+    out["plan_ms"] = (time.perf_counter() - t0) * 1e3
+    for name in ("dense", "bricks"):
+        P = (vct.Pyramid(n, None, "f32", device=dev) if name == "dense" else
+             vct.Pyramid(n, None, "f32", device=dev, layout="bricks", occupied=occ))
+        build_ms = _time(torch, lambda: vct.build_mips(level0, out=P), 5)
+        trace_ms = _time(torch, lambda: vct.trace([P], [view], params, workspace=ws), 5)
+        samples = int(sum(vct.read_stats(ws)["samples"]))
+        out[name] = {"pyramid_bytes": int(P.storage.numel()), "build_ms": build_ms,
+                     "trace_ms": trace_ms, "gsamples_per_s": samples / (trace_ms / 1e3) / 1e9}
+        del P
+        torch.cuda.empty_cache()
+    out["occupied_bricks"] = occ
+    out["bytes_ratio"] = out["bricks"]["pyramid_bytes"] / out["dense"]["pyramid_bytes"]
+    return out
+
+
 def extra_fwd_bwd(torch, vct, dev, n=128, n_views=32, res=512):
     """Learnable 128^3 grid at 0.1, 32 views of 512x512 of a ground-truth box
     scene, L2 loss: forward (mips + trace) and forward + adjoint (trace
@@ -517,7 +550,8 @@ def run_extras(torch, vct, dev, args):
     """Secondary measurements reported beside the main metric."""
     out = {}
     for name, fn in (("fp16_single_view", extra_fp16_single), ("variants", extra_variants),
-                     ("revoxelize", extra_revoxelize), ("fwd_bwd", extra_fwd_bwd),
+                     ("revoxelize", extra_revoxelize), ("bricks_512", extra_bricks),
+                     ("fwd_bwd", extra_fwd_bwd),
                      ("batched_fp16", extra_batched)):
         if name == "batched_fp16" and args.no_batched:
             continue

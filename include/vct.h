@@ -77,23 +77,63 @@ typedef enum { VCT_F32 = 0, VCT_F16 = 1 } vct_dtype;
  * header holds a device status word written by bounded waits
  * (vct_pyramid_status).  The FP32 staging area exists for VCT_F16 only and
  * holds the unrounded values of one intermediate level during the build.
+ *
+ * VCT_LAYOUT_BRICKS (sparse storage: the brick pool of Crassin et al.'s
+ * sparse voxel octree, Ch. 5.1 "Previous Work", with one flat slot table per
+ * level instead of the tree): every level with at least 16 texels per axis
+ * is cut into the 8x8x8 bricks above (brick id = morton(x, y, z) >> 9, its
+ * texels the 512 consecutive Morton codes) and stores one uint32 slot per
+ * brick instead of texels.  The bricks live in a pool shared by all levels:
+ * slot 0 is an all-zero brick to which every empty brick points, occupied
+ * bricks take slots 1, 2, ... in level order, then brick order.  A level-0
+ * brick is occupied if any channel of any of its texels is non-zero; a brick
+ * of level l+1 if any of its 8 child bricks is.  Smaller levels are stored
+ * dense.  Layout:
+ *   [256-byte header][per level: slot table or texels][FP32 staging][pool]
+ * The header also holds the occupied-brick count (uint64 at byte 8).  The
+ * texel values are exactly those of the dense layout; only empty bricks are
+ * not stored.  vct_pyramid_plan_bricks() sizes such a pyramid.
  */
+#define VCT_LAYOUT_DENSE 0
+#define VCT_LAYOUT_BRICKS 1
+
 typedef struct {
   int32_t n;        /* level-0 voxels per axis: a power of two in [2, 1024]  */
   int32_t levels;   /* number of levels, 1 .. log2(n) + 1                    */
   int32_t dtype;    /* vct_dtype of the stored texels                        */
-  int32_t reserved; /* must be 0                                             */
+  int32_t layout;   /* VCT_LAYOUT_DENSE or VCT_LAYOUT_BRICKS                  */
   float origin[3];  /* scene position of the grid's minimum corner           */
   float size;       /* scene edge length of the grid, > 0                    */
   void *data;       /* device memory, >= vct_pyramid_bytes(n, levels, dtype) */
   uint64_t bytes;   /* size of `data` in bytes                               */
 } vct_pyramid;
 
-/* Bytes a pyramid of this shape needs; 0 if the shape is invalid. */
+/* Bytes a dense pyramid of this shape needs; 0 if the shape is invalid. */
 size_t vct_pyramid_bytes(int32_t n, int32_t levels, int32_t dtype);
 
-/* Byte offset of `level` from pyramid.data; 0 if the arguments are invalid
- * (level 0 itself starts at 256). */
+/* Bytes a VCT_LAYOUT_BRICKS pyramid of this shape with `occupied` occupied
+ * bricks (all levels) needs; 0 if the shape is invalid. */
+size_t vct_pyramid_bytes_bricks(int32_t n, int32_t levels, int32_t dtype, uint64_t occupied);
+
+/* Device scratch vct_pyramid_plan_bricks needs (the fixed part of the brick
+ * layout: header, slot tables, small levels, staging); 0 if invalid. */
+size_t vct_pyramid_plan_scratch_bytes(int32_t n, int32_t levels, int32_t dtype);
+
+/*
+ * Counts the bricks that a VCT_LAYOUT_BRICKS pyramid of the dense level-0
+ * grid `level0_dense` ([n][n][n][4] float32, 16-byte aligned) occupies and
+ * returns that count and vct_pyramid_bytes_bricks() for it.  Runs on
+ * `stream` and waits for it (the host needs the count to allocate).
+ * scratch: vct_pyramid_plan_scratch_bytes() bytes of device memory,
+ * 256-byte aligned, overwritten.
+ */
+vct_status vct_pyramid_plan_bricks(const float *level0_dense, int32_t n, int32_t levels,
+                                   int32_t dtype, void *scratch, size_t scratch_bytes,
+                                   uint64_t *occupied_out, uint64_t *bytes_out,
+                                   vct_stream_t stream);
+
+/* Byte offset of `level` from pyramid.data in the dense layout; 0 if the
+ * arguments are invalid (level 0 itself starts at 256). */
 uint64_t vct_pyramid_level_offset(int32_t n, int32_t levels, int32_t dtype,
                                   int32_t level);
 
@@ -106,8 +146,12 @@ uint64_t vct_pyramid_level_offset(int32_t n, int32_t levels, int32_t dtype,
  * Level l+1 is the plain average of the 8 children of level l, computed in
  * float32 from the float32 values of level l; VCT_F16 pyramids store each
  * level rounded to nearest-even after it has been computed in float32.
+ * A VCT_LAYOUT_BRICKS pyramid gets the same texel values; its occupancy is
+ * recomputed from level0_dense.  If its pool cannot hold the occupied bricks
+ * (pyr->bytes below vct_pyramid_bytes_bricks() for this grid) every brick is
+ * left empty and vct_pyramid_status() reports VCT_ERR_WORKSPACE.
  * Errors: VCT_ERR_INVALID_ARG for a NULL or misaligned pointer, a bad shape
- * or pyr->bytes too small; VCT_ERR_CUDA if a launch fails.
+ * or pyr->bytes below the layout's fixed part; VCT_ERR_CUDA if a launch fails.
  */
 vct_status vct_build_mips(const float *level0_dense, const vct_pyramid *pyr,
                           vct_stream_t stream);
@@ -123,7 +167,8 @@ vct_status vct_pyramid_read_level(const vct_pyramid *pyr, int32_t level,
  * Synchronises `stream`, then reads and clears the status word in the
  * pyramid header.  Returns VCT_ERR_TIMEOUT if a kernel that wrote this
  * pyramid gave up a bounded wait (the pyramid contents are then undefined),
- * VCT_OK otherwise.
+ * VCT_ERR_WORKSPACE if a brick pyramid's pool was too small for its occupied
+ * bricks (see vct_build_mips), VCT_OK otherwise.
  */
 vct_status vct_pyramid_status(const vct_pyramid *pyr, vct_stream_t stream);
 

@@ -18,6 +18,7 @@ import ctypes
 import dataclasses
 from dataclasses import dataclass, field
 
+import numpy as np
 import torch
 
 from . import _abi
@@ -30,9 +31,11 @@ __all__ = ["Pyramid", "build_mips", "read_level", "pyramid_status", "make_params
            "trace_backward", "autotune", "read_stats", "TraceFn", "render", "VctError",
            "launch_config", "num_levels", "lib", "FLAG_OCC_SMOOTH", "FLAG_SPEC_GRACE",
            "FLAG_DIFFUSE_FIRST_HIT", "FLAG_SHADE", "FLAG_SHADE_IMPL", "Mesh", "voxelize",
-           "voxelize_workspace", "read_voxelize_stats", "voxel_owner"]
+           "voxelize_workspace", "read_voxelize_stats", "voxel_owner", "plan_bricks"]
 
 DTYPES = {"f32": VCT_F32, "f16": VCT_F16, VCT_F32: VCT_F32, VCT_F16: VCT_F16}
+LAYOUTS = {"dense": _abi.LAYOUT_DENSE, "bricks": _abi.LAYOUT_BRICKS,
+           _abi.LAYOUT_DENSE: _abi.LAYOUT_DENSE, _abi.LAYOUT_BRICKS: _abi.LAYOUT_BRICKS}
 
 
 def lib():
@@ -60,16 +63,26 @@ def launch_config(tile_w=8, tile_h=8, lanes_per_pixel=1, ctas_per_sm=0) -> VctLa
 # pyramids
 # ---------------------------------------------------------------------------
 class Pyramid:
-    """A pyramid in a caller-owned (PyTorch) device buffer."""
+    """A pyramid in a caller-owned (PyTorch) device buffer.  Dense by default;
+    a brick pyramid (layout="bricks") needs the number of occupied bricks it
+    will hold (see plan_bricks)."""
 
     def __init__(self, n: int, levels: int | None = None, dtype="f32",
-                 origin=(0.0, 0.0, 0.0), size: float = 1.0, device=None):
+                 origin=(0.0, 0.0, 0.0), size: float = 1.0, device=None,
+                 layout: str = "dense", occupied: int | None = None):
         self.n = int(n)
         self.levels = num_levels(n) if levels is None else int(levels)
         self.dtype = DTYPES[dtype]
         self.origin = tuple(float(v) for v in origin)
         self.size = float(size)
-        nbytes = lib().vct_pyramid_bytes(self.n, self.levels, self.dtype)
+        self.layout = LAYOUTS[layout]
+        if self.layout == _abi.LAYOUT_BRICKS:
+            if occupied is None:
+                raise VctError(_abi.VCT_ERR_INVALID_ARG, "a brick pyramid needs `occupied`")
+            nbytes = lib().vct_pyramid_bytes_bricks(self.n, self.levels, self.dtype,
+                                                    int(occupied))
+        else:
+            nbytes = lib().vct_pyramid_bytes(self.n, self.levels, self.dtype)
         if nbytes == 0:
             raise VctError(_abi.VCT_ERR_INVALID_ARG,
                            f"invalid pyramid shape n={n} levels={levels} dtype={dtype}")
@@ -77,22 +90,51 @@ class Pyramid:
         self.storage = torch.empty(nbytes, dtype=torch.uint8, device=dev)
 
     def struct(self) -> VctPyramid:
-        return VctPyramid(self.n, self.levels, self.dtype, 0, (ctypes.c_float * 3)(*self.origin),
-                          self.size, self.storage.data_ptr(), self.storage.numel())
+        return VctPyramid(self.n, self.levels, self.dtype, self.layout,
+                          (ctypes.c_float * 3)(*self.origin), self.size,
+                          self.storage.data_ptr(), self.storage.numel())
+
+    def occupied_bricks(self) -> int:
+        """Occupied-brick count recorded by the last build (brick layout)."""
+        return int(self.storage[8:16].cpu().numpy().view(np.uint64)[0])
 
     def level_offset(self, level: int) -> int:
         return int(lib().vct_pyramid_level_offset(self.n, self.levels, self.dtype, level))
 
 
-def build_mips(level0: torch.Tensor, levels: int | None = None, dtype="f32",
-               origin=(0.0, 0.0, 0.0), size: float = 1.0, out: Pyramid | None = None,
-               stream=None) -> Pyramid:
-    """Morton-pack a dense float32 [n,n,n,4] (z,y,x,c) grid and build its mips."""
+def _check_level0(level0):
     if level0.dtype != torch.float32 or not level0.is_cuda or level0.dim() != 4 \
             or level0.shape[3] != 4 or not level0.is_contiguous():
         raise VctError(_abi.VCT_ERR_INVALID_ARG,
                        "level0 must be a contiguous CUDA float32 tensor [n, n, n, 4]")
+
+
+def plan_bricks(level0: torch.Tensor, levels: int | None = None, dtype="f32",
+                stream=None) -> tuple[int, int]:
+    """(occupied bricks, bytes) of a brick pyramid of this grid (synchronises)."""
+    _check_level0(level0)
     n = level0.shape[0]
+    levels = num_levels(n) if levels is None else int(levels)
+    dt = DTYPES[dtype]
+    sb = lib().vct_pyramid_plan_scratch_bytes(n, levels, dt)
+    scratch = torch.empty(max(sb, 256), dtype=torch.uint8, device=level0.device)
+    occ, nbytes = ctypes.c_uint64(), ctypes.c_uint64()
+    check(lib().vct_pyramid_plan_bricks(_ptr(level0), n, levels, dt, _ptr(scratch), sb,
+                                        ctypes.byref(occ), ctypes.byref(nbytes),
+                                        _stream(stream)), "vct_pyramid_plan_bricks")
+    return int(occ.value), int(nbytes.value)
+
+
+def build_mips(level0: torch.Tensor, levels: int | None = None, dtype="f32",
+               origin=(0.0, 0.0, 0.0), size: float = 1.0, out: Pyramid | None = None,
+               stream=None, layout: str = "dense") -> Pyramid:
+    """Morton-pack a dense float32 [n,n,n,4] (z,y,x,c) grid and build its mips
+    (layout="bricks": plan the brick pool first, then build into it)."""
+    _check_level0(level0)
+    n = level0.shape[0]
+    if out is None and LAYOUTS[layout] == _abi.LAYOUT_BRICKS:
+        occ, _ = plan_bricks(level0, levels, dtype, stream)
+        out = Pyramid(n, levels, dtype, origin, size, level0.device, "bricks", occ)
     pyr = out if out is not None else Pyramid(n, levels, dtype, origin, size, level0.device)
     p = pyr.struct()
     check(lib().vct_build_mips(_ptr(level0), ctypes.byref(p), _stream(stream)), "vct_build_mips")

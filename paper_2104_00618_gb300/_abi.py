@@ -14,6 +14,7 @@ MAX_LEVELS = 11
 VCT_OK, VCT_ERR_INVALID_ARG, VCT_ERR_CUDA, VCT_ERR_WORKSPACE, VCT_ERR_UNSUPPORTED, \
     VCT_ERR_TIMEOUT = range(6)
 VCT_F32, VCT_F16 = 0, 1
+LAYOUT_DENSE, LAYOUT_BRICKS = 0, 1
 FLAG_OCC_SMOOTH, FLAG_SPEC_GRACE, FLAG_DIFFUSE_FIRST_HIT, FLAG_SHADE, FLAG_SHADE_IMPL = \
     1, 2, 4, 8, 16
 
@@ -21,7 +22,7 @@ _c_i32, _c_u64, _c_f32, _vp = ctypes.c_int32, ctypes.c_uint64, ctypes.c_float, c
 
 
 class VctPyramid(ctypes.Structure):
-    _fields_ = [("n", _c_i32), ("levels", _c_i32), ("dtype", _c_i32), ("reserved", _c_i32),
+    _fields_ = [("n", _c_i32), ("levels", _c_i32), ("dtype", _c_i32), ("layout", _c_i32),
                 ("origin", _c_f32 * 3), ("size", _c_f32), ("data", _vp), ("bytes", _c_u64)]
 
 
@@ -82,6 +83,10 @@ class VctVoxelizeStats(ctypes.Structure):
 EXPORTS = {
     "vct_pyramid_bytes": (ctypes.c_size_t, [_c_i32, _c_i32, _c_i32]),
     "vct_pyramid_level_offset": (_c_u64, [_c_i32, _c_i32, _c_i32, _c_i32]),
+    "vct_pyramid_bytes_bricks": (ctypes.c_size_t, [_c_i32, _c_i32, _c_i32, _c_u64]),
+    "vct_pyramid_plan_scratch_bytes": (ctypes.c_size_t, [_c_i32, _c_i32, _c_i32]),
+    "vct_pyramid_plan_bricks": (_c_i32, [_vp, _c_i32, _c_i32, _c_i32, _vp, ctypes.c_size_t,
+                                         ctypes.POINTER(_c_u64), ctypes.POINTER(_c_u64), _vp]),
     "vct_build_mips": (_c_i32, [_vp, ctypes.POINTER(VctPyramid), _vp]),
     "vct_pyramid_read_level": (_c_i32, [ctypes.POINTER(VctPyramid), _c_i32, _vp, _vp]),
     "vct_pyramid_status": (_c_i32, [ctypes.POINTER(VctPyramid), _vp]),

@@ -40,7 +40,7 @@ __device__ __forceinline__ float smoothstep0(float e1, float x) {
 // is small and T precise when alpha is close to one; the loop runs while
 // alpha = 1 - T < 1 in float32 and t <= t_max.  kVar instances also take the
 // Ch. 5.4.4 variants selected by `mode`.
-template <int DT, bool kVar>
+template <int DT, bool kVar, bool BR>
 __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const float w[3],
                                         const ConeConst &cc, float T0, const uint32_t *lut,
                                         uint32_t &nsamp, float &trans, int mode = kPlain,
@@ -53,7 +53,7 @@ __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const fl
     step_at(cc, T0, k, T, lam);
     const float F[3] = {fmaf(T, w[0], A.Of[0]), fmaf(T, w[1], A.Of[1]), fmaf(T, w[2], A.Of[2])};
     LodPick lp;
-    float4 s = sample<DT>(P, A, F, lam, lut, om, lp);
+    float4 s = sample<DT, BR>(P, A, F, lam, lut, om, lp);
     if constexpr (kVar) {
       if (mode == kFirstHit) {
         if (s.w > 0.01f) {
@@ -192,8 +192,9 @@ __device__ __forceinline__ void warp_sort_desc(uint32_t *keys, int n) {
 // warp march cones of similar length together (the aperture, hence the
 // length, varies from pixel to pixel with the roughness).
 // kVar instances add the Ch. 5.4.4 cone variants and the shading epilogue
-// (any VCT_FLAG_* set); the plain instances carry none of that code.
-template <int LPP, int DT, bool kVar>
+// (any VCT_FLAG_* set); the plain instances carry none of that code.  BR
+// instances read brick pyramids (VCT_LAYOUT_BRICKS).
+template <int LPP, int DT, bool kVar, bool BR>
 __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(const __grid_constant__ TraceLaunch L) {
   constexpr int kPixPerRound = 32 / LPP;
   constexpr bool kSortSpec = (LPP == 1);
@@ -279,7 +280,8 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
             if (cs.kind == kOcclusion && (L.var.flags & VCT_FLAG_OCC_SMOOTH)) mode = kOccSmooth;
             if (cs.kind == kDiffuse && (L.var.flags & VCT_FLAG_DIFFUSE_FIRST_HIT)) mode = kFirstHit;
           }
-          float4 r = march<DT, kVar>(P, A, w, cc, T0, s_lut, n_samp[cs.kind], trans, mode, &L.var);
+          float4 r =
+              march<DT, kVar, BR>(P, A, w, cc, T0, s_lut, n_samp[cs.kind], trans, mode, &L.var);
           n_cone[cs.kind] += 1u;
           if constexpr (kVar) {
             if (cs.kind == kSpecular && (L.var.flags & VCT_FLAG_SPEC_GRACE)) {
@@ -366,7 +368,7 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
       const ConeConst cc =
           spec_const(P, L.spec_gmin, L.spec_gmax, L.rough_min, L.beta, L.t0_vox, V.rough, p);
       float trans;
-      float4 r = march<DT, false>(P, A, w, cc, T0, s_lut, n_samp[kSpecular], trans);
+      float4 r = march<DT, false, BR>(P, A, w, cc, T0, s_lut, n_samp[kSpecular], trans);
       n_cone[kSpecular] += 1u;
       if constexpr (kVar) {
         if (L.var.flags & VCT_FLAG_SPEC_GRACE) {
@@ -398,24 +400,29 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
   }
 }
 
-template <int LPP, int DT>
+template <int LPP, int DT, bool BR>
 cudaError_t launch_t(const TraceLaunch &L, int grid, cudaStream_t s) {
   if (L.var.flags)
-    trace_kernel<LPP, DT, true><<<grid, kTraceThreads, 0, s>>>(L);
+    trace_kernel<LPP, DT, true, BR><<<grid, kTraceThreads, 0, s>>>(L);
   else
-    trace_kernel<LPP, DT, false><<<grid, kTraceThreads, 0, s>>>(L);
+    trace_kernel<LPP, DT, false, BR><<<grid, kTraceThreads, 0, s>>>(L);
   return cudaGetLastError();
+}
+
+template <int LPP, int DT>
+cudaError_t launch_l(const TraceLaunch &L, bool br, int grid, cudaStream_t s) {
+  return br ? launch_t<LPP, DT, true>(L, grid, s) : launch_t<LPP, DT, false>(L, grid, s);
 }
 
 template <int LPP, int DT>
 int occ_t(bool var) {
   int b = 0;
   if (var)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<LPP, DT, true>, kTraceThreads,
-                                                  0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<LPP, DT, true, false>,
+                                                  kTraceThreads, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<LPP, DT, false>, kTraceThreads,
-                                                  0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<LPP, DT, false, false>,
+                                                  kTraceThreads, 0);
   return b;
 }
 
@@ -423,13 +430,15 @@ int occ_t(bool var) {
 
 static_assert(sizeof(TraceLaunch) <= 32000, "trace launch parameters exceed the 32 KB limit");
 
-cudaError_t launch_trace(const TraceLaunch &L, int lpp, int dtype, int grid, cudaStream_t s) {
+cudaError_t launch_trace(const TraceLaunch &L, int lpp, int dtype, bool bricks, int grid,
+                         cudaStream_t s) {
   const bool h = dtype == VCT_F16;
+  const bool b = bricks;
   switch (lpp) {
-    case 1: return h ? launch_t<1, VCT_F16>(L, grid, s) : launch_t<1, VCT_F32>(L, grid, s);
-    case 2: return h ? launch_t<2, VCT_F16>(L, grid, s) : launch_t<2, VCT_F32>(L, grid, s);
-    case 4: return h ? launch_t<4, VCT_F16>(L, grid, s) : launch_t<4, VCT_F32>(L, grid, s);
-    case 8: return h ? launch_t<8, VCT_F16>(L, grid, s) : launch_t<8, VCT_F32>(L, grid, s);
+    case 1: return h ? launch_l<1, VCT_F16>(L, b, grid, s) : launch_l<1, VCT_F32>(L, b, grid, s);
+    case 2: return h ? launch_l<2, VCT_F16>(L, b, grid, s) : launch_l<2, VCT_F32>(L, b, grid, s);
+    case 4: return h ? launch_l<4, VCT_F16>(L, b, grid, s) : launch_l<4, VCT_F32>(L, b, grid, s);
+    case 8: return h ? launch_l<8, VCT_F16>(L, b, grid, s) : launch_l<8, VCT_F32>(L, b, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

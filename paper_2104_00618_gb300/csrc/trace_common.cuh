@@ -187,15 +187,45 @@ __device__ __forceinline__ float corner_weight(const LevelStencil &s, float lw, 
   return lw * wx * wy * wz;
 }
 
-// Trilinear lookup of one level as seven packed lerps (x, then y, then z);
-// corners outside the grid read as zero.
-template <int DT>
-__device__ __forceinline__ void trilerp(const uint8_t *lvl, const LevelStencil &s, f32x2 &rg,
-                                        f32x2 &ba) {
+// Address of the texel with Morton code `code` in a bricked level: its
+// brick's pool slot (slot 0, the zero brick, for an empty brick).
+template <typename T>
+__device__ __forceinline__ const T *brick_texel(const uint32_t *tbl, const T *pool,
+                                                uint32_t code) {
+  const uint32_t slot = __ldg(tbl + (code >> kBrickShift));
+  return pool + (((size_t)slot << kBrickShift) | (code & 511u));
+}
+
+// Trilinear lookup of level l as seven packed lerps (x, then y, then z);
+// corners outside the grid read as zero.  BR: the pyramid may have bricked
+// levels (VCT_LAYOUT_BRICKS).
+template <int DT, bool BR = false>
+__device__ __forceinline__ void trilerp(const DevPyr &P, int l, const LevelStencil &s,
+                                        f32x2 &rg, f32x2 &ba) {
   using T = typename TexOf<DT>::T;
-  const T *base = reinterpret_cast<const T *>(lvl);
+  const T *base = reinterpret_cast<const T *>(P.lvl[l]);
   f32x2 c_rg[8], c_ba[8];
-  if (s.valid == 0xffu) {
+  if (BR && ((P.bricked >> l) & 1u)) {
+    const uint32_t *tbl = reinterpret_cast<const uint32_t *>(P.lvl[l]);
+    const T *pool = reinterpret_cast<const T *>(P.pool);
+    // Two corners per axis share a brick unless the cell straddles a brick
+    // face; when all eight do (7 cells in 8 per axis), one slot serves all.
+    const uint32_t cross = (s.sx[0] ^ s.sx[1]) | (s.sy[0] ^ s.sy[1]) | (s.sz[0] ^ s.sz[1]);
+    if (s.valid == 0xffu && (cross >> kBrickShift) == 0u) {
+      const uint32_t c0 = corner_index(s, 0);
+      const T *brick = pool + ((size_t)__ldg(tbl + (c0 >> kBrickShift)) << kBrickShift);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) ld_texel2(brick + (corner_index(s, c) & 511u), c_rg[c], c_ba[c]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        c_rg[c] = 0ull;
+        c_ba[c] = 0ull;
+        if ((s.valid >> c) & 1u)
+          ld_texel2(brick_texel(tbl, pool, corner_index(s, c)), c_rg[c], c_ba[c]);
+      }
+    }
+  } else if (s.valid == 0xffu) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) ld_texel2(base + corner_index(s, c), c_rg[c], c_ba[c]);
   } else {
@@ -242,7 +272,7 @@ __device__ __forceinline__ float transparency(float a) { return fmaxf(1.0f - a, 
 // The full sample S(p, lambda) at apex-relative voxel coordinates F (levels
 // floor(lambda) and floor(lambda)+1 blended linearly); `om` receives 1 - a_s.
 // When `st` is non-null the two stencils are kept for the adjoint.
-template <int DT>
+template <int DT, bool BR = false>
 __device__ __forceinline__ float4 sample(const DevPyr &P, const Apex &A, const float F[3],
                                          float lam, const uint32_t *lut, float &om,
                                          LodPick &lp, LevelStencil *st = nullptr) {
@@ -250,12 +280,12 @@ __device__ __forceinline__ float4 sample(const DevPyr &P, const Apex &A, const f
   LevelStencil s;
   f32x2 rg, ba;
   level_stencil(lp.l0, P.n >> lp.l0, A, F, lut, s);
-  trilerp<DT>(P.lvl[lp.l0], s, rg, ba);
+  trilerp<DT, BR>(P, lp.l0, s, rg, ba);
   if (st) st[0] = s;
   if (lp.f > 0.0f) {
     level_stencil(lp.l1, P.n >> lp.l1, A, F, lut, s);
     f32x2 rg1, ba1;
-    trilerp<DT>(P.lvl[lp.l1], s, rg1, ba1);
+    trilerp<DT, BR>(P, lp.l1, s, rg1, ba1);
     const f32x2 tf = f2_pack(lp.f, lp.f);
     rg = f2_lerp(rg, rg1, tf);
     ba = f2_lerp(ba, ba1, tf);

@@ -48,7 +48,8 @@ bool shape_ok(int n, int levels, int dtype) {
 
 vct_status check_pyramid(const vct_pyramid *p, const char *what) {
   if (!p) return fail(VCT_ERR_INVALID_ARG, "%s: NULL pyramid", what);
-  if (!shape_ok(p->n, p->levels, p->dtype) || p->reserved != 0)
+  if (!shape_ok(p->n, p->levels, p->dtype) ||
+      (p->layout != VCT_LAYOUT_DENSE && p->layout != VCT_LAYOUT_BRICKS))
     return fail(VCT_ERR_INVALID_ARG, "%s: bad pyramid shape n=%d levels=%d dtype=%d", what, p->n,
                 p->levels, p->dtype);
   if (!(p->size > 0.0f) || !finite(p->size) || !finite(p->origin[0]) || !finite(p->origin[1]) ||
@@ -56,7 +57,7 @@ vct_status check_pyramid(const vct_pyramid *p, const char *what) {
     return fail(VCT_ERR_INVALID_ARG, "%s: bad pyramid origin/size", what);
   if (!p->data || !aligned(p->data, 256))
     return fail(VCT_ERR_INVALID_ARG, "%s: pyramid data NULL or not 256-byte aligned", what);
-  const Layout L = make_layout(p->n, p->levels, p->dtype);
+  const Layout L = make_layout(p->n, p->levels, p->dtype, p->layout);
   if (p->bytes < L.total)
     return fail(VCT_ERR_INVALID_ARG, "%s: pyramid bytes %llu < required %llu", what,
                 (unsigned long long)p->bytes, (unsigned long long)L.total);
@@ -155,10 +156,12 @@ vct_status check_params(const vct_trace_params *P, bool backward) {
 }
 
 vct_status fill_pyr(const vct_pyramid &p, const vct_trace_params &P, DevPyr &d) {
-  const Layout L = make_layout(p.n, p.levels, p.dtype);
+  const Layout L = make_layout(p.n, p.levels, p.dtype, p.layout);
   memset(&d, 0, sizeof(d));
   for (int l = 0; l < p.levels; ++l)
     d.lvl[l] = static_cast<const uint8_t *>(p.data) + L.level_off[l];
+  d.pool = static_cast<const uint8_t *>(p.data) + L.pool_off;
+  d.bricked = L.bricked;
   for (int a = 0; a < 3; ++a) d.origin[a] = p.origin[a];
   d.scale = (double)p.n / (double)p.size;
   d.tmax_vox = (double)P.t_max * d.scale;
@@ -416,6 +419,47 @@ vct_status vct_pyramid_status(const vct_pyramid *pyr, vct_stream_t stream) {
   if (e != cudaSuccess) return cuda_fail(e, "vct_pyramid_status copy");
   if (word == (uint32_t)VCT_ERR_TIMEOUT)
     return fail(VCT_ERR_TIMEOUT, "a kernel gave up a bounded wait while building this pyramid");
+  if (word == (uint32_t)VCT_ERR_WORKSPACE)
+    return fail(VCT_ERR_WORKSPACE,
+                "the brick pool of this pyramid was too small for its occupied bricks");
+  return VCT_OK;
+}
+
+size_t vct_pyramid_bytes_bricks(int32_t n, int32_t levels, int32_t dtype, uint64_t occupied) {
+  if (!shape_ok(n, levels, dtype)) return 0;
+  const Layout L = make_layout(n, levels, dtype, VCT_LAYOUT_BRICKS);
+  return (size_t)(L.total + occupied * ((uint64_t)texel_bytes(dtype) << kBrickShift));
+}
+
+size_t vct_pyramid_plan_scratch_bytes(int32_t n, int32_t levels, int32_t dtype) {
+  if (!shape_ok(n, levels, dtype)) return 0;
+  return (size_t)make_layout(n, levels, dtype, VCT_LAYOUT_BRICKS).pool_off;
+}
+
+vct_status vct_pyramid_plan_bricks(const float *level0_dense, int32_t n, int32_t levels,
+                                   int32_t dtype, void *scratch, size_t scratch_bytes,
+                                   uint64_t *occupied_out, uint64_t *bytes_out,
+                                   vct_stream_t stream) {
+  if (!shape_ok(n, levels, dtype))
+    return fail(VCT_ERR_INVALID_ARG, "vct_pyramid_plan_bricks: bad shape n=%d levels=%d", n,
+                levels);
+  if (!level0_dense || !aligned(level0_dense, 16))
+    return fail(VCT_ERR_INVALID_ARG, "vct_pyramid_plan_bricks: level0 NULL or misaligned");
+  const Layout L = make_layout(n, levels, dtype, VCT_LAYOUT_BRICKS);
+  if (!scratch || scratch_bytes < L.pool_off || !aligned(scratch, 256))
+    return fail(VCT_ERR_WORKSPACE, "vct_pyramid_plan_bricks: scratch needs %llu bytes",
+                (unsigned long long)L.pool_off);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint8_t *base = static_cast<uint8_t *>(scratch);
+  cudaError_t e = launch_brick_tables(level0_dense, n, levels, L, base, ~0ull, s);
+  if (e != cudaSuccess) return cuda_fail(e, "vct_pyramid_plan_bricks launch");
+  uint64_t count = 0;
+  if ((e = cudaMemcpyAsync(&count, base + kHeaderCountOff, 8, cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_fail(e, "vct_pyramid_plan_bricks copy");
+  if (occupied_out) *occupied_out = count;
+  if (bytes_out) *bytes_out = vct_pyramid_bytes_bricks(n, levels, dtype, count);
   return VCT_OK;
 }
 
@@ -448,10 +492,11 @@ static vct_status trace_impl(const vct_pyramid *pyrs, int32_t n_pyr, const vct_v
   for (int v0 = 0; v0 < n_views; v0 += kMaxViewsPerLaunch) {
     const int nv = std::min(kMaxViewsPerLaunch, n_views - v0);
     int cursor = 0;
-    bool mixed = false;
+    bool mixed = false, bricks = false;
     for (int i = 0; i < nv; ++i) {
       fill_view(views[v0 + i], cfg.tile_w, cfg.tile_h, cursor, L->views[i]);
       mixed |= pyrs[views[v0 + i].pyramid].dtype != pyrs[views[v0].pyramid].dtype;
+      bricks |= pyrs[views[v0 + i].pyramid].layout == VCT_LAYOUT_BRICKS;
     }
     if (mixed)
       return fail(VCT_ERR_UNSUPPORTED, "vct_trace: views of one call must use pyramids of one dtype");
@@ -462,7 +507,8 @@ static vct_status trace_impl(const vct_pyramid *pyrs, int32_t n_pyr, const vct_v
     L->total_tiles = assign_tail_tiles(L->views, nv, cfg.tile_w, cfg.tile_h, tail_px, L->n_big);
     if (v0 > 0 && (e = cudaMemsetAsync(L->queue, 0, 4, stream)) != cudaSuccess)
       return cuda_fail(e, "vct_trace queue clear");
-    e = launch_trace(*L, cfg.lanes_per_pixel, pyrs[views[v0].pyramid].dtype, grid, stream);
+    e = launch_trace(*L, cfg.lanes_per_pixel, pyrs[views[v0].pyramid].dtype, bricks, grid,
+                     stream);
     if (e != cudaSuccess) return cuda_fail(e, "vct_trace launch");
   }
   return VCT_OK;
@@ -563,8 +609,9 @@ vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
                               vct_stream_t stream) {
   vct_status st = check_pyramid(pyr, "vct_trace_backward");
   if (st != VCT_OK) return st;
-  if (pyr->dtype != VCT_F32)
-    return fail(VCT_ERR_UNSUPPORTED, "vct_trace_backward: only VCT_F32 pyramids are supported");
+  if (pyr->dtype != VCT_F32 || pyr->layout != VCT_LAYOUT_DENSE)
+    return fail(VCT_ERR_UNSUPPORTED,
+                "vct_trace_backward: only dense VCT_F32 pyramids are supported");
   if (!views || !grads || n_views < 1)
     return fail(VCT_ERR_INVALID_ARG, "vct_trace_backward: no views");
   if ((st = check_params(params, true)) != VCT_OK) return st;

@@ -38,27 +38,51 @@ __host__ __device__ inline int ilog2(int n) {
 // Edge of the block one CTA of the fused pack/mip kernel handles.
 __host__ __device__ inline int pack_block(int n) { return n < 16 ? n : 16; }
 
+// Brick storage (VCT_LAYOUT_BRICKS): levels with at least kBrickMinEdge
+// texels per axis are cut into 8^3 bricks (brick id = Morton code >> 9) and
+// keep one uint32 pool slot per brick; slot 0 is the shared all-zero brick.
+constexpr int kBrickShift = 9;  // 512 texels per brick
+constexpr int kBrickMinEdge = 16;
+constexpr uint64_t kHeaderCountOff = 8;  // uint64 occupied-brick count in the header
+
+__host__ __device__ inline bool level_bricked(int n, int l, int layout) {
+  return layout == VCT_LAYOUT_BRICKS && (n >> l) >= kBrickMinEdge;
+}
+__host__ __device__ inline uint64_t level_bricks(int n, int l) {
+  return level_texels(n, l) >> kBrickShift;
+}
+
 struct Layout {
-  uint64_t level_off[VCT_MAX_LEVELS];  // bytes from data
-  uint64_t staging_off[2];             // FP32 staging (VCT_F16 only)
-  uint64_t total;
+  uint64_t level_off[VCT_MAX_LEVELS];  // bytes from data (slot table of a bricked level)
+  uint64_t staging_off[2];             // FP32 staging (VCT_F16, or any brick layout)
+  uint64_t pool_off;                   // brick pool (brick layout), else total
+  uint64_t total;                      // dense: whole pyramid; bricks: with the zero brick only
+  uint32_t bricked;                    // bit l: level l is bricked
 };
 
-__host__ __device__ inline Layout make_layout(int n, int levels, int dtype) {
+__host__ __device__ inline Layout make_layout(int n, int levels, int dtype,
+                                              int layout = VCT_LAYOUT_DENSE) {
   Layout L{};
   uint64_t off = kHeaderBytes;
   int tb = texel_bytes(dtype);
   for (int l = 0; l < levels; ++l) {
     L.level_off[l] = off;
-    off += align256(level_texels(n, l) * tb);
+    if (level_bricked(n, l, layout)) {
+      L.bricked |= 1u << l;
+      off += align256(level_bricks(n, l) * 4);
+    } else {
+      off += align256(level_texels(n, l) * tb);
+    }
   }
-  if (dtype == VCT_F16) {
+  if (dtype == VCT_F16 || layout == VCT_LAYOUT_BRICKS) {
     int m0 = ilog2(pack_block(n));
     L.staging_off[0] = off;
     off += align256(level_texels(n, m0) * 16);
     L.staging_off[1] = off;
     off += align256(level_texels(n, m0 < ilog2(n) ? m0 + 1 : m0) * 16);
   }
+  L.pool_off = off;
+  if (layout == VCT_LAYOUT_BRICKS) off += (uint64_t)tb << kBrickShift;  // the zero brick
   L.total = off;
   return L;
 }
@@ -182,7 +206,9 @@ struct ConeConst {
 };
 
 struct DevPyr {
-  const uint8_t *lvl[VCT_MAX_LEVELS];  // level base pointers
+  const uint8_t *lvl[VCT_MAX_LEVELS];  // level base pointers (slot table if bricked)
+  const uint8_t *pool;                 // brick pool (brick layout)
+  uint32_t bricked, pad_b;             // bit l: level l is bricked
   double origin[3];
   double scale;  // n / size: scene units -> level-0 voxel units
   double tmax_vox;  // t_max in level-0 voxel units
@@ -289,10 +315,17 @@ vct_status set_last_error(vct_status st, const char *fmt, ...);
 cudaError_t launch_pack_mips(const float *level0, const vct_pyramid &pyr,
                              const CUtensorMap &map, cudaStream_t s);
 cudaError_t launch_read_level(const vct_pyramid &pyr, int level, float *out, cudaStream_t s);
+// Brick occupancy of a level-0 grid and the slot tables of every bricked
+// level, written at layout L's table offsets from `base`; the occupied count
+// goes to base + kHeaderCountOff.  More than `capacity` bricks (zero brick
+// included) leaves every slot 0 and writes VCT_ERR_WORKSPACE to the status word.
+cudaError_t launch_brick_tables(const float *level0, int n, int levels, const Layout &L,
+                                uint8_t *base, uint64_t capacity, cudaStream_t s);
 cudaError_t launch_mip_adjoint(const float *gpyr_base, const Layout &gl, int n, int levels,
                                float *grad0, cudaStream_t s);
 cudaError_t launch_wait_probe(uint32_t *flag, uint64_t max_ns, cudaStream_t s);
-cudaError_t launch_trace(const TraceLaunch &L, int lpp, int dtype, int grid, cudaStream_t s);
+cudaError_t launch_trace(const TraceLaunch &L, int lpp, int dtype, bool bricks, int grid,
+                         cudaStream_t s);
 int trace_occupancy(int lpp, int dtype, bool variants);
 cudaError_t launch_trace_bwd(const BwdLaunch &L, int lpp, int grid, cudaStream_t s);
 int trace_bwd_occupancy(int lpp, size_t smem);

@@ -178,3 +178,31 @@ def test_voxelize_structs_and_validation(lib):
     assert run(mesh=neg) == _abi.VCT_ERR_INVALID_ARG
     L.light_dir[1] = float("inf")
     assert run() == _abi.VCT_ERR_INVALID_ARG
+
+
+def test_brick_layout_sizes_and_validation(lib):
+    """Brick layout: per bricked level a uint32 slot table, small levels
+    dense, FP32 staging, then the pool (zero brick + occupied bricks)."""
+    def al(x):
+        return (x + 255) // 256 * 256
+    n, levels = 64, 7
+    for dtype, tb in ((0, 16), (1, 8)):
+        fixed = 256
+        for l in range(levels):
+            m = n >> l
+            fixed += al((m ** 3 // 512) * 4) if m >= 16 else al(m ** 3 * tb)
+        fixed += al((n // 16) ** 3 * 16) + al((n // 32) ** 3 * 16)  # staging (block 16)
+        assert lib.vct_pyramid_plan_scratch_bytes(n, levels, dtype) == fixed
+        assert lib.vct_pyramid_bytes_bricks(n, levels, dtype, 0) == fixed + 512 * tb
+        assert lib.vct_pyramid_bytes_bricks(n, levels, dtype, 10) == fixed + 11 * 512 * tb
+    assert lib.vct_pyramid_bytes_bricks(48, 3, 0, 5) == 0
+    p = _abi.VctPyramid(64, 7, 0, 2, (ctypes.c_float * 3)(0, 0, 0), 1.0, 256,
+                        lib.vct_pyramid_bytes(64, 7, 0))
+    assert lib.vct_build_mips(1024, ctypes.byref(p), None) == _abi.VCT_ERR_INVALID_ARG
+    p.layout = _abi.LAYOUT_BRICKS
+    p.bytes = lib.vct_pyramid_plan_scratch_bytes(64, 7, 0)  # no room for the zero brick
+    assert lib.vct_build_mips(1024, ctypes.byref(p), None) == _abi.VCT_ERR_INVALID_ARG
+    occ, nb = ctypes.c_uint64(), ctypes.c_uint64()
+    st = lib.vct_pyramid_plan_bricks(1024, 64, 7, 0, 256, 100, ctypes.byref(occ),
+                                     ctypes.byref(nb), None)
+    assert st == _abi.VCT_ERR_WORKSPACE
