@@ -50,6 +50,8 @@ def parse():
                     help="only warm-up + timed frames (for ncu captures); no e2e/extras/baseline")
     ap.add_argument("--profile-bwd", action="store_true",
                     help="only fwd+bwd steps of a reduced learnable-grid case (for ncu captures)")
+    ap.add_argument("--only-extra", default=None,
+                    help="run one secondary measurement alone and print it (for ncu captures)")
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     return ap.parse_args()
@@ -546,13 +548,13 @@ def extra_batched(torch, vct, dev, grids=(128, 256, 256, 512), views_per_scene=6
             "launches_per_replay": 1, "graph": True, "gen_s": gen_s}
 
 
+EXTRAS = {}
+
+
 def run_extras(torch, vct, dev, args):
     """Secondary measurements reported beside the main metric."""
     out = {}
-    for name, fn in (("fp16_single_view", extra_fp16_single), ("variants", extra_variants),
-                     ("revoxelize", extra_revoxelize), ("bricks_512", extra_bricks),
-                     ("fwd_bwd", extra_fwd_bwd),
-                     ("batched_fp16", extra_batched)):
+    for name, fn in EXTRAS.items():
         if name == "batched_fp16" and args.no_batched:
             continue
         try:
@@ -561,6 +563,27 @@ def run_extras(torch, vct, dev, args):
             out[name] = {"error": f"{type(e).__name__}: {e}"}
         torch.cuda.empty_cache()
     return out
+
+
+def run_only_extra(args):
+    import torch
+    import paper_2104_00618_gb300 as vct
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    vct.lib()
+    return {"only_extra": args.only_extra,
+            args.only_extra: EXTRAS[args.only_extra](torch, vct, dev)}
+
+
+def _register_extras():
+    for name, fn in (("fp16_single_view", extra_fp16_single), ("variants", extra_variants),
+                     ("revoxelize", extra_revoxelize), ("bricks_512", extra_bricks),
+                     ("fwd_bwd", extra_fwd_bwd),
+                     ("batched_fp16", extra_batched)):
+        EXTRAS[name] = fn
+
+
+_register_extras()
 
 
 # ---------------------------------------------------------------------------
@@ -636,6 +659,9 @@ def main():
     args = parse()
     if args.profile_bwd:
         print(json.dumps(run_profile_bwd(args)))
+        return
+    if args.only_extra:
+        print(json.dumps(run_only_extra(args)))
         return
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:

@@ -195,7 +195,7 @@ __device__ __forceinline__ void warp_sort_desc(uint32_t *keys, int n) {
 // (any VCT_FLAG_* set); the plain instances carry none of that code.  BR
 // instances read brick pyramids (VCT_LAYOUT_BRICKS).
 template <int LPP, int DT, bool kVar, bool BR>
-__global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(const __grid_constant__ TraceLaunch L) {
+__global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(const __grid_constant__ TraceLaunch L) {
   constexpr int kPixPerRound = 32 / LPP;
   constexpr bool kSortSpec = (LPP == 1);
   uint32_t n_samp[3] = {0u, 0u, 0u}, n_cone[3] = {0u, 0u, 0u};
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
   const int first_cone = defer_spec ? 1 : 0;  // the specular cone is cone 0
   const float T0 = (float)L.t0_vox;
   __shared__ uint32_t s_lut[1024];
-  __shared__ uint32_t s_keys[kTraceThreads / 32][kMaxSortPixels];
+  __shared__ uint32_t s_keys[kFwdThreads / 32][kMaxSortPixels];
   uint32_t *keys = s_keys[threadIdx.x >> 5];
   fill_spread_lut(s_lut);
 
@@ -403,9 +403,9 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
 template <int LPP, int DT, bool BR>
 cudaError_t launch_t(const TraceLaunch &L, int grid, cudaStream_t s) {
   if (L.var.flags)
-    trace_kernel<LPP, DT, true, BR><<<grid, kTraceThreads, 0, s>>>(L);
+    trace_kernel<LPP, DT, true, BR><<<grid, kFwdThreads, 0, s>>>(L);
   else
-    trace_kernel<LPP, DT, false, BR><<<grid, kTraceThreads, 0, s>>>(L);
+    trace_kernel<LPP, DT, false, BR><<<grid, kFwdThreads, 0, s>>>(L);
   return cudaGetLastError();
 }
 
@@ -419,10 +419,10 @@ int occ_t(bool var) {
   int b = 0;
   if (var)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<LPP, DT, true, false>,
-                                                  kTraceThreads, 0);
+                                                  kFwdThreads, 0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<LPP, DT, false, false>,
-                                                  kTraceThreads, 0);
+                                                  kFwdThreads, 0);
   return b;
 }
 

@@ -64,6 +64,15 @@ __device__ __forceinline__ void reflect_dir(const float x[3], const float cam[3]
   for (int a = 0; a < 3; ++a) R[a] = (float)(v[a] - 2.0 * vn * (double)n[a]);
 }
 
+// floor(v) of |v| < 2^22 as (float, int): v + 1.5 * 2^23 rounded down keeps
+// floor(v) in the low mantissa bits (no float-to-int conversion needed).
+constexpr float kFloorMagic = 12582912.0f;  // 1.5 * 2^23, bits 0x4B400000
+__device__ __forceinline__ float floor_split(float v, int &iv) {
+  const float t = __fadd_rd(v, kFloorMagic);
+  iv = __float_as_int(t) - 0x4B400000;
+  return t - kFloorMagic;
+}
+
 // Step k of a cone: T = t / h0 = T0 * 2^(k l2r) and the mip level
 // lam = log2(d / h0) = lam0 + k l2r (Ch. 4.3.2 step rule in closed form).
 __device__ __forceinline__ void step_at(const ConeConst &cc, float T0, int k, float &T,
@@ -72,9 +81,10 @@ __device__ __forceinline__ void step_at(const ConeConst &cc, float T0, int k, fl
   const float p = kf * cc.l2r_hi;
   float q = fmaf(kf, cc.l2r_hi, -p);
   q = fmaf(kf, cc.l2r_lo, q);
-  const float e = floorf(p);
+  int ie;
+  const float e = floor_split(p, ie);
   const float phi = (p - e) + q;
-  T = T0 * exp2f(phi) * __int_as_float(((int)e + 127) << 23);
+  T = T0 * exp2f(phi) * __int_as_float((ie + 127) << 23);
   lam = (cc.lam0_hi + p) + (q + cc.lam0_lo);
 }
 
@@ -141,9 +151,10 @@ __device__ __forceinline__ void level_stencil(int l, int Nl, const Apex &A, cons
     const int qi = A.Xi[a] >> l;
     // u = (Xi + F) / 2^l - 1/2, formed from small numbers only
     const float v = fmaf(F[a], sc, fmaf((float)ri, sc, -0.5f));
-    const float fl = floorf(v);
+    int iv;
+    const float fl = floor_split(v, iv);
     s.fr[a] = v - fl;
-    b[a] = qi + (int)fl;
+    b[a] = qi + iv;
   }
   const uint32_t x0 = lut[(uint32_t)b[0] & 1023u];
   const uint32_t y0 = lut[(uint32_t)b[1] & 1023u];
@@ -259,8 +270,7 @@ struct LodPick {
 __device__ __forceinline__ LodPick pick_levels(float lam, int levels) {
   LodPick r;
   const float lc = fminf(fmaxf(lam, 0.0f), (float)(levels - 1));
-  r.l0 = (int)lc;
-  r.f = lc - (float)r.l0;
+  r.f = lc - floor_split(lc, r.l0);
   r.l1 = min(r.l0 + 1, levels - 1);
   return r;
 }

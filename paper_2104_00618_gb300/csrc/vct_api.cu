@@ -165,6 +165,9 @@ vct_status fill_pyr(const vct_pyramid &p, const vct_trace_params &P, DevPyr &d) 
   for (int a = 0; a < 3; ++a) d.origin[a] = p.origin[a];
   d.scale = (double)p.n / (double)p.size;
   d.tmax_vox = (double)P.t_max * d.scale;
+  // sample coordinates relative to the apex stay below 2^21 voxels
+  if (d.tmax_vox > 1048576.0)
+    return fail(VCT_ERR_INVALID_ARG, "params: t_max spans more than 2^20 voxels");
   d.n = p.n;
   d.levels = p.levels;
   d.dtype = p.dtype;
@@ -503,7 +506,7 @@ static vct_status trace_impl(const vct_pyramid *pyrs, int32_t n_pyr, const vct_v
     L->n_views = nv;
     const int grid = std::max(1, std::min(cursor, per_sm * sms));
     // about two waves of the launch's warps, in small tiles, at the end
-    const int64_t tail_px = (int64_t)2 * grid * (kTraceThreads / 32) * kSmallTileW * kSmallTileH;
+    const int64_t tail_px = (int64_t)2 * grid * (kFwdThreads / 32) * kSmallTileW * kSmallTileH;
     L->total_tiles = assign_tail_tiles(L->views, nv, cfg.tile_w, cfg.tile_h, tail_px, L->n_big);
     if (v0 > 0 && (e = cudaMemsetAsync(L->queue, 0, 4, stream)) != cudaSuccess)
       return cuda_fail(e, "vct_trace queue clear");

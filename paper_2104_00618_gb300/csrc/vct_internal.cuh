@@ -11,11 +11,17 @@
 namespace vct {
 
 constexpr int kHeaderBytes = 256;
-constexpr int kTraceThreads = 256;      // one CTA shape for every trace kernel
+constexpr int kTraceThreads = 256;      // CTA shape of the adjoint trace kernel
+// Forward trace CTAs: warps work independently, so the CTA size only sets the
+// register budget, 65536 / (kFwdThreads * kTraceMinBlocks) per thread.
+#ifndef VCT_FWD_THREADS
+#define VCT_FWD_THREADS 256
+#endif
 #ifndef VCT_TRACE_MIN_BLOCKS
 #define VCT_TRACE_MIN_BLOCKS 2
 #endif
-constexpr int kTraceMinBlocks = VCT_TRACE_MIN_BLOCKS;  // register budget: 65536 / (256 * this)
+constexpr int kFwdThreads = VCT_FWD_THREADS;
+constexpr int kTraceMinBlocks = VCT_TRACE_MIN_BLOCKS;
 constexpr int kMaxViewsPerLaunch = 256;  // keeps the forward launch under 32 KB
 constexpr int kMaxSortPixels = 256;      // largest pixel tile of one work item
 constexpr int kMaxBwdViewsPerLaunch = 128;
