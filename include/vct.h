@@ -373,6 +373,65 @@ vct_status vct_trace_backward_noalloc(const vct_pyramid *pyr, const vct_view *vi
                                       float *grad_level0_dense, vct_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Host-buffer frame pipeline                                               */
+/* ------------------------------------------------------------------------ */
+/*
+ * Runs the hot path (vct_build_mips + vct_trace of one view) on frames whose
+ * inputs and outputs live in host memory, overlapping the copies of one frame
+ * with the computation of its neighbours: two device slots, one stream for
+ * host-to-device copies, one for the kernels and one for device-to-host
+ * copies, ordered by events.  The thesis's CPU rendering loop syncs data to
+ * the GPU before every frame, then mipmaps and cone-traces (Ch. 5.2); this
+ * is that loop's data movement on a GPU whose copy engines run beside its
+ * SMs.
+ *   - vct_pipeline_create allocates both slots on the current device
+ *     (per slot: dense level 0, pyramid, G-buffer, outputs, trace workspace).
+ *   - vct_pipeline_submit enqueues one frame and returns; host inputs must
+ *     stay unchanged, and host outputs unread, until the frame is joined.
+ *     Host buffers should be page-locked (cudaHostAlloc/cudaHostRegister),
+ *     else the copies do not overlap.  The frame starts after the work
+ *     enqueued so far on `after`.
+ *   - vct_pipeline_join makes `stream` wait (on the GPU, not the host) for
+ *     every frame submitted so far; host outputs are final once `stream` has
+ *     reached that point.
+ * Not thread-safe: one host thread per pipeline.
+ */
+typedef struct vct_pipeline vct_pipeline;
+
+typedef struct {
+  int32_t n, levels, dtype;  /* pyramid shape (dense layout)                  */
+  int32_t width, height;     /* view size, 1 .. 65535                         */
+  int32_t has_roughness;     /* 1: frames carry per-pixel roughness           */
+  int32_t has_mask;          /* 1: frames carry a pixel mask                  */
+  int32_t outputs;           /* bit 0 diffuse, bit 1 specular, bit 2 visibility */
+  float origin[3], size;     /* grid placement in the scene                   */
+} vct_pipeline_desc;
+
+/* One frame in host memory (sizes from the pipeline's description). */
+typedef struct {
+  const float *level0;     /* [n][n][n][4] float32                              */
+  const float *position;   /* [H*W*3]                                           */
+  const float *normal;     /* [H*W*3]                                           */
+  const float *roughness;  /* [H*W] if has_roughness, else ignored              */
+  const uint8_t *mask;     /* [H*W] if has_mask, else ignored                   */
+  float camera[3];
+  float pad;
+  float *out_diffuse;      /* [H*W*4] if outputs bit 0                          */
+  float *out_specular;     /* [H*W*4] if outputs bit 1                          */
+  float *out_visibility;   /* [H*W] if outputs bit 2                            */
+} vct_host_frame;
+
+vct_status vct_pipeline_create(const vct_pipeline_desc *desc, const vct_trace_params *params,
+                               vct_pipeline **out);
+vct_status vct_pipeline_submit(vct_pipeline *p, const vct_host_frame *frame, vct_stream_t after);
+vct_status vct_pipeline_join(vct_pipeline *p, vct_stream_t stream);
+/* Sample and cone counters of the most recently joined frames' slot `slot`
+ * (0 or 1), copied to the host; synchronises with that slot's last frame. */
+vct_status vct_pipeline_stats(vct_pipeline *p, int32_t slot, vct_trace_stats *out);
+/* Waits for all submitted work, then frees the pipeline (NULL is ignored). */
+void vct_pipeline_destroy(vct_pipeline *p);
+
+/* ------------------------------------------------------------------------ */
 /* Voxelization (Ch. 4.4, Ch. 5.4.4 voxelize())                             */
 /* ------------------------------------------------------------------------ */
 /*

@@ -31,7 +31,8 @@ __all__ = ["Pyramid", "build_mips", "read_level", "pyramid_status", "make_params
            "trace_backward", "autotune", "read_stats", "TraceFn", "render", "VctError",
            "launch_config", "num_levels", "lib", "FLAG_OCC_SMOOTH", "FLAG_SPEC_GRACE",
            "FLAG_DIFFUSE_FIRST_HIT", "FLAG_SHADE", "FLAG_SHADE_IMPL", "Mesh", "voxelize",
-           "voxelize_workspace", "read_voxelize_stats", "voxel_owner", "plan_bricks"]
+           "voxelize_workspace", "read_voxelize_stats", "voxel_owner", "plan_bricks",
+           "Pipeline"]
 
 DTYPES = {"f32": VCT_F32, "f16": VCT_F16, VCT_F32: VCT_F32, VCT_F16: VCT_F16}
 LAYOUTS = {"dense": _abi.LAYOUT_DENSE, "bricks": _abi.LAYOUT_BRICKS,
@@ -419,3 +420,73 @@ def voxel_owner(workspace: torch.Tensor, n: int) -> torch.Tensor:
     """The owner grid of the last vct_voxelize on this workspace: [n,n,n]
     int32, triangle index + 1 per voxel (0 = empty)."""
     return workspace[256:256 + 4 * n * n * n].view(torch.int32).reshape(n, n, n)
+
+
+# ---------------------------------------------------------------------------
+# host-buffer frame pipeline
+# ---------------------------------------------------------------------------
+class Pipeline:
+    """Frames whose inputs and outputs live in (page-locked) host memory:
+    copies in, mip build + trace, copies out, overlapped across two device
+    slots by the library (vct_pipeline_*).  Host tensors passed to submit()
+    must stay alive and unchanged until join() has been reached."""
+
+    def __init__(self, n: int, width: int, height: int, params, levels: int | None = None,
+                 dtype="f32", origin=(0.0, 0.0, 0.0), size: float = 1.0,
+                 has_roughness=True, has_mask=True, outputs=7):
+        d = _abi.VctPipelineDesc()
+        d.n, d.levels, d.dtype = int(n), num_levels(n) if levels is None else int(levels), \
+            DTYPES[dtype]
+        d.width, d.height = int(width), int(height)
+        d.has_roughness, d.has_mask, d.outputs = int(has_roughness), int(has_mask), int(outputs)
+        for a in range(3):
+            d.origin[a] = float(origin[a])
+        d.size = float(size)
+        self.desc = d
+        self.params = params if isinstance(params, VctTraceParams) else make_params(params)
+        self._h = ctypes.c_void_p()
+        check(lib().vct_pipeline_create(ctypes.byref(d), ctypes.byref(self.params),
+                                        ctypes.byref(self._h)), "vct_pipeline_create")
+        self._keep = []
+
+    def submit(self, level0, position, normal, camera, out_diffuse=None, out_specular=None,
+               out_visibility=None, roughness=None, mask=None, stream=None):
+        f = _abi.VctHostFrame()
+        f.level0, f.position, f.normal = _ptr(level0), _ptr(position), _ptr(normal)
+        f.roughness, f.mask = _ptr(roughness), _ptr(mask)
+        for a in range(3):
+            f.camera[a] = float(camera[a])
+        f.out_diffuse, f.out_specular = _ptr(out_diffuse), _ptr(out_specular)
+        f.out_visibility = _ptr(out_visibility)
+        self._keep.append((level0, position, normal, roughness, mask, out_diffuse, out_specular,
+                           out_visibility))
+        check(lib().vct_pipeline_submit(self._h, ctypes.byref(f), _stream(stream)),
+              "vct_pipeline_submit")
+
+    def join(self, stream=None):
+        """Makes `stream` (default: the current one) wait for every frame so far."""
+        check(lib().vct_pipeline_join(self._h, _stream(stream)), "vct_pipeline_join")
+
+    def wait(self):
+        """Blocks until every submitted frame is done; host outputs are final."""
+        s = torch.cuda.current_stream()
+        self.join(s)
+        s.synchronize()
+        self._keep = []
+
+    def stats(self, slot: int) -> dict:
+        st = VctTraceStats()
+        check(lib().vct_pipeline_stats(self._h, int(slot), ctypes.byref(st)),
+              "vct_pipeline_stats")
+        return {"samples": list(st.samples), "cones": list(st.cones)}
+
+    def close(self):
+        if self._h:
+            lib().vct_pipeline_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -80,6 +80,18 @@ class VctVoxelizeStats(ctypes.Structure):
                 ("reserved", ctypes.c_uint32)]
 
 
+class VctPipelineDesc(ctypes.Structure):
+    _fields_ = [("n", _c_i32), ("levels", _c_i32), ("dtype", _c_i32), ("width", _c_i32),
+                ("height", _c_i32), ("has_roughness", _c_i32), ("has_mask", _c_i32),
+                ("outputs", _c_i32), ("origin", _c_f32 * 3), ("size", _c_f32)]
+
+
+class VctHostFrame(ctypes.Structure):
+    _fields_ = [("level0", _vp), ("position", _vp), ("normal", _vp), ("roughness", _vp),
+                ("mask", _vp), ("camera", _c_f32 * 3), ("pad", _c_f32), ("out_diffuse", _vp),
+                ("out_specular", _vp), ("out_visibility", _vp)]
+
+
 EXPORTS = {
     "vct_pyramid_bytes": (ctypes.c_size_t, [_c_i32, _c_i32, _c_i32]),
     "vct_pyramid_level_offset": (_c_u64, [_c_i32, _c_i32, _c_i32, _c_i32]),
@@ -110,6 +122,12 @@ EXPORTS = {
     "vct_voxelize_workspace_bytes": (ctypes.c_size_t, [_c_i32, _c_i32]),
     "vct_voxelize": (_c_i32, [ctypes.POINTER(VctMesh), _c_i32, ctypes.POINTER(_c_f32), _c_f32,
                               ctypes.POINTER(VctVoxelLight), _vp, _vp, ctypes.c_size_t, _vp]),
+    "vct_pipeline_create": (_c_i32, [ctypes.POINTER(VctPipelineDesc),
+                                     ctypes.POINTER(VctTraceParams), ctypes.POINTER(_vp)]),
+    "vct_pipeline_submit": (_c_i32, [_vp, ctypes.POINTER(VctHostFrame), _vp]),
+    "vct_pipeline_join": (_c_i32, [_vp, _vp]),
+    "vct_pipeline_stats": (_c_i32, [_vp, _c_i32, ctypes.POINTER(VctTraceStats)]),
+    "vct_pipeline_destroy": (None, [_vp]),
     "vct_status_string": (ctypes.c_char_p, [_c_i32]),
     "vct_last_error": (ctypes.c_char_p, []),
     "vct_version": (_c_i32, []),

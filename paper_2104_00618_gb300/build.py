@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libvct.so")
 
 SOURCES = ["vct_api.cu", "mips.cu", "trace.cu", "trace_bwd.cu", "noalloc.cu", "voxelize.cu",
-           "bricks.cu"]
+           "bricks.cu", "pipeline.cu"]
 HEADERS = [os.path.join(CSRC, "vct_internal.cuh"), os.path.join(CSRC, "trace_common.cuh"),
            os.path.join(CSRC, "voxelize.cuh"), os.path.join(INCLUDE, "vct.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
