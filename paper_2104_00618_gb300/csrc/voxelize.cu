@@ -24,6 +24,7 @@ constexpr int kSub = 256;                 // sub-voxel steps per voxel
 constexpr float kCoordLimit = 524288.0f;  // 2^19 sub-voxel steps
 constexpr int kSmallArea = 64;            // bounding boxes up to this: one thread
 constexpr int kItemPixels = 1024;         // pixels per warp item of a large triangle
+constexpr int kItemBatch = 4;             // consecutive items a warp claims at once
 constexpr int kVoxThreads = 256;
 
 struct LargeEntry {
@@ -66,6 +67,28 @@ __device__ __forceinline__ long long floor_div(long long a, long long b) {
 }
 
 __device__ __forceinline__ long long iabs64(long long a) { return a < 0 ? -a : a; }
+
+// floor(a / b), b != 0: a float32 estimate of the quotient, corrected to the
+// exact value with one multiply (64-bit division only if the estimate is off
+// by more than one, which the 2^-21 relative error of the estimate rules out
+// for the quotients met here, |a / b| < 2^21).
+__device__ __forceinline__ long long floor_div_fast(long long a, long long b) {
+  if (b < 0) {
+    a = -a;
+    b = -b;
+  }
+  long long q = __float2ll_rd(__fdividef(__ll2float_rn(a), __ll2float_rn(b)));
+  long long r = a - q * b;
+  if (r < 0) {
+    --q;
+    r += b;
+  } else if (r >= b) {
+    ++q;
+    r -= b;
+  }
+  if (r < 0 || r >= b) q = floor_div(a, b);
+  return q;
+}
 
 // Component `a` of (x, y, z), a in {0, 1, 2}, without run-time indexing.
 __device__ __forceinline__ long long pick(long long x, long long y, long long z, int a) {
@@ -162,7 +185,7 @@ __device__ __forceinline__ long long fragment(const Tri &T, int n, int i, int j)
     return -1;
   // plane N . (X - V0) = 0 solved for the dominant coordinate, floored
   const long long off = -(T.Nu * (pu - T.Vu) + T.Nv * (pv - T.Vv));
-  const long long depth = T.Vd + floor_div(off, T.Nd);
+  const long long depth = T.Vd + floor_div_fast(off, T.Nd);
   const long long k = floor_div(depth, kSub);
   if (k < 0 || k >= n) return -1;
   const long long nn = n;
@@ -286,51 +309,70 @@ __global__ void __launch_bounds__(kVoxThreads)
   const int lane = threadIdx.x & 31;
   unsigned long long frags = 0;
   for (;;) {
-    unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->item_cursor), 1ull);
-    item = __shfl_sync(0xffffffffu, item, 0);
-    if (item >= total) break;
-    // the listed triangle whose item range holds `item`
+    unsigned long long item0 = 0;
+    if (lane == 0)
+      item0 = atomicAdd(reinterpret_cast<unsigned long long *>(&A.st->item_cursor),
+                        (unsigned long long)kItemBatch);
+    item0 = __shfl_sync(0xffffffffu, item0, 0);
+    if (item0 >= total) break;
+    // the listed triangle whose item range holds item0 (binary search), then
+    // forwards through the batch
     unsigned lo = 0, hi = count - 1;
     while (lo < hi) {
       const unsigned mid = (lo + hi + 1) >> 1;
-      if (A.first[mid] <= item)
+      if (A.first[mid] <= item0)
         lo = mid;
       else
         hi = mid - 1;
     }
-    const int t = (int)A.large[lo].tri;
+    int cur = -1;
     Tri T;
     int ix[3];
-    setup_tri(A, t, T, ix);  // usable: it was listed by setup_kernel
-    const int w = T.i1 - T.i0 + 1;
-    const long long area = (long long)w * (T.j1 - T.j0 + 1);
-    const long long p0 = (long long)(item - A.first[lo]) * kItemPixels;
-    const long long p1 = min(p0 + kItemPixels, area);
-    for (long long p = p0 + lane; p < p1; p += 32) {
-      const int i = T.i0 + (int)(p % w), j = T.j0 + (int)(p / w);
-      const long long v = fragment(T, A.n, i, j);
-      if (v >= 0) {
-        atomicMax(A.owner + v, (unsigned)(t + 1));
-        ++frags;
+    const unsigned long long item_end = min(item0 + (unsigned long long)kItemBatch, total);
+    for (unsigned long long item = item0; item < item_end; ++item) {
+      while (lo + 1 < count && A.first[lo + 1] <= item) ++lo;
+      const int t = (int)A.large[lo].tri;
+      if (t != cur) {
+        setup_tri(A, t, T, ix);  // usable: it was listed by setup_kernel
+        cur = t;
+      }
+      const int w = T.i1 - T.i0 + 1;
+      const long long area = (long long)w * (T.j1 - T.j0 + 1);
+      const long long p0 = (long long)(item - A.first[lo]) * kItemPixels;
+      const long long p1 = min(p0 + kItemPixels, area);
+      for (long long p = p0 + lane; p < p1; p += 32) {
+        const int i = T.i0 + (int)(p % w), j = T.j0 + (int)(p / w);
+        const long long v = fragment(T, A.n, i, j);
+        if (v >= 0) {
+          atomicMax(A.owner + v, (unsigned)(t + 1));
+          ++frags;
+        }
       }
     }
   }
   warp_add_u64(reinterpret_cast<unsigned long long *>(&A.st->fragments), frags);
 }
 
-// Owner grid -> dense RGBA grid, four voxels per thread.
+// Owner grid -> dense RGBA grid.  Each warp covers 128 consecutive voxels
+// per pass, lane-contiguous, so owner loads and RGBA stores coalesce.
 __global__ void __launch_bounds__(kVoxThreads) resolve_kernel(const __grid_constant__ VoxArgs A,
-                                                             long long groups) {
-  const uint4 *own = reinterpret_cast<const uint4 *>(A.owner);
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < groups;
-       g += (long long)gridDim.x * blockDim.x) {
-    const uint4 o = __ldcs(own + g);
-    const uint32_t w[4] = {o.x, o.y, o.z, o.w};
-    float4 *dst = A.out + 4 * g;
+                                                             long long nvox) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp * 128; base < nvox; base += nwarps * 128) {
+    uint32_t o[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      __stcs(dst + k, w[k] ? __ldg(A.colour + (w[k] - 1)) : make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int k = 0; k < 4; ++k) {
+      const long long v = base + 32 * k + lane;
+      o[k] = v < nvox ? __ldcs(A.owner + v) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const long long v = base + 32 * k + lane;
+      if (v < nvox)
+        __stcs(A.out + v, o[k] ? __ldg(A.colour + (o[k] - 1)) : make_float4(0.f, 0.f, 0.f, 0.f));
+    }
   }
 }
 
@@ -384,10 +426,10 @@ cudaError_t launch_voxelize(const vct_mesh &m, int n, const float origin[3], flo
     raster_large_kernel<<<sms * 8, kVoxThreads, 0, s>>>(A);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  const long long groups = (long long)(nvox / 4);
-  const int rgrid = (int)std::min<long long>((groups + kVoxThreads - 1) / kVoxThreads,
+  const long long chunks = (long long)((nvox + 127) / 128);  // one warp pass each
+  const int rgrid = (int)std::min<long long>((chunks + kVoxThreads / 32 - 1) / (kVoxThreads / 32),
                                              (long long)sms * 8);
-  resolve_kernel<<<rgrid, kVoxThreads, 0, s>>>(A, groups);
+  resolve_kernel<<<rgrid, kVoxThreads, 0, s>>>(A, (long long)nvox);
   return cudaGetLastError();
 }
 
