@@ -1,5 +1,7 @@
 // Mip pyramid kernels: fused Morton packing + 2x2x2 box filter (Ch. 4.3.3),
 // level readback, the adjoint of the box filter, and the bounded-wait probe.
+#include <algorithm>
+
 #include "vct_internal.cuh"
 
 namespace vct {
@@ -35,6 +37,8 @@ struct PackArgs {
   float4 *staging;  // FP32 copy of level m_top (VCT_F16 or bricks), else null
   uint32_t *status;
   int n, B, m_top;  // block edge, last level produced inside a block
+  uint32_t nblocks;  // (n / B)^3
+  int lv_texels;     // texels of levels 1..m_top of one block
 };
 
 // Stores the texel with Morton code `code` of level l: in place for a dense
@@ -55,81 +59,177 @@ __device__ __forceinline__ void put(uint8_t *const *lvl, const uint8_t *pool, ui
   }
 }
 
-// One CTA per B^3 block of level 0 (blockIdx.x = Morton index of the block).
-// The dense block arrives by one TMA tensor copy into shared memory; the CTA
-// writes the block's level-0 texels in Morton order and reduces it level by
-// level in shared memory (levels 1..m_top), each child group contiguous.
+// Level 0 (Morton order, into `mort`) and level 1 (into lvf, float32) of
+// one B^3 block from its dense copy in shared memory.  For B = 16 the lanes
+// of a warp take cells and child order such that the eight lanes of each
+// shared-memory phase touch eight different 16-byte bank groups, reading
+// the dense copy and writing `mort`: lane l owns x cell (l >> 1) & 3 (+4
+// with bit 3) and starts at child l, so lanes that share a cell column read
+// opposite x parities.
+template <int DT>
+__device__ __forceinline__ void block_level01(const PackArgs &a, const float4 *dense,
+                                              typename Tex<DT>::T *mort, float4 *lvf) {
+  const int B = a.B;
+  const int B3 = B * B * B;
+  const int cells = B3 / 8;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = threadIdx.x; c < cells; c += blockDim.x) {
+    int cx, cy, cz, rot;
+    if (B == 16) {
+      const int it = c >> 8;  // bit 8 of the cell's thread-pass index
+      cx = ((lane >> 1) & 3) | (((lane >> 3) & 1) << 2);
+      cy = (lane & 1) | (((lane >> 4) & 1) << 1) | ((w & 1) << 2);
+      cz = ((w >> 1) & 3) | (it << 2);
+      rot = lane;
+    } else {
+      cx = compact3(c);
+      cy = compact3(c >> 1);
+      cz = compact3(c >> 2);
+      rot = 0;
+    }
+    const uint32_t code = morton3(cx, cy, cz);
+    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int j = (i + rot) & 7;
+      const int x = 2 * cx + (j & 1), y = 2 * cy + ((j >> 1) & 1), z = 2 * cz + (j >> 2);
+      const float4 v = dense[(z * B + y) * B + x];
+      sum = add4(sum, v);
+      st_texel(mort + 8 * code + j, v);
+    }
+    if (a.m_top >= 1) lvf[code] = mul4(sum, 0.125f);
+  }
+}
+
+// Copies `cnt` texels of level l with Morton codes code .. code+cnt-1 from
+// shared memory to the pyramid (bulk copies; a bricked level gets one copy
+// per occupied brick the range touches, none for empty bricks).
+template <int DT, bool BR>
+__device__ __forceinline__ void store_range(const PackArgs &a, int l, uint32_t code, uint32_t cnt,
+                                            const typename Tex<DT>::T *src) {
+  using T = typename Tex<DT>::T;
+  if (BR && ((a.bricked >> l) & 1u)) {
+    const uint32_t *tbl = reinterpret_cast<const uint32_t *>(a.lvl[l]);
+    T *pool = reinterpret_cast<T *>(a.pool);
+    for (uint32_t c = code; c < code + cnt;) {
+      const uint32_t end = min(code + cnt, ((c >> kBrickShift) + 1u) << kBrickShift);
+      const uint32_t slot = tbl[c >> kBrickShift];
+      T *dst = pool + (((size_t)slot << kBrickShift) | (c & 511u));
+      if (slot != 0u && ((end - c) * sizeof(T)) % 16u != 0u) {
+        for (uint32_t k = c; k < end; ++k) dst[k - c] = src[k - code];
+      } else if (slot != 0u) {
+        bulk_store(dst, src + (c - code), (end - c) * (uint32_t)sizeof(T));
+      }
+      c = end;
+    }
+  } else if ((cnt * sizeof(T)) % 16u != 0u) {
+    // a single binary16 texel: too small for a bulk copy
+    for (uint32_t k = 0; k < cnt; ++k) reinterpret_cast<T *>(a.lvl[l])[code + k] = src[k];
+  } else {
+    bulk_store(reinterpret_cast<T *>(a.lvl[l]) + code, src, cnt * (uint32_t)sizeof(T));
+  }
+}
+
+// Persistent CTAs, each taking blocks blockIdx.x, blockIdx.x + gridDim.x,
+// ... (Morton indices of the B^3 blocks of level 0).  Each block arrives by
+// one TMA tensor copy into one of two shared-memory buffers (the copy of
+// the next block is in flight while this one is reduced); the CTA assembles
+// the block's level-0 texels in Morton order and its levels 1..m_top (each
+// child group contiguous) in shared memory, and bulk copies write them out
+// whole, so the pyramid is written in full lines.
 template <int DT, bool BR>
 __global__ void __launch_bounds__(256) pack_mips_kernel(const __grid_constant__ CUtensorMap map,
                                                         const PackArgs a) {
   using T = typename Tex<DT>::T;
   extern __shared__ __align__(128) uint8_t smem_raw[];
   // TMA destinations must be 128-byte aligned.
-  float4 *dense = reinterpret_cast<float4 *>(
+  float4 *buf0 = reinterpret_cast<float4 *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
   const int B = a.B;
   const int B3 = B * B * B;
-  float4 *lv = dense + B3;  // reduced levels, Morton order, back to back
-  __shared__ __align__(8) uint64_t bar;
+  float4 *const buf1 = buf0 + B3;
+  T *mort = reinterpret_cast<T *>(buf0 + 2 * B3);           // level 0, Morton order
+  float4 *lvf = reinterpret_cast<float4 *>(mort + B3);      // levels 1..m_top, float32
+  const int lv_texels = a.lv_texels;                        // texels of levels 1..m_top
+  T *lvo = DT == VCT_F32 ? reinterpret_cast<T *>(lvf)       // levels 1..m_top as stored
+                         : reinterpret_cast<T *>(lvf + lv_texels);
+  __shared__ __align__(8) uint64_t bar[2];
 
-  const uint32_t blk = blockIdx.x;
-  const int bx = compact3(blk), by = compact3(blk >> 1), bz = compact3(blk >> 2);
-
+  auto issue = [&](uint32_t b, int s) {
+    const int bx = compact3(b), by = compact3(b >> 1), bz = compact3(b >> 2);
+    uint64_t *br = s ? &bar[1] : &bar[0];
+    mbar_expect_tx(br, (uint32_t)B3 * 16u);
+    tma_load_4d(s ? buf1 : buf0, &map, br, 0, bx * B, by * B, bz * B);
+  };
   if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     fence_proxy_async_smem();
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    mbar_expect_tx(&bar, (uint32_t)B3 * 16u);
-    tma_load_4d(dense, &map, &bar, 0, bx * B, by * B, bz * B);
-  }
-  if (!mbar_wait_bounded(&bar, 0, kWaitBudgetNs)) {
-    // Give up: flag it, then wait once more (bounded) for the copy so that no
-    // write into this CTA's shared memory is left in flight.
-    if (threadIdx.x == 0) atomicExch(a.status, (uint32_t)VCT_ERR_TIMEOUT);
-    mbar_wait_bounded(&bar, 0, kWaitBudgetNs);
-    return;
-  }
-
-  // Level 0 (Morton) and level 1.
-  const uint32_t code0 = blk * (uint32_t)B3;
-  const int cells = B3 / 8;
-  for (int c = threadIdx.x; c < cells; c += blockDim.x) {
-    const int cx = compact3(c), cy = compact3(c >> 1), cz = compact3(c >> 2);
-    float4 ch[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int x = 2 * cx + (i & 1), y = 2 * cy + ((i >> 1) & 1), z = 2 * cz + (i >> 2);
-      ch[i] = dense[(z * B + y) * B + x];
+  uint32_t blk = blockIdx.x;
+  if (threadIdx.x == 0 && blk < a.nblocks) issue(blk, 0);
+  uint32_t ph0 = 0u, ph1 = 0u;  // phase of each buffer's barrier
+  int s = 0;
+  for (; blk < a.nblocks; blk += gridDim.x, s ^= 1) {
+    const uint32_t nxt = blk + gridDim.x;
+    if (threadIdx.x == 0 && nxt < a.nblocks) {
+      // buf[s ^ 1] was last read before the barriers that ended the previous block
+      fence_proxy_async_smem();
+      issue(nxt, s ^ 1);
     }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) put<DT, BR>(a.lvl, a.pool, a.bricked, 0, code0 + 8 * c + i, ch[i]);
-    if (a.m_top >= 1) {
-      float4 m = mean8(ch);
-      lv[c] = m;
-      put<DT, BR>(a.lvl, a.pool, a.bricked, 1, blk * (uint32_t)cells + c, m);
+    uint64_t *br = s ? &bar[1] : &bar[0];
+    const uint32_t ph = s ? ph1 : ph0;
+    const bool got = mbar_wait_bounded(br, ph, kWaitBudgetNs);
+    // the previous block's bulk stores have read `mort` and the levels
+    if (threadIdx.x == 0) bulk_wait_read();
+    if (!__syncthreads_and(got)) {
+      // Give up: flag it, then wait once more (bounded) for the copies in
+      // flight so that none is left writing this CTA's shared memory.
+      if (threadIdx.x == 0) atomicExch(a.status, (uint32_t)VCT_ERR_TIMEOUT);
+      mbar_wait_bounded(br, ph, kWaitBudgetNs);
+      if (nxt < a.nblocks)
+        mbar_wait_bounded(s ? &bar[0] : &bar[1], s ? ph0 : ph1, kWaitBudgetNs);
+      if (threadIdx.x == 0) bulk_wait_all();
+      return;
     }
-  }
-  // Levels 2..m_top inside the block.
-  float4 *src = lv;
-  int cnt = cells;
-  for (int l = 2; l <= a.m_top; ++l) {
+    if (s)
+      ph1 ^= 1u;
+    else
+      ph0 ^= 1u;
+    block_level01<DT>(a, s ? buf1 : buf0, mort, lvf);
+    // Levels 2..m_top inside the block.
+    float4 *src = lvf;
+    int cnt = B3 / 8;
+    for (int l = 2; l <= a.m_top; ++l) {
+      __syncthreads();
+      float4 *dst = src + cnt;
+      const int nc = cnt / 8;
+      for (int j = threadIdx.x; j < nc; j += blockDim.x) dst[j] = mean8(src + 8 * j);
+      src = dst;
+      cnt = nc;
+    }
     __syncthreads();
-    float4 *dst = src + cnt;
-    const int nc = cnt / 8;
-    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
-      float4 m = mean8(src + 8 * j);
-      dst[j] = m;
-      put<DT, BR>(a.lvl, a.pool, a.bricked, l, blk * (uint32_t)nc + j, m);
+    if (DT != VCT_F32) {
+      for (int j = threadIdx.x; j < lv_texels; j += blockDim.x) st_texel(lvo + j, lvf[j]);
+      __syncthreads();
     }
-    src = dst;
-    cnt = nc;
+    if (threadIdx.x == 0) {
+      // FP32 copy of the block's top level (one texel, index blk of level
+      // m_top) for the tail kernel; only set when the tail runs.
+      if (a.staging != nullptr) a.staging[blk] = src[0];
+      fence_proxy_async_smem();  // the generic writes above feed the bulk copies
+      store_range<DT, BR>(a, 0, blk * (uint32_t)B3, (uint32_t)B3, mort);
+      const T *lsrc = lvo;
+      for (int l = 1, c = B3 / 8; l <= a.m_top; ++l, c /= 8) {
+        store_range<DT, BR>(a, l, blk * (uint32_t)c, (uint32_t)c, lsrc);
+        lsrc += c;
+      }
+      bulk_commit();
+    }
+    // (the next iteration's barriers order the reuse of the buffers)
   }
-  // FP32 copy of the block's top level (one texel, index blk of level m_top)
-  // for the tail kernel; only set when the tail runs (m_top = log2 B >= 1).
-  __syncthreads();
-  if (a.staging != nullptr && threadIdx.x == 0) a.staging[blk] = src[0];
+  if (threadIdx.x == 0) bulk_wait_all();
 }
 
 struct TailArgs {
@@ -230,7 +330,12 @@ cudaError_t pack_t(const CUtensorMap &map, const PackArgs &a, int blocks, size_t
   cudaError_t e = cudaFuncSetAttribute(pack_mips_kernel<DT, BR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  pack_mips_kernel<DT, BR><<<blocks, 256, smem, s>>>(map, a);
+  int dev = 0, sms = 148, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pack_mips_kernel<DT, BR>, 256, smem);
+  const int grid = std::max(1, std::min(blocks, sms * std::max(per_sm, 1)));
+  pack_mips_kernel<DT, BR><<<grid, 256, smem, s>>>(map, a);
   return cudaGetLastError();
 }
 
@@ -266,10 +371,16 @@ cudaError_t launch_pack_mips(const float *level0, const vct_pyramid &pyr,
   a.staging = ((pyr.dtype == VCT_F16 || br) && tail)
                   ? reinterpret_cast<float4 *>(base + L.staging_off[0]) : nullptr;
   const int B3 = B * B * B;
-  size_t smem = (size_t)B3 * 16 + 128;
-  int c = B3 / 8;
-  for (int l = 1; l <= m_top; ++l, c /= 8) smem += (size_t)c * 16;
+  const size_t tb = (size_t)texel_bytes(pyr.dtype);
+  int lv_texels = 0;
+  for (int l = 1, c = B3 / 8; l <= m_top; ++l, c /= 8) lv_texels += c;
+  a.lv_texels = lv_texels;
+  // two dense input buffers, level 0 in Morton order, levels 1..m_top in
+  // float32 (and as stored, for VCT_F16)
+  size_t smem = 128 + (size_t)B3 * 32 + (size_t)B3 * tb + (size_t)lv_texels * 16 +
+                (pyr.dtype == VCT_F32 ? 0 : (size_t)lv_texels * tb);
   const int blocks = (int)level_texels(pyr.n, mB);  // (n/B)^3
+  a.nblocks = (uint32_t)blocks;
   if (pyr.dtype == VCT_F32)
     e = br ? pack_t<VCT_F32, true>(map, a, blocks, smem, s)
            : pack_t<VCT_F32, false>(map, a, blocks, smem, s);
