@@ -18,38 +18,26 @@ namespace vct {
 
 namespace {
 
-// Levels with at most 16^3 texels are accumulated per CTA in shared memory
-// (every sample of a coarse level lands on a handful of texels, so global
-// atomics there would serialize) and added to global memory once per CTA.
-struct SmemGrad {
-  float *base;      // shared float[4 * texels of levels >= first]
-  int first;        // first level kept in shared memory
-  int off[VCT_MAX_LEVELS];  // texel offset of each such level
-};
-
-__device__ __forceinline__ float *grad_texel(const BwdLaunch &L, const SmemGrad &sg, int l,
-                                             uint32_t idx) {
-  return l >= sg.first ? sg.base + 4 * (sg.off[l] + idx)
-                       : reinterpret_cast<float *>(L.gpyr_lvl[l]) + 4 * (size_t)idx;
+// Gradient texel of level l (float32 gradient pyramid in global memory).
+// Every level is accumulated there with float atomics: measured on the
+// learnable 128^3 workload, per-CTA shared-memory copies of the coarse
+// levels were slower (their flush and the shared-memory atomics cost more
+// than the contention they avoided, the warp reduce-scatter below already
+// merging the lanes that share a cell).
+__device__ __forceinline__ float *grad_texel(const BwdLaunch &L, int l, uint32_t idx) {
+  return reinterpret_cast<float *>(L.gpyr_lvl[l]) + 4 * (size_t)idx;
 }
 
 // Per-lane scatter of one level's 8 corners (lanes in different cells).
-__device__ __forceinline__ void scatter_lane(const BwdLaunch &L, const SmemGrad &sg, int l,
-                                             const LevelStencil &s, float lw, const float g[4]) {
+__device__ __forceinline__ void scatter_lane(const BwdLaunch &L, int l, const LevelStencil &s,
+                                             float lw, const float g[4]) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     if (!((s.valid >> c) & 1u)) continue;
     const float w = corner_weight(s, lw, c);
     if (w == 0.0f) continue;
-    float *t = grad_texel(L, sg, l, corner_index(s, c));
-    if (l >= sg.first) {
-      atomicAdd(t + 0, w * g[0]);
-      atomicAdd(t + 1, w * g[1]);
-      atomicAdd(t + 2, w * g[2]);
-      atomicAdd(t + 3, w * g[3]);
-    } else {
-      atomicAdd(reinterpret_cast<float4 *>(t), make_float4(w * g[0], w * g[1], w * g[2], w * g[3]));
-    }
+    atomicAdd(reinterpret_cast<float4 *>(grad_texel(L, l, corner_index(s, c))),
+              make_float4(w * g[0], w * g[1], w * g[2], w * g[3]));
   }
 }
 
@@ -60,19 +48,19 @@ __device__ __forceinline__ void scatter_lane(const BwdLaunch &L, const SmemGrad 
 // so that lane j ends with the group total of value j, and each lane issues
 // one atomic on a distinct address: contending atomics (the same texel from
 // many lanes) are what makes a naive scatter slow at the coarse levels.
-__device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const SmemGrad &sg, bool act,
-                                             int l, const LevelStencil &s, float lw,
+__device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const uint32_t *code_off,
+                                             bool act, int l, const LevelStencil &s, float lw,
                                              const float g[4]) {
   const unsigned full = 0xffffffffu;
   if (__ballot_sync(full, act) == 0u) return;
   const int lane = threadIdx.x & 31;
-  const unsigned long long key =
-      act ? ((unsigned long long)(uint32_t)l << 40) | ((unsigned long long)s.valid << 32) |
-                (s.sx[0] | s.sy[0] | s.sz[0])
-          : ~0ull;
+  // (level, cell) as one 32-bit key: the cell's Morton code offset by the
+  // texels of all finer levels (< 2^31 for n <= 1024); lanes in one cell of
+  // one level share its corner validity too.
+  const uint32_t key = act ? code_off[l] + (s.sx[0] | s.sy[0] | s.sz[0]) : 0xffffffffu;
   const unsigned grp = __match_any_sync(full, key);
   const bool big = act && __popc(grp) >= 4;
-  if (act && !big) scatter_lane(L, sg, l, s, lw, g);
+  if (act && !big) scatter_lane(L, l, s, lw, g);
   unsigned pending = __ballot_sync(full, big);
   while (pending) {
     const int leader = __ffs(pending) - 1;
@@ -99,20 +87,20 @@ __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const SmemGrad 
     // is the leader's: take its spread coordinates (a shuffle returns the
     // source lane's value, so per-corner choices are made afterwards).
     const int c = lane >> 2, ch = lane & 3;
-    const int ll = __shfl_sync(full, l, leader);
+    const int ll = __shfl_sync(full, l, leader);  // this lane's own level may differ
     const uint32_t lvalid = __shfl_sync(full, s.valid, leader);
     const uint32_t sx0 = __shfl_sync(full, s.sx[0], leader), sx1 = __shfl_sync(full, s.sx[1], leader);
     const uint32_t sy0 = __shfl_sync(full, s.sy[0], leader), sy1 = __shfl_sync(full, s.sy[1], leader);
     const uint32_t sz0 = __shfl_sync(full, s.sz[0], leader), sz1 = __shfl_sync(full, s.sz[1], leader);
     const uint32_t idx = ((c & 1) ? sx1 : sx0) | (((c >> 1) & 1) ? sy1 : sy0) | ((c >> 2) ? sz1 : sz0);
-    if (((lvalid >> c) & 1u) && v[0] != 0.0f) atomicAdd(grad_texel(L, sg, ll, idx) + ch, v[0]);
+    if (((lvalid >> c) & 1u) && v[0] != 0.0f) atomicAdd(grad_texel(L, ll, idx) + ch, v[0]);
     pending &= ~lgrp;
   }
 }
 
 // Adjoint of one cone for every lane of the warp (warp-uniform call; lanes
 // with active == false take no samples).
-__device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const SmemGrad &sg,
+__device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t *code_off,
                                              const uint32_t *lut, bool active,
                                              const Apex &A, const float w[3],
                                              const ConeConst &cc, float T0, float gc0, float gc1,
@@ -174,14 +162,14 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const SmemGrad 
       Q *= om;
       tr_next = tr;
     }
-    scatter_warp(L, sg, act, lp.l0, st[0], 1.0f - lp.f, g);
+    scatter_warp(L, code_off, act, lp.l0, st[0], 1.0f - lp.f, g);
     const bool two = act && lp.f > 0.0f;
-    if (__any_sync(full, two)) scatter_warp(L, sg, two, lp.l1, st[1], lp.f, g);
+    if (__any_sync(full, two)) scatter_warp(L, code_off, two, lp.l1, st[1], lp.f, g);
   }
 }
 
 template <int LPP>
-__global__ void __launch_bounds__(kTraceThreads, 3) trace_bwd_kernel(const __grid_constant__ BwdLaunch L) {
+__global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __grid_constant__ BwdLaunch L) {
   constexpr int kPixPerRound = 32 / LPP;
   const int lane = threadIdx.x & 31;
   const int slot = lane % LPP;
@@ -190,18 +178,17 @@ __global__ void __launch_bounds__(kTraceThreads, 3) trace_bwd_kernel(const __gri
   const float T0 = (float)L.t0_vox;
   const DevPyr &P = L.pyr;
 
-  extern __shared__ __align__(16) float s_grad[];
-  SmemGrad sg;
-  sg.base = s_grad;
-  sg.first = L.smem_first_level;
-  int smem_texels = 0;
-  for (int l = 0; l < VCT_MAX_LEVELS; ++l) {
-    sg.off[l] = smem_texels;
-    if (l >= sg.first && l < P.levels) smem_texels += (int)level_texels(P.n, l);
+  // per level: texels of all finer levels (offsets of the scatter's cell keys)
+  __shared__ uint32_t s_code_off[VCT_MAX_LEVELS];
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int l = 0; l < VCT_MAX_LEVELS; ++l) {
+      s_code_off[l] = acc;
+      if (l < P.levels) acc += (uint32_t)level_texels(P.n, l);
+    }
   }
-  for (int i = threadIdx.x; i < 4 * smem_texels; i += blockDim.x) s_grad[i] = 0.f;
   __shared__ uint32_t s_lut[1024];
-  fill_spread_lut(s_lut);  // (its barrier also covers the zeroing above)
+  fill_spread_lut(s_lut);  // (its barrier also covers s_code_off)
 
   for (;;) {
     const int item = next_item(L.queue);
@@ -282,38 +269,22 @@ __global__ void __launch_bounds__(kTraceThreads, 3) trace_bwd_kernel(const __gri
         }
         const bool on = pix_on && has_cone && (g0 != 0.f || g1 != 0.f || g2 != 0.f || ga != 0.f);
         if (__any_sync(0xffffffffu, on))
-          cone_adjoint(L, sg, s_lut, on, A, w, cc, T0, g0, g1, g2, ga);
+          cone_adjoint(L, s_code_off, s_lut, on, A, w, cc, T0, g0, g1, g2, ga);
       }
-    }
-  }
-  // Add this CTA's coarse-level gradients to global memory.
-  __syncthreads();
-  for (int l = sg.first; l < P.levels; ++l) {
-    const int cnt = (int)level_texels(P.n, l);
-    float4 *g = reinterpret_cast<float4 *>(L.gpyr_lvl[l]);
-    const float4 *src = reinterpret_cast<const float4 *>(s_grad) + sg.off[l];
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      const float4 v = src[i];
-      if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) atomicAdd(g + i, v);
     }
   }
 }
 
 template <int LPP>
-cudaError_t launch_b(const BwdLaunch &L, int grid, size_t smem, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(trace_bwd_kernel<LPP>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  trace_bwd_kernel<LPP><<<grid, kTraceThreads, smem, s>>>(L);
+cudaError_t launch_b(const BwdLaunch &L, int grid, cudaStream_t s) {
+  trace_bwd_kernel<LPP><<<grid, kTraceThreads, 0, s>>>(L);
   return cudaGetLastError();
 }
 
 template <int LPP>
-int occ_b(size_t smem) {
+int occ_b() {
   int b = 0;
-  cudaFuncSetAttribute(trace_bwd_kernel<LPP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_bwd_kernel<LPP>, kTraceThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_bwd_kernel<LPP>, kTraceThreads, 0);
   return b;
 }
 
@@ -321,29 +292,22 @@ int occ_b(size_t smem) {
 
 static_assert(sizeof(BwdLaunch) <= 32000, "adjoint launch parameters exceed the 32 KB limit");
 
-size_t bwd_smem_bytes(int n, int levels, int first) {
-  size_t t = 0;
-  for (int l = first; l < levels; ++l) t += level_texels(n, l);
-  return t * 16;
-}
-
 cudaError_t launch_trace_bwd(const BwdLaunch &L, int lpp, int grid, cudaStream_t s) {
-  const size_t smem = bwd_smem_bytes(L.pyr.n, L.pyr.levels, L.smem_first_level);
   switch (lpp) {
-    case 1: return launch_b<1>(L, grid, smem, s);
-    case 2: return launch_b<2>(L, grid, smem, s);
-    case 4: return launch_b<4>(L, grid, smem, s);
-    case 8: return launch_b<8>(L, grid, smem, s);
+    case 1: return launch_b<1>(L, grid, s);
+    case 2: return launch_b<2>(L, grid, s);
+    case 4: return launch_b<4>(L, grid, s);
+    case 8: return launch_b<8>(L, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-int trace_bwd_occupancy(int lpp, size_t smem) {
+int trace_bwd_occupancy(int lpp) {
   switch (lpp) {
-    case 1: return occ_b<1>(smem);
-    case 2: return occ_b<2>(smem);
-    case 4: return occ_b<4>(smem);
-    case 8: return occ_b<8>(smem);
+    case 1: return occ_b<1>();
+    case 2: return occ_b<2>();
+    case 4: return occ_b<4>();
+    case 8: return occ_b<8>();
     default: return 0;
   }
 }

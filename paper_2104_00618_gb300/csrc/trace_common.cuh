@@ -20,15 +20,24 @@ struct Apex {
 };
 
 // Per-pixel set-up (Ch. 4.2: cone apex on the surface, offset along the
-// normal; Ch. 6.2: an offset of a voxel avoids self-collision).
+// normal; Ch. 6.2: an offset of a voxel avoids self-collision).  The grid
+// coordinate X = (x - origin) * scale is split into floor(X) and a float
+// remainder without double precision: x - origin exactly as s + e (TwoSum),
+// s * scale_hi exactly as p + pe (one fma), and the small terms s * scale_lo
+// and e * scale_hi added to the remainder p - floor(p), which is exact.
 __device__ __forceinline__ void make_apex(const DevPyr &P, const float x[3], const float n[3],
                                           float normal_offset, Apex &A) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double X = ((double)x[a] - P.origin[a]) * P.scale;
-    const double fl = floor(X);
+    const float o = P.origin_f[a];
+    const float sd = x[a] - o;
+    const float bb = sd - x[a];
+    const float e = (x[a] - (sd - bb)) - (o + bb);  // x - o = sd + e exactly
+    const float p = __fmul_rn(sd, P.scale_hi);      // rounded product, never contracted
+    const float pe = fmaf(sd, P.scale_hi, -p);      // sd * scale_hi = p + pe exactly
+    const float fl = floorf(p);
     A.Xi[a] = (int)fl;
-    A.Of[a] = (float)((X - fl) + (double)normal_offset * (double)n[a]);
+    A.Of[a] = (p - fl) + (pe + fmaf(sd, P.scale_lo, e * P.scale_hi)) + normal_offset * n[a];
   }
 }
 

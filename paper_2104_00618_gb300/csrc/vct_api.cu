@@ -162,8 +162,13 @@ vct_status fill_pyr(const vct_pyramid &p, const vct_trace_params &P, DevPyr &d) 
     d.lvl[l] = static_cast<const uint8_t *>(p.data) + L.level_off[l];
   d.pool = static_cast<const uint8_t *>(p.data) + L.pool_off;
   d.bricked = L.bricked;
-  for (int a = 0; a < 3; ++a) d.origin[a] = p.origin[a];
+  for (int a = 0; a < 3; ++a) {
+    d.origin[a] = p.origin[a];
+    d.origin_f[a] = p.origin[a];
+  }
   d.scale = (double)p.n / (double)p.size;
+  d.scale_hi = (float)d.scale;
+  d.scale_lo = (float)(d.scale - (double)d.scale_hi);
   d.tmax_vox = (double)P.t_max * d.scale;
   // sample coordinates relative to the apex stay below 2^21 voxels
   if (d.tmax_vox > 1048576.0)
@@ -644,17 +649,10 @@ vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
   L->queue = reinterpret_cast<unsigned *>(ws);
   L->tile_w = c.tile_w;
   L->tile_h = c.tile_h;
-  {
-    int first = 0;
-    while (first < pyr->levels && (pyr->n >> first) > kBwdSmemMaxEdge) ++first;
-    L->smem_first_level = first;
-  }
-  const size_t smem = bwd_smem_bytes(pyr->n, pyr->levels, L->smem_first_level);
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(ws, 0, gl.total, s);
   if (e != cudaSuccess) return cuda_fail(e, "vct_trace_backward workspace clear");
-  int per_sm =
-      c.ctas_per_sm ? c.ctas_per_sm : std::max(1, trace_bwd_occupancy(c.lanes_per_pixel, smem));
+  int per_sm = c.ctas_per_sm ? c.ctas_per_sm : std::max(1, trace_bwd_occupancy(c.lanes_per_pixel));
   const int sms = sm_count();
   for (int v0 = 0; v0 < n_views; v0 += kMaxBwdViewsPerLaunch) {
     const int nv = std::min(kMaxBwdViewsPerLaunch, n_views - v0);

@@ -220,6 +220,8 @@ struct DevPyr {
   double tmax_vox;  // t_max in level-0 voxel units
   int n, levels, dtype;
   float h0;  // level-0 voxel edge in scene units
+  float origin_f[3];         // origin (float32, as given)
+  float scale_hi, scale_lo;  // n / size as a float pair
   ConeConst diffuse, occ, spec_fixed;
 };
 
@@ -285,8 +287,6 @@ struct BwdLaunch {
   float normal_offset;
   double spec_gmin, spec_gmax, rough_min, beta, t0_vox;
   unsigned *queue;
-  int smem_first_level;             // levels >= this accumulate in shared memory
-  int pad1;
   float *gpyr_lvl[VCT_MAX_LEVELS];  // float32 gradient pyramid levels
   DevPyr pyr;
   BwdView views[kMaxBwdViewsPerLaunch];
@@ -334,8 +334,6 @@ cudaError_t launch_trace(const TraceLaunch &L, int lpp, int dtype, bool bricks, 
                          cudaStream_t s);
 int trace_occupancy(int lpp, int dtype, bool variants);
 cudaError_t launch_trace_bwd(const BwdLaunch &L, int lpp, int grid, cudaStream_t s);
-int trace_bwd_occupancy(int lpp, size_t smem);
-size_t bwd_smem_bytes(int n, int levels, int first);
-constexpr int kBwdSmemMaxEdge = 16;  // levels of at most 16^3 texels use shared memory
+int trace_bwd_occupancy(int lpp);
 
 }  // namespace vct
