@@ -479,9 +479,15 @@ def extra_fwd_bwd(torch, vct, dev, n=128, n_views=32, res=512):
     vct.trace([Pgt], views, params, workspace=ws)
     targets = [(v.out_diffuse.clone(), v.out_specular.clone(), v.out_visibility.clone())
                for v in views]
+    # the training forward also records each cone's length for the adjoint
+    states = [v.alloc_cone_state(params).cone_state for v in views]
     P = vct.Pyramid(n, None, "f32", device=dev)
     bws = vct.backward_workspace(P)
     grad = torch.zeros_like(learn)
+
+    def use_state(on):
+        for v, st in zip(views, states):
+            v.cone_state = st if on else None
 
     def fwd():
         vct.build_mips(learn, out=P)
@@ -494,8 +500,10 @@ def extra_fwd_bwd(torch, vct, dev, n=128, n_views=32, res=512):
         grad.zero_()
         vct.trace_backward(P, views, grads, params, grad_level0=grad, workspace=bws)
 
-    f_ms = _time(torch, fwd, 5)
-    fb_ms = _time(torch, fwd_bwd, 5)
+    use_state(False)
+    f_ms = _time(torch, fwd, 5)         # the plain forward
+    use_state(True)
+    fb_ms = _time(torch, fwd_bwd, 5)    # forward with cone state + adjoint
     samples = int(sum(vct.read_stats(ws)["samples"]))
     return {"workload": f"learnable{n}_{n_views}x{res}^2_f32", "fwd_ms": f_ms, "fwd_bwd_ms": fb_ms,
             "fwd_bwd_over_fwd": fb_ms / f_ms, "samples_per_fwd": samples,

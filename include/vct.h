@@ -259,6 +259,14 @@ typedef struct {
   float *out_visibility; /* [H*W] Vis = 1 - alpha of the occlusion cone       */
   const float *albedo;   /* [H*W*3] material colour for the shading, or NULL (1) */
   float *out_radiance;   /* [H*W*4] shaded colour (VCT_FLAG_SHADE), or NULL  */
+  /* Per-cone march state, or NULL: [n_cones][H*W] pairs (uint32 number of
+   * samples K, float32 transmittance before the last sample), 8-byte
+   * aligned; cones in the order specular (if enabled), occlusion (if
+   * enabled), diffuse 0 .. n_diffuse-1.  vct_trace writes it (masked pixels
+   * are skipped); vct_trace_backward, given the same pyramid, parameters
+   * and view, reads it instead of re-marching every cone to find where it
+   * stopped (its reverse walk needs both values). */
+  void *cone_state;
 } vct_view;
 
 /* Launch shape of the trace kernels (see vct_autotune_trace). */

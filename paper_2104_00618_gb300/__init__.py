@@ -213,6 +213,7 @@ class View:
     out_visibility: torch.Tensor | None = None
     albedo: torch.Tensor | None = None
     out_radiance: torch.Tensor | None = None
+    cone_state: torch.Tensor | None = None
     keep: list = field(default_factory=list)
 
     @staticmethod
@@ -247,7 +248,16 @@ class View:
                        _ptr(self.normal), _ptr(self.roughness), _ptr(self.mask),
                        (ctypes.c_float * 3)(*self.camera), 0.0, _ptr(self.out_diffuse),
                        _ptr(self.out_specular), _ptr(self.out_visibility), _ptr(self.albedo),
-                       _ptr(self.out_radiance))
+                       _ptr(self.out_radiance), _ptr(self.cone_state))
+
+    def alloc_cone_state(self, params) -> "View":
+        """Buffer for the per-cone march state that vct_trace writes and
+        vct_trace_backward reads (8 bytes per cone and pixel)."""
+        P = params if isinstance(params, VctTraceParams) else make_params(params)
+        n_cones = P.n_diffuse + P.spec_enable + P.occ_enable
+        self.cone_state = torch.empty((n_cones, self.width * self.height, 2), dtype=torch.int32,
+                                      device=self.position.device)
+        return self
 
 
 def _workspace(nbytes: int, device) -> torch.Tensor:
@@ -336,6 +346,7 @@ class TraceFn(torch.autograd.Function):
         pyr = build_mips(level0.detach().contiguous(), levels, "f32", origin, size)
         v = dataclasses.replace(view, keep=[])
         v.alloc_outputs()  # no radiance output: the adjoint covers D, S and Vis
+        v.alloc_cone_state(params)  # lets the adjoint skip its forward march
         trace(pyr, [v], params)
         ctx.pyr, ctx.view, ctx.params = pyr, v, params
         return v.out_diffuse, v.out_specular, v.out_visibility

@@ -46,7 +46,7 @@ class VctView(ctypes.Structure):
                 ("position", _vp), ("normal", _vp), ("roughness", _vp), ("mask", _vp),
                 ("camera", _c_f32 * 3), ("pad", _c_f32),
                 ("out_diffuse", _vp), ("out_specular", _vp), ("out_visibility", _vp),
-                ("albedo", _vp), ("out_radiance", _vp)]
+                ("albedo", _vp), ("out_radiance", _vp), ("cone_state", _vp)]
 
 
 class VctLaunchConfig(ctypes.Structure):

@@ -43,9 +43,9 @@ __device__ __forceinline__ float smoothstep0(float e1, float x) {
 template <int DT, bool kVar, bool BR>
 __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const float w[3],
                                         const ConeConst &cc, float T0, const uint32_t *lut,
-                                        uint32_t &nsamp, float &trans, int mode = kPlain,
-                                        const Variants *var = nullptr) {
-  float cr = 0.f, cg = 0.f, cb = 0.f, al = 0.f, tr = 1.f;
+                                        uint32_t &nsamp, float &trans, uint2 &state,
+                                        int mode = kPlain, const Variants *var = nullptr) {
+  float cr = 0.f, cg = 0.f, cb = 0.f, al = 0.f, tr = 1.f, tp = 1.f;
   int k = 0;
   for (; k < cc.kmax; ++k) {
     if (!((1.0f - tr) < 1.0f)) break;
@@ -59,6 +59,7 @@ __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const fl
         if (s.w > 0.01f) {
           nsamp += (uint32_t)(k + 1);
           trans = 0.0f;
+          state = make_uint2((uint32_t)(k + 1), __float_as_uint(tr));
           return make_float4(s.x, s.y, s.z, 1.0f);
         }
         continue;
@@ -74,10 +75,12 @@ __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const fl
     cg = fmaf(wg, s.y, cg);
     cb = fmaf(wg, s.z, cb);
     al += wg;
+    tp = tr;
     tr *= om;
   }
   nsamp += (uint32_t)k;
   trans = tr;
+  state = make_uint2((uint32_t)k, __float_as_uint(tp));
   return make_float4(cr, cg, cb, al);
 }
 
@@ -280,9 +283,11 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
             if (cs.kind == kOcclusion && (L.var.flags & VCT_FLAG_OCC_SMOOTH)) mode = kOccSmooth;
             if (cs.kind == kDiffuse && (L.var.flags & VCT_FLAG_DIFFUSE_FIRST_HIT)) mode = kFirstHit;
           }
-          float4 r =
-              march<DT, kVar, BR>(P, A, w, cc, T0, s_lut, n_samp[cs.kind], trans, mode, &L.var);
+          uint2 cst;
+          float4 r = march<DT, kVar, BR>(P, A, w, cc, T0, s_lut, n_samp[cs.kind], trans, cst,
+                                         mode, &L.var);
           n_cone[cs.kind] += 1u;
+          if (V.state) V.state[(size_t)c * V.W * V.H + p] = cst;
           if constexpr (kVar) {
             if (cs.kind == kSpecular && (L.var.flags & VCT_FLAG_SPEC_GRACE)) {
               const float f = spec_grace(L.var, w);
@@ -368,8 +373,10 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
       const ConeConst cc =
           spec_const(P, L.spec_gmin, L.spec_gmax, L.rough_min, L.beta, L.t0_vox, V.rough, p);
       float trans;
-      float4 r = march<DT, false, BR>(P, A, w, cc, T0, s_lut, n_samp[kSpecular], trans);
+      uint2 cst;
+      float4 r = march<DT, false, BR>(P, A, w, cc, T0, s_lut, n_samp[kSpecular], trans, cst);
       n_cone[kSpecular] += 1u;
+      if (V.state) V.state[p] = cst;  // the specular cone is cone 0
       if constexpr (kVar) {
         if (L.var.flags & VCT_FLAG_SPEC_GRACE) {
           const float f = spec_grace(L.var, w);

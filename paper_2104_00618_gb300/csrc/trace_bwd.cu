@@ -99,12 +99,14 @@ __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const uint32_t 
 }
 
 // Adjoint of one cone for every lane of the warp (warp-uniform call; lanes
-// with active == false take no samples).
+// with active == false take no samples).  With `state` (warp-uniform: null
+// or not for all lanes) the cone's length and transmittance before its last
+// sample come from the forward trace and the forward pass is skipped.
 __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t *code_off,
                                              const uint32_t *lut, bool active,
                                              const Apex &A, const float w[3],
                                              const ConeConst &cc, float T0, float gc0, float gc1,
-                                             float gc2, float ga) {
+                                             float gc2, float ga, const uint2 *state) {
   const unsigned full = 0xffffffffu;
   const DevPyr &P = L.pyr;
   float prod = 1.f, prod_last = 1.f;
@@ -113,6 +115,15 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t 
   int K = active ? -1 : 0;      // this lane's sample count once known
   bool rev = false;             // warp-uniform
   int kr = 0;                   // warp-uniform backward step
+  if (state != nullptr) {
+    if (active) {
+      const uint2 e = *state;
+      K = (int)e.x;
+      prod_last = __uint_as_float(e.y);
+    }
+    rev = true;
+    kr = (int)__reduce_max_sync(full, (unsigned)K);  // decremented before the first step
+  }
   for (;;) {
     if (!rev) {
       if (K < 0 && !(k < cc.kmax && (1.0f - prod) < 1.0f)) K = k;
@@ -268,8 +279,10 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
           ga = wt * gD.w;
         }
         const bool on = pix_on && has_cone && (g0 != 0.f || g1 != 0.f || g2 != 0.f || ga != 0.f);
+        const uint2 *st = V.state == nullptr ? nullptr
+                          : V.state + (on ? (size_t)c * V.W * V.H + p : 0);
         if (__any_sync(0xffffffffu, on))
-          cone_adjoint(L, s_code_off, s_lut, on, A, w, cc, T0, g0, g1, g2, ga);
+          cone_adjoint(L, s_code_off, s_lut, on, A, w, cc, T0, g0, g1, g2, ga, st);
       }
     }
   }

@@ -246,8 +246,9 @@ vct_status check_view(const vct_view &v, int i, int n_pyr, int flags) {
       (v.out_specular && !aligned(v.out_specular, 16)) ||
       (v.out_visibility && !aligned(v.out_visibility, 4)))
     return fail(VCT_ERR_INVALID_ARG, "view %d: outputs must be 16-byte aligned", i);
-  if ((v.albedo && !aligned(v.albedo, 4)) || (v.out_radiance && !aligned(v.out_radiance, 16)))
-    return fail(VCT_ERR_INVALID_ARG, "view %d: albedo/out_radiance misaligned", i);
+  if ((v.albedo && !aligned(v.albedo, 4)) || (v.out_radiance && !aligned(v.out_radiance, 16)) ||
+      (v.cone_state && !aligned(v.cone_state, 8)))
+    return fail(VCT_ERR_INVALID_ARG, "view %d: albedo/out_radiance/cone_state misaligned", i);
   if (need_outputs && v.out_radiance && !(flags & VCT_FLAG_SHADE))
     return fail(VCT_ERR_INVALID_ARG, "view %d: out_radiance needs VCT_FLAG_SHADE", i);
   if (need_outputs && !v.out_diffuse && !v.out_specular && !v.out_visibility && !v.out_radiance)
@@ -267,6 +268,7 @@ void fill_view(const vct_view &v, int tile_w, int tile_h, int &tile_cursor, DevV
   d.outV = v.out_visibility;
   d.albedo = v.albedo;
   d.outL = v.out_radiance;
+  d.state = static_cast<uint2 *>(v.cone_state);
   for (int a = 0; a < 3; ++a) d.cam[a] = v.camera[a];
   d.W = (uint16_t)v.width;
   d.H = (uint16_t)v.height;

@@ -233,6 +233,7 @@ struct DevView {
   float *outD, *outS, *outV;
   const float *albedo;
   float *outL;
+  uint2 *state;  // per-cone (K, transmittance before the last sample), or null
   float cam[3];
   int tile_begin, small_begin;  // first big / small tile item of the view
   uint16_t W, H, pyr, tiles_x;  // big tiles cover rows [0, y_split)

@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(_abi.VctPyramid) == 48
-    assert ctypes.sizeof(_abi.VctView) == 104
+    assert ctypes.sizeof(_abi.VctView) == 112
     assert ctypes.sizeof(_abi.VctLaunchConfig) == 16
     assert ctypes.sizeof(_abi.VctTraceStats) == 56
     assert ctypes.sizeof(_abi.VctTraceParams) == 16 + 32 * 12 + 32 * 4 + 4 * 5 + 12 + 16 + 4 * 9

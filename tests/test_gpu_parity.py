@@ -377,3 +377,28 @@ def test_batched_fp16_pyramids_against_oracle():
         worst_fp16 = max(worst_fp16, worst(res))
     print("batched fp16 worst floored rel error:", worst_fp16)
     assert worst_fp16 < 5e-2
+
+
+def test_backward_with_cone_state_matches_recomputed_march():
+    """The adjoint given the forward's per-cone state (sample count and
+    transmittance before the last sample) equals the adjoint that re-marches
+    every cone, and the state's sample counts add up to the trace's."""
+    gt, views_host, prm, learn = _diff_case()
+    P = gpu_pyramid(learn)
+    outs = {}
+    for with_state in (False, True):
+        views = [vct.View.from_host(v) for v in views_host]
+        if with_state:
+            for v in views:
+                v.alloc_cone_state(prm)
+        ws = vct.trace([P], views, prm)
+        torch.cuda.synchronize()
+        if with_state:
+            st = vct.read_stats(ws)
+            total = sum(int(v.cone_state[..., 0].long()[:, torch.from_numpy(
+                views_host[i]["mask"] != 0).cuda()].sum()) for i, v in enumerate(views))
+            assert total == sum(st["samples"])
+        grads = [(v.out_diffuse * 0.5, v.out_specular, v.out_visibility - 0.25) for v in views]
+        outs[with_state] = vct.trace_backward(P, views, grads, prm).cpu().numpy()
+    a, b = outs[False], outs[True]
+    assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max(), np.abs(a - b).max()
