@@ -155,14 +155,13 @@ __device__ __forceinline__ float4 shade_spec(const Variants &v, const DevView &V
 // Estimated step count of the specular cone (sort key only; float32).
 __device__ __forceinline__ uint32_t spec_steps_estimate(const TraceLaunch &L, const DevPyr &P,
                                                         const float *rough, int p) {
-  float g = (float)L.spec_gmin;
+  float g = L.spec.gmin;
   if (rough != nullptr) {
-    float f = (rough[p] - (float)L.rough_min) / (1.0f - (float)L.rough_min);
-    f = fminf(fmaxf(f, 0.0f), 1.0f);
-    g += f * (float)(L.spec_gmax - L.spec_gmin);
+    const float f = fminf(fmaxf((rough[p] - L.spec.rough_min) * L.spec.inv_rough_span, 0.0f), 1.0f);
+    g = fmaf(f, L.spec.gdelta, g);
   }
-  const float l2r = log1pf(2.0f * (float)L.beta * tanf(0.5f * g)) * 1.44269504f;
-  const float e = log2f((float)(P.tmax_vox / L.t0_vox)) / l2r;
+  const float l2r = log1pf(L.spec.two_beta * tanf(0.5f * g)) * 1.44269504f;
+  const float e = P.log2_tmax_t0 / l2r;
   return (uint32_t)fminf(fmaxf(e + 1.0f, 1.0f), 65535.0f);
 }
 
@@ -208,7 +207,7 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
   const bool defer_spec = kSortSpec && L.spec_enable;
   const int n_cones = L.n_diffuse + L.spec_enable + L.occ_enable;
   const int first_cone = defer_spec ? 1 : 0;  // the specular cone is cone 0
-  const float T0 = (float)L.t0_vox;
+  const float T0 = L.spec.t0_vox;
   __shared__ uint32_t s_lut[1024];
   __shared__ uint32_t s_keys[kFwdThreads / 32][kMaxSortPixels];
   uint32_t *keys = s_keys[threadIdx.x >> 5];
@@ -264,8 +263,7 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
           ConeConst cc;
           if (cs.kind == kSpecular) {
             reflect_dir(x, V.cam, n, w);
-            cc = spec_const(P, L.spec_gmin, L.spec_gmax, L.rough_min, L.beta, L.t0_vox,
-                            V.rough, p);
+            cc = spec_const(P, L.spec, V.rough, p);
           } else if (cs.kind == kOcclusion) {
             w[0] = L.light[0];
             w[1] = L.light[1];
@@ -370,8 +368,7 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
       Apex A;
       make_apex(P, x, n, L.normal_offset, A);
       reflect_dir(x, V.cam, n, w);
-      const ConeConst cc =
-          spec_const(P, L.spec_gmin, L.spec_gmax, L.rough_min, L.beta, L.t0_vox, V.rough, p);
+      const ConeConst cc = spec_const(P, L.spec, V.rough, p);
       float trans;
       uint2 cst;
       float4 r = march<DT, false, BR>(P, A, w, cc, T0, s_lut, n_samp[kSpecular], trans, cst);

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
   const int slot = lane % LPP;
   const int pr = lane / LPP;
   const int n_cones = L.n_diffuse + L.spec_enable + L.occ_enable;
-  const float T0 = (float)L.t0_vox;
+  const float T0 = L.spec.t0_vox;
   const DevPyr &P = L.pyr;
 
   // per level: texels of all finer levels (offsets of the scatter's cell keys)
@@ -259,9 +259,7 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
         float g0, g1, g2, ga;
         if (cs.kind == kSpecular) {
           if (pix_on) reflect_dir(x, V.cam, n, w);
-          cc = pix_on ? spec_const(P, L.spec_gmin, L.spec_gmax, L.rough_min, L.beta, L.t0_vox,
-                                   V.rough, p)
-                      : P.spec_fixed;
+          cc = pix_on ? spec_const(P, L.spec, V.rough, p) : P.spec_fixed;
           g0 = gS.x;
           g1 = gS.y;
           g2 = gS.z;

@@ -58,19 +58,18 @@ __device__ __forceinline__ void tangent_frame(const float n[3], float T[3], floa
   B[2] = n[0] * T[1] - n[1] * T[0];
 }
 
-// Reflection of the view ray about the normal, in FP64 (narrow cones are
-// sensitive to their axis).
+// Reflection of the view ray about the normal.
 __device__ __forceinline__ void reflect_dir(const float x[3], const float cam[3],
                                             const float n[3], float R[3]) {
-  double v[3];
+  float v[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) v[a] = (double)x[a] - (double)cam[a];
-  const double len = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  for (int a = 0; a < 3; ++a) v[a] = x[a] - cam[a];
+  const float len = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) v[a] /= len;
-  const double vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+  for (int a = 0; a < 3; ++a) v[a] = v[a] / len;
+  const float vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) R[a] = (float)(v[a] - 2.0 * vn * (double)n[a]);
+  for (int a = 0; a < 3; ++a) R[a] = fmaf(-2.0f * vn, n[a], v[a]);
 }
 
 // floor(v) of |v| < 2^22 as (float, int): v + 1.5 * 2^23 rounded down keeps
@@ -348,14 +347,22 @@ __device__ __forceinline__ ConeSel select_cone(int c, int spec, int occ) {
 }
 
 // Specular aperture from roughness, and its march constants (FP64).
-__device__ __forceinline__ ConeConst spec_const(const DevPyr &P, double gmin, double gmax,
-                                                double rmin, double beta, double t0_vox,
+// The aperture interpolates linearly in roughness; the step ratio and the
+// first level follow from it as in cone_const, in float32 (log1pf, tanf and
+// log2f are within two units in the last place, which moves the positions
+// of a cone's last steps by less than 1e-6 of their distance).
+__device__ __forceinline__ ConeConst spec_const(const DevPyr &P, const SpecSetup &S,
                                                 const float *rough, int p) {
   if (rough == nullptr) return P.spec_fixed;
-  double f = ((double)rough[p] - rmin) / (1.0 - rmin);
-  f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
-  const double g = gmin + f * (gmax - gmin);
-  return cone_const(g, beta, t0_vox, P.tmax_vox);
+  const float f = fminf(fmaxf((rough[p] - S.rough_min) * S.inv_rough_span, 0.0f), 1.0f);
+  const float g = fmaf(f, S.gdelta, S.gmin);
+  const float th = tanf(0.5f * g);
+  ConeConst c{};
+  c.l2r_hi = log1pf(S.two_beta * th) * 1.44269504088896341f;  // / ln 2
+  c.lam0_hi = log2f(2.0f * S.t0_vox * th);
+  const float e = P.log2_tmax_t0 / c.l2r_hi;
+  c.kmax = e >= 0.0f ? (int)fminf(floorf(e) + 1.0f, (float)(kMaxSteps + 1)) : 0;
+  return c;
 }
 
 }  // namespace vct

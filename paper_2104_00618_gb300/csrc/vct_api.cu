@@ -162,24 +162,22 @@ vct_status fill_pyr(const vct_pyramid &p, const vct_trace_params &P, DevPyr &d) 
     d.lvl[l] = static_cast<const uint8_t *>(p.data) + L.level_off[l];
   d.pool = static_cast<const uint8_t *>(p.data) + L.pool_off;
   d.bricked = L.bricked;
-  for (int a = 0; a < 3; ++a) {
-    d.origin[a] = p.origin[a];
-    d.origin_f[a] = p.origin[a];
-  }
-  d.scale = (double)p.n / (double)p.size;
-  d.scale_hi = (float)d.scale;
-  d.scale_lo = (float)(d.scale - (double)d.scale_hi);
-  d.tmax_vox = (double)P.t_max * d.scale;
+  for (int a = 0; a < 3; ++a) d.origin_f[a] = p.origin[a];
+  const double scale = (double)p.n / (double)p.size;  // scene units -> level-0 voxels
+  d.scale_hi = (float)scale;
+  d.scale_lo = (float)(scale - (double)d.scale_hi);
+  const double tmax_vox = (double)P.t_max * scale;
   // sample coordinates relative to the apex stay below 2^21 voxels
-  if (d.tmax_vox > 1048576.0)
+  if (tmax_vox > 1048576.0)
     return fail(VCT_ERR_INVALID_ARG, "params: t_max spans more than 2^20 voxels");
+  d.log2_tmax_t0 = (float)log2(tmax_vox / (double)P.t0_voxels);
   d.n = p.n;
   d.levels = p.levels;
   d.dtype = p.dtype;
   d.h0 = (float)((double)p.size / (double)p.n);
   const double beta = P.beta, t0 = P.t0_voxels;
   auto mk = [&](float g, ConeConst &c, const char *name) -> vct_status {
-    c = cone_const((double)g, beta, t0, d.tmax_vox);
+    c = cone_const((double)g, beta, t0, tmax_vox);
     if (c.kmax > kMaxSteps)
       return fail(VCT_ERR_INVALID_ARG, "params: %s cone needs more than %d steps", name,
                   kMaxSteps);
@@ -207,11 +205,12 @@ void fill_common(const vct_trace_params &P, LaunchT &L) {
   }
   for (int a = 0; a < 3; ++a) L.light[a] = P.light_dir[a];
   L.normal_offset = P.normal_offset_voxels;
-  L.spec_gmin = P.spec_aperture_min;
-  L.spec_gmax = P.spec_aperture_max;
-  L.rough_min = P.roughness_min;
-  L.beta = P.beta;
-  L.t0_vox = P.t0_voxels;
+  L.spec.gmin = P.spec_aperture_min;
+  L.spec.gdelta = P.spec_aperture_max - P.spec_aperture_min;
+  L.spec.rough_min = P.roughness_min;
+  L.spec.inv_rough_span = (float)(1.0 / (1.0 - (double)P.roughness_min));
+  L.spec.two_beta = 2.0f * P.beta;
+  L.spec.t0_vox = P.t0_voxels;
 }
 
 void fill_variants(const vct_trace_params &P, Variants &v) {

@@ -214,14 +214,12 @@ struct ConeConst {
 struct DevPyr {
   const uint8_t *lvl[VCT_MAX_LEVELS];  // level base pointers (slot table if bricked)
   const uint8_t *pool;                 // brick pool (brick layout)
-  uint32_t bricked, pad_b;             // bit l: level l is bricked
-  double origin[3];
-  double scale;  // n / size: scene units -> level-0 voxel units
-  double tmax_vox;  // t_max in level-0 voxel units
+  uint32_t bricked;                    // bit l: level l is bricked
+  float log2_tmax_t0;                  // log2(t_max / t0), both in level-0 voxels
   int n, levels, dtype;
   float h0;  // level-0 voxel edge in scene units
   float origin_f[3];         // origin (float32, as given)
-  float scale_hi, scale_lo;  // n / size as a float pair
+  float scale_hi, scale_lo;  // n / size (scene units -> level-0 voxels) as a float pair
   ConeConst diffuse, occ, spec_fixed;
 };
 
@@ -254,6 +252,15 @@ struct Variants {
   float light_dir[3];   // as given (not normalised), like the occlusion cone axis
 };
 
+// Launch constants of the specular cone set-up and of the march (float32:
+// the device path has no double-precision arithmetic).
+struct SpecSetup {
+  float gmin, gdelta;      // specular aperture at roughness_min, and its span
+  float rough_min, inv_rough_span;  // roughness_min, 1 / (1 - roughness_min)
+  float two_beta;          // 2 beta
+  float t0_vox;            // start distance in level-0 voxels
+};
+
 // Tail tiles: the last pixels of a launch are handed out in small tiles so
 // that warps finish together (forward trace only).
 constexpr int kSmallTileW = 8, kSmallTileH = 4;
@@ -267,7 +274,7 @@ struct TraceLaunch {
   float diffuse_weight[VCT_MAX_DIFFUSE];
   float light[3];
   float normal_offset;  // voxels
-  double spec_gmin, spec_gmax, rough_min, beta, t0_vox;
+  SpecSetup spec;
   unsigned *queue;
   unsigned long long *stats;  // vct_trace_stats::samples / cones
   DevPyr pyr[VCT_MAX_PYRAMIDS];
@@ -286,15 +293,15 @@ struct BwdLaunch {
   float diffuse_weight[VCT_MAX_DIFFUSE];
   float light[3];
   float normal_offset;
-  double spec_gmin, spec_gmax, rough_min, beta, t0_vox;
+  SpecSetup spec;
   unsigned *queue;
   float *gpyr_lvl[VCT_MAX_LEVELS];  // float32 gradient pyramid levels
   DevPyr pyr;
   BwdView views[kMaxBwdViewsPerLaunch];
 };
 
-// March constants of a cone of full aperture `gamma` (FP64).
-__host__ __device__ inline ConeConst cone_const(double gamma, double beta, double t0_vox,
+// March constants of a cone of full aperture `gamma` (host, FP64).
+inline ConeConst cone_const(double gamma, double beta, double t0_vox,
                                                 double tmax_vox) {
   ConeConst c{};
   double th = tan(0.5 * gamma);
