@@ -52,7 +52,7 @@ class OrcParams(ctypes.Structure):
 
 
 # variant flags (same bit values as the library's, an input convention)
-OCC_SMOOTH, SPEC_GRACE, DIFF_FIRST, SHADE, SHADE_IMPL = 1, 2, 4, 8, 16
+OCC_SMOOTH, SPEC_GRACE, DIFF_FIRST, SHADE, SHADE_IMPL, PREMUL = 1, 2, 4, 8, 16, 32
 
 
 class OrcView(ctypes.Structure):

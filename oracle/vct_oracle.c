@@ -63,6 +63,7 @@
 #define ORC_DIFF_FIRST 4   /* diffuse: colour of the first sample with opacity > 1/100     */
 #define ORC_SHADE 8        /* write the radiance L_vxct                                     */
 #define ORC_SHADE_IMPL 16  /* ... composed as L_impl instead                                */
+#define ORC_PREMUL 32      /* every cone: sample colour premultiplied, c += (1 - alpha) c_s */
 
 typedef struct {
   int32_t n_diffuse;
@@ -344,7 +345,10 @@ static void march_kind(const orc_grid *g, const double o[3], const double w[3],
       rec[k].st = st;
     }
     double wgt = (1.0 - alpha) * v[3];
-    for (int ch = 0; ch < 3; ++ch) c[ch] += wgt * v[ch];
+    /* Straight colour: c += (1 - alpha) a_s c_s (Ch. 4.3.2, reading of the
+     * garbled colour line); premultiplied colour: c += (1 - alpha) c_s. */
+    double cw = (P->flags & ORC_PREMUL) ? (1.0 - alpha) : wgt;
+    for (int ch = 0; ch < 3; ++ch) c[ch] += cw * v[ch];
     alpha += wgt;
     t += P->beta * d;
     ++k;

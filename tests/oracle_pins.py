@@ -813,3 +813,23 @@ def check_voxelize_area_and_clip():
     i, j = np.meshgrid(np.arange(n) + 0.5, np.arange(n) + 0.5, indexing="ij")
     want = int(((i + j) < n).sum())  # the hypotenuse u + v = n passes no centre
     assert st["fragments"] == want and int((o > 0).sum()) == want
+
+
+def check_premultiplied_compositing():
+    """Premultiplied sample colour (c += (1 - alpha) c_s) in a homogeneous
+    medium (c0, a): c = c0 * sum_{k<K} (1-a)^k = c0 (1 - (1-a)^K) / a, alpha
+    as in the straight form; the flag changes every cone kind alike."""
+    n = 64
+    c0 = np.array([0.3, 0.6, 0.9])
+    a, aperture, beta, t_max = 0.2, math.radians(30), 0.5, 0.25
+    g = np.empty((n, n, n, 4))
+    g[..., :3], g[..., 3] = c0, a
+    P = oracle.build_mips(g)
+    prm = dict(base_params(beta=beta, t_max=t_max), flags=oracle.PREMUL)
+    w = np.array([2.0, -1.0, 2.0]) / 3.0
+    K = closed_form_steps(1.0 / n, t_max, aperture, beta)
+    for kind in (-1, 0, 1, 2):
+        out, k = oracle.trace_cone(P, [0.5, 0.5, 0.5], w, aperture, prm, kind=kind)
+        tr = (1.0 - a) ** K
+        assert k == K and rel(out[3], 1.0 - tr) < 1e-12
+        assert rel(out[:3], c0 * (1.0 - tr) / a) < 1e-12, (kind, out)

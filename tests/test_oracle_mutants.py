@@ -20,8 +20,8 @@ MUTANTS = {
         "const double *v = lv + (((size_t)z * nl + y) * nl + x) * 4;",
         "const double *v = lv + (((size_t)x * nl + y) * nl + z) * 4;"),
     "printed colour line taken literally": (
-        "for (int ch = 0; ch < 3; ++ch) c[ch] += wgt * v[ch];",
-        "for (int ch = 0; ch < 3; ++ch) c[ch] = alpha * c[ch] + wgt * v[ch];"),
+        "for (int ch = 0; ch < 3; ++ch) c[ch] += cw * v[ch];",
+        "for (int ch = 0; ch < 3; ++ch) c[ch] = alpha * c[ch] + cw * v[ch];"),
     "level from diameter / scene size": (
         "stencil(g->n, g->levels, q, log2(d / h0), &st);",
         "stencil(g->n, g->levels, q, log2(d / g->size), &st);"),
@@ -71,6 +71,8 @@ MUTANTS = {
     "back-facing light not clamped": ("if (lam < 0.0) lam = 0.0;", ""),
     "x-dominant swizzle transposed": ("au = 2;\n      av = 1;", "au = 1;\n      av = 2;"),
     "snap without the origin": ("float a = v - origin;", "float a = v;"),
+    "premultiplied flag ignored": ("double cw = (P->flags & ORC_PREMUL) ? (1.0 - alpha) : wgt;",
+                                   "double cw = wgt;"),
 }
 
 CHECKS = [name for name in dir(pins) if name.startswith("check_")]
