@@ -197,13 +197,17 @@ vct_status vct_pyramid_status(const vct_pyramid *pyr, vct_stream_t stream);
  *   VCT_FLAG_SHADE_IMPL       with VCT_FLAG_SHADE: L = Vis * D + S + Vis *
  *                             direct instead (the thesis's L_impl, Ch. 5.4.4)
  * vct_trace_backward accepts only the two shading flags (the adjoint covers
- * D, S and Vis of the unmodified cones).
+ * D, S and Vis of the unmodified cones with straight colour).
  */
 #define VCT_FLAG_OCC_SMOOTH 1
 #define VCT_FLAG_SPEC_GRACE 2
 #define VCT_FLAG_DIFFUSE_FIRST_HIT 4
 #define VCT_FLAG_SHADE 8
 #define VCT_FLAG_SHADE_IMPL 16
+/* Every cone composites the sample colour as premultiplied by its opacity:
+ * c += (1 - alpha) c_s instead of c += (1 - alpha) a_s c_s (the other reading
+ * of the thesis's garbled colour line, Ch. 4.3.2); opacity as before. */
+#define VCT_FLAG_PREMULTIPLIED 32
 
 /*
  * Cone set and march parameters (the thesis's VoxSettings, Ch. 5.4.4).

@@ -22,15 +22,16 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import (FLAG_DIFFUSE_FIRST_HIT, FLAG_OCC_SMOOTH, FLAG_SHADE, FLAG_SHADE_IMPL,
-                   FLAG_SPEC_GRACE, VCT_F16, VCT_F32, VctError, VctLaunchConfig, VctMesh,
+from ._abi import (FLAG_DIFFUSE_FIRST_HIT, FLAG_OCC_SMOOTH, FLAG_PREMULTIPLIED, FLAG_SHADE,
+                   FLAG_SHADE_IMPL, FLAG_SPEC_GRACE, VCT_F16, VCT_F32, VctError, VctLaunchConfig, VctMesh,
                    VctPyramid, VctTraceParams, VctTraceStats, VctView, VctViewGrad,
                    VctVoxelizeStats, VctVoxelLight, check, load)
 
 __all__ = ["Pyramid", "build_mips", "read_level", "pyramid_status", "make_params", "trace",
            "trace_backward", "autotune", "read_stats", "TraceFn", "render", "VctError",
            "launch_config", "num_levels", "lib", "FLAG_OCC_SMOOTH", "FLAG_SPEC_GRACE",
-           "FLAG_DIFFUSE_FIRST_HIT", "FLAG_SHADE", "FLAG_SHADE_IMPL", "Mesh", "voxelize",
+           "FLAG_DIFFUSE_FIRST_HIT", "FLAG_SHADE", "FLAG_SHADE_IMPL", "FLAG_PREMULTIPLIED",
+           "Mesh", "voxelize",
            "voxelize_workspace", "read_voxelize_stats", "voxel_owner", "plan_bricks",
            "Pipeline"]
 

@@ -15,8 +15,8 @@ VCT_OK, VCT_ERR_INVALID_ARG, VCT_ERR_CUDA, VCT_ERR_WORKSPACE, VCT_ERR_UNSUPPORTE
     VCT_ERR_TIMEOUT = range(6)
 VCT_F32, VCT_F16 = 0, 1
 LAYOUT_DENSE, LAYOUT_BRICKS = 0, 1
-FLAG_OCC_SMOOTH, FLAG_SPEC_GRACE, FLAG_DIFFUSE_FIRST_HIT, FLAG_SHADE, FLAG_SHADE_IMPL = \
-    1, 2, 4, 8, 16
+FLAG_OCC_SMOOTH, FLAG_SPEC_GRACE, FLAG_DIFFUSE_FIRST_HIT, FLAG_SHADE, FLAG_SHADE_IMPL, \
+    FLAG_PREMULTIPLIED = 1, 2, 4, 8, 16, 32
 
 _c_i32, _c_u64, _c_f32, _vp = ctypes.c_int32, ctypes.c_uint64, ctypes.c_float, ctypes.c_void_p
 

@@ -71,9 +71,13 @@ __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const fl
       }
     }
     const float wg = tr * s.w;  // front-to-back weight T_k a_s
-    cr = fmaf(wg, s.x, cr);
-    cg = fmaf(wg, s.y, cg);
-    cb = fmaf(wg, s.z, cb);
+    float wc = wg;              // colour weight: T_k a_s, or T_k for premultiplied colour
+    if constexpr (kVar) {
+      if (var->flags & VCT_FLAG_PREMULTIPLIED) wc = tr;
+    }
+    cr = fmaf(wc, s.x, cr);
+    cg = fmaf(wc, s.y, cg);
+    cb = fmaf(wc, s.z, cb);
     al += wg;
     tp = tr;
     tr *= om;
@@ -371,7 +375,8 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
       const ConeConst cc = spec_const(P, L.spec, V.rough, p);
       float trans;
       uint2 cst;
-      float4 r = march<DT, false, BR>(P, A, w, cc, T0, s_lut, n_samp[kSpecular], trans, cst);
+      float4 r = march<DT, kVar, BR>(P, A, w, cc, T0, s_lut, n_samp[kSpecular], trans, cst,
+                                     kPlain, &L.var);
       n_cone[kSpecular] += 1u;
       if (V.state) V.state[p] = cst;  // the specular cone is cone 0
       if constexpr (kVar) {

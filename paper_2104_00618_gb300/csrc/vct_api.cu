@@ -94,8 +94,9 @@ constexpr double kPi = 3.14159265358979323846;
 bool aperture_ok(float g) { return finite(g) && g > 0.0f && g < (float)kPi; }
 
 constexpr int kFlagsAll = VCT_FLAG_OCC_SMOOTH | VCT_FLAG_SPEC_GRACE | VCT_FLAG_DIFFUSE_FIRST_HIT |
-                          VCT_FLAG_SHADE | VCT_FLAG_SHADE_IMPL;
-constexpr int kFlagsCone = VCT_FLAG_OCC_SMOOTH | VCT_FLAG_SPEC_GRACE | VCT_FLAG_DIFFUSE_FIRST_HIT;
+                          VCT_FLAG_SHADE | VCT_FLAG_SHADE_IMPL | VCT_FLAG_PREMULTIPLIED;
+constexpr int kFlagsCone = VCT_FLAG_OCC_SMOOTH | VCT_FLAG_SPEC_GRACE | VCT_FLAG_DIFFUSE_FIRST_HIT |
+                           VCT_FLAG_PREMULTIPLIED;
 
 // `backward`: the adjoint covers the unmodified cones only.
 vct_status check_params(const vct_trace_params *P, bool backward) {

@@ -115,7 +115,7 @@ def test_variant_flag_validation_without_gpu(lib):
         return lib.vct_trace(ctypes.byref(p), 1, ctypes.byref(view), 1, ctypes.byref(prm),
                              None, None, 0, None)
 
-    assert run(32) == _abi.VCT_ERR_INVALID_ARG and b"unknown flags" in lib.vct_last_error()
+    assert run(64) == _abi.VCT_ERR_INVALID_ARG and b"unknown flags" in lib.vct_last_error()
     assert run(_abi.FLAG_SHADE_IMPL) == _abi.VCT_ERR_INVALID_ARG
     assert run(_abi.FLAG_OCC_SMOOTH, occ_max_dist=0.0) == _abi.VCT_ERR_INVALID_ARG
     assert run(_abi.FLAG_SPEC_GRACE, shininess=-1.0) == _abi.VCT_ERR_INVALID_ARG
@@ -132,7 +132,7 @@ def test_variant_flag_validation_without_gpu(lib):
     assert run(0, view=vw) == _abi.VCT_ERR_INVALID_ARG
     # every valid combination passes validation (and stops at the workspace)
     vr.out_radiance = 8192
-    for flags in range(32):
+    for flags in range(64):
         if flags & _abi.FLAG_SHADE_IMPL and not flags & _abi.FLAG_SHADE:
             continue
         view = vr if flags & _abi.FLAG_SHADE else v
@@ -142,6 +142,7 @@ def test_variant_flag_validation_without_gpu(lib):
     for flags, want in [(_abi.FLAG_OCC_SMOOTH, _abi.VCT_ERR_UNSUPPORTED),
                         (_abi.FLAG_DIFFUSE_FIRST_HIT, _abi.VCT_ERR_UNSUPPORTED),
                         (_abi.FLAG_SPEC_GRACE, _abi.VCT_ERR_UNSUPPORTED),
+                        (_abi.FLAG_PREMULTIPLIED, _abi.VCT_ERR_UNSUPPORTED),
                         (_abi.FLAG_SHADE, _abi.VCT_ERR_INVALID_ARG)]:
         prm = vct.make_params(dict(base, flags=flags))
         st = lib.vct_trace_backward(ctypes.byref(p), ctypes.byref(v), ctypes.byref(g), 1,

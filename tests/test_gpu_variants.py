@@ -12,9 +12,9 @@ from metrics import report
 
 pytestmark = pytest.mark.gpu
 
-OCC, GRACE, FIRST, SHADE, IMPL = (vct.FLAG_OCC_SMOOTH, vct.FLAG_SPEC_GRACE,
-                                  vct.FLAG_DIFFUSE_FIRST_HIT, vct.FLAG_SHADE,
-                                  vct.FLAG_SHADE_IMPL)
+OCC, GRACE, FIRST, SHADE, IMPL, PREMUL = (vct.FLAG_OCC_SMOOTH, vct.FLAG_SPEC_GRACE,
+                                          vct.FLAG_DIFFUSE_FIRST_HIT, vct.FLAG_SHADE,
+                                          vct.FLAG_SHADE_IMPL, vct.FLAG_PREMULTIPLIED)
 TIE = 1e-5  # |a_s - 1/100| below this: either first-hit decision is correct
 
 
@@ -89,8 +89,8 @@ def _case():
     return _CASE["c"]
 
 
-FLAG_SETS = [OCC, GRACE, FIRST, SHADE, SHADE | IMPL, OCC | GRACE | FIRST | SHADE,
-             OCC | GRACE | FIRST | SHADE | IMPL]
+FLAG_SETS = [OCC, GRACE, FIRST, SHADE, SHADE | IMPL, PREMUL, OCC | GRACE | FIRST | SHADE,
+             OCC | GRACE | FIRST | SHADE | IMPL, PREMUL | OCC | GRACE | SHADE]
 
 
 @pytest.mark.parametrize("flags", FLAG_SETS)
@@ -123,7 +123,7 @@ def test_variants_change_the_result():
     P = gpu_pyramid(scene["grid"])
     base, _ = run_gpu(P, view, variant_params(prm0, 0))
     m = view["mask"] != 0
-    for flags, changed in [(OCC, "Vis"), (GRACE, "S"), (FIRST, "D")]:
+    for flags, changed in [(OCC, "Vis"), (GRACE, "S"), (FIRST, "D")]:  # (PREMUL changes D and S)
         out, _ = run_gpu(P, view, variant_params(prm0, flags))
         for k in ("D", "S", "Vis"):
             err = pixel_errors(out[k][m], base[k][m]).max()
