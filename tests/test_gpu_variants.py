@@ -7,7 +7,7 @@ import torch
 import oracle
 import paper_2104_00618_gb300 as vct
 import vct_synth as vs
-from gpu_cases import FP32_BOUND, gpu_pyramid, room_case
+from gpu_cases import FP32_BOUND, MIN_STEP_MARGIN, gpu_pyramid, room_case
 from metrics import report
 
 pytestmark = pytest.mark.gpu
@@ -167,7 +167,7 @@ def test_variants_room_1080p_sampled():
     idx = np.sort(rng.choice(view["width"] * view["height"], 20000, replace=False))
     O = oracle.build_mips(scene["grid"])
     ref = oracle.trace(O, view, prm, idx=idx)
-    assert ref["margin"] > 1e-9
+    assert ref["margin"] > MIN_STEP_MARGIN, ref["margin"]
     res, ties = check_against_oracle(out, ref, prm, O, view, idx=idx)
     print("1080p variants:", "ties", ties, {k: float(v.max()) for k, v in res.items()})
     for k, v in res.items():
