@@ -69,7 +69,7 @@ class OrcView(ctypes.Structure):
 
 
 def _source_files():
-    return [os.path.join(_HERE, "vct_oracle.c"), os.path.join(_HERE, "vct_voxelize.c")]
+    return [os.path.join(_HERE, f) for f in ("vct_oracle.c", "vct_voxelize.c", "vct_gbuffer.c")]
 
 
 def compile_source(sources, out_dir=None, tag=None) -> str:
@@ -123,6 +123,9 @@ def load_library(path: str):
     lib.orc_voxelize.argtypes = [vp, i64, vp, i64, vp, i32, vp, ctypes.c_float, vp, vp, dbl,
                                  dbl, vp, vp, vp]
     lib.orc_voxelize.restype = None
+    lib.orc_gbuffer.argtypes = [vp, i64, vp, i64, vp, vp, ctypes.c_float, vp, vp, vp, vp,
+                                ctypes.c_float, i32, i32, vp, i64, vp, vp, vp, vp, vp, vp]
+    lib.orc_gbuffer.restype = i32
     for f in ("orc_build_mips", "orc_mip_adjoint", "orc_sample", "orc_sample_lod",
               "orc_trace_cone", "orc_tangent_frame", "orc_trace",
               "orc_trace_backward"):
@@ -410,3 +413,38 @@ def voxelize(mesh: dict, n: int, origin=(0.0, 0.0, 0.0), size: float = 1.0,
                         _p(grid), _p(owner), _p(stats))
     return grid, owner, {"fragments": int(stats[0]), "skipped": int(stats[1]),
                          "degenerate": int(stats[2])}
+
+
+def gbuffer(mesh: dict, camera: dict, pixels=None):
+    """G-buffer of a triangle mesh (dict as for voxelize) seen by a pinhole
+    camera (dict: eye, forward, right, up, tan_half, width, height,
+    frame_origin, frame_size; vectors as float32).  pixels: linear pixel
+    indices (y * width + x) to evaluate, or None for all.  Returns dict of
+    tri [P] int32 (-1 = no hit), position / normal / albedo [P,3] float64,
+    mask [P] uint8 and the stats (skipped, degenerate)."""
+    verts = np.ascontiguousarray(mesh["vertices"], dtype=np.float32).reshape(-1, 3)
+    idx = np.ascontiguousarray(mesh["indices"], dtype=np.int32).reshape(-1, 3)
+    cols = np.ascontiguousarray(mesh["colors"], dtype=np.float32).reshape(-1, 3)
+    assert cols.shape[0] == idx.shape[0]
+    f32 = [np.ascontiguousarray(camera[k], dtype=np.float32).reshape(3)
+           for k in ("frame_origin", "eye", "forward", "right", "up")]
+    W, H = int(camera["width"]), int(camera["height"])
+    sel = None
+    if pixels is not None:
+        sel = np.ascontiguousarray(pixels, dtype=np.int64).reshape(-1)
+        assert sel.size == 0 or (sel.min() >= 0 and sel.max() < W * H)
+    count = W * H if sel is None else sel.size
+    tri = np.empty(count, np.int32)
+    pos, nrm, alb = (np.empty((count, 3), np.float64) for _ in range(3))
+    mask = np.empty(count, np.uint8)
+    stats = np.zeros(2, np.int64)
+    rc = _lib().orc_gbuffer(_p(verts), verts.shape[0], _p(idx), idx.shape[0], _p(cols),
+                            _p(f32[0]), float(np.float32(camera["frame_size"])), _p(f32[1]),
+                            _p(f32[2]), _p(f32[3]), _p(f32[4]),
+                            float(np.float32(camera["tan_half"])), W, H,
+                            None if sel is None else _p(sel), count, _p(tri), _p(pos),
+                            _p(nrm), _p(alb), _p(mask), _p(stats))
+    if rc != 0:
+        raise ValueError(f"orc_gbuffer failed ({rc}): camera outside the frame")
+    return {"tri": tri, "position": pos, "normal": nrm, "albedo": alb, "mask": mask,
+            "skipped": int(stats[0]), "degenerate": int(stats[1])}

@@ -833,3 +833,152 @@ def check_premultiplied_compositing():
         tr = (1.0 - a) ** K
         assert k == K and rel(out[3], 1.0 - tr) < 1e-12
         assert rel(out[:3], c0 * (1.0 - tr) / a) < 1e-12, (kind, out)
+
+
+# --------------------------------------------------------------------------
+# camera G-buffer (Ch. 5.4 geometry pass): closed forms, an independent
+# slab raycaster, exact ties
+# --------------------------------------------------------------------------
+TAN30 = math.tan(math.radians(30.0))
+
+
+def _gb_camera(eye, f, r, u, W, H, origin=(0.0, 0.0, 0.0), size=1.0):
+    v = lambda a: np.asarray(a, np.float32).reshape(3)  # noqa: E731
+    return {"eye": v(eye), "forward": v(f), "right": v(r), "up": v(u),
+            "tan_half": float(np.float32(TAN30)), "width": W, "height": H,
+            "frame_origin": v(origin), "frame_size": float(size)}
+
+
+def _gb_mesh(quads, colours):
+    """Quads (c0, c1, c2, c3) -> triangles (c0, c1, c2), (c0, c2, c3)."""
+    V, I, C = [], [], []
+    for q, col in zip(quads, colours):
+        b = len(V)
+        V.extend(q)
+        I += [[b, b + 1, b + 2], [b, b + 2, b + 3]]
+        C += [col, col]
+    return {"vertices": np.asarray(V, np.float32), "indices": np.asarray(I, np.int32),
+            "colors": np.asarray(C, np.float32)}
+
+
+def _plane_quad(z, lo=-0.9, hi=1.9, flip=False):
+    q = [(lo, lo, z), (hi, lo, z), (hi, hi, z), (lo, hi, z)]
+    return [q[0], q[3], q[2], q[1]] if flip else q  # same diagonal c0 - c2
+
+
+def _pixel_dirs(W, H):
+    """Directions (-sx, sy, 1) of the camera looking along +z with right =
+    -x, up = +y, float64 (the pixel-centre model of a pinhole camera)."""
+    i, j = np.meshgrid(np.arange(W), np.arange(H), indexing="xy")
+    sx = ((2 * i.ravel() + 1) / W - 1.0) * TAN30 * W / H
+    sy = (1.0 - (2 * j.ravel() + 1) / H) * TAN30
+    return np.stack([-sx, sy, np.ones_like(sx)], 1)
+
+
+def check_gbuffer_plane_closed_form():
+    """A plane z = 0.7 facing a camera at z = 0.1: every hit at eye + 0.6 d,
+    normal -z for either winding, the triangle by the side of the diagonal
+    y = x; the same with another fixed-point frame; a pixel subset equals the
+    full image."""
+    W, H, eye = 24, 16, np.array([0.5, 0.5, 0.1])
+    d = _pixel_dirs(W, H)
+    want = eye + 0.6 * d
+    side = want[:, 1] - want[:, 0]
+    for flip, origin, size in ((False, (0, 0, 0), 1.0), (True, (0, 0, 0), 1.0),
+                               (False, (-0.5, 0.25, -1.0), 4.0)):
+        mesh = _gb_mesh([_plane_quad(0.7, flip=flip)], [(0.2, 0.4, 0.6)])
+        mesh["colors"][1] = (0.9, 0.1, 0.3)
+        cam = _gb_camera(eye, (0, 0, 1), (-1, 0, 0), (0, 1, 0), W, H, origin, size)
+        g = oracle.gbuffer(mesh, cam)
+        tol = 2e-5 * size
+        assert g["mask"].all() and np.abs(g["position"] - want).max() < tol, (flip, origin)
+        assert np.array_equal(g["normal"], np.tile([0.0, 0.0, -1.0], (W * H, 1))), flip
+        far = np.abs(side) > 1e-4
+        upper = side > 0  # (c0, c2, c3) of the unflipped quad
+        tri = np.where(upper, 1, 0) if not flip else np.where(upper, 0, 1)
+        assert np.array_equal(g["tri"][far], tri[far]), flip
+        assert np.array_equal(g["albedo"], mesh["colors"][g["tri"]].astype(np.float64))
+        sel = np.array([0, 5, 77, W * H - 1, 200])
+        s = oracle.gbuffer(mesh, cam, pixels=sel)
+        for k in ("tri", "position", "normal", "albedo", "mask"):
+            assert np.array_equal(s[k], g[k][sel]), k
+
+
+def check_gbuffer_depth_order_and_ties():
+    """Nearest plane wins in either index order; coincident triangles and a
+    ray through a shared edge go to the lower index; a plane behind the
+    camera is never hit."""
+    W, H, eye = 25, 15, (0.5, 0.5, 0.1)
+    cam = _gb_camera(eye, (0, 0, 1), (-1, 0, 0), (0, 1, 0), W, H)
+    A, B = (1.0, 0.0, 0.0), (0.0, 1.0, 0.0)
+    near, far, behind = _plane_quad(0.5), _plane_quad(0.8), _plane_quad(-0.3)
+    for quads, cols, win in (([far, near], [A, B], B), ([near, far], [A, B], A),
+                             ([near, near], [A, B], A), ([behind, far], [A, B], B)):
+        g = oracle.gbuffer(_gb_mesh(quads, cols), cam)
+        assert g["mask"].all() and np.all(g["albedo"] == win), (cols, win)
+    g = oracle.gbuffer(_gb_mesh([behind], [A]), cam)
+    assert not g["mask"].any() and np.all(g["tri"] == -1)
+    # a diamond split along x = 0.5: the centre column (sx = 0) looks along
+    # the shared edge's plane exactly; both triangles are hit at equal depth
+    top, right, bot, left = (0.5, 0.9, 0.7), (0.8, 0.5, 0.7), (0.5, 0.1, 0.7), (0.2, 0.5, 0.7)
+    for order in ((0, 1), (1, 0)):
+        tris = [[top, right, bot], [top, bot, left]]
+        tris = [tris[k] for k in order]
+        mesh = {"vertices": np.asarray(tris, np.float32).reshape(-1, 3),
+                "indices": np.arange(6, dtype=np.int32).reshape(2, 3),
+                "colors": np.asarray([A, B], np.float32)}
+        g = oracle.gbuffer(mesh, cam)
+        centre = np.arange(H) * W + W // 2
+        assert g["mask"][centre].all() and np.all(g["tri"][centre] == 0), order
+        # off the edge: the right half of the image (-x side) is the left triangle
+        i = np.arange(W * H) % W
+        wing = [k for k in order].index(1)  # index of [top, bot, left] (x < 0.5)
+        hit = g["mask"].astype(bool)
+        assert np.all(g["tri"][hit & (i > W // 2)] == wing), order
+        assert np.all(g["tri"][hit & (i < W // 2)] == 1 - wing), order
+
+
+def check_gbuffer_against_slab_raycaster():
+    """Boxes and the room as triangles seen from an interior camera: the
+    same mask, face normals and positions as the slab-test raycaster of the
+    input generator (double precision, analytic boxes), up to the pixels
+    whose rays pass within rounding of a box edge."""
+    import vct_synth as vs
+    scene = vs.box_scene(32, 6, 5, room=True)
+    rng = np.random.default_rng(11)
+    W, H = 48, 32
+    mesh = vs.box_mesh(scene, tess=2)
+    for _ in range(2):
+        eye = vs.interior_camera(rng, scene["boxes"], 32)
+        target = vs.interior_camera(rng, scene["boxes"], 32)
+        pos, nrm, mask = vs.raycast_gbuffer(scene, W, H, eye, target)
+        g = oracle.gbuffer(mesh, vs.camera(eye, target, W, H))
+        assert np.array_equal(g["mask"], mask)
+        same = np.all(g["normal"] == nrm.reshape(-1, 3), axis=1)
+        assert same.mean() > 0.99, same.mean()
+        err = np.abs(g["position"] - pos.reshape(-1, 3))[same].max()
+        assert err < 2e-5, err
+
+
+def check_gbuffer_skips_and_frame():
+    """Bad indices and vertices beyond two frame sizes are skipped, zero-area
+    triangles are degenerate; a camera outside the frame is refused."""
+    W, H = 8, 6
+    cam = _gb_camera((0.5, 0.5, 0.1), (0, 0, 1), (-1, 0, 0), (0, 1, 0), W, H)
+    verts = np.array([[-1.9, -1.9, 0.7], [1.9, -1.9, 0.7], [0.5, 1.9, 0.7],   # usable
+                      [-1.0, -1.0, 0.6], [2.5, -1.0, 0.6], [0.5, 2.1, 0.6],   # y > 2
+                      [0.1, 0.1, 0.5], [0.5, 0.5, 0.5], [0.9, 0.9, 0.5]],     # collinear
+                     np.float32)
+    mesh = {"vertices": verts,
+            "indices": np.array([[0, 1, 2], [3, 4, 5], [6, 7, 8], [0, 1, 9]], np.int32),
+            "colors": np.ones((4, 3), np.float32)}
+    g = oracle.gbuffer(mesh, cam)
+    assert (g["skipped"], g["degenerate"]) == (2, 1), g
+    assert g["mask"].all() and np.all(g["tri"] == 0)
+    bad = dict(cam, eye=np.array([0.5, 0.5, 2.5], np.float32))
+    try:
+        oracle.gbuffer(mesh, bad)
+    except ValueError:
+        pass
+    else:
+        raise AssertionError("camera outside the frame accepted")

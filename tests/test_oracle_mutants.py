@@ -12,7 +12,7 @@ import oracle
 import oracle_pins as pins
 
 ORACLE_DIR = os.path.dirname(oracle.__file__)
-SOURCES = ["vct_oracle.c", "vct_voxelize.c"]
+SOURCES = ["vct_oracle.c", "vct_voxelize.c", "vct_gbuffer.c"]
 
 MUTANTS = {
     "texel centre dropped": ("double u = q[a] * nl - 0.5;", "double u = q[a] * nl;"),
@@ -73,6 +73,26 @@ MUTANTS = {
     "snap without the origin": ("float a = v - origin;", "float a = v;"),
     "premultiplied flag ignored": ("double cw = (P->flags & ORC_PREMUL) ? (1.0 - alpha) : wgt;",
                                    "double cw = wgt;"),
+    "image rows not flipped": (
+        "const float sy = (1.0f - (float)(2 * j + 1) / (float)H) * ty;",
+        "const float sy = ((float)(2 * j + 1) / (float)H - 1.0f) * ty;"),
+    "aspect ratio dropped": ("const float tx = (float)((double)tan_half * (double)W / (double)H);",
+                             "const float tx = tan_half;"),
+    "farthest hit wins": ("if (best < 0 || num * bden < bnum * den) {",
+                          "if (best < 0 || num * bden > bnum * den) {"),
+    "equal depth to the higher index": ("if (best < 0 || num * bden < bnum * den) {",
+                                        "if (best < 0 || num * bden <= bnum * den) {"),
+    "edges exclusive (det > 0)": ("hit = v[0] >= 0 && v[1] >= 0 && v[2] >= 0;",
+                                  "hit = v[0] > 0 && v[1] > 0 && v[2] > 0;"),
+    "edges exclusive (det < 0)": ("hit = v[0] <= 0 && v[1] <= 0 && v[2] <= 0;",
+                                  "hit = v[0] < 0 && v[1] < 0 && v[2] < 0;"),
+    "hits behind the camera": ("if (det > 0)\n        hit =", "if (v[0] + v[1] + v[2] > 0)\n        hit ="),
+    "normal not turned to the camera": ("const double sgn = bsigned > 0 ? -1.0 : 1.0;",
+                                        "const double sgn = 1.0;"),
+    "camera frame snap without the origin": ("const float rel = v - origin;",
+                                             "const float rel = v;"),
+    "hit position without the frame origin": (
+        "pos[3 * q + a] =\n          (double)frame_origin[a] + (", "pos[3 * q + a] =\n          ("),
 }
 
 CHECKS = [name for name in dir(pins) if name.startswith("check_")]

@@ -336,7 +336,50 @@ def interior_view(scene, width, height, rng, with_roughness=True):
     rough = None
     if with_roughness:
         rough = rng.uniform(0.05, 1.0, size=width * height).astype(np.float32)
-    return view_dict(pos, nrm, mask, width, height, cam, roughness=rough)
+    v = view_dict(pos, nrm, mask, width, height, cam, roughness=rough)
+    v["target"] = np.asarray(target, dtype=np.float64)
+    return v
+
+
+def camera(eye, target, width, height, fov_deg=60.0, frame_origin=(0.0, 0.0, 0.0),
+           frame_size=1.0):
+    """Pinhole camera of the G-buffer pass: eye, unit forward / right / up
+    (look_at, world up +y) and tan of half the vertical field of view, as
+    float32; frame_origin / frame_size set the fixed-point frame the hit
+    tests run in (the scene must lie within two frame sizes of the origin)."""
+    eye = np.asarray(eye, dtype=np.float64)
+    f, r, u = look_at(eye, target)
+    f32 = lambda a: np.asarray(a, dtype=np.float32).reshape(3)  # noqa: E731
+    return {"eye": f32(eye), "forward": f32(f), "right": f32(r), "up": f32(u),
+            "tan_half": float(np.float32(math.tan(math.radians(fov_deg) / 2.0))),
+            "width": int(width), "height": int(height), "frame_origin": f32(frame_origin),
+            "frame_size": float(np.float32(frame_size))}
+
+
+def box_mesh(scene, tess=1):
+    """The boxes that raycast_gbuffer intersects, as triangles with faces on
+    the box bounds (no inset): boxes outward, the room inward on
+    [1/n, (n-1)/n]^3; scene units; colour per box (room walls grey)."""
+    n = scene["n"]
+    V, I, C = [], [], []
+    count = 0
+
+    def add(faces, colour):
+        nonlocal count
+        for cs, _, _ in faces:
+            verts, tris = _quad_grid(*cs, tess)
+            V.append(verts)
+            I.append(tris + count)
+            C.append(np.broadcast_to(np.asarray(colour, np.float64), (len(tris), 3)))
+            count += len(verts)
+
+    if scene.get("room"):
+        add(_box_faces(np.full(3, 1.0), np.full(3, n - 1.0), 0.0, False), GREY)
+    for lo, hi, col in scene["boxes"]:
+        add(_box_faces(np.asarray(lo, np.float64), np.asarray(hi, np.float64), 0.0, True), col)
+    return {"vertices": (np.concatenate(V) / n).astype(np.float32),
+            "indices": np.concatenate(I).astype(np.int32),
+            "colors": np.concatenate(C).astype(np.float32)}
 
 
 # --------------------------------------------------------------------------
