@@ -516,6 +516,86 @@ vct_status vct_voxelize(const vct_mesh *mesh, int32_t n, const float origin[3], 
                         size_t workspace_bytes, vct_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Camera G-buffer (Ch. 5.4 geometry pass; Ch. 3.2 rasterisation)           */
+/* ------------------------------------------------------------------------ */
+/*
+ * Pinhole camera.  Pixel (i, j) of the width x height image (j = 0 the top
+ * row) looks along d = (forward + sx right) + sy up with
+ *   sx = ((2i+1)/width - 1) tx,  sy = (1 - (2j+1)/height) tan_half_fov,
+ *   tx = float32(tan_half_fov * width / height),
+ * every operation rounded to float32.  The hit tests run in a fixed-point
+ * frame of 2^17 units per frame_size, origin frame_origin: a position p
+ * snaps to X = rint(float32(float32(p - frame_origin) * s)), s =
+ * float32(2^17 / frame_size), and must satisfy |X| < 2^18 (the scene may
+ * reach two frame sizes from the origin); d snaps to rint(float32(d * 2^18)).
+ */
+typedef struct {
+  float eye[3];          /* camera position, inside the frame                   */
+  float forward[3];      /* view direction (unit length expected)               */
+  float right[3];        /* image +x (unit length expected)                     */
+  float up[3];           /* image +y (unit length expected)                     */
+  float tan_half_fov;    /* tan of half the vertical field of view, > 0         */
+  int32_t width, height; /* 1 .. 16384 pixels                                   */
+  float frame_origin[3]; /* fixed-point frame (above)                           */
+  float frame_size;      /* > 0                                                 */
+} vct_camera;
+
+/* Counters at the start of the G-buffer workspace after a call. */
+typedef struct {
+  uint64_t pairs;         /* (16x16 tile, triangle) pairs the binning produced */
+  uint64_t pair_capacity; /* pairs the workspace holds                         */
+  uint32_t skipped;       /* triangles with a bad index or a vertex beyond the frame */
+  uint32_t degenerate;    /* triangles of zero snapped area                    */
+  uint32_t culled;        /* triangles outside the view, or edge-on to the eye */
+  uint32_t wide;          /* triangles passing so close to the eye that they were
+                             binned to every tile                               */
+  uint32_t overflow;      /* 1: pairs > pair_capacity, every pixel left empty   */
+  uint32_t reserved[3];
+} vct_gbuffer_stats;
+
+/* Device workspace vct_gbuffer needs for a width x height image, a mesh of
+ * n_triangles and room for pair_capacity (tile, triangle) pairs (at most
+ * 2^31); 0 for invalid arguments.  Layout: a vct_gbuffer_stats padded to
+ * 256 bytes, 8 bytes per 16x16 tile (+ 4), 96 bytes per triangle, then
+ * 4 bytes per pair, each part 256-byte aligned.  A larger workspace holds
+ * proportionally more pairs. */
+size_t vct_gbuffer_workspace_bytes(int32_t width, int32_t height, int32_t n_triangles,
+                                   uint64_t pair_capacity);
+
+/*
+ * Draws `mesh` into the G-buffer that vct_trace reads (Ch. 5.4: geometry
+ * pass before the cone tracing), for every pixel the nearest triangle on
+ * the ray through the pixel centre.  With A, B, C the snapped vertices
+ * relative to the snapped eye and D the snapped pixel direction, the ray
+ * hits the double-sided triangle when D.(B x C), D.(C x A), D.(A x B) share
+ * the sign of det(A, B, C) (zeros allowed, not all zero); its distance is
+ * det(A, B, C) / (n . D), n = (B - A) x (C - A); the nearest hit wins by
+ * exact comparison, equal distances going to the lower triangle index.
+ * These decisions are exact integer arithmetic, so the result does not
+ * depend on scheduling.  Outputs per pixel p = j * width + i:
+ *   position [p*3]  hit point eye + t D in scene units (float32 t);
+ *   normal   [p*3]  unit geometric normal of the unsnapped triangle,
+ *                   turned towards the eye (by the sign of n . D);
+ *   albedo   [p*3]  the triangle's colour (or NULL);
+ *   mask     [p]    1 hit, 0 none (or NULL);
+ *   triangle [p]    triangle index, -1 none (or NULL).
+ * Pixels without a hit get zeros.  Triangles are binned to 16x16 pixel
+ * tiles by a conservative screen box (guard-band clipping); the pairs must
+ * fit the workspace, else the stats report overflow and every pixel is
+ * left empty (the needed count is in vct_gbuffer_stats.pairs).
+ * position/normal/albedo 4-byte aligned, triangle 4-byte aligned;
+ * workspace 256-byte aligned of at least vct_gbuffer_workspace_bytes(...,
+ * 0) bytes.  The camera needs forward, right and up components of
+ * magnitude <= 1 + 2^-10, |det(right, up, forward)| >= 0.25 (a roughly
+ * orthonormal basis) and tx + tan_half_fov <= 2.99, so that every snapped
+ * direction component stays within 2^20 and the integer arithmetic cannot
+ * overflow; the eye must lie inside the frame.
+ */
+vct_status vct_gbuffer(const vct_mesh *mesh, const vct_camera *camera, float *position,
+                       float *normal, float *albedo, uint8_t *mask, int32_t *triangle,
+                       void *workspace, size_t workspace_bytes, vct_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Diagnostics                                                              */
 /* ------------------------------------------------------------------------ */
 const char *vct_status_string(vct_status status);

@@ -23,7 +23,8 @@ import torch
 
 from . import _abi
 from ._abi import (FLAG_DIFFUSE_FIRST_HIT, FLAG_OCC_SMOOTH, FLAG_PREMULTIPLIED, FLAG_SHADE,
-                   FLAG_SHADE_IMPL, FLAG_SPEC_GRACE, VCT_F16, VCT_F32, VctError, VctLaunchConfig, VctMesh,
+                   FLAG_SHADE_IMPL, FLAG_SPEC_GRACE, VCT_F16, VCT_F32, VctCamera, VctError,
+                   VctGbufferStats, VctLaunchConfig, VctMesh,
                    VctPyramid, VctTraceParams, VctTraceStats, VctView, VctViewGrad,
                    VctVoxelizeStats, VctVoxelLight, check, load)
 
@@ -33,7 +34,8 @@ __all__ = ["Pyramid", "build_mips", "read_level", "pyramid_status", "make_params
            "FLAG_DIFFUSE_FIRST_HIT", "FLAG_SHADE", "FLAG_SHADE_IMPL", "FLAG_PREMULTIPLIED",
            "Mesh", "voxelize",
            "voxelize_workspace", "read_voxelize_stats", "voxel_owner", "plan_bricks",
-           "Pipeline"]
+           "Pipeline", "gbuffer", "gbuffer_workspace", "read_gbuffer_stats", "gbuffer_view",
+           "camera_struct"]
 
 DTYPES = {"f32": VCT_F32, "f16": VCT_F16, VCT_F32: VCT_F32, VCT_F16: VCT_F16}
 LAYOUTS = {"dense": _abi.LAYOUT_DENSE, "bricks": _abi.LAYOUT_BRICKS,
@@ -432,6 +434,87 @@ def voxel_owner(workspace: torch.Tensor, n: int) -> torch.Tensor:
     """The owner grid of the last vct_voxelize on this workspace: [n,n,n]
     int32, triangle index + 1 per voxel (0 = empty)."""
     return workspace[256:256 + 4 * n * n * n].view(torch.int32).reshape(n, n, n)
+
+
+# ---------------------------------------------------------------------------
+# camera G-buffer
+# ---------------------------------------------------------------------------
+def camera_struct(cam: dict) -> VctCamera:
+    """dict(eye, forward, right, up, tan_half, width, height, frame_origin,
+    frame_size) -> vct_camera."""
+    c = VctCamera()
+    for k, f in (("eye", "eye"), ("forward", "forward"), ("right", "right"), ("up", "up"),
+                 ("frame_origin", "frame_origin")):
+        v = [float(x) for x in cam[k]]
+        for a in range(3):
+            getattr(c, f)[a] = v[a]
+    c.tan_half_fov = float(cam["tan_half"])
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    c.frame_size = float(cam.get("frame_size", 1.0))
+    return c
+
+
+def gbuffer_workspace(width: int, height: int, n_triangles: int, pair_capacity: int | None = None,
+                      device="cuda") -> torch.Tensor:
+    """Workspace of vct_gbuffer; by default room for 8 (tile, triangle)
+    pairs per triangle plus 64 per 16x16 tile."""
+    if pair_capacity is None:
+        tiles = ((width + 15) // 16) * ((height + 15) // 16)
+        pair_capacity = 8 * n_triangles + 64 * tiles
+    nbytes = lib().vct_gbuffer_workspace_bytes(int(width), int(height), int(n_triangles),
+                                               int(pair_capacity))
+    if nbytes == 0:
+        raise VctError(_abi.VCT_ERR_INVALID_ARG, f"invalid G-buffer size {width}x{height}")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def read_gbuffer_stats(workspace: torch.Tensor) -> dict:
+    raw = workspace[:ctypes.sizeof(VctGbufferStats)].cpu().numpy().tobytes()
+    st = VctGbufferStats.from_buffer_copy(raw)
+    return {k: int(getattr(st, k)) for k in ("pairs", "pair_capacity", "skipped", "degenerate",
+                                             "culled", "wide", "overflow")}
+
+
+def gbuffer(mesh: Mesh, cam: dict, out: dict | None = None, workspace: torch.Tensor | None = None,
+            verify: bool = True, stream=None) -> dict:
+    """Draws the mesh into a G-buffer (vct_gbuffer).  Returns dict of device
+    tensors position / normal / albedo [H*W,3] float32, mask [H*W] uint8,
+    triangle [H*W] int32 and the workspace.  verify: read the stats back
+    (synchronises) and, if the tile lists overflowed, redo the call with a
+    workspace of the needed size."""
+    W, H = int(cam["width"]), int(cam["height"])
+    dev = mesh.vertices.device
+    if out is None:
+        out = {"position": torch.empty((W * H, 3), device=dev),
+               "normal": torch.empty((W * H, 3), device=dev),
+               "albedo": torch.empty((W * H, 3), device=dev),
+               "mask": torch.empty((W * H,), dtype=torch.uint8, device=dev),
+               "triangle": torch.empty((W * H,), dtype=torch.int32, device=dev)}
+    nt = mesh.indices.shape[0]
+    ws = workspace if workspace is not None else gbuffer_workspace(W, H, nt, device=dev)
+    c, m = camera_struct(cam), mesh.struct()
+    for _ in range(2):
+        check(lib().vct_gbuffer(ctypes.byref(m), ctypes.byref(c), _ptr(out["position"]),
+                                _ptr(out["normal"]), _ptr(out.get("albedo")),
+                                _ptr(out.get("mask")), _ptr(out.get("triangle")), _ptr(ws),
+                                ws.numel(), _stream(stream)), "vct_gbuffer")
+        if not verify:
+            break
+        st = read_gbuffer_stats(ws)
+        if not st["overflow"]:
+            break
+        ws = gbuffer_workspace(W, H, nt, st["pairs"], device=dev)
+    out["workspace"] = ws
+    return out
+
+
+def gbuffer_view(g: dict, cam: dict, roughness: torch.Tensor | None = None,
+                 pyramid: int = 0) -> View:
+    """A View over the buffers of gbuffer() (position, normal, mask, albedo)."""
+    v = View(int(cam["width"]), int(cam["height"]), g["position"], g["normal"],
+             tuple(float(x) for x in cam["eye"]), roughness, g.get("mask"), pyramid)
+    v.albedo = g.get("albedo")
+    return v.alloc_outputs()
 
 
 # ---------------------------------------------------------------------------

@@ -80,6 +80,19 @@ class VctVoxelizeStats(ctypes.Structure):
                 ("reserved", ctypes.c_uint32)]
 
 
+class VctCamera(ctypes.Structure):
+    _fields_ = [("eye", _c_f32 * 3), ("forward", _c_f32 * 3), ("right", _c_f32 * 3),
+                ("up", _c_f32 * 3), ("tan_half_fov", _c_f32), ("width", _c_i32),
+                ("height", _c_i32), ("frame_origin", _c_f32 * 3), ("frame_size", _c_f32)]
+
+
+class VctGbufferStats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_uint64), ("pair_capacity", ctypes.c_uint64),
+                ("skipped", ctypes.c_uint32), ("degenerate", ctypes.c_uint32),
+                ("culled", ctypes.c_uint32), ("wide", ctypes.c_uint32),
+                ("overflow", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+
+
 class VctPipelineDesc(ctypes.Structure):
     _fields_ = [("n", _c_i32), ("levels", _c_i32), ("dtype", _c_i32), ("width", _c_i32),
                 ("height", _c_i32), ("has_roughness", _c_i32), ("has_mask", _c_i32),
@@ -122,6 +135,9 @@ EXPORTS = {
     "vct_voxelize_workspace_bytes": (ctypes.c_size_t, [_c_i32, _c_i32]),
     "vct_voxelize": (_c_i32, [ctypes.POINTER(VctMesh), _c_i32, ctypes.POINTER(_c_f32), _c_f32,
                               ctypes.POINTER(VctVoxelLight), _vp, _vp, ctypes.c_size_t, _vp]),
+    "vct_gbuffer_workspace_bytes": (ctypes.c_size_t, [_c_i32, _c_i32, _c_i32, _c_u64]),
+    "vct_gbuffer": (_c_i32, [ctypes.POINTER(VctMesh), ctypes.POINTER(VctCamera), _vp, _vp, _vp,
+                             _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "vct_pipeline_create": (_c_i32, [ctypes.POINTER(VctPipelineDesc),
                                      ctypes.POINTER(VctTraceParams), ctypes.POINTER(_vp)]),
     "vct_pipeline_submit": (_c_i32, [_vp, ctypes.POINTER(VctHostFrame), _vp]),

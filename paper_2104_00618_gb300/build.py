@@ -19,9 +19,10 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libvct.so")
 
 SOURCES = ["vct_api.cu", "mips.cu", "trace.cu", "trace_bwd.cu", "noalloc.cu", "voxelize.cu",
-           "bricks.cu", "pipeline.cu"]
+           "bricks.cu", "pipeline.cu", "gbuffer.cu"]
 HEADERS = [os.path.join(CSRC, "vct_internal.cuh"), os.path.join(CSRC, "trace_common.cuh"),
-           os.path.join(CSRC, "voxelize.cuh"), os.path.join(INCLUDE, "vct.h")]
+           os.path.join(CSRC, "voxelize.cuh"), os.path.join(CSRC, "gbuffer.cuh"),
+           os.path.join(INCLUDE, "vct.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

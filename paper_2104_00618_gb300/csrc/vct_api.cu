@@ -15,6 +15,7 @@
 #include <tuple>
 #include <vector>
 
+#include "gbuffer.cuh"
 #include "voxelize.cuh"
 
 using namespace vct;
@@ -716,6 +717,71 @@ vct_status vct_voxelize(const vct_mesh *mesh, int32_t n, const float origin[3], 
   cudaError_t e = launch_voxelize(*mesh, n, origin, size, *light, level0_dense, workspace,
                                   sm_count(), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "vct_voxelize launch");
+  return VCT_OK;
+}
+
+size_t vct_gbuffer_workspace_bytes(int32_t width, int32_t height, int32_t n_triangles,
+                                   uint64_t pair_capacity) {
+  if (width < 1 || width > 16384 || height < 1 || height > 16384 || n_triangles < 0 ||
+      n_triangles > (1 << 30) || pair_capacity > (1ull << 31))
+    return 0;
+  return gbuffer_fixed_bytes(width, height, n_triangles) + (size_t)align256(pair_capacity * 4);
+}
+
+vct_status vct_gbuffer(const vct_mesh *mesh, const vct_camera *camera, float *position,
+                       float *normal, float *albedo, uint8_t *mask, int32_t *triangle,
+                       void *workspace, size_t workspace_bytes, vct_stream_t stream) {
+  if (!mesh || !camera) return fail(VCT_ERR_INVALID_ARG, "vct_gbuffer: NULL argument");
+  const vct_camera &c = *camera;
+  if (c.width < 1 || c.width > 16384 || c.height < 1 || c.height > 16384)
+    return fail(VCT_ERR_INVALID_ARG, "vct_gbuffer: image %dx%d outside 1..16384", c.width,
+                c.height);
+  if (mesh->n_vertices < 0 || mesh->n_triangles < 0 || mesh->n_triangles > (1 << 30))
+    return fail(VCT_ERR_INVALID_ARG, "vct_gbuffer: bad mesh counts (%d vertices, %d triangles)",
+                mesh->n_vertices, mesh->n_triangles);
+  if (mesh->n_triangles > 0 &&
+      (!mesh->indices || !mesh->colors || !aligned(mesh->indices, 4) || !aligned(mesh->colors, 4)))
+    return fail(VCT_ERR_INVALID_ARG, "vct_gbuffer: indices/colors NULL or misaligned");
+  if (mesh->n_vertices > 0 && (!mesh->vertices || !aligned(mesh->vertices, 4)))
+    return fail(VCT_ERR_INVALID_ARG, "vct_gbuffer: vertices NULL or misaligned");
+  if (!(c.frame_size > 0.0f) || !finite(c.frame_size) || !(c.tan_half_fov > 0.0f) ||
+      !finite(c.tan_half_fov))
+    return fail(VCT_ERR_INVALID_ARG, "vct_gbuffer: frame_size and tan_half_fov must be > 0");
+  const double lim = 1.0 + 1.0 / 1024.0;
+  for (int a = 0; a < 3; ++a) {
+    if (!finite(c.eye[a]) || !finite(c.frame_origin[a]))
+      return fail(VCT_ERR_INVALID_ARG, "vct_gbuffer: eye/frame_origin not finite");
+    if (!(fabs(c.forward[a]) <= lim) || !(fabs(c.right[a]) <= lim) || !(fabs(c.up[a]) <= lim))
+      return fail(VCT_ERR_INVALID_ARG,
+                  "vct_gbuffer: basis components must have magnitude <= 1 + 2^-10");
+  }
+  const double det =
+      (double)c.right[0] * ((double)c.up[1] * c.forward[2] - (double)c.up[2] * c.forward[1]) -
+      (double)c.up[0] * ((double)c.right[1] * c.forward[2] - (double)c.right[2] * c.forward[1]) +
+      (double)c.forward[0] * ((double)c.right[1] * c.up[2] - (double)c.right[2] * c.up[1]);
+  if (!(fabs(det) >= 0.25))
+    return fail(VCT_ERR_INVALID_ARG, "vct_gbuffer: |det(right, up, forward)| = %g < 0.25", det);
+  const float tx = (float)((double)c.tan_half_fov * (double)c.width / (double)c.height);
+  if (!((double)tx + (double)c.tan_half_fov <= 2.99))
+    return fail(VCT_ERR_INVALID_ARG,
+                "vct_gbuffer: field of view too wide (tx + tan_half_fov = %g > 2.99)",
+                (double)tx + c.tan_half_fov);
+  const float s = (float)((double)kFrameUnits / (double)c.frame_size);
+  for (int a = 0; a < 3; ++a) {
+    long long X;
+    if (!frame_snap(c.eye[a], c.frame_origin[a], s, &X))
+      return fail(VCT_ERR_INVALID_ARG, "vct_gbuffer: eye outside the fixed-point frame");
+  }
+  if (!position || !normal || !aligned(position, 4) || !aligned(normal, 4) ||
+      (albedo && !aligned(albedo, 4)) || (triangle && !aligned(triangle, 4)))
+    return fail(VCT_ERR_INVALID_ARG, "vct_gbuffer: outputs NULL or misaligned");
+  const size_t need = gbuffer_fixed_bytes(c.width, c.height, mesh->n_triangles);
+  if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
+    return fail(VCT_ERR_WORKSPACE, "vct_gbuffer: workspace needs at least %zu bytes, 256-byte "
+                "aligned", need);
+  cudaError_t e = launch_gbuffer(*mesh, c, position, normal, albedo, mask, triangle, workspace,
+                                 workspace_bytes, sm_count(), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "vct_gbuffer launch");
   return VCT_OK;
 }
 

@@ -181,6 +181,54 @@ def test_voxelize_structs_and_validation(lib):
     assert run() == _abi.VCT_ERR_INVALID_ARG
 
 
+def test_gbuffer_structs_and_validation(lib):
+    """Camera G-buffer: workspace layout (stats, tile offsets and cursors,
+    96-byte triangle records, pairs) and every argument check that needs no
+    GPU."""
+    assert ctypes.sizeof(_abi.VctCamera) == 76
+    assert ctypes.sizeof(_abi.VctGbufferStats) == 48
+
+    def al(x):
+        return (x + 255) // 256 * 256
+    W, H, nt = 100, 40, 1000
+    T = 7 * 3
+    fixed = 256 + al((T + 1) * 4) + al(T * 4) + al(nt * 96)
+    assert lib.vct_gbuffer_workspace_bytes(W, H, nt, 0) == fixed
+    assert lib.vct_gbuffer_workspace_bytes(W, H, nt, 1000) == fixed + al(4000)
+    assert lib.vct_gbuffer_workspace_bytes(0, H, nt, 0) == 0
+    assert lib.vct_gbuffer_workspace_bytes(W, 16385, nt, 0) == 0
+    assert lib.vct_gbuffer_workspace_bytes(W, H, nt, (1 << 31) + 1) == 0
+    m = _abi.VctMesh(1024, 2048, 4096, 3, 1)
+    f3 = lambda *v: (ctypes.c_float * 3)(*v)  # noqa: E731
+
+    def cam(**kw):
+        c = _abi.VctCamera(f3(0.5, 0.5, 0.1), f3(0, 0, 1), f3(-1, 0, 0), f3(0, 1, 0), 0.577, W,
+                           H, f3(0, 0, 0), 1.0)
+        for k, v in kw.items():
+            setattr(c, k, v)
+        return c
+
+    need = lib.vct_gbuffer_workspace_bytes(W, H, 1, 0)
+
+    def run(c=None, mesh=m, pos=8192, nrm=16384, ws=1 << 20, ws_bytes=need):
+        c = c or cam()
+        return lib.vct_gbuffer(ctypes.byref(mesh), ctypes.byref(c), pos, nrm, None, None, None,
+                               ws, ws_bytes, None)
+
+    bad = _abi.VCT_ERR_INVALID_ARG
+    assert run(cam(width=0)) == bad
+    assert run(cam(tan_half_fov=0.0)) == bad
+    assert run(cam(tan_half_fov=1.5)) == bad                 # tx + ty > 2.99 at 100x40
+    assert run(cam(frame_size=-1.0)) == bad
+    assert run(cam(eye=f3(0.5, 0.5, 2.5))) == bad            # beyond two frame sizes
+    assert run(cam(forward=f3(0, 0, 1.01))) == bad           # component > 1 + 2^-10
+    assert run(cam(up=f3(0, 0, 1))) == bad                   # basis det 0
+    assert run(pos=0) == bad and run(nrm=16386) == bad
+    assert run(mesh=_abi.VctMesh(1024, 0, 4096, 3, 1)) == bad
+    assert run(ws_bytes=need - 1) == _abi.VCT_ERR_WORKSPACE
+    assert run(ws=(1 << 20) + 16) == _abi.VCT_ERR_WORKSPACE
+
+
 def test_brick_layout_sizes_and_validation(lib):
     """Brick layout: per bricked level a uint32 slot table, small levels
     dense, FP32 staging, then the pool (zero brick + occupied bricks)."""
