@@ -425,10 +425,36 @@ def extra_revoxelize(torch, vct, dev):
     f_ms = _time(torch, frame, 10)
     st = vct.read_voxelize_stats(vws)
     samples = int(sum(vct.read_stats(ws)["samples"]))
-    return {"workload": f"room{n}_1080p_f32_revoxelized", "triangles": int(mesh.indices.shape[0]),
-            "fragments": st["fragments"], "voxelize_ms": v_ms, "voxelize_mips_ms": vm_ms,
-            "frame_ms": f_ms, "mtriangles_per_s": mesh.indices.shape[0] / (v_ms / 1e3) / 1e6,
-            "gsamples_per_s": samples / (f_ms / 1e3) / 1e9}
+    out = {"workload": f"room{n}_1080p_f32_revoxelized", "triangles": int(mesh.indices.shape[0]),
+           "fragments": st["fragments"], "voxelize_ms": v_ms, "voxelize_mips_ms": vm_ms,
+           "frame_ms": f_ms, "mtriangles_per_s": mesh.indices.shape[0] / (v_ms / 1e3) / 1e6,
+           "gsamples_per_s": samples / (f_ms / 1e3) / 1e9}
+    # the whole frame from triangles on the GPU: the G-buffer is drawn from
+    # the same mesh (vct_gbuffer) instead of being uploaded
+    hv = c["views"][0]
+    cam = vs.camera(hv["camera"], hv["target"], hv["width"], hv["height"])
+    g = vct.gbuffer(mesh, cam)  # sizes the workspace (checked once)
+    gws = g["workspace"]
+    gview = vct.gbuffer_view(g, cam)
+
+    def gbuf():
+        vct.gbuffer(mesh, cam, out=g, workspace=gws, verify=False)
+
+    def gpu_frame():
+        vox_mips()
+        gbuf()
+        vct.trace([P], [gview], params, workspace=ws)
+
+    gb_ms = _time(torch, gbuf, 10)
+    gf_ms = _time(torch, gpu_frame, 10)
+    gst = vct.read_gbuffer_stats(gws)
+    gsamples = int(sum(vct.read_stats(ws)["samples"]))
+    out["gbuffer"] = {"gbuffer_ms": gb_ms, "tile_pairs": gst["pairs"],
+                      "triangles_in_view": int(mesh.indices.shape[0]) - gst["culled"]
+                      - gst["degenerate"] - gst["skipped"],
+                      "frame_ms": gf_ms, "gsamples_per_s": gsamples / (gf_ms / 1e3) / 1e9,
+                      "frame": "vct_voxelize + vct_build_mips + vct_gbuffer + vct_trace"}
+    return out
 
 
 def extra_bricks(torch, vct, dev, n=512):

@@ -14,10 +14,10 @@
 // than the image, projected, widened by one pixel (float rounding there only
 // moves the box by far less than a pixel).
 //
-// Kernels: memset (stats, tile counters) -> setup_kernel (one thread per
+// Kernels: memset (stats, tile counters) -> gb_setup_kernel (one thread per
 // triangle: snap, edge-volume coefficients, screen box, tile counts) ->
-// scan_kernel (one CTA: tile offsets) -> fill_kernel (tile lists) ->
-// raster_kernel (one CTA per tile, one pixel per thread, warps of 8x4 pixels).
+// gb_scan_kernel (one CTA: tile offsets) -> gb_fill_kernel (tile lists) ->
+// gb_raster_kernel (one CTA per tile, one pixel per thread, warps of 8x4 pixels).
 #include <algorithm>
 #include <cmath>
 
@@ -216,7 +216,7 @@ __device__ __forceinline__ void for_tiles(const GbArgs &A, int t, bool active, c
   }
 }
 
-__global__ void __launch_bounds__(kSetupThreads) setup_kernel(const __grid_constant__ GbArgs A) {
+__global__ void __launch_bounds__(kSetupThreads) gb_setup_kernel(const __grid_constant__ GbArgs A) {
   unsigned skipped = 0, degenerate = 0, culled = 0, wide = 0;
   const int stride = gridDim.x * blockDim.x;
   // whole warps iterate together (warp-wide tile enumeration and reductions)
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(const __grid_const
 }
 
 // One CTA: tile counts -> exclusive offsets (off[T] = total), overflow flag.
-__global__ void __launch_bounds__(1024) scan_kernel(const __grid_constant__ GbArgs A) {
+__global__ void __launch_bounds__(1024) gb_scan_kernel(const __grid_constant__ GbArgs A) {
   __shared__ unsigned long long s_warp[32];
   const int T = A.tiles_x * A.tiles_y;
   const int chunk = (T + 1023) / 1024;
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const __grid_constant__ GbAr
   }
 }
 
-__global__ void __launch_bounds__(kSetupThreads) fill_kernel(const __grid_constant__ GbArgs A) {
+__global__ void __launch_bounds__(kSetupThreads) gb_fill_kernel(const __grid_constant__ GbArgs A) {
   if (A.st->overflow) return;
   const int stride = gridDim.x * blockDim.x;
   const int nt_pad = (A.nt + 31) & ~31;
@@ -317,7 +317,7 @@ __device__ __forceinline__ float diff_prod(float a, float b, float c, float d) {
   return f + e;
 }
 
-__global__ void __launch_bounds__(kRasterThreads) raster_kernel(const __grid_constant__ GbArgs A) {
+__global__ void __launch_bounds__(kRasterThreads) gb_raster_kernel(const __grid_constant__ GbArgs A) {
   __shared__ uint4 s_rec[kChunk * 6];
   __shared__ int s_tri[kChunk];
   const int tile = blockIdx.x;
@@ -501,16 +501,16 @@ cudaError_t launch_gbuffer(const vct_mesh &m, const vct_camera &cam, float *posi
   const long long need = ((long long)A.nt + kSetupThreads - 1) / kSetupThreads;
   const int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)sms * 8));
   if (A.nt > 0) {
-    setup_kernel<<<grid, kSetupThreads, 0, s>>>(A);
+    gb_setup_kernel<<<grid, kSetupThreads, 0, s>>>(A);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  scan_kernel<<<1, 1024, 0, s>>>(A);
+  gb_scan_kernel<<<1, 1024, 0, s>>>(A);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (A.nt > 0) {
-    fill_kernel<<<grid, kSetupThreads, 0, s>>>(A);
+    gb_fill_kernel<<<grid, kSetupThreads, 0, s>>>(A);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  raster_kernel<<<(unsigned)T, kRasterThreads, 0, s>>>(A);
+  gb_raster_kernel<<<(unsigned)T, kRasterThreads, 0, s>>>(A);
   return cudaGetLastError();
 }
 
