@@ -80,17 +80,45 @@ def sources_hash(files) -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+def ncu_counters(kernel: str, workload: str):
+    """Per-launch ncu counters (DRAM bytes, warp instructions) from the
+    committed summary, if it was taken on the current kernel sources (else
+    an empty dict)."""
     p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(p):
-        return None
+        return {}
     d = json.load(open(p))
     e = d.get(f"{kernel}|{workload}")
     if not e or e.get("sources") != sources_hash(TRACE_SOURCES):
-        return None
-    return float(e["dram_bytes_per_launch"])
+        return {}
+    return e
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, or None."""
+    e = ncu_counters(kernel, workload)
+    return float(e["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in e else None
+
+
+# Instruction issue of the whole GPU: 152 SMs x 4 sub-partitions, each issuing
+# at most one warp instruction per clock.
+ISSUE_SLOTS_PER_CLOCK = 152 * 4
+
+
+def issue_roofline(kernel: str, workload: str, launch_ms: float, clocks: dict):
+    """Warp instructions per launch (ncu) over the event-timed launch, against
+    the issue peak at the SM clock seen during the timed region."""
+    e = ncu_counters(kernel, workload)
+    inst = e.get("warp_inst_per_launch")
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = ISSUE_SLOTS_PER_CLOCK * mhz * 1e6 / 1e9  # G warp instructions / s
+    if inst is None:
+        return {"bound": "issue", "achieved": None, "peak": peak, "unit": "Gwarp-inst/s",
+                "frac": None, "kernel": kernel}
+    achieved = inst / (launch_ms / 1e3) / 1e9
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
+            "frac": achieved / peak, "kernel": kernel, "warp_inst_per_launch": inst,
+            "peak_source": f"{ISSUE_SLOTS_PER_CLOCK} issue slots/clock x {mhz:.0f} MHz"}
 
 
 class ClockSampler:
@@ -278,6 +306,7 @@ def run_ours(args):
                          "frac": achieved / hbm, "traffic": traffic,
                          "kernel": "trace_kernel", "peak_source": peak_kind,
                          "algorithmic_bytes_per_launch": algo_bytes},
+            "roofline_issue": issue_roofline("trace_kernel", workload, trace_avg, clk),
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,
