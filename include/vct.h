@@ -603,6 +603,33 @@ const char *vct_last_error(void);
 int32_t vct_version(void);
 
 /*
+ * Bounds-checked builds.  A library compiled with -DVCT_DEBUG_BOUNDS (the
+ * `libvct_debug_bounds.so` variant of the in-tree build) compares every
+ * computed texel, brick-slot, gradient, mip, voxel and tile-list index with
+ * the length of its array before the access; a bad index sets a bit in a
+ * device flag word and the access is skipped (loads read zero), so a kernel
+ * never traps.  Bits: 1 trace texel, 2 brick slot table / pool, 4 adjoint
+ * gradient texel, 8 mip texel, 16 voxelizer owner / colour, 32 G-buffer
+ * tile lists, 64 the probe below.
+ *
+ * vct_debug_bounds_flags synchronises the device, stores the OR of the flag
+ * words in *flags_out and clears them if `reset`.  In a release build it
+ * stores 0 and returns VCT_ERR_UNSUPPORTED.
+ */
+vct_status vct_debug_bounds_flags(uint32_t *flags_out, int32_t reset);
+
+/*
+ * Check of the bounds checks: one kernel writes i to buf_dev[i] for i <
+ * declared + extra through the check against `declared`, so the last
+ * `extra` writes (1 .. 1024) must be caught (flag bit 64) and skipped.
+ * buf_dev: device uint32 array of declared + extra words (the caught writes
+ * would stay inside it even without the check).  VCT_ERR_UNSUPPORTED in a
+ * release build.
+ */
+vct_status vct_debug_bounds_probe(uint32_t *buf_dev, uint32_t declared, uint32_t extra,
+                                  vct_stream_t stream);
+
+/*
  * Failure-path check of the bounded device waits: launches one CTA that
  * waits on an mbarrier nothing ever arrives at, with the same bounded-wait
  * routine the pipelined kernels use, giving up after about `max_ns`

@@ -1,6 +1,7 @@
 """ctypes mirror of include/vct.h and the loader of libvct.so."""
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import threading
@@ -148,6 +149,8 @@ EXPORTS = {
     "vct_last_error": (ctypes.c_char_p, []),
     "vct_version": (_c_i32, []),
     "vct_debug_wait_probe": (_c_i32, [_vp, _c_u64, _vp]),
+    "vct_debug_bounds_flags": (_c_i32, [ctypes.POINTER(ctypes.c_uint32), _c_i32]),
+    "vct_debug_bounds_probe": (_c_i32, [_vp, ctypes.c_uint32, ctypes.c_uint32, _vp]),
 }
 
 _LOCK = threading.Lock()
@@ -160,27 +163,48 @@ class VctError(RuntimeError):
         self.status = status
 
 
-def library_path() -> str:
-    return _build.LIB
+def library_path(variant: str = "release") -> str:
+    return _build.library_file(variant)
+
+
+def open_library(variant: str = "release", build_if_missing: bool = True):
+    """Load one variant of the library (building it first if needed) with
+    its exports declared.  Raises if unavailable: there is no fallback."""
+    path = _build.build(variant=variant) if build_if_missing else library_path(variant)
+    if not os.path.exists(path):
+        raise RuntimeError(f"{os.path.basename(path)} not found at {path}; run the build first")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
 
 
 def load(build_if_missing: bool = True):
-    """Load libvct.so (building it first if needed).  Raises if unavailable:
-    there is no fallback implementation."""
+    """The library the binding calls: the release libvct.so unless
+    using_variant() selected another."""
     global _LIB
     with _LOCK:
-        if _LIB is not None:
-            return _LIB
-        path = _build.build() if build_if_missing else _build.LIB
-        if not os.path.exists(path):
-            raise RuntimeError(f"libvct.so not found at {path}; run the build first")
-        lib = ctypes.CDLL(path)
-        for name, (res, args) in EXPORTS.items():
-            fn = getattr(lib, name)
-            fn.restype = res
-            fn.argtypes = args
+        if _LIB is None:
+            _LIB = open_library("release", build_if_missing)
+        return _LIB
+
+
+@contextlib.contextmanager
+def using_variant(variant: str):
+    """Route the binding's calls to another variant of the library (e.g.
+    the bounds-checked build) inside the block."""
+    global _LIB
+    lib = open_library(variant)
+    with _LOCK:
+        prev = _LIB
         _LIB = lib
-        return lib
+    try:
+        yield lib
+    finally:
+        with _LOCK:
+            _LIB = prev
 
 
 def check(status: int, what: str) -> None:

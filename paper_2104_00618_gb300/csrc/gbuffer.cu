@@ -239,7 +239,9 @@ __global__ void __launch_bounds__(kSetupThreads) gb_setup_kernel(const __grid_co
       }
       A.rec[t] = R;
     }
-    for_tiles(A, t, r == 0, R, [&](int, int tile) { atomicAdd(A.off + tile, 1u); });
+    for_tiles(A, t, r == 0, R, [&](int, int tile) {
+      if (in_bounds(tile, (uint64_t)A.tiles_x * A.tiles_y, kOobGbuffer)) atomicAdd(A.off + tile, 1u);
+    });
   }
   warp_add(&A.st->skipped, skipped);
   warp_add(&A.st->degenerate, degenerate);
@@ -302,8 +304,9 @@ __global__ void __launch_bounds__(kSetupThreads) gb_fill_kernel(const __grid_con
       active = R.box[0] <= R.box[1];
     }
     for_tiles(A, t, active, R, [&](int tt, int tile) {
+      if (!in_bounds(tile, (uint64_t)A.tiles_x * A.tiles_y, kOobGbuffer)) return;
       const uint32_t k = A.off[tile] + atomicAdd(A.cursor + tile, 1u);
-      A.pairs[k] = (uint32_t)tt;  // k < total <= cap: no overflow here
+      if (in_bounds(k, A.cap, kOobGbuffer)) A.pairs[k] = (uint32_t)tt;  // k < total <= cap
     });
   }
 }
@@ -346,7 +349,8 @@ __global__ void __launch_bounds__(kRasterThreads) gb_raster_kernel(const __grid_
     const int n = (int)min((uint32_t)kChunk, end - base);
     __syncthreads();
     if ((int)threadIdx.x < n) {
-      const int t = (int)A.pairs[base + threadIdx.x];
+      int t = (int)A.pairs[base + threadIdx.x];
+      if (!in_bounds((uint32_t)t, (uint64_t)A.nt, kOobGbuffer)) t = 0;  // nt >= 1 here
       s_tri[threadIdx.x] = t;
       const uint4 *src = reinterpret_cast<const uint4 *>(A.rec + t);
 #pragma unroll
@@ -513,5 +517,7 @@ cudaError_t launch_gbuffer(const vct_mesh &m, const vct_camera &cam, float *posi
   gb_raster_kernel<<<(unsigned)T, kRasterThreads, 0, s>>>(A);
   return cudaGetLastError();
 }
+
+VCT_OOB_ACCESSOR(oob_flags_gbuffer)
 
 }  // namespace vct

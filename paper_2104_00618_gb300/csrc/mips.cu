@@ -54,6 +54,7 @@ struct PackArgs {
   uint8_t *lvl[VCT_MAX_LEVELS];  // level texels, or the slot table of a bricked level
   uint8_t *pool;                 // brick pool (brick layout)
   uint32_t bricked;              // bit l: level l is bricked
+  uint32_t pool_slots;           // bricks the pool holds (bounds checks)
   float4 *staging;  // FP32 copy of level m_top (VCT_F16 or bricks), else null
   uint32_t *status;
   int n, B, m_top;  // block edge, last level produced inside a block
@@ -66,11 +67,12 @@ struct PackArgs {
 // brick, whose slot is the shared zero brick).
 template <int DT, bool BR>
 __device__ __forceinline__ void put(uint8_t *const *lvl, const uint8_t *pool, uint32_t bricked,
-                                    int l, uint32_t code, float4 v) {
+                                    uint32_t pool_slots, int n, int l, uint32_t code, float4 v) {
   using T = typename Tex<DT>::T;
+  if (!in_bounds(code, level_texels(n, l), kOobMip)) return;
   if (BR && ((bricked >> l) & 1u)) {
     const uint32_t slot = reinterpret_cast<const uint32_t *>(lvl[l])[code >> kBrickShift];
-    if (slot != 0u)
+    if (slot != 0u && in_bounds(slot, pool_slots, kOobBrick))
       st_texel(reinterpret_cast<T *>(const_cast<uint8_t *>(pool)) +
                    (((size_t)slot << kBrickShift) | (code & 511u)),
                v);
@@ -128,12 +130,14 @@ template <int DT, bool BR>
 __device__ __forceinline__ void store_range(const PackArgs &a, int l, uint32_t code, uint32_t cnt,
                                             const typename Tex<DT>::T *src) {
   using T = typename Tex<DT>::T;
+  if (!in_bounds((uint64_t)code + cnt, level_texels(a.n, l) + 1, kOobMip)) return;
   if (BR && ((a.bricked >> l) & 1u)) {
     const uint32_t *tbl = reinterpret_cast<const uint32_t *>(a.lvl[l]);
     T *pool = reinterpret_cast<T *>(a.pool);
     for (uint32_t c = code; c < code + cnt;) {
       const uint32_t end = min(code + cnt, ((c >> kBrickShift) + 1u) << kBrickShift);
-      const uint32_t slot = tbl[c >> kBrickShift];
+      uint32_t slot = tbl[c >> kBrickShift];
+      if (!in_bounds(slot, a.pool_slots, kOobBrick)) slot = 0u;
       T *dst = pool + (((size_t)slot << kBrickShift) | (c & 511u));
       if (slot != 0u && ((end - c) * sizeof(T)) % 16u != 0u) {
         for (uint32_t k = c; k < end; ++k) dst[k - c] = src[k - code];
@@ -256,6 +260,7 @@ struct TailArgs {
   uint8_t *lvl[VCT_MAX_LEVELS];
   uint8_t *pool;
   uint32_t bricked;
+  uint32_t pool_slots;
   const float4 *src0;  // FP32 values of level m_top
   float4 *ping[2];     // FP32 scratch for levels above m_top (VCT_F16 or bricks), or null
   int n, levels, m_top;
@@ -276,7 +281,7 @@ __global__ void __launch_bounds__(1024) mip_tail_kernel(const TailArgs a) {
 #pragma unroll
       for (int i = 0; i < 8; ++i) ch[i] = src[8 * j + i];
       float4 m = mean8(ch);
-      put<DT, BR>(a.lvl, a.pool, a.bricked, l, (uint32_t)j, m);
+      put<DT, BR>(a.lvl, a.pool, a.bricked, a.pool_slots, a.n, l, (uint32_t)j, m);
       if (!kInPlace) f32dst[j] = m;
     }
     __syncthreads();
@@ -297,7 +302,7 @@ __global__ void read_level_kernel(const uint8_t *lvl, const uint32_t *tbl, const
     const T *p = tbl ? reinterpret_cast<const T *>(pool) +
                            (((size_t)tbl[code >> kBrickShift] << kBrickShift) | (code & 511u))
                      : reinterpret_cast<const T *>(lvl) + code;
-    out[i] = ld_texel(p);
+    out[i] = in_bounds(code, total, kOobMip) ? ld_texel(p) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
@@ -383,6 +388,10 @@ cudaError_t launch_pack_mips(const float *level0, const vct_pyramid &pyr,
   for (int l = 0; l < pyr.levels; ++l) a.lvl[l] = base + L.level_off[l];
   a.pool = base + L.pool_off;
   a.bricked = L.bricked;
+  a.pool_slots = br ? (uint32_t)std::min<uint64_t>((pyr.bytes - L.pool_off) /
+                                                       ((uint64_t)texel_bytes(pyr.dtype) << kBrickShift),
+                                                   0xffffffffull)
+                    : 0u;
   a.status = reinterpret_cast<uint32_t *>(base);
   a.n = pyr.n;
   a.B = B;
@@ -413,6 +422,7 @@ cudaError_t launch_pack_mips(const float *level0, const vct_pyramid &pyr,
   for (int l = 0; l < pyr.levels; ++l) t.lvl[l] = base + L.level_off[l];
   t.pool = base + L.pool_off;
   t.bricked = L.bricked;
+  t.pool_slots = a.pool_slots;
   t.n = pyr.n;
   t.levels = pyr.levels;
   t.m_top = m_top;
@@ -470,5 +480,7 @@ cudaError_t launch_wait_probe(uint32_t *flag, uint64_t max_ns, cudaStream_t s) {
   wait_probe_kernel<<<1, 32, 0, s>>>(flag, max_ns);
   return cudaGetLastError();
 }
+
+VCT_OOB_ACCESSOR(oob_flags_mips)
 
 }  // namespace vct

@@ -463,4 +463,6 @@ int trace_occupancy(int lpp, int dtype, bool var) {
   }
 }
 
+VCT_OOB_ACCESSOR(oob_flags_trace)
+
 }  // namespace vct

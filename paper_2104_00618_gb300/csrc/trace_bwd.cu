@@ -36,7 +36,9 @@ __device__ __forceinline__ void scatter_lane(const BwdLaunch &L, int l, const Le
     if (!((s.valid >> c) & 1u)) continue;
     const float w = corner_weight(s, lw, c);
     if (w == 0.0f) continue;
-    atomicAdd(reinterpret_cast<float4 *>(grad_texel(L, l, corner_index(s, c))),
+    const uint32_t idx = corner_index(s, c);
+    if (!in_bounds(idx, level_texels(L.pyr.n, l), kOobGrad)) continue;
+    atomicAdd(reinterpret_cast<float4 *>(grad_texel(L, l, idx)),
               make_float4(w * g[0], w * g[1], w * g[2], w * g[3]));
   }
 }
@@ -98,7 +100,9 @@ __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const uint32_t 
     const uint32_t sy0 = __shfl_sync(full, s.sy[0], leader), sy1 = __shfl_sync(full, s.sy[1], leader);
     const uint32_t sz0 = __shfl_sync(full, s.sz[0], leader), sz1 = __shfl_sync(full, s.sz[1], leader);
     const uint32_t idx = ((c & 1) ? sx1 : sx0) | (((c >> 1) & 1) ? sy1 : sy0) | ((c >> 2) ? sz1 : sz0);
-    if (((lvalid >> c) & 1u) && v[0] != 0.0f) atomicAdd(grad_texel(L, ll, idx) + ch, v[0]);
+    if (((lvalid >> c) & 1u) && v[0] != 0.0f &&
+        in_bounds(idx, level_texels(L.pyr.n, ll), kOobGrad))
+      atomicAdd(grad_texel(L, ll, idx) + ch, v[0]);
     pending &= ~lgrp;
   }
 }
@@ -327,5 +331,7 @@ int trace_bwd_occupancy(int lpp) {
     default: return 0;
   }
 }
+
+VCT_OOB_ACCESSOR(oob_flags_trace_bwd)
 
 }  // namespace vct

@@ -215,6 +215,20 @@ __device__ __forceinline__ const T *brick_texel(const uint32_t *tbl, const T *po
   return pool + (((size_t)slot << kBrickShift) | (code & 511u));
 }
 
+// Bounds checks of the lookups (debug-bounds builds; always true otherwise):
+// a valid corner's Morton code lies inside its level, a bricked level's
+// slot inside the pool.
+__device__ __forceinline__ bool texel_ok(const DevPyr &P, int l, uint32_t code) {
+  return in_bounds(code, level_texels(P.n, l), kOobTexel);
+}
+__device__ __forceinline__ bool slot_ok(const DevPyr &P, const uint32_t *tbl, uint32_t code) {
+#ifdef VCT_DEBUG_BOUNDS
+  return in_bounds(__ldg(tbl + (code >> kBrickShift)), P.pool_slots, kOobBrick);
+#else
+  return true;
+#endif
+}
+
 // Trilinear lookup of level l as seven packed lerps (x, then y, then z);
 // corners outside the grid read as zero.  BR: the pyramid may have bricked
 // levels (VCT_LAYOUT_BRICKS).
@@ -232,7 +246,8 @@ __device__ __forceinline__ void trilerp(const DevPyr &P, int l, const LevelStenc
     const uint32_t cross = (s.sx[0] ^ s.sx[1]) | (s.sy[0] ^ s.sy[1]) | (s.sz[0] ^ s.sz[1]);
     if (s.valid == 0xffu && (cross >> kBrickShift) == 0u) {
       const uint32_t c0 = corner_index(s, 0);
-      const T *brick = pool + ((size_t)__ldg(tbl + (c0 >> kBrickShift)) << kBrickShift);
+      const bool ok = texel_ok(P, l, c0) && slot_ok(P, tbl, c0);
+      const T *brick = pool + ((size_t)(ok ? __ldg(tbl + (c0 >> kBrickShift)) : 0u) << kBrickShift);
 #pragma unroll
       for (int c = 0; c < 8; ++c) ld_texel2(brick + (corner_index(s, c) & 511u), c_rg[c], c_ba[c]);
     } else {
@@ -240,19 +255,29 @@ __device__ __forceinline__ void trilerp(const DevPyr &P, int l, const LevelStenc
       for (int c = 0; c < 8; ++c) {
         c_rg[c] = 0ull;
         c_ba[c] = 0ull;
-        if ((s.valid >> c) & 1u)
-          ld_texel2(brick_texel(tbl, pool, corner_index(s, c)), c_rg[c], c_ba[c]);
+        const uint32_t code = corner_index(s, c);
+        if (((s.valid >> c) & 1u) && texel_ok(P, l, code) && slot_ok(P, tbl, code))
+          ld_texel2(brick_texel(tbl, pool, code), c_rg[c], c_ba[c]);
       }
     }
   } else if (s.valid == 0xffu) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) ld_texel2(base + corner_index(s, c), c_rg[c], c_ba[c]);
+    for (int c = 0; c < 8; ++c) {
+      const uint32_t code = corner_index(s, c);
+#ifdef VCT_DEBUG_BOUNDS
+      c_rg[c] = 0ull;
+      c_ba[c] = 0ull;
+      if (texel_ok(P, l, code))
+#endif
+        ld_texel2(base + code, c_rg[c], c_ba[c]);
+    }
   } else {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       c_rg[c] = 0ull;
       c_ba[c] = 0ull;
-      if ((s.valid >> c) & 1u) ld_texel2(base + corner_index(s, c), c_rg[c], c_ba[c]);
+      const uint32_t code = corner_index(s, c);
+      if (((s.valid >> c) & 1u) && texel_ok(P, l, code)) ld_texel2(base + code, c_rg[c], c_ba[c]);
     }
   }
   const f32x2 tx = f2_pack(s.fr[0], s.fr[0]);

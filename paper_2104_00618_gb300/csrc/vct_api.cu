@@ -164,6 +164,9 @@ vct_status fill_pyr(const vct_pyramid &p, const vct_trace_params &P, DevPyr &d) 
     d.lvl[l] = static_cast<const uint8_t *>(p.data) + L.level_off[l];
   d.pool = static_cast<const uint8_t *>(p.data) + L.pool_off;
   d.bricked = L.bricked;
+  if (L.bricked && p.bytes > L.pool_off)
+    d.pool_slots = (uint32_t)std::min<uint64_t>(
+        (p.bytes - L.pool_off) / ((uint64_t)texel_bytes(p.dtype) << kBrickShift), 0xffffffffull);
   for (int a = 0; a < 3; ++a) d.origin_f[a] = p.origin[a];
   const double scale = (double)p.n / (double)p.size;  // scene units -> level-0 voxels
   d.scale_hi = (float)scale;
@@ -353,6 +356,30 @@ vct_status set_last_error(vct_status st, const char *fmt, ...) {
   g_last_error = buf;
   return st;
 }
+}  // namespace vct
+
+namespace vct {
+namespace {
+// Writes index i to buf[i] for i < declared + extra through the bounds check
+// against `declared`: the last `extra` writes are caught and skipped (the
+// caller's buffer holds declared + extra words, so even an unchecked write
+// would stay inside it).
+__global__ void bounds_probe_kernel(uint32_t *buf, uint32_t declared, uint32_t extra) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < declared + extra;
+       i += gridDim.x * blockDim.x)
+    if (in_bounds(i, declared, kOobProbe)) buf[i] = i;
+}
+}  // namespace
+
+cudaError_t launch_bounds_probe(uint32_t *buf, uint32_t declared, uint32_t extra,
+                                cudaStream_t s) {
+  const uint32_t total = declared + extra;
+  const int grid = (int)std::min<uint32_t>((total + 255) / 256, 1024u);
+  bounds_probe_kernel<<<grid, 256, 0, s>>>(buf, declared, extra);
+  return cudaGetLastError();
+}
+
+VCT_OOB_ACCESSOR(oob_flags_api)
 }  // namespace vct
 
 extern "C" {
@@ -783,6 +810,37 @@ vct_status vct_gbuffer(const vct_mesh *mesh, const vct_camera *camera, float *po
                                  workspace_bytes, sm_count(), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "vct_gbuffer launch");
   return VCT_OK;
+}
+
+vct_status vct_debug_bounds_flags(uint32_t *flags_out, int32_t reset) {
+  if (!flags_out) return fail(VCT_ERR_INVALID_ARG, "vct_debug_bounds_flags: NULL argument");
+#ifdef VCT_DEBUG_BOUNDS
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "vct_debug_bounds_flags");
+  const bool r = reset != 0;
+  *flags_out = oob_flags_api(r) | oob_flags_mips(r) | oob_flags_trace(r) |
+               oob_flags_trace_bwd(r) | oob_flags_voxelize(r) | oob_flags_gbuffer(r);
+  return VCT_OK;
+#else
+  (void)reset;
+  *flags_out = 0;
+  return fail(VCT_ERR_UNSUPPORTED, "vct_debug_bounds_flags: not a debug-bounds build");
+#endif
+}
+
+vct_status vct_debug_bounds_probe(uint32_t *buf_dev, uint32_t declared, uint32_t extra,
+                                  vct_stream_t stream) {
+  if (!buf_dev || !aligned(buf_dev, 4) || declared == 0 || extra == 0 || extra > 1024u ||
+      declared > (1u << 30))
+    return fail(VCT_ERR_INVALID_ARG, "vct_debug_bounds_probe: bad arguments");
+#ifdef VCT_DEBUG_BOUNDS
+  cudaError_t e = launch_bounds_probe(buf_dev, declared, extra, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "vct_debug_bounds_probe launch");
+  return VCT_OK;
+#else
+  (void)stream;
+  return fail(VCT_ERR_UNSUPPORTED, "vct_debug_bounds_probe: not a debug-bounds build");
+#endif
 }
 
 vct_status vct_debug_wait_probe(uint32_t *flag_dev, uint64_t max_ns, vct_stream_t stream) {

@@ -123,6 +123,54 @@ __host__ __device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uin
 }
 
 // ---------------------------------------------------------------------------
+// bounds-checked builds (-DVCT_DEBUG_BOUNDS)
+// ---------------------------------------------------------------------------
+// A debug-bounds build compares every computed texel, brick-slot, table and
+// list index with the length of its array before the access.  A bad index
+// sets a bit of its translation unit's flag word (vct_debug_bounds_flags
+// reads and clears them) and the access is skipped (a load reads zero); no
+// kernel traps.  Release builds compile the checks away.
+enum : uint32_t {
+  kOobTexel = 1u,    // trace: texel of a dense level
+  kOobBrick = 2u,    // trace, mips: slot table or brick pool
+  kOobGrad = 4u,     // adjoint: gradient texel
+  kOobMip = 8u,      // mips: stored texel
+  kOobVoxel = 16u,   // voxelizer: owner word or colour table
+  kOobGbuffer = 32u, // G-buffer: tile counters, lists, records
+  kOobProbe = 64u,   // vct_debug_bounds_probe
+};
+#ifdef VCT_DEBUG_BOUNDS
+static __device__ uint32_t g_vct_oob;  // one flag word per translation unit
+__device__ __forceinline__ bool in_bounds(uint64_t i, uint64_t n, uint32_t what) {
+  if (i < n) return true;
+  atomicOr(&g_vct_oob, what);
+  return false;
+}
+// Defines the host accessor of this translation unit's flag word.
+#define VCT_OOB_ACCESSOR(name)                                              \
+  uint32_t name(bool reset) {                                               \
+    uint32_t v = 0;                                                         \
+    if (cudaMemcpyFromSymbol(&v, g_vct_oob, sizeof(v)) != cudaSuccess) return 0xffffffffu; \
+    if (reset) {                                                            \
+      const uint32_t z = 0;                                                 \
+      cudaMemcpyToSymbol(g_vct_oob, &z, sizeof(z));                         \
+    }                                                                       \
+    return v;                                                               \
+  }
+#else
+__device__ __forceinline__ bool in_bounds(uint64_t, uint64_t, uint32_t) { return true; }
+#define VCT_OOB_ACCESSOR(name) \
+  uint32_t name(bool) { return 0u; }
+#endif
+// Per-translation-unit accessors (debug-bounds builds; 0 otherwise).
+uint32_t oob_flags_api(bool reset);
+uint32_t oob_flags_mips(bool reset);
+uint32_t oob_flags_trace(bool reset);
+uint32_t oob_flags_trace_bwd(bool reset);
+uint32_t oob_flags_voxelize(bool reset);
+uint32_t oob_flags_gbuffer(bool reset);
+
+// ---------------------------------------------------------------------------
 // texel load/store
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float4 ld_texel(const float4 *p) { return __ldg(p); }
@@ -215,6 +263,7 @@ struct DevPyr {
   const uint8_t *lvl[VCT_MAX_LEVELS];  // level base pointers (slot table if bricked)
   const uint8_t *pool;                 // brick pool (brick layout)
   uint32_t bricked;                    // bit l: level l is bricked
+  uint32_t pool_slots;                 // bricks the pool holds (bounds checks)
   float log2_tmax_t0;                  // log2(t_max / t0), both in level-0 voxels
   int n, levels, dtype;
   float h0;  // level-0 voxel edge in scene units
@@ -338,6 +387,8 @@ cudaError_t launch_brick_tables(const float *level0, int n, int levels, const La
 cudaError_t launch_mip_adjoint(const float *gpyr_base, const Layout &gl, int n, int levels,
                                float *grad0, cudaStream_t s);
 cudaError_t launch_wait_probe(uint32_t *flag, uint64_t max_ns, cudaStream_t s);
+cudaError_t launch_bounds_probe(uint32_t *buf, uint32_t declared, uint32_t extra,
+                                cudaStream_t s);
 cudaError_t launch_trace(const TraceLaunch &L, int lpp, int dtype, bool bricks, int grid,
                          cudaStream_t s);
 int trace_occupancy(int lpp, int dtype, bool variants);

@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kVoxThreads) setup_kernel(const __grid_constan
       for (int j = T.j0; j <= T.j1; ++j)
         for (int i = T.i0; i <= T.i1; ++i) {
           const long long v = fragment(T, A.n, i, j);
-          if (v >= 0) {
+          if (v >= 0 && in_bounds((uint64_t)v, (uint64_t)A.n * A.n * A.n, kOobVoxel)) {
             atomicMax(A.owner + v, (unsigned)(t + 1));
             ++frags;
           }
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(kVoxThreads)
       for (long long p = p0 + lane; p < p1; p += 32) {
         const int i = T.i0 + (int)(p % w), j = T.j0 + (int)(p / w);
         const long long v = fragment(T, A.n, i, j);
-        if (v >= 0) {
+        if (v >= 0 && in_bounds((uint64_t)v, (uint64_t)A.n * A.n * A.n, kOobVoxel)) {
           atomicMax(A.owner + v, (unsigned)(t + 1));
           ++frags;
         }
@@ -371,7 +371,8 @@ __global__ void __launch_bounds__(kVoxThreads) resolve_kernel(const __grid_const
     for (int k = 0; k < 4; ++k) {
       const long long v = base + 32 * k + lane;
       if (v < nvox)
-        __stcs(A.out + v, o[k] ? __ldg(A.colour + (o[k] - 1)) : make_float4(0.f, 0.f, 0.f, 0.f));
+        __stcs(A.out + v, o[k] && in_bounds(o[k] - 1, (uint64_t)A.nt, kOobVoxel)
+                              ? __ldg(A.colour + (o[k] - 1)) : make_float4(0.f, 0.f, 0.f, 0.f));
     }
   }
 }
@@ -432,5 +433,7 @@ cudaError_t launch_voxelize(const vct_mesh &m, int n, const float origin[3], flo
   resolve_kernel<<<rgrid, kVoxThreads, 0, s>>>(A, (long long)nvox);
   return cudaGetLastError();
 }
+
+VCT_OOB_ACCESSOR(oob_flags_voxelize)
 
 }  // namespace vct

@@ -229,6 +229,20 @@ def test_gbuffer_structs_and_validation(lib):
     assert run(ws=(1 << 20) + 16) == _abi.VCT_ERR_WORKSPACE
 
 
+def test_debug_bounds_variant_loads(lib):
+    """The bounds-checked variant exports the same entry points; the release
+    library reports that it has no bounds checks."""
+    dbg = _abi.open_library("debug_bounds")
+    for name in _abi.EXPORTS:
+        assert hasattr(dbg, name), name
+    out = ctypes.c_uint32(5)
+    assert lib.vct_debug_bounds_flags(ctypes.byref(out), 0) == _abi.VCT_ERR_UNSUPPORTED
+    assert out.value == 0
+    assert lib.vct_debug_bounds_probe(8192, 10, 1, None) == _abi.VCT_ERR_UNSUPPORTED
+    assert lib.vct_debug_bounds_probe(8192, 10, 0, None) == _abi.VCT_ERR_INVALID_ARG
+    assert dbg.vct_debug_bounds_probe(8192, 0, 1, None) == _abi.VCT_ERR_INVALID_ARG
+
+
 def test_brick_layout_sizes_and_validation(lib):
     """Brick layout: per bricked level a uint32 slot table, small levels
     dense, FP32 staging, then the pool (zero brick + occupied bricks)."""
