@@ -555,14 +555,26 @@ def extra_fwd_bwd(torch, vct, dev, n=128, n_views=32, res=512):
         grad.zero_()
         vct.trace_backward(P, views, grads, params, grad_level0=grad, workspace=bws)
 
+    dws = vct.backward_workspace(P, deterministic=True)
+
+    def fwd_bwd_det():
+        fwd()
+        grads = [(v.out_diffuse - t[0], v.out_specular - t[1], v.out_visibility - t[2])
+                 for v, t in zip(views, targets)]
+        grad.zero_()
+        vct.trace_backward(P, views, grads, params, grad_level0=grad, workspace=dws,
+                           deterministic=True)
+
     use_state(False)
     f_ms = _time(torch, fwd, 5)         # the plain forward
     use_state(True)
     fb_ms = _time(torch, fwd_bwd, 5)    # forward with cone state + adjoint
+    fbd_ms = _time(torch, fwd_bwd_det, 3)  # the same with the reproducible adjoint
     samples = int(sum(vct.read_stats(ws)["samples"]))
     return {"workload": f"learnable{n}_{n_views}x{res}^2_f32", "fwd_ms": f_ms, "fwd_bwd_ms": fb_ms,
             "fwd_bwd_over_fwd": fb_ms / f_ms, "samples_per_fwd": samples,
-            "fwd_gsamples_per_s": samples / (f_ms / 1e3) / 1e9}
+            "fwd_gsamples_per_s": samples / (f_ms / 1e3) / 1e9,
+            "fwd_bwd_deterministic_ms": fbd_ms}
 
 
 def extra_batched(torch, vct, dev, grids=(128, 256, 256, 512), views_per_scene=64):

@@ -350,7 +350,8 @@ size_t vct_trace_backward_workspace_bytes(const vct_pyramid *pyr);
  * level down to its children (1/8 each) and ADDS the level-0 result into
  * grad_level0_dense (device float32 [n][n][n][4], z, y, x, channel).
  * Every view must use pyramid index 0 (`pyr`), which must be VCT_F32
- * (VCT_ERR_UNSUPPORTED otherwise).  Scatter order is not deterministic.
+ * (VCT_ERR_UNSUPPORTED otherwise).  Scatter order is not deterministic (see
+ * vct_trace_backward_deterministic for a reproducible variant).
  */
 vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
                               const vct_view_grad *grads, int32_t n_views,
@@ -358,6 +359,27 @@ vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
                               const vct_launch_config *cfg,
                               float *grad_level0_dense, void *workspace,
                               size_t workspace_bytes, vct_stream_t stream);
+
+/* Workspace bytes of vct_trace_backward_deterministic: the float32 gradient
+ * pyramid plus, per level, 4 x uint64 per texel (256-byte aligned). */
+size_t vct_trace_backward_deterministic_workspace_bytes(const vct_pyramid *pyr);
+
+/*
+ * vct_trace_backward with a reproducible result (a debugging mode): every
+ * scattered contribution is rounded to a multiple of 2^-32 and summed as a
+ * 64-bit two's-complement integer, so the order in which warps reach a
+ * texel does not change any bit of the gradient; each level is converted to
+ * float32 (round to nearest) before the mip adjoint.  Contributions below
+ * 2^-33 in magnitude are lost, and every per-texel sum must stay within
+ * (-2^31, 2^31).  Same arguments and checks as vct_trace_backward; workspace
+ * of vct_trace_backward_deterministic_workspace_bytes(pyr) bytes.
+ */
+vct_status vct_trace_backward_deterministic(const vct_pyramid *pyr, const vct_view *views,
+                                            const vct_view_grad *grads, int32_t n_views,
+                                            const vct_trace_params *params,
+                                            const vct_launch_config *cfg,
+                                            float *grad_level0_dense, void *workspace,
+                                            size_t workspace_bytes, vct_stream_t stream);
 
 /*
  * vct_trace_backward without a workspace argument, for callers that cannot

@@ -305,23 +305,27 @@ def autotune(pyramids, views, params, workspace=None, stream=None) -> VctLaunchC
     return best
 
 
-def backward_workspace(pyr: Pyramid) -> torch.Tensor:
+def backward_workspace(pyr: Pyramid, deterministic: bool = False) -> torch.Tensor:
     p = pyr.struct()
-    nbytes = lib().vct_trace_backward_workspace_bytes(ctypes.byref(p))
+    f = (lib().vct_trace_backward_deterministic_workspace_bytes if deterministic
+         else lib().vct_trace_backward_workspace_bytes)
+    nbytes = f(ctypes.byref(p))
     return torch.empty(nbytes, dtype=torch.uint8, device=pyr.storage.device)
 
 
 def trace_backward(pyr: Pyramid, views, grads, params, grad_level0: torch.Tensor | None = None,
                    cfg: VctLaunchConfig | None = None, workspace: torch.Tensor | None = None,
-                   stream=None) -> torch.Tensor:
+                   stream=None, deterministic: bool = False) -> torch.Tensor:
     """Accumulates dL/d(level-0 grid) into grad_level0 ([n,n,n,4] float32).
-    grads: per view (grad_D [H*W,4] | None, grad_S | None, grad_Vis [H*W] | None)."""
+    grads: per view (grad_D [H*W,4] | None, grad_S | None, grad_Vis [H*W] | None).
+    deterministic: the reproducible fixed-point accumulation
+    (vct_trace_backward_deterministic)."""
     vs = list(views) if isinstance(views, (list, tuple)) else [views]
     P = params if isinstance(params, VctTraceParams) else make_params(params)
     if grad_level0 is None:
         grad_level0 = torch.zeros((pyr.n,) * 3 + (4,), dtype=torch.float32,
                                   device=pyr.storage.device)
-    ws = workspace if workspace is not None else backward_workspace(pyr)
+    ws = workspace if workspace is not None else backward_workspace(pyr, deterministic)
     p = pyr.struct()
     varr = (VctView * len(vs))(*[v.struct() for v in vs])
     keep = []
@@ -330,10 +334,10 @@ def trace_backward(pyr: Pyramid, views, grads, params, grad_level0: torch.Tensor
         gd, gs, gv = (None if t is None else t.contiguous() for t in g)
         keep.extend(t for t in (gd, gs, gv) if t is not None)
         garr[i] = VctViewGrad(_ptr(gd), _ptr(gs), _ptr(gv))
-    check(lib().vct_trace_backward(ctypes.byref(p), varr, garr, len(vs), ctypes.byref(P),
-                                   None if cfg is None else ctypes.byref(cfg), _ptr(grad_level0),
-                                   _ptr(ws), ws.numel(), _stream(stream)),
-          "vct_trace_backward")
+    fn = lib().vct_trace_backward_deterministic if deterministic else lib().vct_trace_backward
+    check(fn(ctypes.byref(p), varr, garr, len(vs), ctypes.byref(P),
+             None if cfg is None else ctypes.byref(cfg), _ptr(grad_level0), _ptr(ws), ws.numel(),
+             _stream(stream)), "vct_trace_backward")
     return grad_level0
 
 

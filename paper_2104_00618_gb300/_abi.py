@@ -129,6 +129,14 @@ EXPORTS = {
                                     ctypes.POINTER(VctTraceParams),
                                     ctypes.POINTER(VctLaunchConfig), _vp, _vp, ctypes.c_size_t,
                                     _vp]),
+    "vct_trace_backward_deterministic_workspace_bytes": (ctypes.c_size_t,
+                                                         [ctypes.POINTER(VctPyramid)]),
+    "vct_trace_backward_deterministic": (_c_i32, [ctypes.POINTER(VctPyramid),
+                                                  ctypes.POINTER(VctView),
+                                                  ctypes.POINTER(VctViewGrad), _c_i32,
+                                                  ctypes.POINTER(VctTraceParams),
+                                                  ctypes.POINTER(VctLaunchConfig), _vp, _vp,
+                                                  ctypes.c_size_t, _vp]),
     "vct_trace_backward_noalloc": (_c_i32, [ctypes.POINTER(VctPyramid), ctypes.POINTER(VctView),
                                             ctypes.POINTER(VctViewGrad), _c_i32,
                                             ctypes.POINTER(VctTraceParams),

@@ -12,6 +12,8 @@
 // through the same inlined sample code, so they see bit-identical samples.
 // The derivatives are scattered through the quadrilinear weights into a
 // float32 gradient pyramid with vector atomics.
+#include <algorithm>
+
 #include "trace_common.cuh"
 
 namespace vct {
@@ -28,6 +30,15 @@ __device__ __forceinline__ float *grad_texel(const BwdLaunch &L, int l, uint32_t
   return reinterpret_cast<float *>(L.gpyr_lvl[l]) + 4 * (size_t)idx;
 }
 
+// One contribution in the fixed-point mode: v rounded to a multiple of
+// 2^-32, two's complement (integer addition of these is associative).
+__device__ __forceinline__ unsigned long long to_fix(float v) {
+  return (unsigned long long)__float2ll_rn(v * kFixScale);
+}
+__device__ __forceinline__ unsigned long long *fix_texel(const BwdLaunch &L, int l, uint32_t idx) {
+  return L.gfix_lvl[l] + 4 * (size_t)idx;
+}
+
 // Per-lane scatter of one level's 8 corners (lanes in different cells).
 __device__ __forceinline__ void scatter_lane(const BwdLaunch &L, int l, const LevelStencil &s,
                                              float lw, const float g[4]) {
@@ -38,8 +49,14 @@ __device__ __forceinline__ void scatter_lane(const BwdLaunch &L, int l, const Le
     if (w == 0.0f) continue;
     const uint32_t idx = corner_index(s, c);
     if (!in_bounds(idx, level_texels(L.pyr.n, l), kOobGrad)) continue;
-    atomicAdd(reinterpret_cast<float4 *>(grad_texel(L, l, idx)),
-              make_float4(w * g[0], w * g[1], w * g[2], w * g[3]));
+    if (L.deterministic) {
+      unsigned long long *q = fix_texel(L, l, idx);
+#pragma unroll
+      for (int ch = 0; ch < 4; ++ch) atomicAdd(q + ch, to_fix(w * g[ch]));
+    } else {
+      atomicAdd(reinterpret_cast<float4 *>(grad_texel(L, l, idx)),
+                make_float4(w * g[0], w * g[1], w * g[2], w * g[3]));
+    }
   }
 }
 
@@ -101,8 +118,12 @@ __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const uint32_t 
     const uint32_t sz0 = __shfl_sync(full, s.sz[0], leader), sz1 = __shfl_sync(full, s.sz[1], leader);
     const uint32_t idx = ((c & 1) ? sx1 : sx0) | (((c >> 1) & 1) ? sy1 : sy0) | ((c >> 2) ? sz1 : sz0);
     if (((lvalid >> c) & 1u) && v[0] != 0.0f &&
-        in_bounds(idx, level_texels(L.pyr.n, ll), kOobGrad))
-      atomicAdd(grad_texel(L, ll, idx) + ch, v[0]);
+        in_bounds(idx, level_texels(L.pyr.n, ll), kOobGrad)) {
+      if (L.deterministic)
+        atomicAdd(fix_texel(L, ll, idx) + ch, to_fix(v[0]));
+      else
+        atomicAdd(grad_texel(L, ll, idx) + ch, v[0]);
+    }
     pending &= ~lgrp;
   }
 }
@@ -295,6 +316,12 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
   }
 }
 
+__global__ void fix_to_float_kernel(const unsigned long long *fix, float *out, uint64_t count) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = __ll2float_rn((long long)fix[i]) * (1.0f / kFixScale);
+}
+
 template <int LPP>
 cudaError_t launch_b(const BwdLaunch &L, int grid, cudaStream_t s) {
   trace_bwd_kernel<LPP><<<grid, kTraceThreads, 0, s>>>(L);
@@ -320,6 +347,14 @@ cudaError_t launch_trace_bwd(const BwdLaunch &L, int lpp, int grid, cudaStream_t
     case 8: return launch_b<8>(L, grid, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_fix_to_float(const unsigned long long *fix, float *out, uint64_t count,
+                                cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const int grid = (int)std::min<uint64_t>((count + 255) / 256, 4096);
+  fix_to_float_kernel<<<grid, 256, 0, s>>>(fix, out, count);
+  return cudaGetLastError();
 }
 
 int trace_bwd_occupancy(int lpp) {

@@ -640,11 +640,24 @@ size_t vct_trace_backward_workspace_bytes(const vct_pyramid *pyr) {
   return (size_t)make_layout(pyr->n, pyr->levels, VCT_F32).total;
 }
 
-vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
-                              const vct_view_grad *grads, int32_t n_views,
-                              const vct_trace_params *params, const vct_launch_config *cfg,
-                              float *grad_level0_dense, void *workspace, size_t workspace_bytes,
-                              vct_stream_t stream) {
+}  // extern "C"
+
+namespace {
+
+// Fixed-point levels of the deterministic adjoint: 4 x uint64 per texel,
+// each level 256-byte aligned, after the float32 gradient pyramid.
+uint64_t fix_level_off(const vct::Layout &gl, int n, int l) {
+  uint64_t off = vct::align256(gl.total);
+  for (int k = 0; k < l; ++k) off += vct::align256(vct::level_texels(n, k) * 32);
+  return off;
+}
+
+vct_status trace_backward_impl(const vct_pyramid *pyr, const vct_view *views,
+                               const vct_view_grad *grads, int32_t n_views,
+                               const vct_trace_params *params, const vct_launch_config *cfg,
+                               float *grad_level0_dense, void *workspace, size_t workspace_bytes,
+                               vct_stream_t stream, bool deterministic) {
+  using namespace vct;
   vct_status st = check_pyramid(pyr, "vct_trace_backward");
   if (st != VCT_OK) return st;
   if (pyr->dtype != VCT_F32 || pyr->layout != VCT_LAYOUT_DENSE)
@@ -664,9 +677,10 @@ vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
   if (!grad_level0_dense || !aligned(grad_level0_dense, 16))
     return fail(VCT_ERR_INVALID_ARG, "vct_trace_backward: grad_level0 NULL or misaligned");
   const Layout gl = make_layout(pyr->n, pyr->levels, VCT_F32);
-  if (!workspace || workspace_bytes < gl.total || !aligned(workspace, 256))
+  const uint64_t need = deterministic ? fix_level_off(gl, pyr->n, pyr->levels) : gl.total;
+  if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
     return fail(VCT_ERR_WORKSPACE, "vct_trace_backward: workspace needs %llu bytes, 256-byte aligned",
-                (unsigned long long)gl.total);
+                (unsigned long long)need);
   vct_launch_config c = cfg ? *cfg : vct_launch_config{8, 8, 1, 0};
   if (!cfg_ok(c)) return fail(VCT_ERR_INVALID_ARG, "vct_trace_backward: bad launch config");
 
@@ -675,12 +689,17 @@ vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
   fill_common(*params, *L);
   if ((st = fill_pyr(*pyr, *params, L->pyr)) != VCT_OK) return st;
   uint8_t *ws = static_cast<uint8_t *>(workspace);
-  for (int l = 0; l < pyr->levels; ++l) L->gpyr_lvl[l] = reinterpret_cast<float *>(ws + gl.level_off[l]);
+  for (int l = 0; l < pyr->levels; ++l) {
+    L->gpyr_lvl[l] = reinterpret_cast<float *>(ws + gl.level_off[l]);
+    if (deterministic)
+      L->gfix_lvl[l] = reinterpret_cast<unsigned long long *>(ws + fix_level_off(gl, pyr->n, l));
+  }
+  L->deterministic = deterministic ? 1 : 0;
   L->queue = reinterpret_cast<unsigned *>(ws);
   L->tile_w = c.tile_w;
   L->tile_h = c.tile_h;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaMemsetAsync(ws, 0, gl.total, s);
+  cudaError_t e = cudaMemsetAsync(ws, 0, need, s);
   if (e != cudaSuccess) return cuda_fail(e, "vct_trace_backward workspace clear");
   int per_sm = c.ctas_per_sm ? c.ctas_per_sm : std::max(1, trace_bwd_occupancy(c.lanes_per_pixel));
   const int sms = sm_count();
@@ -702,10 +721,43 @@ vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
     e = launch_trace_bwd(*L, c.lanes_per_pixel, grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "vct_trace_backward launch");
   }
+  if (deterministic)
+    for (int l = 0; l < pyr->levels; ++l) {
+      e = launch_fix_to_float(L->gfix_lvl[l], L->gpyr_lvl[l], level_texels(pyr->n, l) * 4, s);
+      if (e != cudaSuccess) return cuda_fail(e, "vct_trace_backward fixed-point conversion");
+    }
   e = launch_mip_adjoint(reinterpret_cast<const float *>(ws), gl, pyr->n, pyr->levels,
                          grad_level0_dense, s);
   if (e != cudaSuccess) return cuda_fail(e, "vct_trace_backward mip adjoint launch");
   return VCT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
+                              const vct_view_grad *grads, int32_t n_views,
+                              const vct_trace_params *params, const vct_launch_config *cfg,
+                              float *grad_level0_dense, void *workspace, size_t workspace_bytes,
+                              vct_stream_t stream) {
+  return trace_backward_impl(pyr, views, grads, n_views, params, cfg, grad_level0_dense,
+                             workspace, workspace_bytes, stream, false);
+}
+
+size_t vct_trace_backward_deterministic_workspace_bytes(const vct_pyramid *pyr) {
+  if (!pyr || !shape_ok(pyr->n, pyr->levels, pyr->dtype)) return 0;
+  return (size_t)fix_level_off(make_layout(pyr->n, pyr->levels, VCT_F32), pyr->n, pyr->levels);
+}
+
+vct_status vct_trace_backward_deterministic(const vct_pyramid *pyr, const vct_view *views,
+                                            const vct_view_grad *grads, int32_t n_views,
+                                            const vct_trace_params *params,
+                                            const vct_launch_config *cfg,
+                                            float *grad_level0_dense, void *workspace,
+                                            size_t workspace_bytes, vct_stream_t stream) {
+  return trace_backward_impl(pyr, views, grads, n_views, params, cfg, grad_level0_dense,
+                             workspace, workspace_bytes, stream, true);
 }
 
 size_t vct_voxelize_workspace_bytes(int32_t n, int32_t n_triangles) {

@@ -337,7 +337,8 @@ struct BwdView {
 
 struct BwdLaunch {
   int n_views, total_tiles, tile_w, tile_h;
-  int n_diffuse, spec_enable, occ_enable, pad0;
+  int n_diffuse, spec_enable, occ_enable;
+  int deterministic;  // 1: accumulate in 64-bit fixed point (gfix_lvl), not float
   float diffuse_dir[VCT_MAX_DIFFUSE][3];
   float diffuse_weight[VCT_MAX_DIFFUSE];
   float light[3];
@@ -345,6 +346,7 @@ struct BwdLaunch {
   SpecSetup spec;
   unsigned *queue;
   float *gpyr_lvl[VCT_MAX_LEVELS];  // float32 gradient pyramid levels
+  unsigned long long *gfix_lvl[VCT_MAX_LEVELS];  // fixed-point levels (deterministic mode)
   DevPyr pyr;
   BwdView views[kMaxBwdViewsPerLaunch];
 };
@@ -393,6 +395,12 @@ cudaError_t launch_trace(const TraceLaunch &L, int lpp, int dtype, bool bricks, 
                          cudaStream_t s);
 int trace_occupancy(int lpp, int dtype, bool variants);
 cudaError_t launch_trace_bwd(const BwdLaunch &L, int lpp, int grid, cudaStream_t s);
+// Fixed-point gradient (units of 2^-32) -> float32, `count` values.
+cudaError_t launch_fix_to_float(const unsigned long long *fix, float *out, uint64_t count,
+                                cudaStream_t s);
+// Deterministic adjoint: contributions are rounded to multiples of 2^-32 and
+// summed as 64-bit integers, so the order of the atomics does not matter.
+constexpr float kFixScale = 4294967296.0f;  // 2^32
 int trace_bwd_occupancy(int lpp);
 
 }  // namespace vct

@@ -404,3 +404,36 @@ def test_backward_with_cone_state_matches_recomputed_march():
         outs[with_state] = vct.trace_backward(P, views, grads, prm).cpu().numpy()
     a, b = outs[False], outs[True]
     assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max(), np.abs(a - b).max()
+
+
+@pytest.mark.parametrize("lpp", [1, 4])
+def test_deterministic_backward_reproducible_and_close(lpp):
+    """vct_trace_backward_deterministic: the same gradient bit for bit on
+    every run (fixed-point sums do not depend on the order of the atomics),
+    within the fixed-point rounding of the float adjoint, and as close to the
+    FP64 adjoint as the float adjoint is."""
+    gt, views, prm, learn = _diff_case()
+    O_gt = oracle.build_mips(gt["grid"])
+    O = oracle.build_mips(learn)
+    grad_ref = np.zeros(learn.shape)
+    gpu_grads = []
+    for v in views:
+        t, r = oracle.trace(O_gt, v, prm), oracle.trace(O, v, prm)
+        gD, gS, gV = r["D"] - t["D"], r["S"] - t["S"], r["Vis"] - t["Vis"]
+        grad_ref += oracle.trace_backward(O, v, prm, gD, gS, gV)
+        gpu_grads.append(tuple(torch.from_numpy(a.astype(np.float32)).cuda()
+                               for a in (gD, gS, gV)))
+    P = gpu_pyramid(learn)
+    gviews = [vct.View.from_host(v) for v in views]
+    cfg = vct.launch_config(8, 8, lpp)
+    runs = [vct.trace_backward(P, gviews, gpu_grads, prm, cfg=cfg, deterministic=True)
+            for _ in range(3)]
+    assert all(torch.equal(runs[0], r) for r in runs[1:])
+    flt = vct.trace_backward(P, gviews, gpu_grads, prm, cfg=cfg).cpu().numpy()
+    det = runs[0].cpu().numpy().astype(np.float64)
+    scale = np.abs(grad_ref).max()
+    assert np.abs(det - flt).max() <= 1e-5 * scale
+    err = np.abs(det - grad_ref)
+    print("deterministic gradient: max abs err / max |grad| =", err.max() / scale)
+    assert err.max() <= 1e-4 * scale
+    assert np.linalg.norm(det - grad_ref) <= 1e-5 * np.linalg.norm(grad_ref)
