@@ -349,8 +349,12 @@ size_t vct_trace_backward_workspace_bytes(const vct_pyramid *pyr);
  * weights into a float32 gradient pyramid in `workspace`, then pushes each
  * level down to its children (1/8 each) and ADDS the level-0 result into
  * grad_level0_dense (device float32 [n][n][n][4], z, y, x, channel).
- * Every view must use pyramid index 0 (`pyr`), which must be VCT_F32
- * (VCT_ERR_UNSUPPORTED otherwise).  Scatter order is not deterministic (see
+ * Every view must use pyramid index 0 (`pyr`), of either dtype and layout:
+ * the march is recomputed from the stored (FP16 or brick) texels exactly as
+ * vct_trace read them, and the rounding of FP16 storage is passed through
+ * as identity (the gradient is that of the pyramid as stored, with respect
+ * to the values it was built from).  The gradient pyramid is always dense
+ * float32.  Scatter order is not deterministic (see
  * vct_trace_backward_deterministic for a reproducible variant).
  */
 vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,

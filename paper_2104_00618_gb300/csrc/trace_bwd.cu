@@ -132,6 +132,7 @@ __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const uint32_t 
 // with active == false take no samples).  With `state` (warp-uniform: null
 // or not for all lanes) the cone's length and transmittance before its last
 // sample come from the forward trace and the forward pass is skipped.
+template <int DT, bool BR>
 __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t *code_off,
                                              const uint32_t *lut, bool active,
                                              const Apex &A, const float w[3],
@@ -179,7 +180,7 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t 
       float T, lam;
       step_at(cc, T0, ks, T, lam);
       const float F[3] = {fmaf(T, w[0], A.Of[0]), fmaf(T, w[1], A.Of[1]), fmaf(T, w[2], A.Of[2])};
-      v = sample<VCT_F32>(P, A, F, lam, lut, om, lp, st);
+      v = sample<DT, BR>(P, A, F, lam, lut, om, lp, st);
     }
     if (!rev) {
       if (act) {
@@ -209,7 +210,7 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t 
   }
 }
 
-template <int LPP>
+template <int LPP, int DT, bool BR>
 __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __grid_constant__ BwdLaunch L) {
   constexpr int kPixPerRound = 32 / LPP;
   const int lane = threadIdx.x & 31;
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
         const uint2 *st = V.state == nullptr ? nullptr
                           : V.state + (on ? (size_t)c * V.W * V.H + p : 0);
         if (__any_sync(0xffffffffu, on))
-          cone_adjoint(L, s_code_off, s_lut, on, A, w, cc, T0, g0, g1, g2, ga, st);
+          cone_adjoint<DT, BR>(L, s_code_off, s_lut, on, A, w, cc, T0, g0, g1, g2, ga, st);
       }
     }
   }
@@ -322,17 +323,40 @@ __global__ void fix_to_float_kernel(const unsigned long long *fix, float *out, u
     out[i] = __ll2float_rn((long long)fix[i]) * (1.0f / kFixScale);
 }
 
-template <int LPP>
+template <int LPP, int DT, bool BR>
 cudaError_t launch_b(const BwdLaunch &L, int grid, cudaStream_t s) {
-  trace_bwd_kernel<LPP><<<grid, kTraceThreads, 0, s>>>(L);
+  trace_bwd_kernel<LPP, DT, BR><<<grid, kTraceThreads, 0, s>>>(L);
   return cudaGetLastError();
 }
 
-template <int LPP>
+template <int LPP, int DT, bool BR>
 int occ_b() {
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_bwd_kernel<LPP>, kTraceThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_bwd_kernel<LPP, DT, BR>, kTraceThreads,
+                                                0);
   return b;
+}
+
+template <int DT, bool BR>
+cudaError_t launch_lpp(const BwdLaunch &L, int lpp, int grid, cudaStream_t s) {
+  switch (lpp) {
+    case 1: return launch_b<1, DT, BR>(L, grid, s);
+    case 2: return launch_b<2, DT, BR>(L, grid, s);
+    case 4: return launch_b<4, DT, BR>(L, grid, s);
+    case 8: return launch_b<8, DT, BR>(L, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int DT, bool BR>
+int occ_lpp(int lpp) {
+  switch (lpp) {
+    case 1: return occ_b<1, DT, BR>();
+    case 2: return occ_b<2, DT, BR>();
+    case 4: return occ_b<4, DT, BR>();
+    case 8: return occ_b<8, DT, BR>();
+    default: return 0;
+  }
 }
 
 }  // namespace
@@ -340,13 +364,10 @@ int occ_b() {
 static_assert(sizeof(BwdLaunch) <= 32000, "adjoint launch parameters exceed the 32 KB limit");
 
 cudaError_t launch_trace_bwd(const BwdLaunch &L, int lpp, int grid, cudaStream_t s) {
-  switch (lpp) {
-    case 1: return launch_b<1>(L, grid, s);
-    case 2: return launch_b<2>(L, grid, s);
-    case 4: return launch_b<4>(L, grid, s);
-    case 8: return launch_b<8>(L, grid, s);
-    default: return cudaErrorInvalidValue;
-  }
+  const bool br = L.pyr.bricked != 0;
+  if (L.pyr.dtype == VCT_F16)
+    return br ? launch_lpp<VCT_F16, true>(L, lpp, grid, s) : launch_lpp<VCT_F16, false>(L, lpp, grid, s);
+  return br ? launch_lpp<VCT_F32, true>(L, lpp, grid, s) : launch_lpp<VCT_F32, false>(L, lpp, grid, s);
 }
 
 cudaError_t launch_fix_to_float(const unsigned long long *fix, float *out, uint64_t count,
@@ -357,14 +378,9 @@ cudaError_t launch_fix_to_float(const unsigned long long *fix, float *out, uint6
   return cudaGetLastError();
 }
 
-int trace_bwd_occupancy(int lpp) {
-  switch (lpp) {
-    case 1: return occ_b<1>();
-    case 2: return occ_b<2>();
-    case 4: return occ_b<4>();
-    case 8: return occ_b<8>();
-    default: return 0;
-  }
+int trace_bwd_occupancy(int lpp, int dtype, bool bricks) {
+  if (dtype == VCT_F16) return bricks ? occ_lpp<VCT_F16, true>(lpp) : occ_lpp<VCT_F16, false>(lpp);
+  return bricks ? occ_lpp<VCT_F32, true>(lpp) : occ_lpp<VCT_F32, false>(lpp);
 }
 
 VCT_OOB_ACCESSOR(oob_flags_trace_bwd)

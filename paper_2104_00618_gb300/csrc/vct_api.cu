@@ -660,9 +660,6 @@ vct_status trace_backward_impl(const vct_pyramid *pyr, const vct_view *views,
   using namespace vct;
   vct_status st = check_pyramid(pyr, "vct_trace_backward");
   if (st != VCT_OK) return st;
-  if (pyr->dtype != VCT_F32 || pyr->layout != VCT_LAYOUT_DENSE)
-    return fail(VCT_ERR_UNSUPPORTED,
-                "vct_trace_backward: only dense VCT_F32 pyramids are supported");
   if (!views || !grads || n_views < 1)
     return fail(VCT_ERR_INVALID_ARG, "vct_trace_backward: no views");
   if ((st = check_params(params, true)) != VCT_OK) return st;
@@ -701,7 +698,9 @@ vct_status trace_backward_impl(const vct_pyramid *pyr, const vct_view *views,
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(ws, 0, need, s);
   if (e != cudaSuccess) return cuda_fail(e, "vct_trace_backward workspace clear");
-  int per_sm = c.ctas_per_sm ? c.ctas_per_sm : std::max(1, trace_bwd_occupancy(c.lanes_per_pixel));
+  int per_sm = c.ctas_per_sm ? c.ctas_per_sm
+                             : std::max(1, trace_bwd_occupancy(c.lanes_per_pixel, pyr->dtype,
+                                                               L->pyr.bricked != 0));
   const int sms = sm_count();
   for (int v0 = 0; v0 < n_views; v0 += kMaxBwdViewsPerLaunch) {
     const int nv = std::min(kMaxBwdViewsPerLaunch, n_views - v0);

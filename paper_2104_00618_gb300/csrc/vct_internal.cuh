@@ -401,6 +401,6 @@ cudaError_t launch_fix_to_float(const unsigned long long *fix, float *out, uint6
 // Deterministic adjoint: contributions are rounded to multiples of 2^-32 and
 // summed as 64-bit integers, so the order of the atomics does not matter.
 constexpr float kFixScale = 4294967296.0f;  // 2^32
-int trace_bwd_occupancy(int lpp);
+int trace_bwd_occupancy(int lpp, int dtype, bool bricks);
 
 }  // namespace vct

@@ -120,14 +120,26 @@ def test_pool_too_small_is_reported():
     vct.pyramid_status(ok)
 
 
-def test_backward_rejects_bricks():
-    scene, view, prm = room_case(n=32, width=20, height=16)
-    P = vct.build_mips(torch.from_numpy(scene["grid"]).cuda(), layout="bricks")
-    v = vct.View.from_host(view)
-    vct.trace([P], [v], prm)
-    with pytest.raises(vct.VctError) as e:
-        vct.trace_backward(P, [v], [(v.out_diffuse, None, None)], prm)
-    assert e.value.status == vct._abi.VCT_ERR_UNSUPPORTED
+def test_backward_bricks_equals_dense():
+    """The adjoint reads a brick pyramid's texels as the forward did: the
+    gradient equals the dense pyramid's (up to the order of the float
+    atomics), also with the forward's per-cone state."""
+    g = sparse_grid(64, 21)
+    scene, view, prm = room_case(n=64, width=40, height=28)
+    level0 = torch.from_numpy(g).cuda()
+    grads = {}
+    for layout in ("dense", "bricks"):
+        P = vct.build_mips(level0, layout=layout)
+        v = vct.View.from_host(view).alloc_cone_state(prm)
+        vct.trace([P], [v], prm)
+        gr = [(v.out_diffuse * 0.5, v.out_specular, v.out_visibility - 0.25)]
+        grads[layout] = vct.trace_backward(P, [v], gr, prm).cpu().numpy()
+        grads[layout + "_det"] = vct.trace_backward(P, [v], gr, prm,
+                                                    deterministic=True).cpu().numpy()
+    a, b = grads["dense"], grads["bricks"]
+    assert np.abs(a).max() > 0
+    assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max()
+    assert np.array_equal(grads["dense_det"], grads["bricks_det"])
 
 
 def test_voxelized_512_room_in_bricks():

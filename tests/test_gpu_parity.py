@@ -318,9 +318,11 @@ def test_invalid_arguments_rejected():
     bad = dict(prm, spec_aperture_min=1e-7)
     with pytest.raises(vct.VctError):
         vct.trace([P], [vct.View.from_host(view)], bad)
-    P16 = gpu_pyramid(np.zeros((8, 8, 8, 4), np.float32), dtype="f16")
-    with pytest.raises(vct.VctError):
-        vct.trace_backward(P16, [vct.View.from_host(view)], [(None, None, None)], prm)
+    # the adjoint of the modified cones is not built
+    first_hit = vs.variant_params(prm, vct.FLAG_DIFFUSE_FIRST_HIT)
+    with pytest.raises(vct.VctError) as e:
+        vct.trace_backward(P, [vct.View.from_host(view)], [(None, None, None)], first_hit)
+    assert e.value.status == vct._abi.VCT_ERR_UNSUPPORTED
 
 
 # ---------------------------------------------------------------------------
@@ -437,3 +439,45 @@ def test_deterministic_backward_reproducible_and_close(lpp):
     print("deterministic gradient: max abs err / max |grad| =", err.max() / scale)
     assert err.max() <= 1e-4 * scale
     assert np.linalg.norm(det - grad_ref) <= 1e-5 * np.linalg.norm(grad_ref)
+
+
+def test_backward_fp16_pyramid():
+    """FP16 storage in the adjoint: on the constant learnable grid (0.1 at
+    every level) the FP16 pyramid holds exactly binary16(0.1) everywhere, so
+    its gradient equals the FP32 adjoint's, and the FP64 adjoint's, on that
+    grid; on a box scene it stays within FP16 storage error of the FP32
+    gradient."""
+    gt, views, prm, learn = _diff_case()
+    h = np.float32(np.float16(0.1))
+    learn_h = np.full_like(learn, h)
+    O_gt = oracle.build_mips(gt["grid"])
+    O = oracle.build_mips(learn_h)
+    grad_ref = np.zeros(learn.shape)
+    gpu_grads = []
+    for v in views:
+        t, r = oracle.trace(O_gt, v, prm), oracle.trace(O, v, prm)
+        gD, gS, gV = r["D"] - t["D"], r["S"] - t["S"], r["Vis"] - t["Vis"]
+        grad_ref += oracle.trace_backward(O, v, prm, gD, gS, gV)
+        gpu_grads.append(tuple(torch.from_numpy(a.astype(np.float32)).cuda()
+                               for a in (gD, gS, gV)))
+    gviews = [vct.View.from_host(v) for v in views]
+    P16 = gpu_pyramid(learn, dtype="f16")
+    P32 = gpu_pyramid(learn_h)
+    g16 = vct.trace_backward(P16, gviews, gpu_grads, prm).cpu().numpy().astype(np.float64)
+    g32 = vct.trace_backward(P32, gviews, gpu_grads, prm).cpu().numpy().astype(np.float64)
+    scale = np.abs(grad_ref).max()
+    assert np.abs(g16 - g32).max() <= 1e-6 * scale
+    assert np.abs(g16 - grad_ref).max() <= 1e-4 * scale
+    # a box scene: FP16 texels differ from FP32 by half an ulp of binary16
+    scene, view, prm2 = room_case(n=32, width=30, height=20, seed=8)
+    outs = {}
+    for dt in ("f32", "f16"):
+        P = gpu_pyramid(scene["grid"], dtype=dt)
+        v = vct.View.from_host(view)
+        vct.trace([P], [v], prm2)
+        gr = [(torch.ones_like(v.out_diffuse), torch.ones_like(v.out_specular),
+               torch.ones_like(v.out_visibility))]
+        outs[dt] = vct.trace_backward(P, [v], gr, prm2).cpu().numpy()
+    rel = np.abs(outs["f16"] - outs["f32"]).max() / np.abs(outs["f32"]).max()
+    print("fp16 adjoint vs fp32, box scene:", rel)
+    assert rel < 5e-3
