@@ -263,6 +263,7 @@ void orc_sample_lod(const double *pyr, int n, int levels, const double *q,
 /* ---------------------------------------------------------------------- */
 typedef struct {
   double t, a, c[3], trans; /* step position, sample alpha/colour, T_k   */
+  double sa;                /* d a / d (sampled alpha): the occlusion fade */
   orc_stencil st;
 } orc_step;
 
@@ -271,6 +272,7 @@ typedef struct {
   int64_t steps;
   double margin;     /* min |t - t_max| / t_max over the tested t values  */
   double hit_margin; /* min |a_s - 1/100| over first-hit tests (variant)  */
+  int hit;           /* first-hit variant: the cone stopped on a sample    */
 } orc_cone_result;
 
 /* Marches one cone.  If `rec` is non-NULL the per-step state is stored
@@ -307,6 +309,7 @@ static void march_kind(const orc_grid *g, const double o[3], const double w[3],
   double alpha = 0.0, c[3] = {0.0, 0.0, 0.0};
   double margin = INFINITY;
   int64_t k = 0;
+  res->hit = 0;
   for (;;) {
     double m = fabs(t - P->t_max) / P->t_max;
     if (m < margin) margin = m;
@@ -326,6 +329,15 @@ static void march_kind(const orc_grid *g, const double o[3], const double w[3],
       if (v[3] > 0.01) {
         for (int ch = 0; ch < 3; ++ch) c[ch] = v[ch];
         alpha = 1.0;
+        if (rec && k < cap) { /* the returned sample, for the adjoint */
+          rec[k].t = t;
+          rec[k].a = v[3];
+          for (int ch = 0; ch < 3; ++ch) rec[k].c[ch] = v[ch];
+          rec[k].trans = 1.0;
+          rec[k].sa = 1.0;
+          rec[k].st = st;
+        }
+        res->hit = 1;
         ++k;
         break;
       }
@@ -333,10 +345,13 @@ static void march_kind(const orc_grid *g, const double o[3], const double w[3],
       ++k;
       continue;
     }
+    double fade = 1.0;
     if (occ_smooth) /* Ch. 5.4.4 occlusion cone: fade near the apex */
-      v[3] *= smoothstep(0.0, P->occ_max_dist, sqrt(t) * P->shadow_str);
+      fade = smoothstep(0.0, P->occ_max_dist, sqrt(t) * P->shadow_str);
+    v[3] *= fade;
     if (rec && k < cap) {
       rec[k].t = t;
+      rec[k].sa = fade;
       rec[k].a = v[3];
       rec[k].c[0] = v[0];
       rec[k].c[1] = v[1];
@@ -612,43 +627,65 @@ void orc_trace(const double *pyr, int n, int levels, const double *origin,
  *   dC/dc_k = T_k a_k
  *   dC/da_k = T_k (c_k - R_{k+1}),  R_k = a_k c_k + (1 - a_k) R_{k+1}, R_K = 0
  *   dA/da_k = T_k Q_{k+1},          Q_k = (1 - a_k) Q_{k+1},           Q_K = 1
+ * With premultiplied sample colour (C = sum_k T_k c_k):
+ *   dC/dc_k = T_k,  dC/da_k = -T_k R'_{k+1},  R'_k = c_k + (1 - a_k) R'_{k+1}.
+ * The occlusion fade scales the sampled alpha by a factor of t alone, so the
+ * texel alpha receives dL/da_k times that factor.  A first-hit diffuse cone
+ * returns (c_k, 1) of its hit sample: only that sample's colour has a
+ * derivative (the choice of the sample is piecewise constant).
  * The step schedule does not depend on the voxel values (only the stopping
  * step does, which is piecewise constant), so these are the derivatives.
  */
+static void scatter_sample(const orc_grid *g, double *gpyr, const orc_step *s,
+                           const double dc[3], double da) {
+  for (int lk = 0; lk < 2; ++lk) {
+    int nl = g->n >> s->st.level[lk];
+    double *lv = gpyr + orc_level_offset(g->n, s->st.level[lk]);
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          int x = s->st.base[lk][0] + dx, y = s->st.base[lk][1] + dy,
+              z = s->st.base[lk][2] + dz;
+          if (x < 0 || y < 0 || z < 0 || x >= nl || y >= nl || z >= nl)
+            continue;
+          double w = corner_weight(&s->st, lk, dx, dy, dz);
+          if (w == 0.0) continue;
+          double *t = lv + (((size_t)z * nl + y) * nl + x) * 4;
+          for (int ch = 0; ch < 3; ++ch) {
+#pragma omp atomic
+            t[ch] += w * dc[ch];
+          }
+#pragma omp atomic
+          t[3] += w * da;
+        }
+  }
+}
+
 static void cone_adjoint(const orc_grid *g, double *gpyr, const orc_step *rec,
-                         int64_t K, const double gc[3], double ga) {
+                         const orc_cone_result *r, int first_hit, int premul,
+                         const double gc[3], double ga) {
+  if (first_hit) {
+    if (r->hit) scatter_sample(g, gpyr, rec + r->steps - 1, gc, 0.0);
+    return;
+  }
   double R[3] = {0.0, 0.0, 0.0}, Q = 1.0;
-  for (int64_t k = K - 1; k >= 0; --k) {
+  for (int64_t k = r->steps - 1; k >= 0; --k) {
     const orc_step *s = rec + k;
     double dc[3], da = 0.0;
     for (int ch = 0; ch < 3; ++ch) {
-      dc[ch] = gc[ch] * s->trans * s->a;
-      da += gc[ch] * s->trans * (s->c[ch] - R[ch]);
+      if (premul) {
+        dc[ch] = gc[ch] * s->trans;
+        da -= gc[ch] * s->trans * R[ch];
+      } else {
+        dc[ch] = gc[ch] * s->trans * s->a;
+        da += gc[ch] * s->trans * (s->c[ch] - R[ch]);
+      }
     }
     da += ga * s->trans * Q;
-    for (int ch = 0; ch < 3; ++ch) R[ch] = s->a * s->c[ch] + (1.0 - s->a) * R[ch];
+    for (int ch = 0; ch < 3; ++ch)
+      R[ch] = (premul ? s->c[ch] : s->a * s->c[ch]) + (1.0 - s->a) * R[ch];
     Q = (1.0 - s->a) * Q;
-    for (int lk = 0; lk < 2; ++lk) {
-      int nl = g->n >> s->st.level[lk];
-      double *lv = gpyr + orc_level_offset(g->n, s->st.level[lk]);
-      for (int dz = 0; dz < 2; ++dz)
-        for (int dy = 0; dy < 2; ++dy)
-          for (int dx = 0; dx < 2; ++dx) {
-            int x = s->st.base[lk][0] + dx, y = s->st.base[lk][1] + dy,
-                z = s->st.base[lk][2] + dz;
-            if (x < 0 || y < 0 || z < 0 || x >= nl || y >= nl || z >= nl)
-              continue;
-            double w = corner_weight(&s->st, lk, dx, dy, dz);
-            if (w == 0.0) continue;
-            double *t = lv + (((size_t)z * nl + y) * nl + x) * 4;
-            for (int ch = 0; ch < 3; ++ch) {
-#pragma omp atomic
-              t[ch] += w * dc[ch];
-            }
-#pragma omp atomic
-            t[3] += w * da;
-          }
-    }
+    scatter_sample(g, gpyr, s, dc, da * s->sa);
   }
 }
 
@@ -677,23 +714,26 @@ void orc_trace_backward(const double *pyr, int n, int levels,
       cone_set(&g, v, px, P, &cs);
       for (int c = 0; c < cs.count; ++c) {
         orc_cone_result r;
-        march(&g, cs.apex, cs.dir[c], cs.aperture[c], P, &r, rec, cap);
+        march_kind(&g, cs.apex, cs.dir[c], cs.aperture[c], P, cs.kind[c], &r, rec, cap);
         if (r.steps > cap) { /* grow and redo */
           cap = r.steps;
           rec = (orc_step *)realloc(rec, sizeof(orc_step) * cap);
-          march(&g, cs.apex, cs.dir[c], cs.aperture[c], P, &r, rec, cap);
+          march_kind(&g, cs.apex, cs.dir[c], cs.aperture[c], P, cs.kind[c], &r, rec, cap);
         }
         double gc[3] = {0.0, 0.0, 0.0}, ga = 0.0;
         if (cs.kind[c] == 0) {
           for (int ch = 0; ch < 3; ++ch) gc[ch] = cs.weight[c] * gD[4 * i + ch];
           ga = cs.weight[c] * gD[4 * i + 3];
         } else if (cs.kind[c] == 1) {
-          for (int ch = 0; ch < 3; ++ch) gc[ch] = gS[4 * i + ch];
+          /* the angular-grace factor scales the specular colour only */
+          double f = (P->flags & ORC_SPEC_GRACE) ? spec_grace(cs.dir[c], P) : 1.0;
+          for (int ch = 0; ch < 3; ++ch) gc[ch] = f * gS[4 * i + ch];
           ga = gS[4 * i + 3];
         } else {
           ga = gV ? -gV[i] : 0.0;
         }
-        cone_adjoint(&g, gpyr, rec, r.steps, gc, ga);
+        const int first_hit = cs.kind[c] == 0 && (P->flags & ORC_DIFF_FIRST);
+        cone_adjoint(&g, gpyr, rec, &r, first_hit, (P->flags & ORC_PREMUL) != 0, gc, ga);
       }
     }
     free(rec);

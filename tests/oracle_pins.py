@@ -464,6 +464,61 @@ def check_gradient_fd():
     assert np.abs(grad).max() > 1e-3
 
 
+def _fd_check(g, view, prm, targets, picks, eps, tol):
+    L, r = _loss(g, view, prm, targets)
+    tD, tS, tV = targets
+    grad = oracle.trace_backward(oracle.build_mips(g), view, prm, r["D"] - tD, r["S"] - tS,
+                                 r["Vis"] - tV)
+    for flat in picks:
+        gp, gm = g.copy(), g.copy()
+        gp.reshape(-1)[flat] += eps
+        gm.reshape(-1)[flat] -= eps
+        fd = (_loss(gp, view, prm, targets)[0] - _loss(gm, view, prm, targets)[0]) / (2 * eps)
+        an = grad.reshape(-1)[flat]
+        assert abs(fd - an) <= tol * max(1e-3, abs(an)), (prm["flags"], flat, fd, an)
+    return grad, r
+
+
+def check_gradient_fd_modified_cones():
+    """Central differences against the adjoint with each of the thesis's
+    modified cones (Ch. 5.4.4) and with premultiplied compositing: the
+    occlusion fade (a factor of t alone on the sample opacity), the angular
+    grace (a factor of the cone axis alone on the specular colour), the
+    first-hit diffuse cone (the hit sample's colour; no first-hit decision
+    within reach of the perturbation) and c += T_k c_s."""
+    import vct_synth as vs
+    for flags in (1, 2, 4, 32, 1 | 2 | 32):
+        # first hit: opacities around the 1/100 threshold, so that some cones
+        # hit after their first sample, and a perturbation below the margin
+        eps = 1e-5 if flags & 4 else 1e-4
+        for seed in range(20, 40):
+            g, view, prm, targets = _small_diff_problem(seed=seed)
+            if flags & 4:
+                g[..., 3] *= 0.1
+            # a fade that is still below one at the samples of this small grid
+            prm = dict(vs.variant_params(prm, flags), occ_max_dist=1.0)
+            r = oracle.trace(oracle.build_mips(g), view, prm)
+            if not (flags & 4) or (r["hit_margin"] > 4 * eps and r["steps"][0] > r["cones"][0]):
+                break
+        else:
+            raise AssertionError("no seed keeps the first-hit decisions away from the threshold")
+        L, r = _loss(g, view, prm, targets)
+        tD, tS, tV = targets
+        grad = oracle.trace_backward(oracle.build_mips(g), view, prm, r["D"] - tD,
+                                     r["S"] - tS, r["Vis"] - tV)
+        rng = np.random.default_rng(seed + 100)
+        big = np.argsort(-np.abs(grad).reshape(-1))[:10]
+        picks = list(big) + list(rng.integers(0, g.size, 8))
+        if flags & 4:  # the hit samples' colours, and an alpha (zero gradient)
+            picks += list(np.flatnonzero(np.abs(grad[..., 3]).reshape(-1) == 0)[:2] * 4 + 3)
+        _fd_check(g, view, prm, targets, picks, eps, 1e-6)
+        assert np.abs(grad).max() > 1e-3, flags
+        if flags & 4:  # the first-hit diffuse cones pass no gradient to alpha
+            only_d = oracle.trace_backward(oracle.build_mips(g), view, prm, r["D"] - tD,
+                                           np.zeros_like(tS), np.zeros(len(tV)))
+            assert not np.any(only_d[..., 3]) and np.abs(only_d[..., :3]).max() > 0
+
+
 # --------------------------------------------------------------------------
 # the thesis's modified cones (Ch. 5.4.4) and the shading epilogue
 # --------------------------------------------------------------------------

@@ -42,8 +42,20 @@ MUTANTS = {
         " z = z < 0 ? 0 : (z >= nl ? nl - 1 : z); }"),
     "adjoint drops Q": ("da += ga * s->trans * Q;", "da += ga * Q;"),
     "adjoint suffix not attenuated": (
-        "R[ch] = s->a * s->c[ch] + (1.0 - s->a) * R[ch];",
-        "R[ch] = s->a * s->c[ch] + R[ch];"),
+        "R[ch] = (premul ? s->c[ch] : s->a * s->c[ch]) + (1.0 - s->a) * R[ch];",
+        "R[ch] = (premul ? s->c[ch] : s->a * s->c[ch]) + R[ch];"),
+    "premultiplied adjoint takes the straight colour weight": (
+        "dc[ch] = gc[ch] * s->trans;", "dc[ch] = gc[ch] * s->trans * s->a;"),
+    "premultiplied adjoint: opacity term sign": ("da -= gc[ch] * s->trans * R[ch];",
+                                                 "da += gc[ch] * s->trans * R[ch];"),
+    "occlusion fade left out of the adjoint": ("scatter_sample(g, gpyr, s, dc, da * s->sa);",
+                                               "scatter_sample(g, gpyr, s, dc, da);"),
+    "first-hit gradient to the first sample": (
+        "if (r->hit) scatter_sample(g, gpyr, rec + r->steps - 1, gc, 0.0);",
+        "if (r->hit) scatter_sample(g, gpyr, rec, gc, 0.0);"),
+    "grace factor left out of the adjoint": (
+        "double f = (P->flags & ORC_SPEC_GRACE) ? spec_grace(cs.dir[c], P) : 1.0;",
+        "double f = 1.0;"),
     "mip adjoint weight": ("gp[(((size_t)(z / 2) * np + y / 2) * np + x / 2) * 4 + c] / 8.0;",
                            "gp[(((size_t)(z / 2) * np + y / 2) * np + x / 2) * 4 + c] / 4.0;"),
     "diffuse weight dropped": ("d[ch] += cs.weight[c] * r.c[ch];", "d[ch] += r.c[ch];"),
