@@ -325,6 +325,11 @@ def trace_backward(pyr: Pyramid, views, grads, params, grad_level0: torch.Tensor
     if grad_level0 is None:
         grad_level0 = torch.zeros((pyr.n,) * 3 + (4,), dtype=torch.float32,
                                   device=pyr.storage.device)
+    elif (tuple(grad_level0.shape) != (pyr.n,) * 3 + (4,) or grad_level0.dtype != torch.float32
+          or not grad_level0.is_contiguous() or grad_level0.device != pyr.storage.device):
+        raise ValueError(f"grad_level0 must be a contiguous float32 [{pyr.n}]^3 x 4 tensor on "
+                         f"{pyr.storage.device}, got {tuple(grad_level0.shape)} "
+                         f"{grad_level0.dtype} on {grad_level0.device}")
     ws = workspace if workspace is not None else backward_workspace(pyr, deterministic)
     p = pyr.struct()
     varr = (VctView * len(vs))(*[v.struct() for v in vs])

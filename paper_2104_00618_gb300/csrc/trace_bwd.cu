@@ -132,14 +132,24 @@ __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const uint32_t 
 // with active == false take no samples).  With `state` (warp-uniform: null
 // or not for all lanes) the cone's length and transmittance before its last
 // sample come from the forward trace and the forward pass is skipped.
-template <int DT, bool BR>
+// `mode` (per lane) is the cone's march variant (Ch. 5.4.4), recomputed
+// exactly as the forward marched it: the occlusion fade scales the sampled
+// opacity by a factor of t alone (the texel opacity receives dL/da times
+// it); a first-hit diffuse cone returns its hit sample's colour, so only that
+// sample's colour channels receive gradient.  With premultiplied colour
+// (C = sum T_k c_k): dC/dc_k = T_k, dC/da_k = -T_k R'_{k+1}, R'_k = c_k +
+// (1 - a_k) R'_{k+1}.
+template <int DT, bool BR, bool kVar>
 __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t *code_off,
                                              const uint32_t *lut, bool active,
                                              const Apex &A, const float w[3],
                                              const ConeConst &cc, float T0, float gc0, float gc1,
-                                             float gc2, float ga, const uint2 *state) {
+                                             float gc2, float ga, const uint2 *state, int mode) {
   const unsigned full = 0xffffffffu;
   const DevPyr &P = L.pyr;
+  // kVar: a launch with a cone variant; the plain instances keep none of it
+  const bool premul = kVar && (L.var.flags & VCT_FLAG_PREMULTIPLIED) != 0;
+  if constexpr (!kVar) mode = kPlain;
   float prod = 1.f, prod_last = 1.f;
   float tr_next = 0.f, R0 = 0.f, R1 = 0.f, R2 = 0.f, Q = 1.f;
   int k = 0;                    // this lane's forward step
@@ -165,8 +175,16 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t 
     } else {
       --kr;
     }
-    if (rev && kr < 0) break;
-    const bool act = rev ? (kr < K) : (K < 0);
+    // a first-hit cone needs its last step only; the walk ends when every
+    // lane has passed its lowest step (lanes without samples have K = 0)
+    bool act;
+    if constexpr (kVar) {
+      if (rev && __all_sync(full, kr < 0 || (mode == kFirstHit && kr < K - 1))) break;
+      act = rev ? (kr >= 0 && kr < K && (mode != kFirstHit || kr == K - 1)) : (K < 0);
+    } else {
+      if (rev && kr < 0) break;
+      act = rev ? (kr < K) : (K < 0);
+    }
     const int ks = rev ? kr : k;
     LevelStencil st[2];
     st[0].valid = 0u;
@@ -175,32 +193,58 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t 
     lp.l0 = lp.l1 = 0;
     lp.f = 0.f;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    float om = 1.f;
+    float om = 1.f, fade = 1.f;
     if (act) {
       float T, lam;
       step_at(cc, T0, ks, T, lam);
       const float F[3] = {fmaf(T, w[0], A.Of[0]), fmaf(T, w[1], A.Of[1]), fmaf(T, w[2], A.Of[2])};
       v = sample<DT, BR>(P, A, F, lam, lut, om, lp, st);
+      if (kVar && mode == kOccSmooth) {  // as the forward march
+        fade = smoothstep0(L.var.occ_max_dist, sqrtf(T * P.h0) * L.var.shadow_str);
+        v.w *= fade;
+        om = transparency(v.w);
+      }
     }
     if (!rev) {
       if (act) {
-        prod_last = prod;
-        prod *= om;
+        if (kVar && mode == kFirstHit) {
+          if (v.w > 0.01f) K = k + 1;  // the hit ends the cone
+        } else {
+          prod_last = prod;
+          prod *= om;
+        }
         ++k;
       }
       continue;
     }
     float g[4] = {0.f, 0.f, 0.f, 0.f};
-    if (act) {
+    if (kVar && act && mode == kFirstHit) {
+      if (v.w > 0.01f) {  // a hit (not the end of the cone without one)
+        g[0] = gc0;
+        g[1] = gc1;
+        g[2] = gc2;
+      }
+    } else if (act) {
       const float tr = (kr == K - 1) ? prod_last : tr_next / om;
-      const float ta = tr * v.w;  // same T_k as the forward's colour weight
-      g[0] = gc0 * ta;
-      g[1] = gc1 * ta;
-      g[2] = gc2 * ta;
-      g[3] = tr * (gc0 * (v.x - R0) + gc1 * (v.y - R1) + gc2 * (v.z - R2) + ga * Q);
-      R0 = fmaf(v.w, v.x, om * R0);
-      R1 = fmaf(v.w, v.y, om * R1);
-      R2 = fmaf(v.w, v.z, om * R2);
+      if (premul) {
+        g[0] = gc0 * tr;
+        g[1] = gc1 * tr;
+        g[2] = gc2 * tr;
+        g[3] = tr * (ga * Q - (gc0 * R0 + gc1 * R1 + gc2 * R2));
+        R0 = fmaf(om, R0, v.x);
+        R1 = fmaf(om, R1, v.y);
+        R2 = fmaf(om, R2, v.z);
+      } else {
+        const float ta = tr * v.w;  // same T_k as the forward's colour weight
+        g[0] = gc0 * ta;
+        g[1] = gc1 * ta;
+        g[2] = gc2 * ta;
+        g[3] = tr * (gc0 * (v.x - R0) + gc1 * (v.y - R1) + gc2 * (v.z - R2) + ga * Q);
+        R0 = fmaf(v.w, v.x, om * R0);
+        R1 = fmaf(v.w, v.y, om * R1);
+        R2 = fmaf(v.w, v.z, om * R2);
+      }
+      if constexpr (kVar) g[3] *= fade;
       Q *= om;
       tr_next = tr;
     }
@@ -210,7 +254,7 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t 
   }
 }
 
-template <int LPP, int DT, bool BR>
+template <int LPP, int DT, bool BR, bool kVar>
 __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __grid_constant__ BwdLaunch L) {
   constexpr int kPixPerRound = 32 / LPP;
   const int lane = threadIdx.x & 31;
@@ -283,12 +327,16 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
         float w[3] = {0.f, 0.f, 1.f};
         ConeConst cc = P.diffuse;
         float g0, g1, g2, ga;
+        int mode = kPlain;
         if (cs.kind == kSpecular) {
           if (pix_on) reflect_dir(x, V.cam, n, w);
           cc = pix_on ? spec_const(P, L.spec, V.rough, p) : P.spec_fixed;
-          g0 = gS.x;
-          g1 = gS.y;
-          g2 = gS.z;
+          // the angular-grace factor scales the specular colour only
+          const float f =
+              (kVar && (L.var.flags & VCT_FLAG_SPEC_GRACE)) ? spec_grace(L.var, w) : 1.0f;
+          g0 = f * gS.x;
+          g1 = f * gS.y;
+          g2 = f * gS.z;
           ga = gS.w;
         } else if (cs.kind == kOcclusion) {
           w[0] = L.light[0];
@@ -297,6 +345,7 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
           cc = P.occ;
           g0 = g1 = g2 = 0.f;
           ga = -gV;  // Vis = 1 - alpha
+          if (L.var.flags & VCT_FLAG_OCC_SMOOTH) mode = kOccSmooth;
         } else {
           const float *d = L.diffuse_dir[cs.diffuse_index];
 #pragma unroll
@@ -306,12 +355,14 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
           g1 = wt * gD.y;
           g2 = wt * gD.z;
           ga = wt * gD.w;
+          if (L.var.flags & VCT_FLAG_DIFFUSE_FIRST_HIT) mode = kFirstHit;
         }
         const bool on = pix_on && has_cone && (g0 != 0.f || g1 != 0.f || g2 != 0.f || ga != 0.f);
         const uint2 *st = V.state == nullptr ? nullptr
                           : V.state + (on ? (size_t)c * V.W * V.H + p : 0);
         if (__any_sync(0xffffffffu, on))
-          cone_adjoint<DT, BR>(L, s_code_off, s_lut, on, A, w, cc, T0, g0, g1, g2, ga, st);
+          cone_adjoint<DT, BR, kVar>(L, s_code_off, s_lut, on, A, w, cc, T0, g0, g1, g2, ga, st,
+                                     mode);
       }
     }
   }
@@ -323,38 +374,44 @@ __global__ void fix_to_float_kernel(const unsigned long long *fix, float *out, u
     out[i] = __ll2float_rn((long long)fix[i]) * (1.0f / kFixScale);
 }
 
-template <int LPP, int DT, bool BR>
+template <int LPP, int DT, bool BR, bool kVar>
 cudaError_t launch_b(const BwdLaunch &L, int grid, cudaStream_t s) {
-  trace_bwd_kernel<LPP, DT, BR><<<grid, kTraceThreads, 0, s>>>(L);
+  trace_bwd_kernel<LPP, DT, BR, kVar><<<grid, kTraceThreads, 0, s>>>(L);
   return cudaGetLastError();
 }
 
-template <int LPP, int DT, bool BR>
+template <int LPP, int DT, bool BR, bool kVar>
 int occ_b() {
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_bwd_kernel<LPP, DT, BR>, kTraceThreads,
-                                                0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_bwd_kernel<LPP, DT, BR, kVar>,
+                                                kTraceThreads, 0);
   return b;
 }
 
-template <int DT, bool BR>
+template <int DT, bool BR, bool kVar>
 cudaError_t launch_lpp(const BwdLaunch &L, int lpp, int grid, cudaStream_t s) {
   switch (lpp) {
-    case 1: return launch_b<1, DT, BR>(L, grid, s);
-    case 2: return launch_b<2, DT, BR>(L, grid, s);
-    case 4: return launch_b<4, DT, BR>(L, grid, s);
-    case 8: return launch_b<8, DT, BR>(L, grid, s);
+    case 1: return launch_b<1, DT, BR, kVar>(L, grid, s);
+    case 2: return launch_b<2, DT, BR, kVar>(L, grid, s);
+    case 4: return launch_b<4, DT, BR, kVar>(L, grid, s);
+    case 8: return launch_b<8, DT, BR, kVar>(L, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <int DT, bool BR>
+cudaError_t launch_var(const BwdLaunch &L, int lpp, int grid, cudaStream_t s) {
+  return bwd_has_variants(L.var.flags) ? launch_lpp<DT, BR, true>(L, lpp, grid, s)
+                                       : launch_lpp<DT, BR, false>(L, lpp, grid, s);
+}
+
+template <int DT, bool BR>
 int occ_lpp(int lpp) {
   switch (lpp) {
-    case 1: return occ_b<1, DT, BR>();
-    case 2: return occ_b<2, DT, BR>();
-    case 4: return occ_b<4, DT, BR>();
-    case 8: return occ_b<8, DT, BR>();
+    case 1: return occ_b<1, DT, BR, false>();
+    case 2: return occ_b<2, DT, BR, false>();
+    case 4: return occ_b<4, DT, BR, false>();
+    case 8: return occ_b<8, DT, BR, false>();
     default: return 0;
   }
 }
@@ -366,8 +423,8 @@ static_assert(sizeof(BwdLaunch) <= 32000, "adjoint launch parameters exceed the 
 cudaError_t launch_trace_bwd(const BwdLaunch &L, int lpp, int grid, cudaStream_t s) {
   const bool br = L.pyr.bricked != 0;
   if (L.pyr.dtype == VCT_F16)
-    return br ? launch_lpp<VCT_F16, true>(L, lpp, grid, s) : launch_lpp<VCT_F16, false>(L, lpp, grid, s);
-  return br ? launch_lpp<VCT_F32, true>(L, lpp, grid, s) : launch_lpp<VCT_F32, false>(L, lpp, grid, s);
+    return br ? launch_var<VCT_F16, true>(L, lpp, grid, s) : launch_var<VCT_F16, false>(L, lpp, grid, s);
+  return br ? launch_var<VCT_F32, true>(L, lpp, grid, s) : launch_var<VCT_F32, false>(L, lpp, grid, s);
 }
 
 cudaError_t launch_fix_to_float(const unsigned long long *fix, float *out, uint64_t count,

@@ -339,6 +339,31 @@ __device__ __forceinline__ float4 sample(const DevPyr &P, const Apex &A, const f
   return make_float4(v0.x, v0.y, v1.x, v1.y);
 }
 
+// Cone march variants (Ch. 5.4.4): the plain march, the occlusion cone that
+// fades its samples near the apex, and the diffuse cone that stops at the
+// first sample with opacity above 1/100.
+enum MarchMode { kPlain = 0, kOccSmooth = 1, kFirstHit = 2 };
+
+// GLSL smoothstep(0, e1, x).
+__device__ __forceinline__ float smoothstep0(float e1, float x) {
+  const float u = fminf(fmaxf(x / e1, 0.0f), 1.0f);
+  return u * u * (3.0f - 2.0f * u);
+}
+
+// Angular-grace specular BRDF (Ch. 5.4.4): (1 - max(0, g - p) / pi)^q with g
+// the angle between the cone axis w and the light direction, taken as
+// atan2(|w x l|, w . l) (well conditioned at every angle).
+__device__ __forceinline__ float spec_grace(const Variants &v, const float w[3]) {
+  const float *l = v.light_dir;
+  const float cx = w[1] * l[2] - w[2] * l[1];
+  const float cy = w[2] * l[0] - w[0] * l[2];
+  const float cz = w[0] * l[1] - w[1] * l[0];
+  const float d = w[0] * l[0] + w[1] * l[1] + w[2] * l[2];
+  const float g = atan2f(sqrtf(cx * cx + cy * cy + cz * cz), d);
+  const float e = fmaxf(g - v.grace, 0.0f);
+  return powf(1.0f - e * 0.318309886f, v.falloff);
+}
+
 // Fills the Morton spread table (shared memory) of a CTA.
 __device__ __forceinline__ void fill_spread_lut(uint32_t *lut) {
   for (int i = threadIdx.x; i < 1024; i += blockDim.x) lut[i] = spread3((uint32_t)i);

@@ -96,11 +96,11 @@ bool aperture_ok(float g) { return finite(g) && g > 0.0f && g < (float)kPi; }
 
 constexpr int kFlagsAll = VCT_FLAG_OCC_SMOOTH | VCT_FLAG_SPEC_GRACE | VCT_FLAG_DIFFUSE_FIRST_HIT |
                           VCT_FLAG_SHADE | VCT_FLAG_SHADE_IMPL | VCT_FLAG_PREMULTIPLIED;
-constexpr int kFlagsCone = VCT_FLAG_OCC_SMOOTH | VCT_FLAG_SPEC_GRACE | VCT_FLAG_DIFFUSE_FIRST_HIT |
-                           VCT_FLAG_PREMULTIPLIED;
 
-// `backward`: the adjoint covers the unmodified cones only.
+// `backward`: checked for the adjoint, which covers every cone variant; the
+// shading flags only add the radiance output, which the adjoint leaves out.
 vct_status check_params(const vct_trace_params *P, bool backward) {
+  (void)backward;
   if (!P) return fail(VCT_ERR_INVALID_ARG, "params: NULL");
   if (P->n_diffuse < 0 || P->n_diffuse > VCT_MAX_DIFFUSE)
     return fail(VCT_ERR_INVALID_ARG, "params: n_diffuse %d out of [0, %d]", P->n_diffuse,
@@ -110,10 +110,6 @@ vct_status check_params(const vct_trace_params *P, bool backward) {
   if (P->flags & ~kFlagsAll) return fail(VCT_ERR_INVALID_ARG, "params: unknown flags 0x%x", P->flags);
   if ((P->flags & VCT_FLAG_SHADE_IMPL) && !(P->flags & VCT_FLAG_SHADE))
     return fail(VCT_ERR_INVALID_ARG, "params: VCT_FLAG_SHADE_IMPL needs VCT_FLAG_SHADE");
-  if (backward && (P->flags & kFlagsCone))
-    return fail(VCT_ERR_UNSUPPORTED,
-                "params: the adjoint does not cover the modified cones (flags 0x%x)",
-                P->flags & kFlagsCone);
   if ((P->flags & VCT_FLAG_OCC_SMOOTH) &&
       (!finite(P->shadow_str) || !(P->occ_max_dist > 0.0f) || !finite(P->occ_max_dist)))
     return fail(VCT_ERR_INVALID_ARG, "params: shadow_str must be finite and occ_max_dist > 0");
@@ -684,6 +680,7 @@ vct_status trace_backward_impl(const vct_pyramid *pyr, const vct_view *views,
   auto L = std::make_unique<BwdLaunch>();
   memset(L.get(), 0, sizeof(BwdLaunch));
   fill_common(*params, *L);
+  fill_variants(*params, L->var);
   if ((st = fill_pyr(*pyr, *params, L->pyr)) != VCT_OK) return st;
   uint8_t *ws = static_cast<uint8_t *>(workspace);
   for (int l = 0; l < pyr->levels; ++l) {

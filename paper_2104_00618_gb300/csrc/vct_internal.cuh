@@ -344,12 +344,20 @@ struct BwdLaunch {
   float light[3];
   float normal_offset;
   SpecSetup spec;
+  Variants var;  // the modified cones (Ch. 5.4.4) and compositing variant
   unsigned *queue;
   float *gpyr_lvl[VCT_MAX_LEVELS];  // float32 gradient pyramid levels
   unsigned long long *gfix_lvl[VCT_MAX_LEVELS];  // fixed-point levels (deterministic mode)
   DevPyr pyr;
   BwdView views[kMaxBwdViewsPerLaunch];
 };
+
+// Flags that change the adjoint's march or walk (the shading flags only add
+// an output the adjoint does not differentiate).
+inline bool bwd_has_variants(int flags) {
+  return (flags & (VCT_FLAG_OCC_SMOOTH | VCT_FLAG_SPEC_GRACE | VCT_FLAG_DIFFUSE_FIRST_HIT |
+                   VCT_FLAG_PREMULTIPLIED)) != 0;
+}
 
 // March constants of a cone of full aperture `gamma` (host, FP64).
 inline ConeConst cone_const(double gamma, double beta, double t0_vox,

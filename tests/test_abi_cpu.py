@@ -137,12 +137,12 @@ def test_variant_flag_validation_without_gpu(lib):
             continue
         view = vr if flags & _abi.FLAG_SHADE else v
         assert run(flags, view=view) == _abi.VCT_ERR_WORKSPACE, (flags, lib.vct_last_error())
-    # the adjoint takes the shading flags but not the modified cones
+    # the adjoint takes every flag (validation then stops at the missing gradient grid)
     g = _abi.VctViewGrad()
-    for flags, want in [(_abi.FLAG_OCC_SMOOTH, _abi.VCT_ERR_UNSUPPORTED),
-                        (_abi.FLAG_DIFFUSE_FIRST_HIT, _abi.VCT_ERR_UNSUPPORTED),
-                        (_abi.FLAG_SPEC_GRACE, _abi.VCT_ERR_UNSUPPORTED),
-                        (_abi.FLAG_PREMULTIPLIED, _abi.VCT_ERR_UNSUPPORTED),
+    for flags, want in [(_abi.FLAG_OCC_SMOOTH, _abi.VCT_ERR_INVALID_ARG),
+                        (_abi.FLAG_DIFFUSE_FIRST_HIT, _abi.VCT_ERR_INVALID_ARG),
+                        (_abi.FLAG_SPEC_GRACE, _abi.VCT_ERR_INVALID_ARG),
+                        (_abi.FLAG_PREMULTIPLIED, _abi.VCT_ERR_INVALID_ARG),
                         (_abi.FLAG_SHADE, _abi.VCT_ERR_INVALID_ARG)]:
         prm = vct.make_params(dict(base, flags=flags))
         st = lib.vct_trace_backward(ctypes.byref(p), ctypes.byref(v), ctypes.byref(g), 1,

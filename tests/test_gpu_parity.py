@@ -318,11 +318,10 @@ def test_invalid_arguments_rejected():
     bad = dict(prm, spec_aperture_min=1e-7)
     with pytest.raises(vct.VctError):
         vct.trace([P], [vct.View.from_host(view)], bad)
-    # the adjoint of the modified cones is not built
-    first_hit = vs.variant_params(prm, vct.FLAG_DIFFUSE_FIRST_HIT)
-    with pytest.raises(vct.VctError) as e:
-        vct.trace_backward(P, [vct.View.from_host(view)], [(None, None, None)], first_hit)
-    assert e.value.status == vct._abi.VCT_ERR_UNSUPPORTED
+    # a gradient grid of the wrong shape
+    with pytest.raises(ValueError):
+        vct.trace_backward(P, [vct.View.from_host(view)], [(None, None, None)], prm,
+                           grad_level0=torch.zeros((4, 4, 4, 4), device="cuda"))
 
 
 # ---------------------------------------------------------------------------
