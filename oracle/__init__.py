@@ -119,7 +119,7 @@ def load_library(path: str):
     lib.orc_trace.argtypes = [vp, i32, i32, vp, dbl, vp, vp, vp, i64, vp, vp,
                               vp, vp, vp, vp, vp, vp]
     lib.orc_trace_backward.argtypes = [vp, i32, i32, vp, dbl, vp, vp, vp, i64,
-                                       vp, vp, vp, vp, vp]
+                                       vp, vp, vp, vp, vp, vp]
     lib.orc_voxelize.argtypes = [vp, i64, vp, i64, vp, i32, vp, ctypes.c_float, vp, vp, dbl,
                                  dbl, vp, vp, vp]
     lib.orc_voxelize.restype = None
@@ -369,8 +369,9 @@ def trace(pyr: Pyramid, view: dict, prm: dict, idx=None):
     return out
 
 
-def trace_backward(pyr: Pyramid, view: dict, prm: dict, gD, gS, gV, idx=None):
-    """dL/d(level-0 grid) [n,n,n,4] for upstream gradients of the listed pixels."""
+def trace_backward(pyr: Pyramid, view: dict, prm: dict, gD, gS, gV, idx=None, gL=None):
+    """dL/d(level-0 grid) [n,n,n,4] for upstream gradients of the listed pixels
+    (gL: of the shaded radiance [k,4], with the shading flag)."""
     keep: list = []
     V = _view_struct(view, keep)
     P = params_struct(prm)
@@ -381,12 +382,13 @@ def trace_backward(pyr: Pyramid, view: dict, prm: dict, gD, gS, gV, idx=None):
         count = len(idx_arr)
     gD, gS = _f64(gD).reshape(count, 4), _f64(gS).reshape(count, 4)
     gV = None if gV is None else _f64(gV).reshape(count)
+    gL = None if gL is None else _f64(gL).reshape(count, 4)
     n = pyr.n
     scratch = np.empty(level_offset(n, pyr.levels))
     grad0 = np.zeros(n * n * n * 4)
     _lib().orc_trace_backward(_p(pyr.data), n, pyr.levels, _p(pyr.origin), pyr.size,
                               ctypes.byref(V), ctypes.byref(P), _p(idx_arr), count,
-                              _p(gD), _p(gS), _p(gV), _p(scratch), _p(grad0))
+                              _p(gD), _p(gS), _p(gV), _p(gL), _p(scratch), _p(grad0))
     return grad0.reshape(n, n, n, 4)
 
 

@@ -526,13 +526,15 @@ double orc_spec_grace(const double *w, const orc_params *P) { return spec_grace(
  * (Ch. 4.2.2) replaces the ambient term by the indirect light:
  *   L = albedo (c_d D + c_s S) + Vis direct;
  * L_impl (Ch. 5.4.4): L = o_min D + S + Vis direct (o_min = Vis, one light). */
-static void shade(const orc_view *v, size_t px, const orc_params *P, const double *D,
-                  const double *S, double vis, double *out) {
-  double x[3], n[3], alb[3] = {1.0, 1.0, 1.0};
+/* The direct light of pixel px (Ch. 3.3 Phong listing, one directional
+ * light) and its albedo. */
+static void shade_direct(const orc_view *v, size_t px, const orc_params *P, double direct[3],
+                         double alb[3]) {
+  double x[3], n[3];
   for (int a = 0; a < 3; ++a) {
     x[a] = v->position[3 * px + a];
     n[a] = v->normal[3 * px + a];
-    if (v->albedo) alb[a] = v->albedo[3 * px + a];
+    alb[a] = v->albedo ? v->albedo[3 * px + a] : 1.0;
   }
   const double *l = P->light_dir;
   double nl = n[0] * l[0] + n[1] * l[1] + n[2] * l[2];
@@ -545,14 +547,71 @@ static void shade(const orc_view *v, size_t px, const orc_params *P, const doubl
   double wr = w[0] * R[0] + w[1] * R[1] + w[2] * R[2];
   double diff = nl > 0.0 ? nl : 0.0;
   double gloss = pow(wr > 0.0 ? wr : 0.0, P->shininess);
+  for (int ch = 0; ch < 3; ++ch)
+    direct[ch] = P->light_color[ch] * alb[ch] * (P->diffuse_str * diff + P->specular_str * gloss);
+}
+
+static void shade(const orc_view *v, size_t px, const orc_params *P, const double *D,
+                  const double *S, double vis, double *out) {
+  double direct[3], alb[3];
+  shade_direct(v, px, P, direct, alb);
   for (int ch = 0; ch < 3; ++ch) {
-    double direct = P->light_color[ch] * alb[ch] * (P->diffuse_str * diff + P->specular_str * gloss);
     if (P->flags & ORC_SHADE_IMPL)
-      out[ch] = vis * D[ch] + S[ch] + vis * direct;
+      out[ch] = vis * D[ch] + S[ch] + vis * direct[ch];
     else
-      out[ch] = alb[ch] * (P->diffuse_str * D[ch] + P->specular_str * S[ch]) + vis * direct;
+      out[ch] = alb[ch] * (P->diffuse_str * D[ch] + P->specular_str * S[ch]) + vis * direct[ch];
   }
   out[3] = 1.0;
+}
+
+/* Partial derivatives of shade()'s L_ch with respect to D_ch, S_ch and Vis
+ * (L_ch depends on no other channel; L.a is the constant 1). */
+static void shade_partials(const orc_view *v, size_t px, const orc_params *P, const double *D,
+                           double vis, double dD[3], double dS[3], double dV[3]) {
+  double direct[3], alb[3];
+  shade_direct(v, px, P, direct, alb);
+  for (int ch = 0; ch < 3; ++ch) {
+    if (P->flags & ORC_SHADE_IMPL) {
+      dD[ch] = vis;
+      dS[ch] = 1.0;
+      dV[ch] = D[ch] + direct[ch];
+    } else {
+      dD[ch] = alb[ch] * P->diffuse_str;
+      dS[ch] = alb[ch] * P->specular_str;
+      dV[ch] = direct[ch];
+    }
+  }
+}
+
+/* D, S (RGBA) and Vis of one pixel; the per-kind step and cone counts and
+ * the margins accumulate into st, cn, mg, hm when those are non-NULL. */
+static void pixel_outputs(const orc_grid *g, const orc_view *v, size_t px, const orc_params *P,
+                          double *d, double *s, double *vis, int64_t *st, int64_t *cn,
+                          double *mg, double *hm) {
+  d[0] = d[1] = d[2] = d[3] = 0.0;
+  s[0] = s[1] = s[2] = s[3] = 0.0;
+  *vis = 1.0;
+  orc_coneset cs;
+  cone_set(g, v, px, P, &cs);
+  for (int c = 0; c < cs.count; ++c) {
+    orc_cone_result r;
+    march_kind(g, cs.apex, cs.dir[c], cs.aperture[c], P, cs.kind[c], &r, NULL, 0);
+    if (st) st[cs.kind[c]] += r.steps;
+    if (cn) cn[cs.kind[c]] += 1;
+    if (mg && r.margin < *mg) *mg = r.margin;
+    if (hm && r.hit_margin < *hm) *hm = r.hit_margin;
+    if (cs.kind[c] == 0) {
+      for (int ch = 0; ch < 3; ++ch) d[ch] += cs.weight[c] * r.c[ch];
+      d[3] += cs.weight[c] * r.alpha;
+    } else if (cs.kind[c] == 1) {
+      double f = 1.0;
+      if (P->flags & ORC_SPEC_GRACE) f = spec_grace(cs.dir[c], P);
+      for (int ch = 0; ch < 3; ++ch) s[ch] = f * r.c[ch];
+      s[3] = r.alpha;
+    } else {
+      *vis = 1.0 - r.alpha;
+    }
+  }
 }
 
 void orc_trace(const double *pyr, int n, int levels, const double *origin,
@@ -576,27 +635,7 @@ void orc_trace(const double *pyr, int n, int levels, const double *origin,
       Vis[i] = 1.0;
       if (L) L[4 * i] = L[4 * i + 1] = L[4 * i + 2] = L[4 * i + 3] = 0.0;
       if (v->mask && !v->mask[px]) continue;
-      orc_coneset cs;
-      cone_set(&g, v, px, P, &cs);
-      for (int c = 0; c < cs.count; ++c) {
-        orc_cone_result r;
-        march_kind(&g, cs.apex, cs.dir[c], cs.aperture[c], P, cs.kind[c], &r, NULL, 0);
-        lst[cs.kind[c]] += r.steps;
-        lcn[cs.kind[c]] += 1;
-        if (r.margin < lmg) lmg = r.margin;
-        if (r.hit_margin < lhm) lhm = r.hit_margin;
-        if (cs.kind[c] == 0) {
-          for (int ch = 0; ch < 3; ++ch) d[ch] += cs.weight[c] * r.c[ch];
-          d[3] += cs.weight[c] * r.alpha;
-        } else if (cs.kind[c] == 1) {
-          double f = 1.0;
-          if (P->flags & ORC_SPEC_GRACE) f = spec_grace(cs.dir[c], P);
-          for (int ch = 0; ch < 3; ++ch) s[ch] = f * r.c[ch];
-          s[3] = r.alpha;
-        } else {
-          Vis[i] = 1.0 - r.alpha;
-        }
-      }
+      pixel_outputs(&g, v, px, P, d, s, &Vis[i], lst, lcn, &lmg, &lhm);
       if (L && (P->flags & ORC_SHADE)) shade(v, px, P, d, s, Vis[i], L + 4 * i);
     }
 #pragma omp critical
@@ -699,7 +738,7 @@ void orc_trace_backward(const double *pyr, int n, int levels,
                         const double *origin, double size, const orc_view *v,
                         const orc_params *P, const int64_t *idx, int64_t count,
                         const double *gD, const double *gS, const double *gV,
-                        double *gpyr, double *grad0) {
+                        const double *gL, double *gpyr, double *grad0) {
   orc_grid g = {pyr, n, levels, {origin[0], origin[1], origin[2]}, size};
   memset(gpyr, 0, orc_level_offset(n, levels) * sizeof(double));
 #pragma omp parallel
@@ -710,6 +749,23 @@ void orc_trace_backward(const double *pyr, int n, int levels,
     for (int64_t i = 0; i < count; ++i) {
       size_t px = idx ? (size_t)idx[i] : (size_t)i;
       if (v->mask && !v->mask[px]) continue;
+      /* upstream gradients of D, S, Vis, plus those the shaded radiance
+       * passes down (its chain rule through shade()) */
+      double pD[4], pS[4], pV = gV ? gV[i] : 0.0;
+      for (int ch = 0; ch < 4; ++ch) {
+        pD[ch] = gD[4 * i + ch];
+        pS[ch] = gS[4 * i + ch];
+      }
+      if (gL && (P->flags & ORC_SHADE)) {
+        double d[4], s[4], vis, dD[3], dS[3], dV[3];
+        pixel_outputs(&g, v, px, P, d, s, &vis, NULL, NULL, NULL, NULL);
+        shade_partials(v, px, P, d, vis, dD, dS, dV);
+        for (int ch = 0; ch < 3; ++ch) {
+          pD[ch] += gL[4 * i + ch] * dD[ch];
+          pS[ch] += gL[4 * i + ch] * dS[ch];
+          pV += gL[4 * i + ch] * dV[ch];
+        }
+      }
       orc_coneset cs;
       cone_set(&g, v, px, P, &cs);
       for (int c = 0; c < cs.count; ++c) {
@@ -722,15 +778,15 @@ void orc_trace_backward(const double *pyr, int n, int levels,
         }
         double gc[3] = {0.0, 0.0, 0.0}, ga = 0.0;
         if (cs.kind[c] == 0) {
-          for (int ch = 0; ch < 3; ++ch) gc[ch] = cs.weight[c] * gD[4 * i + ch];
-          ga = cs.weight[c] * gD[4 * i + 3];
+          for (int ch = 0; ch < 3; ++ch) gc[ch] = cs.weight[c] * pD[ch];
+          ga = cs.weight[c] * pD[3];
         } else if (cs.kind[c] == 1) {
           /* the angular-grace factor scales the specular colour only */
           double f = (P->flags & ORC_SPEC_GRACE) ? spec_grace(cs.dir[c], P) : 1.0;
-          for (int ch = 0; ch < 3; ++ch) gc[ch] = f * gS[4 * i + ch];
-          ga = gS[4 * i + 3];
+          for (int ch = 0; ch < 3; ++ch) gc[ch] = f * pS[ch];
+          ga = pS[3];
         } else {
-          ga = gV ? -gV[i] : 0.0;
+          ga = -pV;
         }
         const int first_hit = cs.kind[c] == 0 && (P->flags & ORC_DIFF_FIRST);
         cone_adjoint(&g, gpyr, rec, &r, first_hit, (P->flags & ORC_PREMUL) != 0, gc, ga);

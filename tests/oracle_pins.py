@@ -519,6 +519,40 @@ def check_gradient_fd_modified_cones():
             assert not np.any(only_d[..., 3]) and np.abs(only_d[..., :3]).max() > 0
 
 
+def check_gradient_fd_shading():
+    """Central differences of a loss on the shaded radiance (L_vxct and
+    L_impl, Ch. 4.2.2 / Ch. 5.4.4) against the adjoint given dL/dL: the
+    chain rule through the shading epilogue (linear in D and S, bilinear in
+    Vis and D for L_impl) into the cones."""
+    import vct_synth as vs
+    eps = 1e-4
+    for flags in (8, 8 | 16, 8 | 1 | 2):
+        g, view, prm, _ = _small_diff_problem(seed=33)
+        view = dict(view, albedo=np.random.default_rng(3).uniform(0.2, 1.0, (9, 3)))
+        prm = dict(vs.variant_params(prm, flags), occ_max_dist=1.0)
+        tL = np.random.default_rng(4).random((9, 4))
+
+        def loss(grid):
+            r = oracle.trace(oracle.build_mips(grid), view, prm)
+            return 0.5 * np.sum((r["L"][:, :3] - tL[:, :3]) ** 2), r
+
+        L0, r = loss(g)
+        gL = np.zeros((9, 4))
+        gL[:, :3] = r["L"][:, :3] - tL[:, :3]
+        z4, z1 = np.zeros((9, 4)), np.zeros(9)
+        grad = oracle.trace_backward(oracle.build_mips(g), view, prm, z4, z4, z1, gL=gL)
+        rng = np.random.default_rng(flags)
+        big = np.argsort(-np.abs(grad).reshape(-1))[:10]
+        for flat in list(big) + list(rng.integers(0, g.size, 8)):
+            gp, gm = g.copy(), g.copy()
+            gp.reshape(-1)[flat] += eps
+            gm.reshape(-1)[flat] -= eps
+            fd = (loss(gp)[0] - loss(gm)[0]) / (2 * eps)
+            an = grad.reshape(-1)[flat]
+            assert abs(fd - an) <= 1e-6 * max(1e-3, abs(an)), (flags, flat, fd, an)
+        assert np.abs(grad).max() > 1e-3, flags
+
+
 # --------------------------------------------------------------------------
 # the thesis's modified cones (Ch. 5.4.4) and the shading epilogue
 # --------------------------------------------------------------------------

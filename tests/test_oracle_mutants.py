@@ -53,6 +53,11 @@ MUTANTS = {
     "first-hit gradient to the first sample": (
         "if (r->hit) scatter_sample(g, gpyr, rec + r->steps - 1, gc, 0.0);",
         "if (r->hit) scatter_sample(g, gpyr, rec, gc, 0.0);"),
+    "L_impl: dL/dD without Vis": ("dD[ch] = vis;", "dD[ch] = 1.0;"),
+    "L_impl: dL/dVis without D": ("dV[ch] = D[ch] + direct[ch];", "dV[ch] = direct[ch];"),
+    "L_vxct: direct light not occluded in the adjoint": ("dV[ch] = direct[ch];", "dV[ch] = 0.0;"),
+    "L_vxct: specular ratio dropped in the adjoint": ("dS[ch] = alb[ch] * P->specular_str;",
+                                                      "dS[ch] = alb[ch];"),
     "grace factor left out of the adjoint": (
         "double f = (P->flags & ORC_SPEC_GRACE) ? spec_grace(cs.dir[c], P) : 1.0;",
         "double f = 1.0;"),
@@ -67,8 +72,8 @@ MUTANTS = {
     "light reflected the wrong way": ("R[a] = -l[a] + 2.0 * nl * n[a];",
                                       "R[a] = l[a] - 2.0 * nl * n[a];"),
     "direct light not occluded": (
-        "out[ch] = alb[ch] * (P->diffuse_str * D[ch] + P->specular_str * S[ch]) + vis * direct;",
-        "out[ch] = alb[ch] * (P->diffuse_str * D[ch] + P->specular_str * S[ch]) + direct;"),
+        "out[ch] = alb[ch] * (P->diffuse_str * D[ch] + P->specular_str * S[ch]) + vis * direct[ch];",
+        "out[ch] = alb[ch] * (P->diffuse_str * D[ch] + P->specular_str * S[ch]) + direct[ch];"),
     "top-left rule inverted": ("return ev < 0 || (ev == 0 && eu < 0);",
                                "return ev > 0 || (ev == 0 && eu > 0);"),
     "centre at the pixel corner": ("int64_t p[2] = {SUB * i + SUB / 2, SUB * j + SUB / 2};",
