@@ -336,6 +336,12 @@ typedef struct {
   const float *grad_diffuse;    /* [H*W*4] dL/dD, or NULL (zero)             */
   const float *grad_specular;   /* [H*W*4] dL/dS, or NULL (zero)             */
   const float *grad_visibility; /* [H*W]   dL/dVis, or NULL (zero)           */
+  /* [H*W*4] dL/d(shaded radiance), or NULL: with VCT_FLAG_SHADE the adjoint
+   * passes it down to D, S and Vis through the shading epilogue (L.a is the
+   * constant 1 and takes no gradient).  With VCT_FLAG_SHADE_IMPL, where L
+   * depends on Vis * D, the view's out_diffuse (and out_visibility when the
+   * occlusion cone is on) must hold the forward trace's outputs. */
+  const float *grad_radiance;
 } vct_view_grad;
 
 /* Device workspace bytes vct_trace_backward needs for `pyr` (a float32

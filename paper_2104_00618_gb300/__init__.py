@@ -317,7 +317,8 @@ def trace_backward(pyr: Pyramid, views, grads, params, grad_level0: torch.Tensor
                    cfg: VctLaunchConfig | None = None, workspace: torch.Tensor | None = None,
                    stream=None, deterministic: bool = False) -> torch.Tensor:
     """Accumulates dL/d(level-0 grid) into grad_level0 ([n,n,n,4] float32).
-    grads: per view (grad_D [H*W,4] | None, grad_S | None, grad_Vis [H*W] | None).
+    grads: per view (grad_D [H*W,4] | None, grad_S | None, grad_Vis [H*W] | None
+    [, grad_L [H*W,4] | None]), grad_L the gradient of the shaded radiance.
     deterministic: the reproducible fixed-point accumulation
     (vct_trace_backward_deterministic)."""
     vs = list(views) if isinstance(views, (list, tuple)) else [views]
@@ -336,9 +337,10 @@ def trace_backward(pyr: Pyramid, views, grads, params, grad_level0: torch.Tensor
     keep = []
     garr = (VctViewGrad * len(vs))()
     for i, g in enumerate(grads):
-        gd, gs, gv = (None if t is None else t.contiguous() for t in g)
-        keep.extend(t for t in (gd, gs, gv) if t is not None)
-        garr[i] = VctViewGrad(_ptr(gd), _ptr(gs), _ptr(gv))
+        g = tuple(g) + (None,) * (4 - len(g))
+        gd, gs, gv, gl = (None if t is None else t.contiguous() for t in g)
+        keep.extend(t for t in (gd, gs, gv, gl) if t is not None)
+        garr[i] = VctViewGrad(_ptr(gd), _ptr(gs), _ptr(gv), _ptr(gl))
     fn = lib().vct_trace_backward_deterministic if deterministic else lib().vct_trace_backward
     check(fn(ctypes.byref(p), varr, garr, len(vs), ctypes.byref(P),
              None if cfg is None else ctypes.byref(cfg), _ptr(grad_level0), _ptr(ws), ws.numel(),

@@ -61,7 +61,8 @@ class VctTraceStats(ctypes.Structure):
 
 
 class VctViewGrad(ctypes.Structure):
-    _fields_ = [("grad_diffuse", _vp), ("grad_specular", _vp), ("grad_visibility", _vp)]
+    _fields_ = [("grad_diffuse", _vp), ("grad_specular", _vp), ("grad_visibility", _vp),
+                ("grad_radiance", _vp)]
 
 
 class VctMesh(ctypes.Structure):

@@ -85,32 +85,14 @@ __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const fl
 // L_impl (Ch. 5.4.4): L = Vis D + S + Vis direct.
 __device__ __forceinline__ float4 shade_first(const Variants &v, const DevView &V, int p,
                                               const float4 &D, float vis) {
-  float x[3], n[3], alb[3] = {1.0f, 1.0f, 1.0f};
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    x[a] = V.pos[3 * p + a];
-    n[a] = V.nrm[3 * p + a];
-    if (V.albedo) alb[a] = V.albedo[3 * p + a];
-  }
-  const float *l = v.light_dir;
-  const float nl = n[0] * l[0] + n[1] * l[1] + n[2] * l[2];
-  float R[3], e[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    R[a] = fmaf(2.0f * nl, n[a], -l[a]);
-    e[a] = V.cam[a] - x[a];
-  }
-  const float inv = rsqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
-  const float wr = (e[0] * R[0] + e[1] * R[1] + e[2] * R[2]) * inv;
-  const float lobe = v.kd * fmaxf(nl, 0.0f) + v.ks * powf(fmaxf(wr, 0.0f), v.shininess);
+  float direct[3], alb[3];
+  shade_direct(v, V, p, direct, alb);
   const bool impl = (v.flags & VCT_FLAG_SHADE_IMPL) != 0;
   const float Dc[3] = {D.x, D.y, D.z};
   float o[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float direct = v.light_color[a] * alb[a] * lobe;
-    o[a] = impl ? vis * (Dc[a] + direct) : fmaf(alb[a] * v.kd, Dc[a], vis * direct);
-  }
+  for (int a = 0; a < 3; ++a)
+    o[a] = impl ? vis * (Dc[a] + direct[a]) : fmaf(alb[a] * v.kd, Dc[a], vis * direct[a]);
   return make_float4(o[0], o[1], o[2], 1.0f);
 }
 

@@ -313,6 +313,41 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
         if (BV.gD) gD = reinterpret_cast<const float4 *>(BV.gD)[p];
         if (BV.gS) gS = reinterpret_cast<const float4 *>(BV.gS)[p];
         if (BV.gV) gV = BV.gV[p];
+        if (BV.gL && (L.var.flags & VCT_FLAG_SHADE)) {
+          // chain rule through the shading epilogue: L_ch depends on D_ch,
+          // S_ch and Vis (L_vxct = alb (kd D + ks S) + Vis direct; L_impl =
+          // Vis (D + direct) + S, which needs the forward's D and Vis)
+          const float4 gL = reinterpret_cast<const float4 *>(BV.gL)[p];
+          float direct[3], alb[3];
+          shade_direct(L.var, V, p, direct, alb);
+          const float gl[3] = {gL.x, gL.y, gL.z};
+          float dD[3], dS[3], dV = 0.f;
+          if (L.var.flags & VCT_FLAG_SHADE_IMPL) {
+            const float4 Df = reinterpret_cast<const float4 *>(V.outD)[p];
+            const float vis = (L.occ_enable && V.outV) ? V.outV[p] : 1.0f;
+            const float Dc[3] = {Df.x, Df.y, Df.z};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              dD[a] = gl[a] * vis;
+              dS[a] = gl[a];
+              dV = fmaf(gl[a], Dc[a] + direct[a], dV);
+            }
+          } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              dD[a] = gl[a] * alb[a] * L.var.kd;
+              dS[a] = gl[a] * alb[a] * L.var.ks;
+              dV = fmaf(gl[a], direct[a], dV);
+            }
+          }
+          gD.x += dD[0];
+          gD.y += dD[1];
+          gD.z += dD[2];
+          gS.x += dS[0];
+          gS.y += dS[1];
+          gS.z += dS[2];
+          gV += dV;
+        }
       }
       Apex A;
       make_apex(P, x, n, L.normal_offset, A);

@@ -364,6 +364,33 @@ __device__ __forceinline__ float spec_grace(const Variants &v, const float w[3])
   return powf(1.0f - e * 0.318309886f, v.falloff);
 }
 
+// Direct light of pixel p for the shading epilogue: Phong with one
+// directional light (Ch. 3.3), direct = light_color * albedo * lobe with
+// lobe = kd max(n.l, 0) + ks max(v.R, 0)^shininess; alb receives the albedo.
+__device__ __forceinline__ void shade_direct(const Variants &v, const DevView &V, int p,
+                                             float direct[3], float alb[3]) {
+  float x[3], n[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    x[a] = V.pos[3 * p + a];
+    n[a] = V.nrm[3 * p + a];
+    alb[a] = V.albedo ? V.albedo[3 * p + a] : 1.0f;
+  }
+  const float *l = v.light_dir;
+  const float nl = n[0] * l[0] + n[1] * l[1] + n[2] * l[2];
+  float R[3], e[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R[a] = fmaf(2.0f * nl, n[a], -l[a]);
+    e[a] = V.cam[a] - x[a];
+  }
+  const float inv = rsqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+  const float wr = (e[0] * R[0] + e[1] * R[1] + e[2] * R[2]) * inv;
+  const float lobe = v.kd * fmaxf(nl, 0.0f) + v.ks * powf(fmaxf(wr, 0.0f), v.shininess);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) direct[a] = v.light_color[a] * alb[a] * lobe;
+}
+
 // Fills the Morton spread table (shared memory) of a CTA.
 __device__ __forceinline__ void fill_spread_lut(uint32_t *lut) {
   for (int i = threadIdx.x; i < 1024; i += blockDim.x) lut[i] = spread3((uint32_t)i);

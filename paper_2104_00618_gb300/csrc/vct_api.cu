@@ -664,8 +664,17 @@ vct_status trace_backward_impl(const vct_pyramid *pyr, const vct_view *views,
     const vct_view_grad &g = grads[i];
     if ((g.grad_diffuse && !aligned(g.grad_diffuse, 16)) ||
         (g.grad_specular && !aligned(g.grad_specular, 16)) ||
-        (g.grad_visibility && !aligned(g.grad_visibility, 4)))
+        (g.grad_visibility && !aligned(g.grad_visibility, 4)) ||
+        (g.grad_radiance && !aligned(g.grad_radiance, 16)))
       return fail(VCT_ERR_INVALID_ARG, "view %d: gradients must be 16-byte aligned", i);
+    if (g.grad_radiance && !(params->flags & VCT_FLAG_SHADE))
+      return fail(VCT_ERR_INVALID_ARG, "view %d: grad_radiance needs VCT_FLAG_SHADE", i);
+    // L_impl = Vis (D + direct) + S: its adjoint reads the forward's D and Vis
+    if (g.grad_radiance && (params->flags & VCT_FLAG_SHADE_IMPL) &&
+        (!views[i].out_diffuse || (params->occ_enable && !views[i].out_visibility)))
+      return fail(VCT_ERR_INVALID_ARG,
+                  "view %d: grad_radiance of L_impl needs the forward's out_diffuse and "
+                  "out_visibility", i);
   }
   if (!grad_level0_dense || !aligned(grad_level0_dense, 16))
     return fail(VCT_ERR_INVALID_ARG, "vct_trace_backward: grad_level0 NULL or misaligned");
@@ -708,6 +717,7 @@ vct_status trace_backward_impl(const vct_pyramid *pyr, const vct_view *views,
       L->views[i].gD = grads[v0 + i].grad_diffuse;
       L->views[i].gS = grads[v0 + i].grad_specular;
       L->views[i].gV = grads[v0 + i].grad_visibility;
+      L->views[i].gL = grads[v0 + i].grad_radiance;
     }
     L->n_views = nv;
     L->total_tiles = cursor;

@@ -333,6 +333,7 @@ struct TraceLaunch {
 struct BwdView {
   DevView v;
   const float *gD, *gS, *gV;
+  const float *gL;  // dL/d(shaded radiance), or null
 };
 
 struct BwdLaunch {

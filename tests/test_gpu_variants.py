@@ -231,3 +231,34 @@ def test_variant_adjoint_matches_oracle(flags, lpp):
     if flags & FIRST:  # the first-hit cones add nothing to the opacity channel
         only_d = oracle.trace_backward(O, view, prm, gD, np.zeros_like(gS), np.zeros(npx))
         assert not np.any(only_d[..., 3])
+
+
+@pytest.mark.parametrize("flags", [SHADE, SHADE | IMPL, SHADE | IMPL | OCC | GRACE | PREMUL])
+def test_shading_adjoint_matches_oracle(flags):
+    """dL/d(shaded radiance) passed down through the shading epilogue (L_vxct
+    and L_impl) together with dL/dD, against the FP64 adjoint; L_impl reads
+    the forward's D and Vis from the view's outputs."""
+    scene, view, prm0 = room_case(n=32, width=30, height=20, seed=4)
+    view = with_albedo(view, 9)
+    prm = dict(variant_params(prm0, flags), occ_max_dist=0.5)
+    O = oracle.build_mips(scene["grid"])
+    rng = np.random.default_rng(77)
+    npx = view["width"] * view["height"]
+    gD, gL = rng.normal(size=(npx, 4)), rng.normal(size=(npx, 4))
+    gL[:, 3] = 0.0
+    z4, z1 = np.zeros((npx, 4)), np.zeros(npx)
+    ref = oracle.trace_backward(O, view, prm, gD, z4, z1, gL=gL)
+    P = gpu_pyramid(scene["grid"])
+    v = vct.View.from_host(view, outputs=False)
+    v.alloc_outputs(radiance=True)
+    vct.trace([P], [v], prm)
+    cuda = [torch.from_numpy(a.astype(np.float32)).cuda() for a in (gD, gL)]
+    g = vct.trace_backward(P, [v], [(cuda[0], None, None, cuda[1])], prm).cpu().numpy()
+    scale = np.abs(ref).max()
+    err = np.abs(g.astype(np.float64) - ref)
+    print(f"shading flags {flags}: max abs err / max |grad| = {err.max() / scale:.3g}")
+    assert scale > 0 and err.max() <= 1e-4 * scale
+    assert np.linalg.norm(g - ref) <= 1e-5 * np.linalg.norm(ref)
+    # without the shading flag the radiance gradient is refused
+    with pytest.raises(vct.VctError):
+        vct.trace_backward(P, [v], [(cuda[0], None, None, cuda[1])], prm0)
