@@ -352,30 +352,44 @@ def trace_backward(pyr: Pyramid, views, grads, params, grad_level0: torch.Tensor
 # autograd
 # ---------------------------------------------------------------------------
 class TraceFn(torch.autograd.Function):
-    """(level-0 grid) -> (D, S, Vis) of one view; backward through the cone
-    march and the mip box filter by the hand-written adjoint kernels."""
+    """(level-0 grid) -> (D, S, Vis, L) of one view; backward through the
+    cone march (any variant), the shading epilogue and the mip box filter by
+    the hand-written adjoint kernels.  L is an empty tensor unless the
+    params carry VCT_FLAG_SHADE."""
 
     @staticmethod
-    def forward(ctx, level0, view: View, params, levels, origin, size):
-        pyr = build_mips(level0.detach().contiguous(), levels, "f32", origin, size)
+    def forward(ctx, level0, view: View, params, levels, origin, size, dtype, layout,
+                deterministic):
+        pyr = build_mips(level0.detach().contiguous(), levels, dtype, origin, size,
+                         layout=layout)
         v = dataclasses.replace(view, keep=[])
-        v.alloc_outputs()  # no radiance output: the adjoint covers D, S and Vis
+        shade = bool(params.flags & FLAG_SHADE)
+        v.alloc_outputs(radiance=shade)
         v.alloc_cone_state(params)  # lets the adjoint skip its forward march
         trace(pyr, [v], params)
-        ctx.pyr, ctx.view, ctx.params = pyr, v, params
-        return v.out_diffuse, v.out_specular, v.out_visibility
+        ctx.pyr, ctx.view, ctx.params, ctx.det = pyr, v, params, deterministic
+        L = v.out_radiance if shade else torch.empty(0, device=level0.device)
+        return v.out_diffuse, v.out_specular, v.out_visibility, L
 
     @staticmethod
-    def backward(ctx, gD, gS, gV):
-        grad = trace_backward(ctx.pyr, [ctx.view], [(gD, gS, gV)], ctx.params)
-        return grad, None, None, None, None, None
+    def backward(ctx, gD, gS, gV, gL):
+        gl = gL if (ctx.params.flags & FLAG_SHADE) and gL is not None and gL.numel() else None
+        grad = trace_backward(ctx.pyr, [ctx.view], [(gD, gS, gV, gl)], ctx.params,
+                              deterministic=ctx.det)
+        return grad, None, None, None, None, None, None, None, None
 
 
 def render(level0: torch.Tensor, view: View, params, levels=None, origin=(0.0, 0.0, 0.0),
-           size: float = 1.0):
-    """Differentiable (D, S, Vis) of one view from a level-0 grid."""
+           size: float = 1.0, dtype: str = "f32", layout: str = "dense",
+           deterministic: bool = False):
+    """Differentiable (D, S, Vis) of one view from a level-0 grid, plus the
+    shaded radiance L when the params carry the shading flag.  dtype /
+    layout: the pyramid's storage (the gradient is always float32, dense);
+    deterministic: the reproducible fixed-point adjoint."""
     P = params if isinstance(params, VctTraceParams) else make_params(params)
-    return TraceFn.apply(level0, view, P, levels, origin, size)
+    D, S, V, L = TraceFn.apply(level0, view, P, levels, origin, size, dtype, layout,
+                               deterministic)
+    return (D, S, V, L) if P.flags & FLAG_SHADE else (D, S, V)
 
 
 # ---------------------------------------------------------------------------

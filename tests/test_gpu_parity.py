@@ -294,6 +294,31 @@ def test_autograd_render():
     assert torch.allclose(g.grad, ref, rtol=1e-5, atol=1e-7 * ref.abs().max().item())
 
 
+@pytest.mark.parametrize("dtype,layout,det", [("f32", "dense", True), ("f16", "bricks", False)])
+def test_autograd_render_shaded_variants(dtype, layout, det):
+    """render() with the shading epilogue and the modified cones, FP16 /
+    brick storage and the reproducible adjoint: the autograd gradient of a
+    loss on L and D equals the explicit adjoint call with dL/dL and dL/dD."""
+    gt, views, prm, learn = _diff_case(n=32, W=20, H=12, seed=82)
+    prm = dict(vs.variant_params(prm, vct.FLAG_SHADE | vct.FLAG_OCC_SMOOTH |
+                                 vct.FLAG_SPEC_GRACE), occ_max_dist=0.5)
+    v = vct.View.from_host(views[0])
+    grid = np.asarray(gt["grid"], np.float32)
+    g = torch.from_numpy(grid).cuda().requires_grad_(True)
+    D, S, V, L = vct.render(g, v, prm, dtype=dtype, layout=layout, deterministic=det)
+    loss = L[:, :3].square().sum() + D.square().sum()
+    loss.backward()
+    P = vct.build_mips(torch.from_numpy(grid).cuda(), dtype=dtype, layout=layout)
+    w = vct.View.from_host(views[0], outputs=False)
+    w.alloc_outputs(radiance=True)
+    vct.trace([P], [w], prm)
+    gL = 2 * L.detach()
+    gL[:, 3] = 0
+    ref = vct.trace_backward(P, [w], [(2 * D.detach(), None, None, gL)], prm, deterministic=det)
+    assert ref.abs().max() > 0
+    assert torch.allclose(g.grad, ref, rtol=1e-5, atol=1e-6 * ref.abs().max().item())
+
+
 # ---------------------------------------------------------------------------
 # failure paths
 # ---------------------------------------------------------------------------
