@@ -53,6 +53,7 @@ class OrcParams(ctypes.Structure):
 
 # variant flags (same bit values as the library's, an input convention)
 OCC_SMOOTH, SPEC_GRACE, DIFF_FIRST, SHADE, SHADE_IMPL, PREMUL = 1, 2, 4, 8, 16, 32
+ANISO = 64  # internal: the pyramid is anisotropic (set from Pyramid.aniso)
 
 
 class OrcView(ctypes.Structure):
@@ -110,6 +111,12 @@ def load_library(path: str):
     lib.orc_mip_adjoint.argtypes = [vp, i32, i32, vp]
     lib.orc_sample.argtypes = [vp, i32, i32, vp, dbl, vp, dbl, vp]
     lib.orc_sample_lod.argtypes = [vp, i32, i32, vp, dbl, vp]
+    lib.orc_sample_lod_aniso.argtypes = [vp, i32, i32, vp, dbl, vp, vp]
+    lib.orc_sample_lod_aniso.restype = None
+    lib.orc_aniso_offset.argtypes = [i32, i32, i32]
+    lib.orc_aniso_offset.restype = ctypes.c_size_t
+    lib.orc_build_mips_aniso.argtypes = [vp, i32, i32, vp]
+    lib.orc_build_mips_aniso.restype = None
     lib.orc_trace_cone.argtypes = [vp, i32, i32, vp, dbl, vp, vp, dbl, vp, i32, vp, vp]
     lib.orc_spec_grace.argtypes = [vp, vp]
     lib.orc_spec_grace.restype = dbl
@@ -187,17 +194,23 @@ def num_levels(n: int) -> int:
 
 
 class Pyramid:
-    """Dense FP64 pyramid: ``data`` holds all levels back to back."""
+    """Dense FP64 pyramid: ``data`` holds all levels back to back (with
+    ``aniso``, six directional volumes per level >= 1, see
+    orc_build_mips_aniso)."""
 
     def __init__(self, data: np.ndarray, n: int, levels: int,
-                 origin=(0.0, 0.0, 0.0), size: float = 1.0):
+                 origin=(0.0, 0.0, 0.0), size: float = 1.0, aniso: bool = False):
         self.data, self.n, self.levels = data, n, levels
         self.origin = _f64(origin)
         self.size = float(size)
+        self.aniso = aniso
 
-    def level(self, l: int) -> np.ndarray:
+    def level(self, l: int, direction: int = 0) -> np.ndarray:
+        """Level l ([z,y,x,4]); of an anisotropic pyramid the volume for
+        travel direction 0..5 = +x, -x, +y, -y, +z, -z (level 0 has one)."""
         m = self.n >> l
-        off = level_offset(self.n, l)
+        off = (_lib().orc_aniso_offset(self.n, l, direction) if self.aniso
+               else level_offset(self.n, l))
         return self.data[off:off + m * m * m * 4].reshape(m, m, m, 4)
 
 
@@ -210,6 +223,28 @@ def build_mips(level0: np.ndarray, levels: int | None = None,
     out = np.empty(level_offset(n, levels), dtype=np.float64)
     _lib().orc_build_mips(_p(level0), n, levels, _p(out))
     return Pyramid(out, n, levels, origin, size)
+
+
+def build_mips_aniso(level0: np.ndarray, levels: int | None = None,
+                     origin=(0.0, 0.0, 0.0), size: float = 1.0) -> Pyramid:
+    """Anisotropic pyramid: level 0 isotropic, six directional volumes per
+    coarser level (orc_build_mips_aniso)."""
+    level0 = _f64(level0)
+    n = level0.shape[0]
+    assert level0.shape == (n, n, n, 4)
+    levels = num_levels(n) if levels is None else levels
+    out = np.empty(_lib().orc_aniso_offset(n, levels, 0), dtype=np.float64)
+    _lib().orc_build_mips_aniso(_p(level0), n, levels, _p(out))
+    return Pyramid(out, n, levels, origin, size, aniso=True)
+
+
+def sample_lod_aniso(pyr: Pyramid, q, lam: float, w) -> np.ndarray:
+    """Lookup of an anisotropic pyramid at level lam for travel along w."""
+    out = np.zeros(4)
+    q, w = _f64(q), _f64(w)
+    _lib().orc_sample_lod_aniso(_p(pyr.data), pyr.n, pyr.levels, _p(q), float(lam), _p(w),
+                                _p(out))
+    return out
 
 
 def mip_adjoint(gpyr: np.ndarray, n: int, levels: int) -> np.ndarray:
@@ -258,7 +293,7 @@ def params_struct(prm: dict) -> OrcParams:
     P.t0_voxels = float(prm["t0_voxels"])
     P.normal_offset_voxels = float(prm["normal_offset_voxels"])
     P.t_max = float(prm["t_max"])
-    P.flags = int(prm.get("flags", 0))
+    P.flags = int(prm.get("flags", 0)) & ~ANISO
     P.shadow_str = float(prm.get("shadow_str", 1.0))
     P.occ_max_dist = float(prm.get("occ_max_dist", 1.0))
     P.shininess = float(prm.get("shininess", 32.0))
@@ -275,6 +310,8 @@ def trace_cone(pyr: Pyramid, apex, direction, aperture: float, prm: dict, kind: 
     """One cone; returns (rgba, number of samples).  kind (0 diffuse, 1
     specular, 2 occlusion) selects the variant enabled by prm["flags"]."""
     P = params_struct(prm)
+    if pyr.aniso:
+        P.flags |= ANISO
     out = np.zeros(4)
     steps = np.zeros(1, dtype=np.int64)
     apex, direction = _f64(apex), _f64(direction)
@@ -345,6 +382,8 @@ def trace(pyr: Pyramid, view: dict, prm: dict, idx=None):
     keep: list = []
     V = _view_struct(view, keep)
     P = params_struct(prm)
+    if pyr.aniso:
+        P.flags |= ANISO
     if idx is None:
         count, idx_arr = V.width * V.height, None
     else:
@@ -372,6 +411,8 @@ def trace(pyr: Pyramid, view: dict, prm: dict, idx=None):
 def trace_backward(pyr: Pyramid, view: dict, prm: dict, gD, gS, gV, idx=None, gL=None):
     """dL/d(level-0 grid) [n,n,n,4] for upstream gradients of the listed pixels
     (gL: of the shaded radiance [k,4], with the shading flag)."""
+    if pyr.aniso:
+        raise NotImplementedError("the adjoint of an anisotropic pyramid is not built")
     keep: list = []
     V = _view_struct(view, keep)
     P = params_struct(prm)

@@ -64,6 +64,7 @@
 #define ORC_SHADE 8        /* write the radiance L_vxct                                     */
 #define ORC_SHADE_IMPL 16  /* ... composed as L_impl instead                                */
 #define ORC_PREMUL 32      /* every cone: sample colour premultiplied, c += (1 - alpha) c_s */
+#define ORC_ANISO 64       /* the pyramid is anisotropic (orc_build_mips_aniso)               */
 
 typedef struct {
   int32_t n_diffuse;
@@ -90,6 +91,7 @@ typedef struct {
   const double *data;
   int32_t n, levels;
   double origin[3], size;
+  int aniso; /* levels >= 1 hold six directional volumes (orc_build_mips_aniso) */
 } orc_grid;
 
 /* Per-view G-buffer as the caller holds it (float32 inputs). */
@@ -147,6 +149,72 @@ void orc_build_mips(const double *level0, int n, int levels, double *pyr) {
                 }
             dst[(((size_t)z * np + y) * np + x) * 4 + c] = s / 8.0;
           }
+  }
+}
+
+/* ---------------------------------------------------------------------- */
+/* anisotropic mips (Villegas' anisotropic filtering, Ch. 5.1)             */
+/* ---------------------------------------------------------------------- */
+/*
+ * Level 0 is the isotropic grid.  Every level l >= 1 holds six volumes, one
+ * per direction of travel d = +x, -x, +y, -y, +z, -z (index 2 axis + (sign <
+ * 0)), each dense [z][y][x][4] with n >> l texels per axis, back to back
+ * after level 0.  A texel of volume d at level l+1 is the straight 4-channel
+ * mean (as the isotropic filter) over the four child pairs along axis(d) of
+ * the pair seen along d: front = the child met first when travelling along d,
+ *   alpha = a_f + (1 - a_f) a_b,
+ *   colour = (a_f c_f + (1 - a_f) a_b c_b) / alpha  (0 where alpha = 0).
+ * The children are level 0's texels for l = 0, else volume d of level l.
+ */
+size_t orc_aniso_offset(int n, int level, int dir) {
+  if (level == 0) return 0;
+  size_t off = (size_t)n * n * n * 4;
+  for (int l = 1; l < level; ++l) {
+    size_t m = (size_t)(n >> l);
+    off += 6 * m * m * m * 4;
+  }
+  size_t m = (size_t)(n >> level);
+  return off + (size_t)dir * m * m * m * 4;
+}
+
+void orc_build_mips_aniso(const double *level0, int n, int levels, double *pyr) {
+  memcpy(pyr, level0, (size_t)n * n * n * 4 * sizeof(double));
+  for (int l = 1; l < levels; ++l) {
+    int nc = n >> (l - 1), np = n >> l;
+    for (int d = 0; d < 6; ++d) {
+      const int axis = d / 2, neg = d & 1;
+      const double *src = pyr + orc_aniso_offset(n, l - 1, l == 1 ? 0 : d);
+      double *dst = pyr + orc_aniso_offset(n, l, d);
+#pragma omp parallel for
+      for (int z = 0; z < np; ++z)
+        for (int y = 0; y < np; ++y)
+          for (int x = 0; x < np; ++x) {
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            /* the four pairs: offsets along the two other axes */
+            for (int u = 0; u < 2; ++u)
+              for (int v = 0; v < 2; ++v) {
+                const double *ch[2];
+                for (int k = 0; k < 2; ++k) {
+                  int o[3];
+                  o[axis] = k;
+                  o[(axis + 1) % 3] = u;
+                  o[(axis + 2) % 3] = v;
+                  size_t i = (((size_t)(2 * z + o[2]) * nc + (2 * y + o[1])) * nc +
+                              (2 * x + o[0])) * 4;
+                  ch[k] = src + i;
+                }
+                const double *f = neg ? ch[1] : ch[0], *b = neg ? ch[0] : ch[1];
+                double a = f[3] + (1.0 - f[3]) * b[3];
+                for (int c = 0; c < 3; ++c) {
+                  double pre = f[3] * f[c] + (1.0 - f[3]) * b[3] * b[c];
+                  acc[c] += a > 0.0 ? pre / a : 0.0;
+                }
+                acc[3] += a;
+              }
+            double *t = dst + (((size_t)z * np + y) * np + x) * 4;
+            for (int c = 0; c < 4; ++c) t[c] = acc[c] / 4.0;
+          }
+    }
   }
 }
 
@@ -213,23 +281,42 @@ static double corner_weight(const orc_stencil *s, int k, int dx, int dy,
   return s->level_w[k] * wx * wy * wz;
 }
 
-static void apply_stencil(const orc_grid *g, const orc_stencil *s,
+/* Trilinear lookup of stencil level k in the level array lv, times `scale`,
+ * added to out. */
+static void tri_add(const orc_stencil *s, int k, const double *lv, int nl, double scale,
+                    double out[4]) {
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        int x = s->base[k][0] + dx, y = s->base[k][1] + dy, z = s->base[k][2] + dz;
+        if (x < 0 || y < 0 || z < 0 || x >= nl || y >= nl || z >= nl)
+          continue; /* outside the grid: empty */
+        double w = scale * corner_weight(s, k, dx, dy, dz);
+        const double *v = lv + (((size_t)z * nl + y) * nl + x) * 4;
+        for (int c = 0; c < 4; ++c) out[c] += w * v[c];
+      }
+}
+
+/* The quadrilinear sample of the stencil.  In an anisotropic pyramid a level
+ * l >= 1 is read from the three volumes facing the direction of travel w,
+ * weighted by w_a^2 / |w|^2 (the volume of the sign of w_a along axis a). */
+static void apply_stencil(const orc_grid *g, const orc_stencil *s, const double *w,
                           double out[4]) {
   out[0] = out[1] = out[2] = out[3] = 0.0;
   for (int k = 0; k < 2; ++k) {
     int nl = g->n >> s->level[k];
-    const double *lv = g->data + orc_level_offset(g->n, s->level[k]);
-    for (int dz = 0; dz < 2; ++dz)
-      for (int dy = 0; dy < 2; ++dy)
-        for (int dx = 0; dx < 2; ++dx) {
-          int x = s->base[k][0] + dx, y = s->base[k][1] + dy,
-              z = s->base[k][2] + dz;
-          if (x < 0 || y < 0 || z < 0 || x >= nl || y >= nl || z >= nl)
-            continue; /* outside the grid: empty */
-          double w = corner_weight(s, k, dx, dy, dz);
-          const double *v = lv + (((size_t)z * nl + y) * nl + x) * 4;
-          for (int c = 0; c < 4; ++c) out[c] += w * v[c];
-        }
+    if (g->aniso && s->level[k] >= 1) {
+      double w2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+      for (int a = 0; a < 3; ++a) {
+        double wa = w[a] * w[a] / w2;
+        if (wa == 0.0) continue;
+        int d = 2 * a + (w[a] < 0.0 ? 1 : 0);
+        tri_add(s, k, g->data + orc_aniso_offset(g->n, s->level[k], d), nl, wa, out);
+      }
+    } else {
+      const double *lv = g->data + (g->aniso ? 0 : orc_level_offset(g->n, s->level[k]));
+      tri_add(s, k, lv, nl, 1.0, out);
+    }
   }
 }
 
@@ -246,7 +333,7 @@ void orc_sample(const double *pyr, int n, int levels, const double *origin,
   double h0 = size / n;
   orc_stencil s;
   stencil(n, levels, q, log2(diameter / h0), &s);
-  apply_stencil(&g, &s, out);
+  apply_stencil(&g, &s, NULL, out);
 }
 
 /* Lookup at an explicit level (for tests of the filter itself). */
@@ -255,7 +342,16 @@ void orc_sample_lod(const double *pyr, int n, int levels, const double *q,
   orc_grid g = {pyr, n, levels, {0.0, 0.0, 0.0}, 1.0};
   orc_stencil s;
   stencil(n, levels, q, lambda, &s);
-  apply_stencil(&g, &s, out);
+  apply_stencil(&g, &s, NULL, out);
+}
+
+/* Lookup at an explicit level of an anisotropic pyramid for travel along w. */
+void orc_sample_lod_aniso(const double *pyr, int n, int levels, const double *q,
+                          double lambda, const double *w, double *out) {
+  orc_grid g = {pyr, n, levels, {0.0, 0.0, 0.0}, 1.0, 1};
+  orc_stencil s;
+  stencil(n, levels, q, lambda, &s);
+  apply_stencil(&g, &s, w, out);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -291,12 +387,6 @@ static void march_kind(const orc_grid *g, const double o[3], const double w[3],
                        double aperture, const orc_params *P, int kind,
                        orc_cone_result *res, orc_step *rec, int64_t cap);
 
-static void march(const orc_grid *g, const double o[3], const double w[3],
-                  double aperture, const orc_params *P, orc_cone_result *res,
-                  orc_step *rec, int64_t cap) {
-  march_kind(g, o, w, aperture, P, -1, res, rec, cap);
-}
-
 static void march_kind(const orc_grid *g, const double o[3], const double w[3],
                        double aperture, const orc_params *P, int kind,
                        orc_cone_result *res, orc_step *rec, int64_t cap) {
@@ -321,7 +411,7 @@ static void march_kind(const orc_grid *g, const double o[3], const double w[3],
     orc_stencil st;
     stencil(g->n, g->levels, q, log2(d / h0), &st);
     double v[4];
-    apply_stencil(g, &st, v);
+    apply_stencil(g, &st, w, v);
     if (first_hit) {
       /* Ch. 5.4.4 diffuse cone: the first sample whose opacity exceeds
        * 1/100 ends the trace and its colour is returned. */
@@ -381,7 +471,8 @@ void orc_trace_cone(const double *pyr, int n, int levels, const double *origin,
                     double size, const double *apex, const double *dir,
                     double aperture, const orc_params *P, int kind, double *out_rgba,
                     int64_t *steps) {
-  orc_grid g = {pyr, n, levels, {origin[0], origin[1], origin[2]}, size};
+  orc_grid g = {pyr, n, levels, {origin[0], origin[1], origin[2]}, size,
+                (P->flags & ORC_ANISO) != 0};
   orc_cone_result r;
   march_kind(&g, apex, dir, aperture, P, kind, &r, NULL, 0);
   out_rgba[0] = r.c[0];
@@ -619,7 +710,8 @@ void orc_trace(const double *pyr, int n, int levels, const double *origin,
                const int64_t *idx, int64_t count, double *D, double *S,
                double *Vis, double *L, int64_t *steps, int64_t *cones, double *margin,
                double *hit_margin) {
-  orc_grid g = {pyr, n, levels, {origin[0], origin[1], origin[2]}, size};
+  orc_grid g = {pyr, n, levels, {origin[0], origin[1], origin[2]}, size,
+                (P->flags & ORC_ANISO) != 0};
   int64_t st[3] = {0, 0, 0}, cn[3] = {0, 0, 0};
   double mg = INFINITY, hm = INFINITY;
 #pragma omp parallel

@@ -1071,3 +1071,143 @@ def check_gbuffer_skips_and_frame():
         pass
     else:
         raise AssertionError("camera outside the frame accepted")
+
+
+# --------------------------------------------------------------------------
+# anisotropic mips (Villegas' anisotropic filtering, Ch. 5.1): brute force
+# of the definition, closed forms, the direction-weighted sampler
+# --------------------------------------------------------------------------
+def bf_aniso_levels(level0, levels):
+    """Directional volumes by numpy: for direction d (axis, sign) the mean
+    over the 4 child pairs along the axis of the pair composited in the
+    order of travel (front first), colour stored straight."""
+    out = {0: {d: level0 for d in range(6)}}
+    for l in range(1, levels):
+        out[l] = {}
+        for d in range(6):
+            axis, neg = d // 2, d % 2
+            src = out[l - 1][d]  # [z, y, x, 4]
+            ax = 2 - axis        # array axis of this coordinate
+            lo = np.take(src, np.arange(0, src.shape[ax], 2), axis=ax)
+            hi = np.take(src, np.arange(1, src.shape[ax], 2), axis=ax)
+            f, b = (hi, lo) if neg else (lo, hi)
+            a = f[..., 3:] + (1 - f[..., 3:]) * b[..., 3:]
+            pre = f[..., 3:] * f[..., :3] + (1 - f[..., 3:]) * b[..., 3:] * b[..., :3]
+            c = np.where(a > 0, pre / np.where(a > 0, a, 1), 0.0)
+            comp = np.concatenate([c, a], axis=-1)
+            m = comp.shape
+            # mean over the two remaining axes' pairs
+            sh = list(m)
+            for other in range(3):
+                if other == ax:
+                    continue
+                sh[other] //= 2
+            r = comp
+            for other in range(3):
+                if other == ax:
+                    continue
+                r = 0.5 * (np.take(r, np.arange(0, r.shape[other], 2), axis=other) +
+                           np.take(r, np.arange(1, r.shape[other], 2), axis=other))
+            out[l][d] = r
+    return out
+
+
+def check_aniso_mips_bruteforce():
+    rng = np.random.default_rng(41)
+    for n in (2, 8):
+        g = rng.random((n, n, n, 4))
+        g[rng.random((n, n, n)) < 0.4] = 0.0  # empty voxels, alpha-0 pairs
+        P = oracle.build_mips_aniso(g)
+        bf = bf_aniso_levels(g, P.levels)
+        for l in range(1, P.levels):
+            for d in range(6):
+                assert np.allclose(P.level(l, d), bf[l][d], rtol=1e-12, atol=1e-14), (n, l, d)
+
+
+def check_aniso_constant_closed_form():
+    """A homogeneous medium (c, a): every directional texel of level l has
+    the colour c and the opacity of 2^l voxels in a row, 1 - (1 - a)^(2^l)."""
+    n, a = 16, 0.3
+    c0 = np.array([0.2, 0.5, 0.8])
+    g = np.empty((n, n, n, 4))
+    g[..., :3], g[..., 3] = c0, a
+    P = oracle.build_mips_aniso(g)
+    for l in range(1, P.levels):
+        for d in range(6):
+            v = P.level(l, d)
+            assert np.allclose(v[..., :3], c0, rtol=1e-12), (l, d)
+            assert np.allclose(v[..., 3], 1 - (1 - a) ** (2 ** l), rtol=1e-12), (l, d)
+
+
+def check_aniso_direction_weights():
+    """The sampler reads level >= 1 from the three volumes facing the travel
+    direction, weighted w_a^2 / |w|^2: an axis direction reads one volume
+    (its sign picks +/-), a general one the weighted sum; level 0 is the
+    isotropic grid."""
+    rng = np.random.default_rng(43)
+    n = 8
+    g = rng.random((n, n, n, 4))
+    P = oracle.build_mips_aniso(g)
+    bf = bf_aniso_levels(g, P.levels)
+    iso = oracle.build_mips(g)
+    for _ in range(40):
+        q = rng.uniform(-0.1, 1.1, 3)
+        lam = float(rng.choice([1.0, 2.0, 1.6, 2.3]))
+        l0 = int(np.floor(lam))
+        f = lam - l0
+        l1 = min(l0 + 1, P.levels - 1)
+        w = rng.normal(size=3)
+        got = oracle.sample_lod_aniso(P, q, lam, w)
+        want = np.zeros(4)
+        for lk, lw in ((l0, 1 - f), (l1, f)):
+            for ax in range(3):
+                d = 2 * ax + (1 if w[ax] < 0 else 0)
+                one = oracle.Pyramid(_dense_pyr(bf, d, P.levels), n, P.levels)
+                want += lw * w[ax] ** 2 / (w @ w) * bf_sample(_levels_of(one), q, lk)
+        assert np.allclose(got, want, rtol=1e-10, atol=1e-12), (q, lam, got, want)
+        e = np.zeros(3)
+        e[rng.integers(3)] = rng.choice([-1.0, 1.0])
+        ax = int(np.flatnonzero(e)[0])
+        d = 2 * ax + (1 if e[ax] < 0 else 0)
+        one = oracle.Pyramid(_dense_pyr(bf, d, P.levels), n, P.levels)
+        assert np.allclose(oracle.sample_lod_aniso(P, q, 2.0, e),
+                           bf_sample(_levels_of(one), q, 2.0), rtol=1e-10, atol=1e-12)
+        assert np.allclose(oracle.sample_lod_aniso(P, q, 0.0, w), oracle.sample_lod(iso, q, 0.0))
+
+
+def _dense_pyr(bf, d, levels):
+    return np.concatenate([bf[l][d].reshape(-1) for l in range(levels)])
+
+
+def _levels_of(pyr):
+    return [pyr.level(l) for l in range(pyr.levels)]
+
+
+def check_aniso_homogeneous_march():
+    """A cone through a homogeneous medium of an anisotropic pyramid: each
+    sample's opacity is the level blend of 1 - (1 - a)^(2^l) (the colour
+    stays c), composited front to back: alpha = 1 - prod (1 - a_k)."""
+    n, a = 64, 0.05
+    c0 = np.array([0.3, 0.6, 0.9])
+    g = np.empty((n, n, n, 4))
+    g[..., :3], g[..., 3] = c0, a
+    P = oracle.build_mips_aniso(g)
+    aperture, beta, t_max = math.radians(30), 0.5, 0.25
+    prm = base_params(beta=beta, t_max=t_max)
+    h0 = 1.0 / n
+    w = np.array([2.0, -1.0, 2.0]) / 3.0
+    out, k = oracle.trace_cone(P, [0.5, 0.5, 0.5], w, aperture, prm)
+    t, trans, alpha, K = h0, 1.0, 0.0, 0
+    while alpha < 1 and t <= t_max:
+        d = 2 * t * math.tan(aperture / 2)
+        lam = min(max(math.log2(d / h0), 0.0), P.levels - 1)
+        l0 = math.floor(lam)
+        f = lam - l0
+        l1 = min(l0 + 1, P.levels - 1)
+        a_s = (1 - f) * (1 - (1 - a) ** (2 ** l0)) + f * (1 - (1 - a) ** (2 ** l1))
+        alpha += trans * a_s
+        trans *= 1 - a_s
+        t += beta * d
+        K += 1
+    assert k == K and abs(out[3] - (1 - trans)) < 1e-12, (k, K, out[3], 1 - trans)
+    assert np.allclose(out[:3], c0 * (1 - trans), rtol=1e-12)

@@ -58,6 +58,16 @@ MUTANTS = {
     "L_vxct: direct light not occluded in the adjoint": ("dV[ch] = direct[ch];", "dV[ch] = 0.0;"),
     "L_vxct: specular ratio dropped in the adjoint": ("dS[ch] = alb[ch] * P->specular_str;",
                                                       "dS[ch] = alb[ch];"),
+    "aniso: front and back of a pair swapped": (
+        "const double *f = neg ? ch[1] : ch[0], *b = neg ? ch[0] : ch[1];",
+        "const double *f = neg ? ch[0] : ch[1], *b = neg ? ch[1] : ch[0];"),
+    "aniso: direction weights |w_a| instead of w_a^2": (
+        "double wa = w[a] * w[a] / w2;", "double wa = fabs(w[a]) / sqrt(w2);"),
+    "aniso: the opposite volume": ("int d = 2 * a + (w[a] < 0.0 ? 1 : 0);",
+                                   "int d = 2 * a + (w[a] > 0.0 ? 1 : 0);"),
+    "aniso: coarse levels from the isotropic level 0": (
+        "pyr + orc_aniso_offset(n, l - 1, l == 1 ? 0 : d);", "pyr + orc_aniso_offset(n, l - 1, 0);"),
+    "aniso: premultiplied colour stored": ("acc[c] += a > 0.0 ? pre / a : 0.0;", "acc[c] += pre;"),
     "grace factor left out of the adjoint": (
         "double f = (P->flags & ORC_SPEC_GRACE) ? spec_grace(cs.dir[c], P) : 1.0;",
         "double f = 1.0;"),
