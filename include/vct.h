@@ -96,6 +96,21 @@ typedef enum { VCT_F32 = 0, VCT_F16 = 1 } vct_dtype;
  */
 #define VCT_LAYOUT_DENSE 0
 #define VCT_LAYOUT_BRICKS 1
+/*
+ * VCT_LAYOUT_ANISO (VCT_F32 only): anisotropic mips (Villegas' anisotropic
+ * filtering, Ch. 5.1).  Level 0 is the isotropic grid; every level l >= 1
+ * holds six volumes, one per direction of travel d = +x, -x, +y, -y, +z, -z
+ * (index 2 axis + (sign < 0)), each in the level's Morton order, back to
+ * back at vct_pyramid_level_offset() (volume d at + d * (n >> l)^3 * 16).
+ * A texel of volume d at level l+1 is the straight 4-channel mean over the
+ * four child pairs along axis(d) of the pair seen along d (front = the child
+ * met first): alpha = a_f + (1 - a_f) a_b, colour = (a_f c_f + (1 - a_f)
+ * a_b c_b) / alpha (0 where alpha = 0); the children are level 0's texels
+ * for l = 0, else volume d of level l.  vct_trace samples a level l >= 1
+ * for a cone of axis w as sum_a (w_a^2 / |w|^2) * (volume of axis a facing
+ * the sign of w_a); level 0 as usual.  The adjoint does not cover it.
+ */
+#define VCT_LAYOUT_ANISO 2
 
 typedef struct {
   int32_t n;        /* level-0 voxels per axis: a power of two in [2, 1024]  */
@@ -132,6 +147,10 @@ vct_status vct_pyramid_plan_bricks(const float *level0_dense, int32_t n, int32_t
                                    uint64_t *occupied_out, uint64_t *bytes_out,
                                    vct_stream_t stream);
 
+/* Bytes a VCT_LAYOUT_ANISO pyramid of this shape needs; 0 if the shape is
+ * invalid or dtype is not VCT_F32. */
+size_t vct_pyramid_bytes_aniso(int32_t n, int32_t levels, int32_t dtype);
+
 /* Byte offset of `level` from pyramid.data in the dense layout; 0 if the
  * arguments are invalid (level 0 itself starts at 256). */
 uint64_t vct_pyramid_level_offset(int32_t n, int32_t levels, int32_t dtype,
@@ -162,6 +181,14 @@ vct_status vct_build_mips(const float *level0_dense, const vct_pyramid *pyr,
  */
 vct_status vct_pyramid_read_level(const vct_pyramid *pyr, int32_t level,
                                   float *dense_out, vct_stream_t stream);
+
+/*
+ * Like vct_pyramid_read_level for one directional volume (0..5 = +x, -x,
+ * +y, -y, +z, -z) of level `level` >= 1 of a VCT_LAYOUT_ANISO pyramid;
+ * direction must be 0 for level 0 and for the other layouts.
+ */
+vct_status vct_pyramid_read_volume(const vct_pyramid *pyr, int32_t level, int32_t direction,
+                                   float *dense_out, vct_stream_t stream);
 
 /*
  * Synchronises `stream`, then reads and clears the status word in the

@@ -28,7 +28,7 @@ from ._abi import (FLAG_DIFFUSE_FIRST_HIT, FLAG_OCC_SMOOTH, FLAG_PREMULTIPLIED, 
                    VctPyramid, VctTraceParams, VctTraceStats, VctView, VctViewGrad,
                    VctVoxelizeStats, VctVoxelLight, check, load)
 
-__all__ = ["Pyramid", "build_mips", "read_level", "pyramid_status", "make_params", "trace",
+__all__ = ["Pyramid", "build_mips", "read_level", "read_volume", "pyramid_status", "make_params", "trace",
            "trace_backward", "autotune", "read_stats", "TraceFn", "render", "VctError",
            "launch_config", "num_levels", "lib", "FLAG_OCC_SMOOTH", "FLAG_SPEC_GRACE",
            "FLAG_DIFFUSE_FIRST_HIT", "FLAG_SHADE", "FLAG_SHADE_IMPL", "FLAG_PREMULTIPLIED",
@@ -38,7 +38,8 @@ __all__ = ["Pyramid", "build_mips", "read_level", "pyramid_status", "make_params
            "camera_struct"]
 
 DTYPES = {"f32": VCT_F32, "f16": VCT_F16, VCT_F32: VCT_F32, VCT_F16: VCT_F16}
-LAYOUTS = {"dense": _abi.LAYOUT_DENSE, "bricks": _abi.LAYOUT_BRICKS,
+LAYOUTS = {"dense": _abi.LAYOUT_DENSE, "bricks": _abi.LAYOUT_BRICKS, "aniso": _abi.LAYOUT_ANISO,
+           _abi.LAYOUT_ANISO: _abi.LAYOUT_ANISO,
            _abi.LAYOUT_DENSE: _abi.LAYOUT_DENSE, _abi.LAYOUT_BRICKS: _abi.LAYOUT_BRICKS}
 
 
@@ -69,7 +70,8 @@ def launch_config(tile_w=8, tile_h=8, lanes_per_pixel=1, ctas_per_sm=0) -> VctLa
 class Pyramid:
     """A pyramid in a caller-owned (PyTorch) device buffer.  Dense by default;
     a brick pyramid (layout="bricks") needs the number of occupied bricks it
-    will hold (see plan_bricks)."""
+    will hold (see plan_bricks); layout="aniso" holds six directional
+    volumes per coarse level (float32 only)."""
 
     def __init__(self, n: int, levels: int | None = None, dtype="f32",
                  origin=(0.0, 0.0, 0.0), size: float = 1.0, device=None,
@@ -85,6 +87,8 @@ class Pyramid:
                 raise VctError(_abi.VCT_ERR_INVALID_ARG, "a brick pyramid needs `occupied`")
             nbytes = lib().vct_pyramid_bytes_bricks(self.n, self.levels, self.dtype,
                                                     int(occupied))
+        elif self.layout == _abi.LAYOUT_ANISO:
+            nbytes = lib().vct_pyramid_bytes_aniso(self.n, self.levels, self.dtype)
         else:
             nbytes = lib().vct_pyramid_bytes(self.n, self.levels, self.dtype)
         if nbytes == 0:
@@ -139,7 +143,8 @@ def build_mips(level0: torch.Tensor, levels: int | None = None, dtype="f32",
     if out is None and LAYOUTS[layout] == _abi.LAYOUT_BRICKS:
         occ, _ = plan_bricks(level0, levels, dtype, stream)
         out = Pyramid(n, levels, dtype, origin, size, level0.device, "bricks", occ)
-    pyr = out if out is not None else Pyramid(n, levels, dtype, origin, size, level0.device)
+    pyr = out if out is not None else Pyramid(n, levels, dtype, origin, size, level0.device,
+                                              layout)
     p = pyr.struct()
     check(lib().vct_build_mips(_ptr(level0), ctypes.byref(p), _stream(stream)), "vct_build_mips")
     return pyr
@@ -151,6 +156,17 @@ def read_level(pyr: Pyramid, level: int, stream=None) -> torch.Tensor:
     p = pyr.struct()
     check(lib().vct_pyramid_read_level(ctypes.byref(p), level, _ptr(out), _stream(stream)),
           "vct_pyramid_read_level")
+    return out
+
+
+def read_volume(pyr: Pyramid, level: int, direction: int, stream=None) -> torch.Tensor:
+    """Volume `direction` (0..5 = +x, -x, +y, -y, +z, -z) of level `level` of
+    an anisotropic pyramid as a dense [m,m,m,4] grid (direction 0 otherwise)."""
+    m = pyr.n >> level
+    out = torch.empty((m, m, m, 4), dtype=torch.float32, device=pyr.storage.device)
+    p = pyr.struct()
+    check(lib().vct_pyramid_read_volume(ctypes.byref(p), level, direction, _ptr(out),
+                                        _stream(stream)), "vct_pyramid_read_volume")
     return out
 
 

@@ -15,7 +15,7 @@ MAX_LEVELS = 11
 VCT_OK, VCT_ERR_INVALID_ARG, VCT_ERR_CUDA, VCT_ERR_WORKSPACE, VCT_ERR_UNSUPPORTED, \
     VCT_ERR_TIMEOUT = range(6)
 VCT_F32, VCT_F16 = 0, 1
-LAYOUT_DENSE, LAYOUT_BRICKS = 0, 1
+LAYOUT_DENSE, LAYOUT_BRICKS, LAYOUT_ANISO = 0, 1, 2
 FLAG_OCC_SMOOTH, FLAG_SPEC_GRACE, FLAG_DIFFUSE_FIRST_HIT, FLAG_SHADE, FLAG_SHADE_IMPL, \
     FLAG_PREMULTIPLIED = 1, 2, 4, 8, 16, 32
 
@@ -111,6 +111,8 @@ EXPORTS = {
     "vct_pyramid_bytes": (ctypes.c_size_t, [_c_i32, _c_i32, _c_i32]),
     "vct_pyramid_level_offset": (_c_u64, [_c_i32, _c_i32, _c_i32, _c_i32]),
     "vct_pyramid_bytes_bricks": (ctypes.c_size_t, [_c_i32, _c_i32, _c_i32, _c_u64]),
+    "vct_pyramid_bytes_aniso": (ctypes.c_size_t, [_c_i32, _c_i32, _c_i32]),
+    "vct_pyramid_read_volume": (_c_i32, [ctypes.POINTER(VctPyramid), _c_i32, _c_i32, _vp, _vp]),
     "vct_pyramid_plan_scratch_bytes": (ctypes.c_size_t, [_c_i32, _c_i32, _c_i32]),
     "vct_pyramid_plan_bricks": (_c_i32, [_vp, _c_i32, _c_i32, _c_i32, _vp, ctypes.c_size_t,
                                          ctypes.POINTER(_c_u64), ctypes.POINTER(_c_u64), _vp]),

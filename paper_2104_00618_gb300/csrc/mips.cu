@@ -306,6 +306,64 @@ __global__ void read_level_kernel(const uint8_t *lvl, const uint32_t *tbl, const
   }
 }
 
+// ---------------------------------------------------------------------------
+// anisotropic mips (VCT_LAYOUT_ANISO, float32)
+// ---------------------------------------------------------------------------
+// Level 0 in Morton order from the dense grid: one thread per texel, reading
+// along the dense rows (coalesced) and writing scattered 16-byte texels.
+__global__ void aniso_level0_kernel(const float4 *__restrict__ dense, float4 *__restrict__ lvl0,
+                                    int n) {
+  const uint64_t total = (uint64_t)n * n * n;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t x = (uint32_t)(i % n), y = (uint32_t)((i / n) % n),
+                   z = (uint32_t)(i / ((uint64_t)n * n));
+    const uint32_t code = morton3(x, y, z);
+    if (in_bounds(code, total, kOobMip)) lvl0[code] = __ldcs(dense + i);
+  }
+}
+
+// The pair (front, back) seen along the direction of travel: front-to-back
+// opacity and the straight colour of the premultiplied composite.
+__device__ __forceinline__ float4 pair_composite(float4 f, float4 b) {
+  const float t = 1.0f - f.w;
+  const float a = fmaf(t, b.w, f.w);
+  const float tb = t * b.w;
+  if (!(a > 0.0f)) return make_float4(0.f, 0.f, 0.f, 0.f);
+  return make_float4(__fdiv_rn(fmaf(f.w, f.x, tb * b.x), a), __fdiv_rn(fmaf(f.w, f.y, tb * b.y), a),
+                     __fdiv_rn(fmaf(f.w, f.z, tb * b.z), a), a);
+}
+
+// Level l (>= 1) of all six directions: one thread per (direction, texel).
+// The 8 children of texel j are j*8 .. j*8+7 of the source volume, child
+// c = dx | dy << 1 | dz << 2; along axis a the pairs are (c, c | 1 << a).
+__global__ void aniso_level_kernel(const float4 *__restrict__ src_level, uint64_t src_texels,
+                                   bool src_iso, float4 *__restrict__ dst_level,
+                                   uint64_t dst_texels) {
+  const uint64_t total = 6 * dst_texels;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const int d = (int)(i / dst_texels);
+    const uint64_t j = i - (uint64_t)d * dst_texels;
+    const int axis = d >> 1, neg = d & 1;
+    const float4 *src = src_level + (src_iso ? 0 : (uint64_t)d * src_texels) + 8 * j;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if ((c >> axis) & 1) continue;
+      const float4 lo = __ldg(src + c), hi = __ldg(src + (c | (1 << axis)));
+      const float4 p = neg ? pair_composite(hi, lo) : pair_composite(lo, hi);
+      acc.x += p.x;
+      acc.y += p.y;
+      acc.z += p.z;
+      acc.w += p.w;
+    }
+    if (in_bounds(j, dst_texels, kOobMip))
+      dst_level[(uint64_t)d * dst_texels + j] = make_float4(acc.x * 0.25f, acc.y * 0.25f,
+                                                            acc.z * 0.25f, acc.w * 0.25f);
+  }
+}
+
 struct AdjArgs {
   const float4 *g[VCT_MAX_LEVELS];
   int n, levels;
@@ -365,6 +423,27 @@ cudaError_t pack_t(const CUtensorMap &map, const PackArgs &a, int blocks, size_t
 }
 
 }  // namespace
+
+cudaError_t launch_build_aniso(const float *level0, const vct_pyramid &pyr, int sms,
+                               cudaStream_t s) {
+  const Layout L = make_layout(pyr.n, pyr.levels, pyr.dtype, pyr.layout);
+  uint8_t *base = static_cast<uint8_t *>(pyr.data);
+  const int n = pyr.n;
+  auto grid_of = [&](uint64_t work) {
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 16));
+  };
+  aniso_level0_kernel<<<grid_of(level_texels(n, 0)), 256, 0, s>>>(
+      reinterpret_cast<const float4 *>(level0), reinterpret_cast<float4 *>(base + L.level_off[0]),
+      n);
+  cudaError_t e = cudaGetLastError();
+  for (int l = 1; l < pyr.levels && e == cudaSuccess; ++l) {
+    aniso_level_kernel<<<grid_of(6 * level_texels(n, l)), 256, 0, s>>>(
+        reinterpret_cast<const float4 *>(base + L.level_off[l - 1]), level_texels(n, l - 1),
+        l == 1, reinterpret_cast<float4 *>(base + L.level_off[l]), level_texels(n, l));
+    e = cudaGetLastError();
+  }
+  return e;
+}
 
 cudaError_t launch_pack_mips(const float *level0, const vct_pyramid &pyr,
                              const CUtensorMap &map, cudaStream_t s) {
@@ -445,10 +524,12 @@ cudaError_t launch_pack_mips(const float *level0, const vct_pyramid &pyr,
   return cudaGetLastError();
 }
 
-cudaError_t launch_read_level(const vct_pyramid &pyr, int level, float *out, cudaStream_t s) {
+cudaError_t launch_read_level(const vct_pyramid &pyr, int level, float *out, cudaStream_t s,
+                              int direction) {
   const Layout L = make_layout(pyr.n, pyr.levels, pyr.dtype, pyr.layout);
   const uint8_t *base = static_cast<const uint8_t *>(pyr.data);
-  const uint8_t *lvl = base + L.level_off[level];
+  const uint8_t *lvl = base + L.level_off[level] +
+                       (uint64_t)direction * level_texels(pyr.n, level) * texel_bytes(pyr.dtype);
   const uint32_t *tbl =
       ((L.bricked >> level) & 1u) ? reinterpret_cast<const uint32_t *>(lvl) : nullptr;
   const uint8_t *pool = base + L.pool_off;

@@ -29,20 +29,26 @@ __device__ __forceinline__ int find_view(const TraceLaunch &L, int item, bool sm
 // is small and T precise when alpha is close to one; the loop runs while
 // alpha = 1 - T < 1 in float32 and t <= t_max.  kVar instances also take the
 // Ch. 5.4.4 variants selected by `mode`.
-template <int DT, bool kVar, bool BR>
+template <int DT, bool kVar, bool BR, bool AN = false>
 __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const float w[3],
                                         const ConeConst &cc, float T0, const uint32_t *lut,
                                         uint32_t &nsamp, float &trans, uint2 &state,
                                         int mode = kPlain, const Variants *var = nullptr) {
   float cr = 0.f, cg = 0.f, cb = 0.f, al = 0.f, tr = 1.f, tp = 1.f;
   int k = 0;
+  AnisoW aw;
+  if constexpr (AN) aw = aniso_weights(w);
   for (; k < cc.kmax; ++k) {
     if (!((1.0f - tr) < 1.0f)) break;
     float T, lam, om;
     step_at(cc, T0, k, T, lam);
     const float F[3] = {fmaf(T, w[0], A.Of[0]), fmaf(T, w[1], A.Of[1]), fmaf(T, w[2], A.Of[2])};
     LodPick lp;
-    float4 s = sample<DT, BR>(P, A, F, lam, lut, om, lp);
+    float4 s;
+    if constexpr (AN)
+      s = sample_aniso(P, A, F, lam, lut, aw, om, lp);
+    else
+      s = sample<DT, BR>(P, A, F, lam, lut, om, lp);
     if constexpr (kVar) {
       if (mode == kFirstHit) {
         if (s.w > 0.01f) {
@@ -157,7 +163,7 @@ __device__ __forceinline__ void warp_sort_desc(uint32_t *keys, int n) {
 // kVar instances add the Ch. 5.4.4 cone variants and the shading epilogue
 // (any VCT_FLAG_* set); the plain instances carry none of that code.  BR
 // instances read brick pyramids (VCT_LAYOUT_BRICKS).
-template <int LPP, int DT, bool kVar, bool BR>
+template <int LPP, int DT, bool kVar, bool BR, bool AN>
 __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(const __grid_constant__ TraceLaunch L) {
   constexpr int kPixPerRound = 32 / LPP;
   constexpr bool kSortSpec = (LPP == 1);
@@ -243,7 +249,7 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
             if (cs.kind == kDiffuse && (L.var.flags & VCT_FLAG_DIFFUSE_FIRST_HIT)) mode = kFirstHit;
           }
           uint2 cst;
-          float4 r = march<DT, kVar, BR>(P, A, w, cc, T0, s_lut, n_samp[cs.kind], trans, cst,
+          float4 r = march<DT, kVar, BR, AN>(P, A, w, cc, T0, s_lut, n_samp[cs.kind], trans, cst,
                                          mode, &L.var);
           n_cone[cs.kind] += 1u;
           if (V.state) V.state[(size_t)c * V.W * V.H + p] = cst;
@@ -332,7 +338,7 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
       const ConeConst cc = spec_const(P, L.spec, V.rough, p);
       float trans;
       uint2 cst;
-      float4 r = march<DT, kVar, BR>(P, A, w, cc, T0, s_lut, n_samp[kSpecular], trans, cst,
+      float4 r = march<DT, kVar, BR, AN>(P, A, w, cc, T0, s_lut, n_samp[kSpecular], trans, cst,
                                      kPlain, &L.var);
       n_cone[kSpecular] += 1u;
       if (V.state) V.state[p] = cst;  // the specular cone is cone 0
@@ -366,17 +372,22 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
   }
 }
 
-template <int LPP, int DT, bool BR>
+template <int LPP, int DT, bool BR, bool AN = false>
 cudaError_t launch_t(const TraceLaunch &L, int grid, cudaStream_t s) {
   if (L.var.flags)
-    trace_kernel<LPP, DT, true, BR><<<grid, kFwdThreads, 0, s>>>(L);
+    trace_kernel<LPP, DT, true, BR, AN><<<grid, kFwdThreads, 0, s>>>(L);
   else
-    trace_kernel<LPP, DT, false, BR><<<grid, kFwdThreads, 0, s>>>(L);
+    trace_kernel<LPP, DT, false, BR, AN><<<grid, kFwdThreads, 0, s>>>(L);
   return cudaGetLastError();
 }
 
+// Anisotropic pyramids are float32 and dense (no brick instance).
 template <int LPP, int DT>
-cudaError_t launch_l(const TraceLaunch &L, bool br, int grid, cudaStream_t s) {
+cudaError_t launch_l(const TraceLaunch &L, bool br, int grid, cudaStream_t s, bool an) {
+  if constexpr (DT == VCT_F32) {
+    if (an) return launch_t<LPP, DT, false, true>(L, grid, s);
+  }
+  if (an) return cudaErrorInvalidValue;
   return br ? launch_t<LPP, DT, true>(L, grid, s) : launch_t<LPP, DT, false>(L, grid, s);
 }
 
@@ -384,10 +395,10 @@ template <int LPP, int DT>
 int occ_t(bool var) {
   int b = 0;
   if (var)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<LPP, DT, true, false>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<LPP, DT, true, false, false>,
                                                   kFwdThreads, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<LPP, DT, false, false>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<LPP, DT, false, false, false>,
                                                   kFwdThreads, 0);
   return b;
 }
@@ -397,14 +408,15 @@ int occ_t(bool var) {
 static_assert(sizeof(TraceLaunch) <= 32000, "trace launch parameters exceed the 32 KB limit");
 
 cudaError_t launch_trace(const TraceLaunch &L, int lpp, int dtype, bool bricks, int grid,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool aniso) {
   const bool h = dtype == VCT_F16;
   const bool b = bricks;
+  const bool a = aniso;
   switch (lpp) {
-    case 1: return h ? launch_l<1, VCT_F16>(L, b, grid, s) : launch_l<1, VCT_F32>(L, b, grid, s);
-    case 2: return h ? launch_l<2, VCT_F16>(L, b, grid, s) : launch_l<2, VCT_F32>(L, b, grid, s);
-    case 4: return h ? launch_l<4, VCT_F16>(L, b, grid, s) : launch_l<4, VCT_F32>(L, b, grid, s);
-    case 8: return h ? launch_l<8, VCT_F16>(L, b, grid, s) : launch_l<8, VCT_F32>(L, b, grid, s);
+    case 1: return h ? launch_l<1, VCT_F16>(L, b, grid, s, a) : launch_l<1, VCT_F32>(L, b, grid, s, a);
+    case 2: return h ? launch_l<2, VCT_F16>(L, b, grid, s, a) : launch_l<2, VCT_F32>(L, b, grid, s, a);
+    case 4: return h ? launch_l<4, VCT_F16>(L, b, grid, s, a) : launch_l<4, VCT_F32>(L, b, grid, s, a);
+    case 8: return h ? launch_l<8, VCT_F16>(L, b, grid, s, a) : launch_l<8, VCT_F32>(L, b, grid, s, a);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -391,6 +391,98 @@ __device__ __forceinline__ void shade_direct(const Variants &v, const DevView &V
   for (int a = 0; a < 3; ++a) direct[a] = v.light_color[a] * alb[a] * lobe;
 }
 
+// ---------------------------------------------------------------------------
+// anisotropic pyramids (VCT_LAYOUT_ANISO, float32)
+// ---------------------------------------------------------------------------
+// A level l >= 1 is read as sum_a wt[a] * (volume vol[a] of level l), wt[a]
+// = w_a^2 / |w|^2 and vol[a] = 2 a + (w_a < 0) for a cone of axis w.
+struct AnisoW {
+  float wt[3];
+  int vol[3];
+};
+__device__ __forceinline__ AnisoW aniso_weights(const float w[3]) {
+  AnisoW r;
+  const float inv = 1.0f / (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    r.wt[a] = w[a] * w[a] * inv;
+    r.vol[a] = 2 * a + (w[a] < 0.0f ? 1 : 0);
+  }
+  return r;
+}
+
+// Trilinear lookup (seven packed lerps) in volume `vol` of level l of an
+// anisotropic pyramid; corners outside the grid read as zero.
+__device__ __forceinline__ void trilerp_vol(const DevPyr &P, int l, int vol, const LevelStencil &s,
+                                            f32x2 &rg, f32x2 &ba) {
+  const uint64_t texels = level_texels(P.n, l);
+  const float4 *base = reinterpret_cast<const float4 *>(P.lvl[l]) + (uint64_t)vol * texels;
+  f32x2 c_rg[8], c_ba[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    c_rg[c] = 0ull;
+    c_ba[c] = 0ull;
+    const uint32_t code = corner_index(s, c);
+    if (((s.valid >> c) & 1u) && in_bounds(code, texels, kOobTexel))
+      ld_texel2(base + code, c_rg[c], c_ba[c]);
+  }
+  const f32x2 tx = f2_pack(s.fr[0], s.fr[0]);
+  const f32x2 ty = f2_pack(s.fr[1], s.fr[1]);
+  const f32x2 tz = f2_pack(s.fr[2], s.fr[2]);
+  f32x2 e_rg[4], e_ba[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    e_rg[i] = f2_lerp(c_rg[2 * i], c_rg[2 * i + 1], tx);
+    e_ba[i] = f2_lerp(c_ba[2 * i], c_ba[2 * i + 1], tx);
+  }
+  const f32x2 g0_rg = f2_lerp(e_rg[0], e_rg[1], ty), g1_rg = f2_lerp(e_rg[2], e_rg[3], ty);
+  const f32x2 g0_ba = f2_lerp(e_ba[0], e_ba[1], ty), g1_ba = f2_lerp(e_ba[2], e_ba[3], ty);
+  rg = f2_lerp(g0_rg, g1_rg, tz);
+  ba = f2_lerp(g0_ba, g1_ba, tz);
+}
+
+// One level of an anisotropic pyramid: level 0 is isotropic, a coarser
+// level the direction-weighted sum of three volumes.
+__device__ __forceinline__ void aniso_level(const DevPyr &P, int l, const LevelStencil &s,
+                                            const AnisoW &aw, f32x2 &rg, f32x2 &ba) {
+  if (l == 0) {
+    trilerp_vol(P, 0, 0, s, rg, ba);
+    return;
+  }
+  rg = 0ull;
+  ba = 0ull;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    f32x2 r, b;
+    trilerp_vol(P, l, aw.vol[a], s, r, b);
+    const f32x2 wt = f2_pack(aw.wt[a], aw.wt[a]);
+    rg = f2_fma(wt, r, rg);
+    ba = f2_fma(wt, b, ba);
+  }
+}
+
+// S(p, lambda) of an anisotropic pyramid for travel along the cone axis.
+__device__ __forceinline__ float4 sample_aniso(const DevPyr &P, const Apex &A, const float F[3],
+                                               float lam, const uint32_t *lut, const AnisoW &aw,
+                                               float &om, LodPick &lp) {
+  lp = pick_levels(lam, P.levels);
+  LevelStencil s;
+  f32x2 rg, ba;
+  level_stencil(lp.l0, P.n >> lp.l0, A, F, lut, s);
+  aniso_level(P, lp.l0, s, aw, rg, ba);
+  if (lp.f > 0.0f) {
+    level_stencil(lp.l1, P.n >> lp.l1, A, F, lut, s);
+    f32x2 rg1, ba1;
+    aniso_level(P, lp.l1, s, aw, rg1, ba1);
+    const f32x2 tf = f2_pack(lp.f, lp.f);
+    rg = f2_lerp(rg, rg1, tf);
+    ba = f2_lerp(ba, ba1, tf);
+  }
+  const float2 v0 = f2_unpack(rg), v1 = f2_unpack(ba);
+  om = transparency(v1.y);
+  return make_float4(v0.x, v0.y, v1.x, v1.y);
+}
+
 // Fills the Morton spread table (shared memory) of a CTA.
 __device__ __forceinline__ void fill_spread_lut(uint32_t *lut) {
   for (int i = threadIdx.x; i < 1024; i += blockDim.x) lut[i] = spread3((uint32_t)i);

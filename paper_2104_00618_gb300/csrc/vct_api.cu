@@ -50,9 +50,12 @@ bool shape_ok(int n, int levels, int dtype) {
 vct_status check_pyramid(const vct_pyramid *p, const char *what) {
   if (!p) return fail(VCT_ERR_INVALID_ARG, "%s: NULL pyramid", what);
   if (!shape_ok(p->n, p->levels, p->dtype) ||
-      (p->layout != VCT_LAYOUT_DENSE && p->layout != VCT_LAYOUT_BRICKS))
+      (p->layout != VCT_LAYOUT_DENSE && p->layout != VCT_LAYOUT_BRICKS &&
+       p->layout != VCT_LAYOUT_ANISO))
     return fail(VCT_ERR_INVALID_ARG, "%s: bad pyramid shape n=%d levels=%d dtype=%d", what, p->n,
                 p->levels, p->dtype);
+  if (p->layout == VCT_LAYOUT_ANISO && p->dtype != VCT_F32)
+    return fail(VCT_ERR_UNSUPPORTED, "%s: anisotropic pyramids are VCT_F32 only", what);
   if (!(p->size > 0.0f) || !finite(p->size) || !finite(p->origin[0]) || !finite(p->origin[1]) ||
       !finite(p->origin[2]))
     return fail(VCT_ERR_INVALID_ARG, "%s: bad pyramid origin/size", what);
@@ -401,6 +404,11 @@ size_t vct_pyramid_bytes(int32_t n, int32_t levels, int32_t dtype) {
   return (size_t)make_layout(n, levels, dtype).total;
 }
 
+size_t vct_pyramid_bytes_aniso(int32_t n, int32_t levels, int32_t dtype) {
+  if (!shape_ok(n, levels, dtype) || dtype != VCT_F32) return 0;
+  return (size_t)make_layout(n, levels, dtype, VCT_LAYOUT_ANISO).total;
+}
+
 uint64_t vct_pyramid_level_offset(int32_t n, int32_t levels, int32_t dtype, int32_t level) {
   if (!shape_ok(n, levels, dtype) || level < 0 || level >= levels) return 0;
   return make_layout(n, levels, dtype).level_off[level];
@@ -411,6 +419,11 @@ vct_status vct_build_mips(const float *level0_dense, const vct_pyramid *pyr, vct
   if (st != VCT_OK) return st;
   if (!level0_dense || !aligned(level0_dense, 16))
     return fail(VCT_ERR_INVALID_ARG, "vct_build_mips: level0 NULL or not 16-byte aligned");
+  if (pyr->layout == VCT_LAYOUT_ANISO) {
+    cudaError_t e = launch_build_aniso(level0_dense, *pyr, sm_count(), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "vct_build_mips (anisotropic) launch");
+    return VCT_OK;
+  }
   auto enc = encode_fn();
   if (!enc) return fail(VCT_ERR_CUDA, "vct_build_mips: cuTensorMapEncodeTiled unavailable");
   const int n = pyr->n, B = pack_block(n);
@@ -439,6 +452,23 @@ vct_status vct_pyramid_read_level(const vct_pyramid *pyr, int32_t level, float *
     return fail(VCT_ERR_INVALID_ARG, "vct_pyramid_read_level: output NULL or misaligned");
   cudaError_t e = launch_read_level(*pyr, level, dense_out, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "vct_pyramid_read_level launch");
+  return VCT_OK;
+}
+
+vct_status vct_pyramid_read_volume(const vct_pyramid *pyr, int32_t level, int32_t direction,
+                                   float *dense_out, vct_stream_t stream) {
+  vct_status st = check_pyramid(pyr, "vct_pyramid_read_volume");
+  if (st != VCT_OK) return st;
+  if (level < 0 || level >= pyr->levels)
+    return fail(VCT_ERR_INVALID_ARG, "vct_pyramid_read_volume: level %d out of range", level);
+  const int dirs = (pyr->layout == VCT_LAYOUT_ANISO && level >= 1) ? 6 : 1;
+  if (direction < 0 || direction >= dirs)
+    return fail(VCT_ERR_INVALID_ARG, "vct_pyramid_read_volume: direction %d out of range",
+                direction);
+  if (!dense_out || !aligned(dense_out, 16))
+    return fail(VCT_ERR_INVALID_ARG, "vct_pyramid_read_volume: output NULL or misaligned");
+  cudaError_t e = launch_read_level(*pyr, level, dense_out, (cudaStream_t)stream, direction);
+  if (e != cudaSuccess) return cuda_fail(e, "vct_pyramid_read_volume launch");
   return VCT_OK;
 }
 
@@ -527,13 +557,17 @@ static vct_status trace_impl(const vct_pyramid *pyrs, int32_t n_pyr, const vct_v
     const int nv = std::min(kMaxViewsPerLaunch, n_views - v0);
     int cursor = 0;
     bool mixed = false, bricks = false;
+    const bool aniso = pyrs[views[v0].pyramid].layout == VCT_LAYOUT_ANISO;
     for (int i = 0; i < nv; ++i) {
       fill_view(views[v0 + i], cfg.tile_w, cfg.tile_h, cursor, L->views[i]);
       mixed |= pyrs[views[v0 + i].pyramid].dtype != pyrs[views[v0].pyramid].dtype;
+      mixed |= (pyrs[views[v0 + i].pyramid].layout == VCT_LAYOUT_ANISO) != aniso;
       bricks |= pyrs[views[v0 + i].pyramid].layout == VCT_LAYOUT_BRICKS;
     }
     if (mixed)
-      return fail(VCT_ERR_UNSUPPORTED, "vct_trace: views of one call must use pyramids of one dtype");
+      return fail(VCT_ERR_UNSUPPORTED,
+                  "vct_trace: views of one call must use pyramids of one dtype, and all or "
+                  "none anisotropic");
     L->n_views = nv;
     const int grid = std::max(1, std::min(cursor, per_sm * sms));
     // about two waves of the launch's warps, in small tiles, at the end
@@ -542,7 +576,7 @@ static vct_status trace_impl(const vct_pyramid *pyrs, int32_t n_pyr, const vct_v
     if (v0 > 0 && (e = cudaMemsetAsync(L->queue, 0, 4, stream)) != cudaSuccess)
       return cuda_fail(e, "vct_trace queue clear");
     e = launch_trace(*L, cfg.lanes_per_pixel, pyrs[views[v0].pyramid].dtype, bricks, grid,
-                     stream);
+                     stream, aniso);
     if (e != cudaSuccess) return cuda_fail(e, "vct_trace launch");
   }
   return VCT_OK;
@@ -656,6 +690,8 @@ vct_status trace_backward_impl(const vct_pyramid *pyr, const vct_view *views,
   using namespace vct;
   vct_status st = check_pyramid(pyr, "vct_trace_backward");
   if (st != VCT_OK) return st;
+  if (pyr->layout == VCT_LAYOUT_ANISO)
+    return fail(VCT_ERR_UNSUPPORTED, "vct_trace_backward: anisotropic pyramids have no adjoint");
   if (!views || !grads || n_views < 1)
     return fail(VCT_ERR_INVALID_ARG, "vct_trace_backward: no views");
   if ((st = check_params(params, true)) != VCT_OK) return st;

@@ -76,6 +76,8 @@ __host__ __device__ inline Layout make_layout(int n, int levels, int dtype,
     if (level_bricked(n, l, layout)) {
       L.bricked |= 1u << l;
       off += align256(level_bricks(n, l) * 4);
+    } else if (layout == VCT_LAYOUT_ANISO && l >= 1) {
+      off += align256(6 * level_texels(n, l) * tb);  // six directional volumes
     } else {
       off += align256(level_texels(n, l) * tb);
     }
@@ -388,7 +390,10 @@ vct_status set_last_error(vct_status st, const char *fmt, ...);
 // Host entry points implemented in the .cu files (internal linkage across TUs).
 cudaError_t launch_pack_mips(const float *level0, const vct_pyramid &pyr,
                              const CUtensorMap &map, cudaStream_t s);
-cudaError_t launch_read_level(const vct_pyramid &pyr, int level, float *out, cudaStream_t s);
+cudaError_t launch_read_level(const vct_pyramid &pyr, int level, float *out, cudaStream_t s,
+                              int direction = 0);
+cudaError_t launch_build_aniso(const float *level0, const vct_pyramid &pyr, int sms,
+                               cudaStream_t s);
 // Brick occupancy of a level-0 grid and the slot tables of every bricked
 // level, written at layout L's table offsets from `base`; the occupied count
 // goes to base + kHeaderCountOff.  More than `capacity` bricks (zero brick
@@ -401,7 +406,7 @@ cudaError_t launch_wait_probe(uint32_t *flag, uint64_t max_ns, cudaStream_t s);
 cudaError_t launch_bounds_probe(uint32_t *buf, uint32_t declared, uint32_t extra,
                                 cudaStream_t s);
 cudaError_t launch_trace(const TraceLaunch &L, int lpp, int dtype, bool bricks, int grid,
-                         cudaStream_t s);
+                         cudaStream_t s, bool aniso = false);
 int trace_occupancy(int lpp, int dtype, bool variants);
 cudaError_t launch_trace_bwd(const BwdLaunch &L, int lpp, int grid, cudaStream_t s);
 // Fixed-point gradient (units of 2^-32) -> float32, `count` values.
