@@ -535,6 +535,29 @@ def extra_bricks(torch, vct, dev, n=512):
     return out
 
 
+def extra_aniso(torch, vct, dev):
+    """The 1080p room frame (FP32) on an anisotropic pyramid (six directional
+    volumes per coarse level, Ch. 5.1) beside the isotropic one: pyramid
+    bytes, mip build and trace time."""
+    cfg = make_workload()
+    scene, hv, prm = cfg["scenes"][0], cfg["views"][0], cfg["params"]
+    level0 = torch.from_numpy(scene["grid"]).to(dev)
+    view = vct.View.from_host(hv, device=dev)
+    params = vct.make_params(prm)
+    ws = torch.zeros(256, dtype=torch.uint8, device=dev)
+    out = {"workload": "room256_1080p_f32_aniso"}
+    for name in ("dense", "aniso"):
+        P = vct.Pyramid(scene["n"], None, "f32", device=dev, layout=name)
+        build_ms = _time(torch, lambda: vct.build_mips(level0, out=P), 10)
+        trace_ms = _time(torch, lambda: vct.trace([P], [view], params, workspace=ws), 10)
+        samples = int(sum(vct.read_stats(ws)["samples"]))
+        out[name] = {"pyramid_bytes": int(P.storage.numel()), "build_ms": build_ms,
+                     "trace_ms": trace_ms, "gsamples_per_s": samples / (trace_ms / 1e3) / 1e9}
+        del P
+    out["bytes_ratio"] = out["aniso"]["pyramid_bytes"] / out["dense"]["pyramid_bytes"]
+    return out
+
+
 def extra_fwd_bwd(torch, vct, dev, n=128, n_views=32, res=512):
     """Learnable 128^3 grid at 0.1, 32 views of 512x512 of a ground-truth box
     scene, L2 loss: forward (mips + trace) and forward + adjoint (trace
@@ -666,6 +689,7 @@ def run_only_extra(args):
 def _register_extras():
     for name, fn in (("fp16_single_view", extra_fp16_single), ("variants", extra_variants),
                      ("revoxelize", extra_revoxelize), ("bricks_512", extra_bricks),
+                     ("aniso", extra_aniso),
                      ("fwd_bwd", extra_fwd_bwd),
                      ("batched_fp16", extra_batched)):
         EXTRAS[name] = fn

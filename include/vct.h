@@ -100,8 +100,12 @@ typedef enum { VCT_F32 = 0, VCT_F16 = 1 } vct_dtype;
  * VCT_LAYOUT_ANISO (VCT_F32 only): anisotropic mips (Villegas' anisotropic
  * filtering, Ch. 5.1).  Level 0 is the isotropic grid; every level l >= 1
  * holds six volumes, one per direction of travel d = +x, -x, +y, -y, +z, -z
- * (index 2 axis + (sign < 0)), each in the level's Morton order, back to
- * back at vct_pyramid_level_offset() (volume d at + d * (n >> l)^3 * 16).
+ * (index 2 axis + (sign < 0)), each in the level's Morton order.  Level 0
+ * starts at byte 256 as in the dense layout; level l >= 1 follows level
+ * l - 1 (each level's size rounded up to 256 bytes) and holds its six
+ * volumes back to back (volume d at + d * (n >> l)^3 * 16).  These offsets
+ * differ from vct_pyramid_level_offset()'s, which is the dense layout's:
+ * read a volume with vct_pyramid_read_volume().
  * A texel of volume d at level l+1 is the straight 4-channel mean over the
  * four child pairs along axis(d) of the pair seen along d (front = the child
  * met first): alpha = a_f + (1 - a_f) a_b, colour = (a_f c_f + (1 - a_f)
@@ -116,7 +120,7 @@ typedef struct {
   int32_t n;        /* level-0 voxels per axis: a power of two in [2, 1024]  */
   int32_t levels;   /* number of levels, 1 .. log2(n) + 1                    */
   int32_t dtype;    /* vct_dtype of the stored texels                        */
-  int32_t layout;   /* VCT_LAYOUT_DENSE or VCT_LAYOUT_BRICKS                  */
+  int32_t layout;   /* VCT_LAYOUT_DENSE, VCT_LAYOUT_BRICKS or VCT_LAYOUT_ANISO */
   float origin[3];  /* scene position of the grid's minimum corner           */
   float size;       /* scene edge length of the grid, > 0                    */
   void *data;       /* device memory, >= vct_pyramid_bytes(n, levels, dtype) */
