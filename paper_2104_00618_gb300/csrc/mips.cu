@@ -334,33 +334,66 @@ __device__ __forceinline__ float4 pair_composite(float4 f, float4 b) {
                      __fdiv_rn(fmaf(f.w, f.z, tb * b.z), a), a);
 }
 
-// Level l (>= 1) of all six directions: one thread per (direction, texel).
-// The 8 children of texel j are j*8 .. j*8+7 of the source volume, child
-// c = dx | dy << 1 | dz << 2; along axis a the pairs are (c, c | 1 << a).
+// Texel of direction d (axis d >> 1, negative travel if d & 1) from its 8
+// children, child c = dx | dy << 1 | dz << 2: the mean over the four pairs
+// (c, c | 1 << axis) along the axis, each composited in the order of travel.
+__device__ __forceinline__ float4 aniso_texel(const float4 ch[8], int d) {
+  const int axis = d >> 1, neg = d & 1;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if ((c >> axis) & 1) continue;
+    const float4 lo = ch[c], hi = ch[c | (1 << axis)];
+    const float4 p = neg ? pair_composite(hi, lo) : pair_composite(lo, hi);
+    acc.x += p.x;
+    acc.y += p.y;
+    acc.z += p.z;
+    acc.w += p.w;
+  }
+  return make_float4(acc.x * 0.25f, acc.y * 0.25f, acc.z * 0.25f, acc.w * 0.25f);
+}
+
+// Levels 0 and 1 in one pass: one thread per level-1 texel j reads its 2x2x2
+// block of the dense grid once, stores it as level-0 texels 8j .. 8j+7 (128
+// contiguous bytes) and writes texel j of all six level-1 volumes.
+__global__ void aniso_level01_kernel(const float4 *__restrict__ dense, float4 *__restrict__ lvl0,
+                                     float4 *__restrict__ lvl1, int n) {
+  const uint32_t m = (uint32_t)n >> 1;
+  const uint64_t texels1 = (uint64_t)m * m * m, texels0 = 8 * texels1;
+  for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < texels1;
+       j += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t x1 = compact3((uint32_t)j), y1 = compact3((uint32_t)(j >> 1)),
+                   z1 = compact3((uint32_t)(j >> 2));
+    float4 ch[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const uint64_t x = 2 * x1 + (c & 1), y = 2 * y1 + ((c >> 1) & 1), z = 2 * z1 + (c >> 2);
+      ch[c] = __ldcs(dense + (z * (uint64_t)n + y) * (uint64_t)n + x);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (in_bounds(8 * j + c, texels0, kOobMip)) lvl0[8 * j + c] = ch[c];
+#pragma unroll
+    for (int d = 0; d < 6; ++d)
+      if (in_bounds(j, texels1, kOobMip)) lvl1[(uint64_t)d * texels1 + j] = aniso_texel(ch, d);
+  }
+}
+
+// Level l >= 2 of all six directions: one thread per (direction, texel); the
+// 8 children of texel j are j*8 .. j*8+7 of the same direction's volume of
+// level l - 1.
 __global__ void aniso_level_kernel(const float4 *__restrict__ src_level, uint64_t src_texels,
-                                   bool src_iso, float4 *__restrict__ dst_level,
-                                   uint64_t dst_texels) {
+                                   float4 *__restrict__ dst_level, uint64_t dst_texels) {
   const uint64_t total = 6 * dst_texels;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const int d = (int)(i / dst_texels);
     const uint64_t j = i - (uint64_t)d * dst_texels;
-    const int axis = d >> 1, neg = d & 1;
-    const float4 *src = src_level + (src_iso ? 0 : (uint64_t)d * src_texels) + 8 * j;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 *src = src_level + (uint64_t)d * src_texels + 8 * j;
+    float4 ch[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      if ((c >> axis) & 1) continue;
-      const float4 lo = __ldg(src + c), hi = __ldg(src + (c | (1 << axis)));
-      const float4 p = neg ? pair_composite(hi, lo) : pair_composite(lo, hi);
-      acc.x += p.x;
-      acc.y += p.y;
-      acc.z += p.z;
-      acc.w += p.w;
-    }
-    if (in_bounds(j, dst_texels, kOobMip))
-      dst_level[(uint64_t)d * dst_texels + j] = make_float4(acc.x * 0.25f, acc.y * 0.25f,
-                                                            acc.z * 0.25f, acc.w * 0.25f);
+    for (int c = 0; c < 8; ++c) ch[c] = __ldg(src + c);
+    if (in_bounds(j, dst_texels, kOobMip)) dst_level[(uint64_t)d * dst_texels + j] = aniso_texel(ch, d);
   }
 }
 
@@ -432,14 +465,20 @@ cudaError_t launch_build_aniso(const float *level0, const vct_pyramid &pyr, int 
   auto grid_of = [&](uint64_t work) {
     return (int)std::max<uint64_t>(1, std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 16));
   };
-  aniso_level0_kernel<<<grid_of(level_texels(n, 0)), 256, 0, s>>>(
+  if (pyr.levels == 1) {
+    aniso_level0_kernel<<<grid_of(level_texels(n, 0)), 256, 0, s>>>(
+        reinterpret_cast<const float4 *>(level0), reinterpret_cast<float4 *>(base + L.level_off[0]),
+        n);
+    return cudaGetLastError();
+  }
+  aniso_level01_kernel<<<grid_of(level_texels(n, 1)), 256, 0, s>>>(
       reinterpret_cast<const float4 *>(level0), reinterpret_cast<float4 *>(base + L.level_off[0]),
-      n);
+      reinterpret_cast<float4 *>(base + L.level_off[1]), n);
   cudaError_t e = cudaGetLastError();
-  for (int l = 1; l < pyr.levels && e == cudaSuccess; ++l) {
+  for (int l = 2; l < pyr.levels && e == cudaSuccess; ++l) {
     aniso_level_kernel<<<grid_of(6 * level_texels(n, l)), 256, 0, s>>>(
         reinterpret_cast<const float4 *>(base + L.level_off[l - 1]), level_texels(n, l - 1),
-        l == 1, reinterpret_cast<float4 *>(base + L.level_off[l]), level_texels(n, l));
+        reinterpret_cast<float4 *>(base + L.level_off[l]), level_texels(n, l));
     e = cudaGetLastError();
   }
   return e;

@@ -395,7 +395,11 @@ __device__ __forceinline__ void shade_direct(const Variants &v, const DevView &V
 // anisotropic pyramids (VCT_LAYOUT_ANISO, float32)
 // ---------------------------------------------------------------------------
 // A level l >= 1 is read as sum_a wt[a] * (volume vol[a] of level l), wt[a]
-// = w_a^2 / |w|^2 and vol[a] = 2 a + (w_a < 0) for a cone of axis w.
+// = w_a^2 / |w|^2 and vol[a] = 2 a + (w_a < 0) for a cone of axis w.  A
+// volume whose weight is below 2^-24 (its share of the unit weight sum is
+// below float32 resolution) is not read: axis-aligned cones, whose other
+// components are float roundings of cos(90 deg) ~ 1e-17, read one volume.
+constexpr float kAnisoSkip = 5.9604645e-08f;  // 2^-24
 struct AnisoW {
   float wt[3];
   int vol[3];
@@ -418,13 +422,26 @@ __device__ __forceinline__ void trilerp_vol(const DevPyr &P, int l, int vol, con
   const uint64_t texels = level_texels(P.n, l);
   const float4 *base = reinterpret_cast<const float4 *>(P.lvl[l]) + (uint64_t)vol * texels;
   f32x2 c_rg[8], c_ba[8];
+  if (s.valid == 0xffu) {  // interior cell: no per-corner test
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    c_rg[c] = 0ull;
-    c_ba[c] = 0ull;
-    const uint32_t code = corner_index(s, c);
-    if (((s.valid >> c) & 1u) && in_bounds(code, texels, kOobTexel))
-      ld_texel2(base + code, c_rg[c], c_ba[c]);
+    for (int c = 0; c < 8; ++c) {
+      const uint32_t code = corner_index(s, c);
+#ifdef VCT_DEBUG_BOUNDS
+      c_rg[c] = 0ull;
+      c_ba[c] = 0ull;
+      if (in_bounds(code, texels, kOobTexel))
+#endif
+        ld_texel2(base + code, c_rg[c], c_ba[c]);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      c_rg[c] = 0ull;
+      c_ba[c] = 0ull;
+      const uint32_t code = corner_index(s, c);
+      if (((s.valid >> c) & 1u) && in_bounds(code, texels, kOobTexel))
+        ld_texel2(base + code, c_rg[c], c_ba[c]);
+    }
   }
   const f32x2 tx = f2_pack(s.fr[0], s.fr[0]);
   const f32x2 ty = f2_pack(s.fr[1], s.fr[1]);
@@ -453,6 +470,7 @@ __device__ __forceinline__ void aniso_level(const DevPyr &P, int l, const LevelS
   ba = 0ull;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
+    if (aw.wt[a] < kAnisoSkip) continue;
     f32x2 r, b;
     trilerp_vol(P, l, aw.vol[a], s, r, b);
     const f32x2 wt = f2_pack(aw.wt[a], aw.wt[a]);

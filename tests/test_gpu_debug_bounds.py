@@ -1,6 +1,7 @@
 """The bounds-checked build (-DVCT_DEBUG_BOUNDS, libvct_debug_bounds.so) on
 small cases: grids of 2 .. 32 voxels per axis with hand-placed single
-voxels, 1 .. 4 pixels on the domain's edges, every entry point and layout.
+voxels, 1 .. 4 pixels on the domain's edges, every entry point and layout
+(dense, bricks, anisotropic).
 No index may leave its array (flag word 0), and the outputs must equal the
 release library's (the checks change no arithmetic).  The probe checks that
 a planted out-of-range index is caught and its write skipped."""
@@ -88,6 +89,21 @@ def run_everything():
                                                           torch.ones_like(v.out_specular),
                                                           torch.ones_like(v.out_visibility))], prm)
                         out[f"bw{n}{count}"] = gl.cpu().numpy()
+        # anisotropic mips: every directional volume, traces under all shapes
+        P = vct.build_mips(level0, layout="aniso")
+        out[f"an{n}lvl0"] = vct.read_level(P, 0).cpu().numpy()
+        for l in range(1, P.levels):
+            for d in range(6):
+                out[f"an{n}lvl{l}d{d}"] = vct.read_volume(P, l, d).cpu().numpy()
+        for count in (1, 4):
+            view = edge_view(n, count, n + count)
+            for shape in SHAPES:
+                v = vct.View.from_host(view)
+                vct.trace([P], [v], prm, cfg=vct.launch_config(*shape))
+                key = f"an{n}{count}{shape}"
+                out[key + "D"] = v.out_diffuse.cpu().numpy()
+                out[key + "S"] = v.out_specular.cpu().numpy()
+                out[key + "V"] = v.out_visibility.cpu().numpy()
     # voxelizer and G-buffer on a few triangles, one crossing the grid border
     mesh = {"vertices": np.array([[-0.2, 0.1, 0.5], [1.2, 0.3, 0.55], [0.4, 1.1, 0.45],
                                   [0.1, 0.1, 0.9], [0.9, 0.1, 0.9], [0.5, 0.9, 0.9]], np.float32),
