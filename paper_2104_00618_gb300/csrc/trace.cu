@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
   const int n_cones = L.n_diffuse + L.spec_enable + L.occ_enable;
   const int first_cone = defer_spec ? 1 : 0;  // the specular cone is cone 0
   const float T0 = L.spec.t0_vox;
-  __shared__ uint32_t s_lut[1024];
+  __shared__ uint32_t s_lut[kSpreadLut];
   __shared__ uint32_t s_keys[kFwdThreads / 32][kMaxSortPixels];
   uint32_t *keys = s_keys[threadIdx.x >> 5];
   fill_spread_lut(s_lut);

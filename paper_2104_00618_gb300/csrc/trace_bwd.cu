@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
       if (l < P.levels) acc += (uint32_t)level_texels(P.n, l);
     }
   }
-  __shared__ uint32_t s_lut[1024];
+  __shared__ uint32_t s_lut[kSpreadLut];
   fill_spread_lut(s_lut);  // (its barrier also covers s_code_off)
 
   for (;;) {

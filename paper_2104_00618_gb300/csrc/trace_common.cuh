@@ -147,7 +147,8 @@ struct LevelStencil {
   uint32_t valid;  // bit c set if corner c = dx | dy<<1 | dz<<2 is inside the level
 };
 
-// lut: spread3 of 0..1023 (shared memory).
+// lut: three tables of 1024 entries (shared memory): spread3(i), spread3(i)
+// << 1 and spread3(i) << 2, the Morton bits of x, y and z already in place.
 __device__ __forceinline__ void level_stencil(int l, int Nl, const Apex &A, const float F[3],
                                               const uint32_t *lut, LevelStencil &s) {
   const float sc = __int_as_float((127 - l) << 23);  // 2^-l
@@ -165,14 +166,14 @@ __device__ __forceinline__ void level_stencil(int l, int Nl, const Apex &A, cons
     b[a] = qi + iv;
   }
   const uint32_t x0 = lut[(uint32_t)b[0] & 1023u];
-  const uint32_t y0 = lut[(uint32_t)b[1] & 1023u];
-  const uint32_t z0 = lut[(uint32_t)b[2] & 1023u];
+  const uint32_t y0 = lut[1024u + ((uint32_t)b[1] & 1023u)];
+  const uint32_t z0 = lut[2048u + ((uint32_t)b[2] & 1023u)];
   s.sx[0] = x0;
   s.sx[1] = spread3_inc(x0);
-  s.sy[0] = y0 << 1;
-  s.sy[1] = spread3_inc(y0) << 1;
-  s.sz[0] = z0 << 2;
-  s.sz[1] = spread3_inc(z0) << 2;
+  s.sy[0] = y0;
+  s.sy[1] = (y0 - (kMortonX << 1)) & (kMortonX << 1);  // spread3_inc in place
+  s.sz[0] = z0;
+  s.sz[1] = (z0 - (kMortonX << 2)) & (kMortonX << 2);
   // Interior cells (the common case) need no per-corner test.
   const uint32_t lim = (uint32_t)Nl - 1u;
   if ((uint32_t)b[0] < lim && (uint32_t)b[1] < lim && (uint32_t)b[2] < lim) {
@@ -501,9 +502,11 @@ __device__ __forceinline__ float4 sample_aniso(const DevPyr &P, const Apex &A, c
   return make_float4(v0.x, v0.y, v1.x, v1.y);
 }
 
-// Fills the Morton spread table (shared memory) of a CTA.
+// Fills the Morton spread tables (shared memory, kSpreadLut entries) of a CTA.
+constexpr int kSpreadLut = 3 * 1024;
 __device__ __forceinline__ void fill_spread_lut(uint32_t *lut) {
-  for (int i = threadIdx.x; i < 1024; i += blockDim.x) lut[i] = spread3((uint32_t)i);
+  for (int i = threadIdx.x; i < kSpreadLut; i += blockDim.x)
+    lut[i] = spread3((uint32_t)i & 1023u) << (i >> 10);
   __syncthreads();
 }
 
