@@ -117,6 +117,8 @@ def load_library(path: str):
     lib.orc_aniso_offset.restype = ctypes.c_size_t
     lib.orc_build_mips_aniso.argtypes = [vp, i32, i32, vp]
     lib.orc_build_mips_aniso.restype = None
+    lib.orc_mip_adjoint_aniso.argtypes = [vp, vp, i32, i32, vp]
+    lib.orc_mip_adjoint_aniso.restype = None
     lib.orc_trace_cone.argtypes = [vp, i32, i32, vp, dbl, vp, vp, dbl, vp, i32, vp, vp]
     lib.orc_spec_grace.argtypes = [vp, vp]
     lib.orc_spec_grace.restype = dbl
@@ -253,6 +255,17 @@ def mip_adjoint(gpyr: np.ndarray, n: int, levels: int) -> np.ndarray:
     out = np.zeros(n * n * n * 4, dtype=np.float64)
     _lib().orc_mip_adjoint(_p(g), n, levels, _p(out))
     return out.reshape(n, n, n, 4)
+
+
+def mip_adjoint_aniso(pyr: Pyramid, gpyr: np.ndarray) -> np.ndarray:
+    """Adjoint of build_mips_aniso at the pyramid pyr: gradients of every
+    texel (pyr's layout) -> level-0 gradient (orc_mip_adjoint_aniso)."""
+    assert pyr.aniso
+    g = _f64(gpyr).copy()
+    assert g.size == pyr.data.size
+    out = np.zeros(pyr.n ** 3 * 4, dtype=np.float64)
+    _lib().orc_mip_adjoint_aniso(_p(pyr.data), _p(g), pyr.n, pyr.levels, _p(out))
+    return out.reshape(pyr.n, pyr.n, pyr.n, 4)
 
 
 def sample(pyr: Pyramid, p, diameter: float) -> np.ndarray:
@@ -411,11 +424,11 @@ def trace(pyr: Pyramid, view: dict, prm: dict, idx=None):
 def trace_backward(pyr: Pyramid, view: dict, prm: dict, gD, gS, gV, idx=None, gL=None):
     """dL/d(level-0 grid) [n,n,n,4] for upstream gradients of the listed pixels
     (gL: of the shaded radiance [k,4], with the shading flag)."""
-    if pyr.aniso:
-        raise NotImplementedError("the adjoint of an anisotropic pyramid is not built")
     keep: list = []
     V = _view_struct(view, keep)
     P = params_struct(prm)
+    if pyr.aniso:
+        P.flags |= ANISO
     if idx is None:
         count, idx_arr = V.width * V.height, None
     else:
@@ -425,7 +438,8 @@ def trace_backward(pyr: Pyramid, view: dict, prm: dict, gD, gS, gV, idx=None, gL
     gV = None if gV is None else _f64(gV).reshape(count)
     gL = None if gL is None else _f64(gL).reshape(count, 4)
     n = pyr.n
-    scratch = np.empty(level_offset(n, pyr.levels))
+    scratch = np.empty(_lib().orc_aniso_offset(n, pyr.levels, 0) if pyr.aniso
+                       else level_offset(n, pyr.levels))
     grad0 = np.zeros(n * n * n * 4)
     _lib().orc_trace_backward(_p(pyr.data), n, pyr.levels, _p(pyr.origin), pyr.size,
                               ctypes.byref(V), ctypes.byref(P), _p(idx_arr), count,

@@ -239,6 +239,75 @@ void orc_mip_adjoint(double *gpyr, int n, int levels, double *grad0) {
   for (size_t i = 0; i < m0; ++i) grad0[i] += gpyr[i];
 }
 
+/*
+ * Adjoint of orc_build_mips_aniso.  gpyr holds dL/d(texel) for every texel of
+ * the anisotropic pyramid pyr (same layout).  Coarse to fine, each texel of
+ * volume d at level l passes its gradient to its 8 children: the texel is
+ * (1/4) sum over the four pairs (f, b) along axis(d), f the child met first,
+ * of P = (C, alpha) with
+ *   alpha = a_f + (1 - a_f) a_b,  C = (a_f c_f + (1 - a_f) a_b c_b) / alpha,
+ * whose partials are
+ *   dC/dc_f = a_f / alpha,  dC/dc_b = (1 - a_f) a_b / alpha,
+ *   dC/da_f = (c_f - a_b c_b - C (1 - a_b)) / alpha,
+ *   dC/da_b = (1 - a_f) (c_b - C) / alpha,
+ *   dalpha/da_f = 1 - a_b,  dalpha/da_b = 1 - a_f.
+ * Where alpha = 0 (both children empty) C is 0 by definition and not
+ * differentiable in the opacities: its colour partials are taken as 0 there.
+ * The children of level 1 are level 0's texels (all six directions add into
+ * them); the level-0 result is ADDED into grad0.
+ */
+void orc_mip_adjoint_aniso(const double *pyr, double *gpyr, int n, int levels, double *grad0) {
+  for (int l = levels - 1; l >= 1; --l) {
+    int nc = n >> (l - 1), np = n >> l;
+    for (int d = 0; d < 6; ++d) {
+      const int axis = d / 2, neg = d & 1, child_vol = l == 1 ? 0 : d;
+      const double *src = pyr + orc_aniso_offset(n, l - 1, child_vol);
+      double *gsrc = gpyr + orc_aniso_offset(n, l - 1, child_vol);
+      const double *gdst = gpyr + orc_aniso_offset(n, l, d);
+#pragma omp parallel for
+      for (int z = 0; z < np; ++z)
+        for (int y = 0; y < np; ++y)
+          for (int x = 0; x < np; ++x) {
+            const double *G = gdst + (((size_t)z * np + y) * np + x) * 4;
+            for (int u = 0; u < 2; ++u)
+              for (int v = 0; v < 2; ++v) {
+                size_t ci[2];
+                for (int k = 0; k < 2; ++k) {
+                  int o[3];
+                  o[axis] = k;
+                  o[(axis + 1) % 3] = u;
+                  o[(axis + 2) % 3] = v;
+                  ci[k] = (((size_t)(2 * z + o[2]) * nc + (2 * y + o[1])) * nc + (2 * x + o[0])) * 4;
+                }
+                const size_t fi = neg ? ci[1] : ci[0], bi = neg ? ci[0] : ci[1];
+                const double *f = src + fi, *b = src + bi;
+                const double af = f[3], ab = b[3];
+                const double alpha = af + (1.0 - af) * ab;
+                double gf[4] = {0.0, 0.0, 0.0, 0.0}, gb[4] = {0.0, 0.0, 0.0, 0.0};
+                gf[3] = G[3] / 4.0 * (1.0 - ab);
+                gb[3] = G[3] / 4.0 * (1.0 - af);
+                if (alpha > 0.0) {
+                  for (int c = 0; c < 3; ++c) {
+                    const double gC = G[c] / 4.0;
+                    const double C = (af * f[c] + (1.0 - af) * ab * b[c]) / alpha;
+                    gf[c] = gC * af / alpha;
+                    gb[c] = gC * (1.0 - af) * ab / alpha;
+                    gf[3] += gC * (f[c] - ab * b[c] - C * (1.0 - ab)) / alpha;
+                    gb[3] += gC * (1.0 - af) * (b[c] - C) / alpha;
+                  }
+                }
+                for (int c = 0; c < 4; ++c) {
+                  gsrc[fi + c] += gf[c];
+                  gsrc[bi + c] += gb[c];
+                }
+              }
+          }
+    }
+  }
+  size_t m0 = (size_t)n * n * n * 4;
+  for (size_t i = 0; i < m0; ++i) grad0[i] += gpyr[i];
+}
+
 /* ---------------------------------------------------------------------- */
 /* sampling (Ch. 4.5 colour supersampler, Ch. 4.3.3 texture filtering)      */
 /* ---------------------------------------------------------------------- */
@@ -300,18 +369,26 @@ static void tri_add(const orc_stencil *s, int k, const double *lv, int nl, doubl
 /* The quadrilinear sample of the stencil.  In an anisotropic pyramid a level
  * l >= 1 is read from the three volumes facing the direction of travel w,
  * weighted by w_a^2 / |w|^2 (the volume of the sign of w_a along axis a). */
+static void aniso_dirs(const double *w, double wa[3], int dir[3]) {
+  double w2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  for (int a = 0; a < 3; ++a) {
+    wa[a] = w[a] * w[a] / w2;
+    dir[a] = 2 * a + (w[a] < 0.0 ? 1 : 0);
+  }
+}
+
 static void apply_stencil(const orc_grid *g, const orc_stencil *s, const double *w,
                           double out[4]) {
   out[0] = out[1] = out[2] = out[3] = 0.0;
   for (int k = 0; k < 2; ++k) {
     int nl = g->n >> s->level[k];
     if (g->aniso && s->level[k] >= 1) {
-      double w2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+      double wa[3];
+      int dir[3];
+      aniso_dirs(w, wa, dir);
       for (int a = 0; a < 3; ++a) {
-        double wa = w[a] * w[a] / w2;
-        if (wa == 0.0) continue;
-        int d = 2 * a + (w[a] < 0.0 ? 1 : 0);
-        tri_add(s, k, g->data + orc_aniso_offset(g->n, s->level[k], d), nl, wa, out);
+        if (wa[a] == 0.0) continue;
+        tri_add(s, k, g->data + orc_aniso_offset(g->n, s->level[k], dir[a]), nl, wa[a], out);
       }
     } else {
       const double *lv = g->data + (g->aniso ? 0 : orc_level_offset(g->n, s->level[k]));
@@ -767,36 +844,53 @@ void orc_trace(const double *pyr, int n, int levels, const double *origin,
  * The step schedule does not depend on the voxel values (only the stopping
  * step does, which is piecewise constant), so these are the derivatives.
  */
-static void scatter_sample(const orc_grid *g, double *gpyr, const orc_step *s,
+static void scatter_level(const orc_stencil *st, int lk, double *lv, int nl, double scale,
+                          const double dc[3], double da) {
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        int x = st->base[lk][0] + dx, y = st->base[lk][1] + dy, z = st->base[lk][2] + dz;
+        if (x < 0 || y < 0 || z < 0 || x >= nl || y >= nl || z >= nl)
+          continue;
+        double w = scale * corner_weight(st, lk, dx, dy, dz);
+        if (w == 0.0) continue;
+        double *t = lv + (((size_t)z * nl + y) * nl + x) * 4;
+        for (int ch = 0; ch < 3; ++ch) {
+#pragma omp atomic
+          t[ch] += w * dc[ch];
+        }
+#pragma omp atomic
+        t[3] += w * da;
+      }
+}
+
+/* The transpose of apply_stencil for one sample of a cone of axis w: the
+ * derivatives reach each texel through its trilinear and level weights (and,
+ * in an anisotropic pyramid, the direction weight of its volume). */
+static void scatter_sample(const orc_grid *g, double *gpyr, const orc_step *s, const double *w,
                            const double dc[3], double da) {
   for (int lk = 0; lk < 2; ++lk) {
-    int nl = g->n >> s->st.level[lk];
-    double *lv = gpyr + orc_level_offset(g->n, s->st.level[lk]);
-    for (int dz = 0; dz < 2; ++dz)
-      for (int dy = 0; dy < 2; ++dy)
-        for (int dx = 0; dx < 2; ++dx) {
-          int x = s->st.base[lk][0] + dx, y = s->st.base[lk][1] + dy,
-              z = s->st.base[lk][2] + dz;
-          if (x < 0 || y < 0 || z < 0 || x >= nl || y >= nl || z >= nl)
-            continue;
-          double w = corner_weight(&s->st, lk, dx, dy, dz);
-          if (w == 0.0) continue;
-          double *t = lv + (((size_t)z * nl + y) * nl + x) * 4;
-          for (int ch = 0; ch < 3; ++ch) {
-#pragma omp atomic
-            t[ch] += w * dc[ch];
-          }
-#pragma omp atomic
-          t[3] += w * da;
-        }
+    int l = s->st.level[lk], nl = g->n >> l;
+    if (g->aniso && l >= 1) {
+      double wa[3];
+      int dir[3];
+      aniso_dirs(w, wa, dir);
+      for (int a = 0; a < 3; ++a) {
+        if (wa[a] == 0.0) continue;
+        scatter_level(&s->st, lk, gpyr + orc_aniso_offset(g->n, l, dir[a]), nl, wa[a], dc, da);
+      }
+    } else {
+      double *lv = gpyr + (g->aniso ? 0 : orc_level_offset(g->n, l));
+      scatter_level(&s->st, lk, lv, nl, 1.0, dc, da);
+    }
   }
 }
 
 static void cone_adjoint(const orc_grid *g, double *gpyr, const orc_step *rec,
-                         const orc_cone_result *r, int first_hit, int premul,
+                         const orc_cone_result *r, const double *w, int first_hit, int premul,
                          const double gc[3], double ga) {
   if (first_hit) {
-    if (r->hit) scatter_sample(g, gpyr, rec + r->steps - 1, gc, 0.0);
+    if (r->hit) scatter_sample(g, gpyr, rec + r->steps - 1, w, gc, 0.0);
     return;
   }
   double R[3] = {0.0, 0.0, 0.0}, Q = 1.0;
@@ -816,23 +910,27 @@ static void cone_adjoint(const orc_grid *g, double *gpyr, const orc_step *rec,
     for (int ch = 0; ch < 3; ++ch)
       R[ch] = (premul ? s->c[ch] : s->a * s->c[ch]) + (1.0 - s->a) * R[ch];
     Q = (1.0 - s->a) * Q;
-    scatter_sample(g, gpyr, s, dc, da * s->sa);
+    scatter_sample(g, gpyr, s, w, dc, da * s->sa);
   }
 }
 
 /*
  * Gradient of L with respect to the level-0 grid, given dL/dD, dL/dS and
  * dL/dVis for the listed pixels (same layout as orc_trace's outputs).
- * gpyr is caller scratch of orc_level_offset(n, levels) doubles (zeroed
- * here); the level-0 gradient is ADDED into grad0 ([n][n][n][4]).
+ * gpyr is caller scratch of orc_level_offset(n, levels) doubles, or of
+ * orc_aniso_offset(n, levels, 0) for an anisotropic pyramid (ORC_ANISO in
+ * P->flags), zeroed here; the level-0 gradient is ADDED into grad0
+ * ([n][n][n][4]).
  */
 void orc_trace_backward(const double *pyr, int n, int levels,
                         const double *origin, double size, const orc_view *v,
                         const orc_params *P, const int64_t *idx, int64_t count,
                         const double *gD, const double *gS, const double *gV,
                         const double *gL, double *gpyr, double *grad0) {
-  orc_grid g = {pyr, n, levels, {origin[0], origin[1], origin[2]}, size};
-  memset(gpyr, 0, orc_level_offset(n, levels) * sizeof(double));
+  orc_grid g = {pyr, n, levels, {origin[0], origin[1], origin[2]}, size,
+                (P->flags & ORC_ANISO) != 0};
+  memset(gpyr, 0, (g.aniso ? orc_aniso_offset(n, levels, 0) : orc_level_offset(n, levels)) *
+                      sizeof(double));
 #pragma omp parallel
   {
     int64_t cap = 4096;
@@ -881,10 +979,14 @@ void orc_trace_backward(const double *pyr, int n, int levels,
           ga = -pV;
         }
         const int first_hit = cs.kind[c] == 0 && (P->flags & ORC_DIFF_FIRST);
-        cone_adjoint(&g, gpyr, rec, &r, first_hit, (P->flags & ORC_PREMUL) != 0, gc, ga);
+        cone_adjoint(&g, gpyr, rec, &r, cs.dir[c], first_hit, (P->flags & ORC_PREMUL) != 0, gc,
+                     ga);
       }
     }
     free(rec);
   }
-  orc_mip_adjoint(gpyr, n, levels, grad0);
+  if (g.aniso)
+    orc_mip_adjoint_aniso(pyr, gpyr, n, levels, grad0);
+  else
+    orc_mip_adjoint(gpyr, n, levels, grad0);
 }

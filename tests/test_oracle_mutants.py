@@ -48,11 +48,11 @@ MUTANTS = {
         "dc[ch] = gc[ch] * s->trans;", "dc[ch] = gc[ch] * s->trans * s->a;"),
     "premultiplied adjoint: opacity term sign": ("da -= gc[ch] * s->trans * R[ch];",
                                                  "da += gc[ch] * s->trans * R[ch];"),
-    "occlusion fade left out of the adjoint": ("scatter_sample(g, gpyr, s, dc, da * s->sa);",
-                                               "scatter_sample(g, gpyr, s, dc, da);"),
+    "occlusion fade left out of the adjoint": ("scatter_sample(g, gpyr, s, w, dc, da * s->sa);",
+                                               "scatter_sample(g, gpyr, s, w, dc, da);"),
     "first-hit gradient to the first sample": (
-        "if (r->hit) scatter_sample(g, gpyr, rec + r->steps - 1, gc, 0.0);",
-        "if (r->hit) scatter_sample(g, gpyr, rec, gc, 0.0);"),
+        "if (r->hit) scatter_sample(g, gpyr, rec + r->steps - 1, w, gc, 0.0);",
+        "if (r->hit) scatter_sample(g, gpyr, rec, w, gc, 0.0);"),
     "L_impl: dL/dD without Vis": ("dD[ch] = vis;", "dD[ch] = 1.0;"),
     "L_impl: dL/dVis without D": ("dV[ch] = D[ch] + direct[ch];", "dV[ch] = direct[ch];"),
     "L_vxct: direct light not occluded in the adjoint": ("dV[ch] = direct[ch];", "dV[ch] = 0.0;"),
@@ -62,12 +62,22 @@ MUTANTS = {
         "const double *f = neg ? ch[1] : ch[0], *b = neg ? ch[0] : ch[1];",
         "const double *f = neg ? ch[0] : ch[1], *b = neg ? ch[1] : ch[0];"),
     "aniso: direction weights |w_a| instead of w_a^2": (
-        "double wa = w[a] * w[a] / w2;", "double wa = fabs(w[a]) / sqrt(w2);"),
-    "aniso: the opposite volume": ("int d = 2 * a + (w[a] < 0.0 ? 1 : 0);",
-                                   "int d = 2 * a + (w[a] > 0.0 ? 1 : 0);"),
+        "wa[a] = w[a] * w[a] / w2;", "wa[a] = fabs(w[a]) / sqrt(w2);"),
+    "aniso: the opposite volume": ("dir[a] = 2 * a + (w[a] < 0.0 ? 1 : 0);",
+                                   "dir[a] = 2 * a + (w[a] > 0.0 ? 1 : 0);"),
     "aniso: coarse levels from the isotropic level 0": (
         "pyr + orc_aniso_offset(n, l - 1, l == 1 ? 0 : d);", "pyr + orc_aniso_offset(n, l - 1, 0);"),
     "aniso: premultiplied colour stored": ("acc[c] += a > 0.0 ? pre / a : 0.0;", "acc[c] += pre;"),
+    "aniso adjoint: opacity partial without (1 - a_b)": ("gf[3] = G[3] / 4.0 * (1.0 - ab);",
+                                                          "gf[3] = G[3] / 4.0;"),
+    "aniso adjoint: back colour partial without a_b": (
+        "gb[c] = gC * (1.0 - af) * ab / alpha;", "gb[c] = gC * (1.0 - af) / alpha;"),
+    "aniso adjoint: front and back swapped": (
+        "const size_t fi = neg ? ci[1] : ci[0], bi = neg ? ci[0] : ci[1];",
+        "const size_t fi = neg ? ci[0] : ci[1], bi = neg ? ci[1] : ci[0];"),
+    "aniso adjoint: scatter without the direction weight": (
+        "scatter_level(&s->st, lk, gpyr + orc_aniso_offset(g->n, l, dir[a]), nl, wa[a], dc, da);",
+        "scatter_level(&s->st, lk, gpyr + orc_aniso_offset(g->n, l, dir[a]), nl, 1.0, dc, da);"),
     "grace factor left out of the adjoint": (
         "double f = (P->flags & ORC_SPEC_GRACE) ? spec_grace(cs.dir[c], P) : 1.0;",
         "double f = 1.0;"),
