@@ -112,7 +112,8 @@ typedef enum { VCT_F32 = 0, VCT_F16 = 1 } vct_dtype;
  * a_b c_b) / alpha (0 where alpha = 0); the children are level 0's texels
  * for l = 0, else volume d of level l.  vct_trace samples a level l >= 1
  * for a cone of axis w as sum_a (w_a^2 / |w|^2) * (volume of axis a facing
- * the sign of w_a); level 0 as usual.  The adjoint does not cover it.
+ * the sign of w_a); level 0 as usual.  vct_trace_backward differentiates
+ * through both (see there).
  */
 #define VCT_LAYOUT_ANISO 2
 
@@ -376,7 +377,8 @@ typedef struct {
 } vct_view_grad;
 
 /* Device workspace bytes vct_trace_backward needs for `pyr` (a float32
- * gradient pyramid plus a header). */
+ * gradient pyramid plus a header; in the anisotropic layout for a
+ * VCT_LAYOUT_ANISO pyramid, else dense). */
 size_t vct_trace_backward_workspace_bytes(const vct_pyramid *pyr);
 
 /*
@@ -390,9 +392,14 @@ size_t vct_trace_backward_workspace_bytes(const vct_pyramid *pyr);
  * the march is recomputed from the stored (FP16 or brick) texels exactly as
  * vct_trace read them, and the rounding of FP16 storage is passed through
  * as identity (the gradient is that of the pyramid as stored, with respect
- * to the values it was built from).  The gradient pyramid is always dense
- * float32.  Scatter order is not deterministic (see
- * vct_trace_backward_deterministic for a reproducible variant).
+ * to the values it was built from).  The gradient pyramid is dense float32,
+ * except for a VCT_LAYOUT_ANISO pyramid: its derivatives go to the
+ * directional volumes a sample read (times w_a^2 / |w|^2), and the levels
+ * are pushed down through the derivatives of the pair composite (at the
+ * forward texels in `pyr`, which must still hold the pyramid the forward
+ * traced; colour derivatives are 0 where a pair's alpha is 0).  Scatter
+ * order is not deterministic (see vct_trace_backward_deterministic for a
+ * reproducible variant).
  */
 vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
                               const vct_view_grad *grads, int32_t n_views,

@@ -421,9 +421,12 @@ def trace(pyr: Pyramid, view: dict, prm: dict, idx=None):
     return out
 
 
-def trace_backward(pyr: Pyramid, view: dict, prm: dict, gD, gS, gV, idx=None, gL=None):
+def trace_backward(pyr: Pyramid, view: dict, prm: dict, gD, gS, gV, idx=None, gL=None,
+                   per_level: bool = False):
     """dL/d(level-0 grid) [n,n,n,4] for upstream gradients of the listed pixels
-    (gL: of the shaded radiance [k,4], with the shading flag)."""
+    (gL: of the shaded radiance [k,4], with the shading flag).  per_level:
+    return instead dL/d(every texel of the pyramid), in the pyramid's layout
+    (before the mip adjoint)."""
     keep: list = []
     V = _view_struct(view, keep)
     P = params_struct(prm)
@@ -443,8 +446,9 @@ def trace_backward(pyr: Pyramid, view: dict, prm: dict, gD, gS, gV, idx=None, gL
     grad0 = np.zeros(n * n * n * 4)
     _lib().orc_trace_backward(_p(pyr.data), n, pyr.levels, _p(pyr.origin), pyr.size,
                               ctypes.byref(V), ctypes.byref(P), _p(idx_arr), count,
-                              _p(gD), _p(gS), _p(gV), _p(gL), _p(scratch), _p(grad0))
-    return grad0.reshape(n, n, n, 4)
+                              _p(gD), _p(gS), _p(gV), _p(gL), _p(scratch),
+                              None if per_level else _p(grad0))
+    return scratch if per_level else grad0.reshape(n, n, n, 4)
 
 
 def voxelize(mesh: dict, n: int, origin=(0.0, 0.0, 0.0), size: float = 1.0,

@@ -920,7 +920,8 @@ static void cone_adjoint(const orc_grid *g, double *gpyr, const orc_step *rec,
  * gpyr is caller scratch of orc_level_offset(n, levels) doubles, or of
  * orc_aniso_offset(n, levels, 0) for an anisotropic pyramid (ORC_ANISO in
  * P->flags), zeroed here; the level-0 gradient is ADDED into grad0
- * ([n][n][n][4]).
+ * ([n][n][n][4]).  With grad0 NULL the mip adjoint is skipped and gpyr keeps
+ * the gradient of every texel of every level.
  */
 void orc_trace_backward(const double *pyr, int n, int levels,
                         const double *origin, double size, const orc_view *v,
@@ -985,6 +986,7 @@ void orc_trace_backward(const double *pyr, int n, int levels,
     }
     free(rec);
   }
+  if (!grad0) return; /* the per-level gradients stay in gpyr */
   if (g.aniso)
     orc_mip_adjoint_aniso(pyr, gpyr, n, levels, grad0);
   else

@@ -397,6 +397,86 @@ __global__ void aniso_level_kernel(const float4 *__restrict__ src_level, uint64_
   }
 }
 
+// Adjoint of pair_composite for one child of the pair (f, b): G is the
+// gradient of the pair's (C, alpha) (the texel's gradient times 1/4).  With
+// the front and back weights w_f = a_f / alpha, w_b = (1 - a_f) a_b / alpha
+// (C = w_f c_f + w_b c_b, w_f + w_b = 1) and D = c_b - c_f:
+//   dalpha/da_f = 1 - a_b,  dalpha/da_b = 1 - a_f,
+//   dC/dc_f = w_f,  dC/dc_b = w_b,
+//   dC/da_f = -D (w_b + a_b w_f) / alpha,  dC/da_b = (1 - a_f) w_f D / alpha,
+// the same partials as (c_f - a_b c_b - C (1 - a_b)) / alpha and
+// (1 - a_f) (c_b - C) / alpha written without their cancellation when the
+// two colours are close.  Where alpha = 0 the colour is 0 by definition and
+// passes no gradient.
+__device__ __forceinline__ float4 pair_adjoint(float4 f, float4 b, float4 G, bool own_front) {
+  const float af = f.w, ab = b.w;
+  const float a = fmaf(1.0f - af, ab, af);
+  float4 r = make_float4(0.f, 0.f, 0.f, G.w * (own_front ? 1.0f - ab : 1.0f - af));
+  if (!(a > 0.0f)) return r;
+  const float wf = __fdiv_rn(af, a), wb = __fdiv_rn((1.0f - af) * ab, a);
+  const float fc[3] = {f.x, f.y, f.z}, bc[3] = {b.x, b.y, b.z}, gc[3] = {G.x, G.y, G.z};
+  // dC/da of this child per unit colour difference D
+  const float k = own_front ? -__fdiv_rn(fmaf(ab, wf, wb), a) : __fdiv_rn((1.0f - af) * wf, a);
+  const float wo = own_front ? wf : wb;
+  float o[3], ga = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    o[c] = gc[c] * wo;
+    ga = fmaf(gc[c], bc[c] - fc[c], ga);
+  }
+  r.x = o[0];
+  r.y = o[1];
+  r.z = o[2];
+  r.w = fmaf(k, ga, r.w);
+  return r;
+}
+
+// Transpose of aniso_level_kernel for level l >= 2: one thread per (direction
+// d, child k of level l - 1): the child k gets, from its parent k >> 3 in
+// volume d, the pair adjoint of its pair along axis(d) (partner k ^ 1 << axis;
+// the front child is the one whose axis bit equals the travel sign bit).
+__global__ void aniso_adjoint_level_kernel(const float4 *__restrict__ fwd_child,
+                                           float4 *__restrict__ g_child,
+                                           const float4 *__restrict__ g_parent,
+                                           uint64_t child_texels) {
+  const uint64_t total = 6 * child_texels, parent_texels = child_texels >> 3;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const int d = (int)(i / child_texels);
+    const uint64_t k = i - (uint64_t)d * child_texels;
+    const int axis = d >> 1, neg = d & 1;
+    const bool own_front = (int)((k >> axis) & 1u) == neg;
+    const float4 *vol = fwd_child + (uint64_t)d * child_texels;
+    const float4 own = __ldg(vol + k), oth = __ldg(vol + (k ^ (1ull << axis)));
+    const float4 G = mul4(__ldg(g_parent + (uint64_t)d * parent_texels + (k >> 3)), 0.25f);
+    const float4 r = own_front ? pair_adjoint(own, oth, G, true) : pair_adjoint(oth, own, G, false);
+    const uint64_t o = (uint64_t)d * child_texels + k;
+    if (in_bounds(o, total, kOobMip)) g_child[o] = add4(g_child[o], r);
+  }
+}
+
+// Level 1 -> level 0: one thread per level-0 texel k, summing the pair
+// adjoints of its six parents (one per direction).
+__global__ void aniso_adjoint_level0_kernel(const float4 *__restrict__ lvl0,
+                                            float4 *__restrict__ g0,
+                                            const float4 *__restrict__ g1, uint64_t texels0) {
+  const uint64_t texels1 = texels0 >> 3;
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < texels0;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    const float4 own = __ldg(lvl0 + k);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      const int axis = d >> 1, neg = d & 1;
+      const bool own_front = (int)((k >> axis) & 1u) == neg;
+      const float4 oth = __ldg(lvl0 + (k ^ (1ull << axis)));
+      const float4 G = mul4(__ldg(g1 + (uint64_t)d * texels1 + (k >> 3)), 0.25f);
+      acc = add4(acc, own_front ? pair_adjoint(own, oth, G, true) : pair_adjoint(oth, own, G, false));
+    }
+    if (in_bounds(k, texels0, kOobMip)) g0[k] = add4(g0[k], acc);
+  }
+}
+
 struct AdjArgs {
   const float4 *g[VCT_MAX_LEVELS];
   int n, levels;
@@ -594,6 +674,34 @@ cudaError_t launch_mip_adjoint(const float *gpyr_base, const Layout &gl, int n, 
   const int grid = grid_for(level_texels(n, 0), 256);
   mip_adjoint_kernel<<<grid, 256, 0, s>>>(a, reinterpret_cast<float4 *>(grad0));
   return cudaGetLastError();
+}
+
+cudaError_t launch_mip_adjoint_aniso(const vct_pyramid &pyr, const float *gpyr_base,
+                                     float *grad0, int sms, cudaStream_t s) {
+  const Layout L = make_layout(pyr.n, pyr.levels, VCT_F32, VCT_LAYOUT_ANISO);
+  const uint8_t *fwd = static_cast<const uint8_t *>(pyr.data);
+  uint8_t *g = reinterpret_cast<uint8_t *>(const_cast<float *>(gpyr_base));
+  const int n = pyr.n;
+  auto grid_of = [&](uint64_t work) {
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 16));
+  };
+  cudaError_t e = cudaSuccess;
+  for (int l = pyr.levels - 1; l >= 2 && e == cudaSuccess; --l) {
+    aniso_adjoint_level_kernel<<<grid_of(6 * level_texels(n, l - 1)), 256, 0, s>>>(
+        reinterpret_cast<const float4 *>(fwd + L.level_off[l - 1]),
+        reinterpret_cast<float4 *>(g + L.level_off[l - 1]),
+        reinterpret_cast<const float4 *>(g + L.level_off[l]), level_texels(n, l - 1));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && pyr.levels >= 2) {
+    aniso_adjoint_level0_kernel<<<grid_of(level_texels(n, 0)), 256, 0, s>>>(
+        reinterpret_cast<const float4 *>(fwd + L.level_off[0]),
+        reinterpret_cast<float4 *>(g + L.level_off[0]),
+        reinterpret_cast<const float4 *>(g + L.level_off[1]), level_texels(n, 0));
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return e;
+  return launch_mip_adjoint(gpyr_base, L, n, 1, grad0, s);  // unpack level 0
 }
 
 cudaError_t launch_wait_probe(uint32_t *flag, uint64_t max_ns, cudaStream_t s) {

@@ -11,7 +11,8 @@
 // one, otherwise the march would have stopped at k).  Both passes go
 // through the same inlined sample code, so they see bit-identical samples.
 // The derivatives are scattered through the quadrilinear weights into a
-// float32 gradient pyramid with vector atomics.
+// float32 gradient pyramid with vector atomics (for an anisotropic pyramid,
+// into the directional volumes a sample read, times their weights).
 #include <algorithm>
 
 #include "trace_common.cuh"
@@ -39,16 +40,19 @@ __device__ __forceinline__ unsigned long long *fix_texel(const BwdLaunch &L, int
   return L.gfix_lvl[l] + 4 * (size_t)idx;
 }
 
-// Per-lane scatter of one level's 8 corners (lanes in different cells).
-__device__ __forceinline__ void scatter_lane(const BwdLaunch &L, int l, const LevelStencil &s,
-                                             float lw, const float g[4]) {
+// Per-lane scatter of one level's 8 corners (lanes in different cells) into
+// the gradient texels vbase + code (vbase: the volume's first texel in an
+// anisotropic level, else 0; lim: the texels of the gradient level).
+__device__ __forceinline__ void scatter_lane(const BwdLaunch &L, int l, uint32_t vbase,
+                                             uint32_t lim, const LevelStencil &s, float lw,
+                                             const float g[4]) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     if (!((s.valid >> c) & 1u)) continue;
     const float w = corner_weight(s, lw, c);
     if (w == 0.0f) continue;
-    const uint32_t idx = corner_index(s, c);
-    if (!in_bounds(idx, level_texels(L.pyr.n, l), kOobGrad)) continue;
+    const uint32_t idx = vbase + corner_index(s, c);
+    if (!in_bounds(idx, lim, kOobGrad)) continue;
     if (L.deterministic) {
       unsigned long long *q = fix_texel(L, l, idx);
 #pragma unroll
@@ -72,19 +76,46 @@ __device__ __forceinline__ void scatter_lane(const BwdLaunch &L, int l, const Le
 // 544 ms without the reduction.
 constexpr int kReduceMin = 16;
 
+// Slot of the key-offset table holding the total (after the per-level offsets).
+constexpr int kKeyTotal = VCT_MAX_LEVELS;
+
+template <bool AN>
 __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const uint32_t *code_off,
-                                             bool act, int l, const LevelStencil &s, float lw,
-                                             const float g[4]) {
+                                             bool act, int l, uint32_t vbase, uint32_t lim,
+                                             const LevelStencil &s, float lw, const float g[4]) {
   const unsigned full = 0xffffffffu;
+  act = act && s.valid != 0u;  // a cell wholly outside the level has nothing to scatter
   if (__ballot_sync(full, act) == 0u) return;
   const int lane = threadIdx.x & 31;
-  // (level, cell) as one 32-bit key: the cell's Morton code offset by the
-  // texels of all finer levels (< 2^31 for n <= 1024); lanes in one cell of
-  // one level share its corner validity too.
-  const uint32_t key = act ? code_off[l] + (s.sx[0] | s.sy[0] | s.sz[0]) : 0xffffffffu;
+  // (level, volume, cell) as one 32-bit key: the cell's Morton code offset by
+  // its volume's first texel and by the texels of all finer levels (< 2^31
+  // for n <= 1024, anisotropic levels included); lanes with one key share the
+  // cell's corners and their validity.  The Morton code names the cell only
+  // while its lower corner (corner 0) lies inside the level; a cell with a
+  // valid corner but its lower corner outside starts at -1 on some axes (its
+  // spread code there is that of 1023, the 10-bit wrap of -1).  Such a cell
+  // is keyed by bit 31, the mask of those axes (bits 28-30) and the offset
+  // code of the cell moved to 0 on them, which is unique while every key
+  // offset stays below 2^28 (code_off[kKeyTotal], n <= 512); above that
+  // the lane takes a key of its own and scatters alone.
+  uint32_t key = 0xffffffffu;
+  if (act) {
+    if (s.valid & 1u) {
+      key = code_off[l] + vbase + (s.sx[0] | s.sy[0] | s.sz[0]);
+    } else if (code_off[kKeyTotal] < (1u << 28)) {
+      const uint32_t mx = s.sx[0] == kMortonX ? 1u : 0u;
+      const uint32_t my = s.sy[0] == (kMortonX << 1) ? 2u : 0u;
+      const uint32_t mz = s.sz[0] == (kMortonX << 2) ? 4u : 0u;
+      const uint32_t cell = (mx ? s.sx[1] : s.sx[0]) | (my ? s.sy[1] : s.sy[0]) |
+                            (mz ? s.sz[1] : s.sz[0]);
+      key = 0x80000000u | ((mx | my | mz) << 28) | (code_off[l] + vbase + cell);
+    } else {
+      key = 0xffffff00u + (uint32_t)lane;
+    }
+  }
   const unsigned grp = __match_any_sync(full, key);
   const bool big = act && __popc(grp) >= kReduceMin;
-  if (act && !big) scatter_lane(L, l, s, lw, g);
+  if (act && !big) scatter_lane(L, l, vbase, lim, s, lw, g);
   unsigned pending = __ballot_sync(full, big);
   while (pending) {
     const int leader = __ffs(pending) - 1;
@@ -112,19 +143,49 @@ __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const uint32_t 
     // source lane's value, so per-corner choices are made afterwards).
     const int c = lane >> 2, ch = lane & 3;
     const int ll = __shfl_sync(full, l, leader);  // this lane's own level may differ
+    uint32_t lvbase = 0u, llim;
+    if constexpr (AN) {
+      lvbase = __shfl_sync(full, vbase, leader);
+      llim = __shfl_sync(full, lim, leader);
+    } else {
+      llim = (uint32_t)level_texels(L.pyr.n, ll);
+    }
     const uint32_t lvalid = __shfl_sync(full, s.valid, leader);
     const uint32_t sx0 = __shfl_sync(full, s.sx[0], leader), sx1 = __shfl_sync(full, s.sx[1], leader);
     const uint32_t sy0 = __shfl_sync(full, s.sy[0], leader), sy1 = __shfl_sync(full, s.sy[1], leader);
     const uint32_t sz0 = __shfl_sync(full, s.sz[0], leader), sz1 = __shfl_sync(full, s.sz[1], leader);
-    const uint32_t idx = ((c & 1) ? sx1 : sx0) | (((c >> 1) & 1) ? sy1 : sy0) | ((c >> 2) ? sz1 : sz0);
-    if (((lvalid >> c) & 1u) && v[0] != 0.0f &&
-        in_bounds(idx, level_texels(L.pyr.n, ll), kOobGrad)) {
+    const uint32_t idx =
+        lvbase + (((c & 1) ? sx1 : sx0) | (((c >> 1) & 1) ? sy1 : sy0) | ((c >> 2) ? sz1 : sz0));
+    if (((lvalid >> c) & 1u) && v[0] != 0.0f && in_bounds(idx, llim, kOobGrad)) {
       if (L.deterministic)
         atomicAdd(fix_texel(L, ll, idx) + ch, to_fix(v[0]));
       else
         atomicAdd(grad_texel(L, ll, idx) + ch, v[0]);
     }
     pending &= ~lgrp;
+  }
+}
+
+// Scatter of one level of the quadrilinear stencil (level weight lw).  In an
+// anisotropic pyramid a level >= 1 was read from up to three volumes weighted
+// by w_a^2: each receives the derivatives times its weight, the volumes the
+// forward skipped none (warp-uniform trip count).
+template <bool AN>
+__device__ __forceinline__ void scatter_level(const BwdLaunch &L, const uint32_t *code_off,
+                                              bool act, int l, const LevelStencil &s, float lw,
+                                              const float g[4], const AnisoW &aw) {
+  const uint32_t tex = (uint32_t)level_texels(L.pyr.n, l);
+  if constexpr (!AN) {
+    scatter_warp<false>(L, code_off, act, l, 0u, tex, s, lw, g);
+  } else {
+    const bool dir = l >= 1;
+#pragma unroll 1
+    for (int a = 0; a < 3; ++a) {
+      const bool on = act && (dir ? aw.wt[a] >= kAnisoSkip : a == 0);
+      if (__any_sync(0xffffffffu, on))
+        scatter_warp<true>(L, code_off, on, l, dir ? (uint32_t)aw.vol[a] * tex : 0u,
+                     dir ? 6u * tex : tex, s, dir ? lw * aw.wt[a] : lw, g);
+    }
   }
 }
 
@@ -139,7 +200,7 @@ __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const uint32_t 
 // sample's colour channels receive gradient.  With premultiplied colour
 // (C = sum T_k c_k): dC/dc_k = T_k, dC/da_k = -T_k R'_{k+1}, R'_k = c_k +
 // (1 - a_k) R'_{k+1}.
-template <int DT, bool BR, bool kVar>
+template <int DT, bool BR, bool kVar, bool AN = false>
 __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t *code_off,
                                              const uint32_t *lut, bool active,
                                              const Apex &A, const float w[3],
@@ -150,6 +211,8 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t 
   // kVar: a launch with a cone variant; the plain instances keep none of it
   const bool premul = kVar && (L.var.flags & VCT_FLAG_PREMULTIPLIED) != 0;
   if constexpr (!kVar) mode = kPlain;
+  AnisoW aw{};
+  if constexpr (AN) aw = aniso_weights(w);
   float prod = 1.f, prod_last = 1.f;
   float tr_next = 0.f, R0 = 0.f, R1 = 0.f, R2 = 0.f, Q = 1.f;
   int k = 0;                    // this lane's forward step
@@ -198,7 +261,10 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t 
       float T, lam;
       step_at(cc, T0, ks, T, lam);
       const float F[3] = {fmaf(T, w[0], A.Of[0]), fmaf(T, w[1], A.Of[1]), fmaf(T, w[2], A.Of[2])};
-      v = sample<DT, BR>(P, A, F, lam, lut, om, lp, st);
+      if constexpr (AN)
+        v = sample_aniso(P, A, F, lam, lut, aw, om, lp, st);
+      else
+        v = sample<DT, BR>(P, A, F, lam, lut, om, lp, st);
       if (kVar && mode == kOccSmooth) {  // as the forward march
         fade = smoothstep0(L.var.occ_max_dist, sqrtf(T * P.h0) * L.var.shadow_str);
         v.w *= fade;
@@ -248,13 +314,13 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t 
       Q *= om;
       tr_next = tr;
     }
-    scatter_warp(L, code_off, act, lp.l0, st[0], 1.0f - lp.f, g);
+    scatter_level<AN>(L, code_off, act, lp.l0, st[0], 1.0f - lp.f, g, aw);
     const bool two = act && lp.f > 0.0f;
-    if (__any_sync(full, two)) scatter_warp(L, code_off, two, lp.l1, st[1], lp.f, g);
+    if (__any_sync(full, two)) scatter_level<AN>(L, code_off, two, lp.l1, st[1], lp.f, g, aw);
   }
 }
 
-template <int LPP, int DT, bool BR, bool kVar>
+template <int LPP, int DT, bool BR, bool kVar, bool AN = false>
 __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __grid_constant__ BwdLaunch L) {
   constexpr int kPixPerRound = 32 / LPP;
   const int lane = threadIdx.x & 31;
@@ -264,14 +330,16 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
   const float T0 = L.spec.t0_vox;
   const DevPyr &P = L.pyr;
 
-  // per level: texels of all finer levels (offsets of the scatter's cell keys)
-  __shared__ uint32_t s_code_off[VCT_MAX_LEVELS];
+  // per level: texels of all finer levels (offsets of the scatter's cell
+  // keys; six volumes per anisotropic level >= 1); slot kKeyTotal: all of them
+  __shared__ uint32_t s_code_off[kKeyTotal + 1];
   if (threadIdx.x == 0) {
     uint32_t acc = 0;
     for (int l = 0; l < VCT_MAX_LEVELS; ++l) {
       s_code_off[l] = acc;
-      if (l < P.levels) acc += (uint32_t)level_texels(P.n, l);
+      if (l < P.levels) acc += (uint32_t)level_texels(P.n, l) * ((AN && l >= 1) ? 6u : 1u);
     }
+    s_code_off[kKeyTotal] = acc;
   }
   __shared__ uint32_t s_lut[kSpreadLut];
   fill_spread_lut(s_lut);  // (its barrier also covers s_code_off)
@@ -396,8 +464,8 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
         const uint2 *st = V.state == nullptr ? nullptr
                           : V.state + (on ? (size_t)c * V.W * V.H + p : 0);
         if (__any_sync(0xffffffffu, on))
-          cone_adjoint<DT, BR, kVar>(L, s_code_off, s_lut, on, A, w, cc, T0, g0, g1, g2, ga, st,
-                                     mode);
+          cone_adjoint<DT, BR, kVar, AN>(L, s_code_off, s_lut, on, A, w, cc, T0, g0, g1, g2, ga,
+                                         st, mode);
       }
     }
   }
@@ -409,9 +477,9 @@ __global__ void fix_to_float_kernel(const unsigned long long *fix, float *out, u
     out[i] = __ll2float_rn((long long)fix[i]) * (1.0f / kFixScale);
 }
 
-template <int LPP, int DT, bool BR, bool kVar>
+template <int LPP, int DT, bool BR, bool kVar, bool AN = false>
 cudaError_t launch_b(const BwdLaunch &L, int grid, cudaStream_t s) {
-  trace_bwd_kernel<LPP, DT, BR, kVar><<<grid, kTraceThreads, 0, s>>>(L);
+  trace_bwd_kernel<LPP, DT, BR, kVar, AN><<<grid, kTraceThreads, 0, s>>>(L);
   return cudaGetLastError();
 }
 
@@ -423,21 +491,21 @@ int occ_b() {
   return b;
 }
 
-template <int DT, bool BR, bool kVar>
+template <int DT, bool BR, bool kVar, bool AN = false>
 cudaError_t launch_lpp(const BwdLaunch &L, int lpp, int grid, cudaStream_t s) {
   switch (lpp) {
-    case 1: return launch_b<1, DT, BR, kVar>(L, grid, s);
-    case 2: return launch_b<2, DT, BR, kVar>(L, grid, s);
-    case 4: return launch_b<4, DT, BR, kVar>(L, grid, s);
-    case 8: return launch_b<8, DT, BR, kVar>(L, grid, s);
+    case 1: return launch_b<1, DT, BR, kVar, AN>(L, grid, s);
+    case 2: return launch_b<2, DT, BR, kVar, AN>(L, grid, s);
+    case 4: return launch_b<4, DT, BR, kVar, AN>(L, grid, s);
+    case 8: return launch_b<8, DT, BR, kVar, AN>(L, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <int DT, bool BR>
+template <int DT, bool BR, bool AN = false>
 cudaError_t launch_var(const BwdLaunch &L, int lpp, int grid, cudaStream_t s) {
-  return bwd_has_variants(L.var.flags) ? launch_lpp<DT, BR, true>(L, lpp, grid, s)
-                                       : launch_lpp<DT, BR, false>(L, lpp, grid, s);
+  return bwd_has_variants(L.var.flags) ? launch_lpp<DT, BR, true, AN>(L, lpp, grid, s)
+                                       : launch_lpp<DT, BR, false, AN>(L, lpp, grid, s);
 }
 
 template <int DT, bool BR>
@@ -456,6 +524,7 @@ int occ_lpp(int lpp) {
 static_assert(sizeof(BwdLaunch) <= 32000, "adjoint launch parameters exceed the 32 KB limit");
 
 cudaError_t launch_trace_bwd(const BwdLaunch &L, int lpp, int grid, cudaStream_t s) {
+  if (L.aniso) return launch_var<VCT_F32, false, true>(L, lpp, grid, s);  // FP32, dense only
   const bool br = L.pyr.bricked != 0;
   if (L.pyr.dtype == VCT_F16)
     return br ? launch_var<VCT_F16, true>(L, lpp, grid, s) : launch_var<VCT_F16, false>(L, lpp, grid, s);

@@ -483,12 +483,14 @@ __device__ __forceinline__ void aniso_level(const DevPyr &P, int l, const LevelS
 // S(p, lambda) of an anisotropic pyramid for travel along the cone axis.
 __device__ __forceinline__ float4 sample_aniso(const DevPyr &P, const Apex &A, const float F[3],
                                                float lam, const uint32_t *lut, const AnisoW &aw,
-                                               float &om, LodPick &lp) {
+                                               float &om, LodPick &lp,
+                                               LevelStencil *st = nullptr) {
   lp = pick_levels(lam, P.levels);
   LevelStencil s;
   f32x2 rg, ba;
   level_stencil(lp.l0, P.n >> lp.l0, A, F, lut, s);
   aniso_level(P, lp.l0, s, aw, rg, ba);
+  if (st) st[0] = s;
   if (lp.f > 0.0f) {
     level_stencil(lp.l1, P.n >> lp.l1, A, F, lut, s);
     f32x2 rg1, ba1;
@@ -496,6 +498,7 @@ __device__ __forceinline__ float4 sample_aniso(const DevPyr &P, const Apex &A, c
     const f32x2 tf = f2_pack(lp.f, lp.f);
     rg = f2_lerp(rg, rg1, tf);
     ba = f2_lerp(ba, ba1, tf);
+    if (st) st[1] = s;
   }
   const float2 v0 = f2_unpack(rg), v1 = f2_unpack(ba);
   om = transparency(v1.y);

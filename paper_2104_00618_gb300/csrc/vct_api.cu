@@ -83,6 +83,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+// Layout of the float32 gradient pyramid of the adjoint: dense for dense and
+// brick pyramids, anisotropic (six volumes per level >= 1) for anisotropic ones.
+int grad_layout(const vct_pyramid &p) {
+  return p.layout == VCT_LAYOUT_ANISO ? VCT_LAYOUT_ANISO : VCT_LAYOUT_DENSE;
+}
+
 int sm_count() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -667,18 +673,23 @@ vct_status vct_autotune_trace(const vct_pyramid *pyrs, int32_t n_pyr, const vct_
 
 size_t vct_trace_backward_workspace_bytes(const vct_pyramid *pyr) {
   if (!pyr || !shape_ok(pyr->n, pyr->levels, pyr->dtype)) return 0;
-  return (size_t)make_layout(pyr->n, pyr->levels, VCT_F32).total;
+  return (size_t)make_layout(pyr->n, pyr->levels, VCT_F32, grad_layout(*pyr)).total;
 }
 
 }  // extern "C"
 
 namespace {
 
+// Texels of gradient level l: six volumes per anisotropic level >= 1.
+uint64_t grad_texels(int n, int l, bool aniso) {
+  return vct::level_texels(n, l) * ((aniso && l >= 1) ? 6 : 1);
+}
+
 // Fixed-point levels of the deterministic adjoint: 4 x uint64 per texel,
 // each level 256-byte aligned, after the float32 gradient pyramid.
-uint64_t fix_level_off(const vct::Layout &gl, int n, int l) {
+uint64_t fix_level_off(const vct::Layout &gl, int n, int l, bool aniso) {
   uint64_t off = vct::align256(gl.total);
-  for (int k = 0; k < l; ++k) off += vct::align256(vct::level_texels(n, k) * 32);
+  for (int k = 0; k < l; ++k) off += vct::align256(grad_texels(n, k, aniso) * 32);
   return off;
 }
 
@@ -690,8 +701,7 @@ vct_status trace_backward_impl(const vct_pyramid *pyr, const vct_view *views,
   using namespace vct;
   vct_status st = check_pyramid(pyr, "vct_trace_backward");
   if (st != VCT_OK) return st;
-  if (pyr->layout == VCT_LAYOUT_ANISO)
-    return fail(VCT_ERR_UNSUPPORTED, "vct_trace_backward: anisotropic pyramids have no adjoint");
+  const bool aniso = pyr->layout == VCT_LAYOUT_ANISO;
   if (!views || !grads || n_views < 1)
     return fail(VCT_ERR_INVALID_ARG, "vct_trace_backward: no views");
   if ((st = check_params(params, true)) != VCT_OK) return st;
@@ -714,8 +724,8 @@ vct_status trace_backward_impl(const vct_pyramid *pyr, const vct_view *views,
   }
   if (!grad_level0_dense || !aligned(grad_level0_dense, 16))
     return fail(VCT_ERR_INVALID_ARG, "vct_trace_backward: grad_level0 NULL or misaligned");
-  const Layout gl = make_layout(pyr->n, pyr->levels, VCT_F32);
-  const uint64_t need = deterministic ? fix_level_off(gl, pyr->n, pyr->levels) : gl.total;
+  const Layout gl = make_layout(pyr->n, pyr->levels, VCT_F32, grad_layout(*pyr));
+  const uint64_t need = deterministic ? fix_level_off(gl, pyr->n, pyr->levels, aniso) : gl.total;
   if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
     return fail(VCT_ERR_WORKSPACE, "vct_trace_backward: workspace needs %llu bytes, 256-byte aligned",
                 (unsigned long long)need);
@@ -731,9 +741,11 @@ vct_status trace_backward_impl(const vct_pyramid *pyr, const vct_view *views,
   for (int l = 0; l < pyr->levels; ++l) {
     L->gpyr_lvl[l] = reinterpret_cast<float *>(ws + gl.level_off[l]);
     if (deterministic)
-      L->gfix_lvl[l] = reinterpret_cast<unsigned long long *>(ws + fix_level_off(gl, pyr->n, l));
+      L->gfix_lvl[l] =
+          reinterpret_cast<unsigned long long *>(ws + fix_level_off(gl, pyr->n, l, aniso));
   }
   L->deterministic = deterministic ? 1 : 0;
+  L->aniso = aniso ? 1 : 0;
   L->queue = reinterpret_cast<unsigned *>(ws);
   L->tile_w = c.tile_w;
   L->tile_h = c.tile_h;
@@ -765,11 +777,14 @@ vct_status trace_backward_impl(const vct_pyramid *pyr, const vct_view *views,
   }
   if (deterministic)
     for (int l = 0; l < pyr->levels; ++l) {
-      e = launch_fix_to_float(L->gfix_lvl[l], L->gpyr_lvl[l], level_texels(pyr->n, l) * 4, s);
+      e = launch_fix_to_float(L->gfix_lvl[l], L->gpyr_lvl[l], grad_texels(pyr->n, l, aniso) * 4,
+                              s);
       if (e != cudaSuccess) return cuda_fail(e, "vct_trace_backward fixed-point conversion");
     }
-  e = launch_mip_adjoint(reinterpret_cast<const float *>(ws), gl, pyr->n, pyr->levels,
-                         grad_level0_dense, s);
+  e = aniso ? launch_mip_adjoint_aniso(*pyr, reinterpret_cast<const float *>(ws),
+                                       grad_level0_dense, sms, s)
+            : launch_mip_adjoint(reinterpret_cast<const float *>(ws), gl, pyr->n, pyr->levels,
+                                 grad_level0_dense, s);
   if (e != cudaSuccess) return cuda_fail(e, "vct_trace_backward mip adjoint launch");
   return VCT_OK;
 }
@@ -789,7 +804,8 @@ vct_status vct_trace_backward(const vct_pyramid *pyr, const vct_view *views,
 
 size_t vct_trace_backward_deterministic_workspace_bytes(const vct_pyramid *pyr) {
   if (!pyr || !shape_ok(pyr->n, pyr->levels, pyr->dtype)) return 0;
-  return (size_t)fix_level_off(make_layout(pyr->n, pyr->levels, VCT_F32), pyr->n, pyr->levels);
+  return (size_t)fix_level_off(make_layout(pyr->n, pyr->levels, VCT_F32, grad_layout(*pyr)),
+                               pyr->n, pyr->levels, pyr->layout == VCT_LAYOUT_ANISO);
 }
 
 vct_status vct_trace_backward_deterministic(const vct_pyramid *pyr, const vct_view *views,

@@ -342,6 +342,7 @@ struct BwdLaunch {
   int n_views, total_tiles, tile_w, tile_h;
   int n_diffuse, spec_enable, occ_enable;
   int deterministic;  // 1: accumulate in 64-bit fixed point (gfix_lvl), not float
+  int aniso;          // 1: anisotropic pyramid (gradient levels >= 1 hold six volumes)
   float diffuse_dir[VCT_MAX_DIFFUSE][3];
   float diffuse_weight[VCT_MAX_DIFFUSE];
   float light[3];
@@ -402,6 +403,11 @@ cudaError_t launch_brick_tables(const float *level0, int n, int levels, const La
                                 uint8_t *base, uint64_t capacity, cudaStream_t s);
 cudaError_t launch_mip_adjoint(const float *gpyr_base, const Layout &gl, int n, int levels,
                                float *grad0, cudaStream_t s);
+// Adjoint of launch_build_aniso at the anisotropic pyramid `pyr`: the
+// gradient pyramid at gpyr_base (same layout) is pushed down coarse to fine
+// (in place), then its level 0 is added into the dense grad0.
+cudaError_t launch_mip_adjoint_aniso(const vct_pyramid &pyr, const float *gpyr_base,
+                                     float *grad0, int sms, cudaStream_t s);
 cudaError_t launch_wait_probe(uint32_t *flag, uint64_t max_ns, cudaStream_t s);
 cudaError_t launch_bounds_probe(uint32_t *buf, uint32_t declared, uint32_t extra,
                                 cudaStream_t s);

@@ -104,6 +104,12 @@ def run_everything():
                 out[key + "D"] = v.out_diffuse.cpu().numpy()
                 out[key + "S"] = v.out_specular.cpu().numpy()
                 out[key + "V"] = v.out_visibility.cpu().numpy()
+            v = vct.View.from_host(view)
+            vct.trace([P], [v], prm)
+            gl = vct.trace_backward(P, [v], [(torch.ones_like(v.out_diffuse),
+                                              torch.ones_like(v.out_specular),
+                                              torch.ones_like(v.out_visibility))], prm)
+            out[f"bwan{n}{count}"] = gl.cpu().numpy()
     # voxelizer and G-buffer on a few triangles, one crossing the grid border
     mesh = {"vertices": np.array([[-0.2, 0.1, 0.5], [1.2, 0.3, 0.55], [0.4, 1.1, 0.45],
                                   [0.1, 0.1, 0.9], [0.9, 0.1, 0.9], [0.5, 0.9, 0.9]], np.float32),
