@@ -1,6 +1,7 @@
 """Two CPU ranks (gloo): views sharded over ranks, per-rank FP64 adjoints of
 the oracle summed with the package's gradient reduction, against one rank
-doing everything.  Exercises the exchange the sharded path needs."""
+doing everything, for an isotropic and an anisotropic pyramid.  Exercises
+the exchange the sharded path needs."""
 import math
 import os
 import socket
@@ -28,8 +29,9 @@ def _case():
     return gt, views, prm, learn
 
 
-def _grad(views, prm, learn, gt):
-    P, Pgt = oracle.build_mips(learn), oracle.build_mips(gt["grid"])
+def _grad(views, prm, learn, gt, aniso=False):
+    build = oracle.build_mips_aniso if aniso else oracle.build_mips
+    P, Pgt = build(learn), build(gt["grid"])
     g = np.zeros(learn.shape)
     for v in views:
         r, t = oracle.trace(P, v, prm), oracle.trace(Pgt, v, prm)
@@ -38,12 +40,12 @@ def _grad(views, prm, learn, gt):
     return g
 
 
-def _worker(rank, world, port, out_path):
+def _worker(rank, world, port, out_path, aniso):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     gt, views, prm, learn = _case()
     mine = shard(views, rank, world)
-    g = torch.from_numpy(_grad(mine, prm, learn, gt))
+    g = torch.from_numpy(_grad(mine, prm, learn, gt, aniso))
     reduce_gradient(g)
     if rank == 0:
         np.save(out_path, g.numpy())
@@ -64,12 +66,13 @@ def test_shard_covers_every_item_once():
     assert max(map(len, parts)) - min(map(len, parts)) <= 1
 
 
-def test_two_rank_gradient_equals_single_rank(tmp_path):
+@pytest.mark.parametrize("aniso", [False, True])
+def test_two_rank_gradient_equals_single_rank(tmp_path, aniso):
     oracle.build()  # compile before spawning
     out = str(tmp_path / "g.npy")
-    mp.spawn(_worker, args=(2, _free_port(), out), nprocs=2, join=True)
+    mp.spawn(_worker, args=(2, _free_port(), out, aniso), nprocs=2, join=True)
     gt, views, prm, learn = _case()
-    ref = _grad(views, prm, learn, gt)
+    ref = _grad(views, prm, learn, gt, aniso)
     got = np.load(out)
     assert np.abs(got).max() > 0
     assert np.allclose(got, ref, rtol=1e-12, atol=1e-15 * np.abs(ref).max())
