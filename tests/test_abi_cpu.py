@@ -269,3 +269,24 @@ def test_brick_layout_sizes_and_validation(lib):
     st = lib.vct_pyramid_plan_bricks(1024, 64, 7, 0, 256, 100, ctypes.byref(occ),
                                      ctypes.byref(nb), None)
     assert st == _abi.VCT_ERR_WORKSPACE
+
+
+def test_aniso_layout_and_adjoint_workspace_sizes(lib):
+    """Anisotropic pyramids: level 0 as dense, six volumes per level >= 1
+    (each level 256-byte aligned after a 256-byte header); FP32 only.  The
+    adjoint's float32 gradient pyramid takes the same layout, and the
+    reproducible mode adds 4 x uint64 per texel of every volume."""
+    al = lambda x: (x + 255) // 256 * 256
+    for n in (2, 8, 64, 256):
+        L = n.bit_length()
+        levels = [(n >> l) ** 3 * (6 if l >= 1 else 1) for l in range(L)]
+        total = 256 + sum(al(t * 16) for t in levels)
+        assert lib.vct_pyramid_bytes_aniso(n, L, 0) == total
+        p = _abi.VctPyramid(n, L, 0, _abi.LAYOUT_ANISO)
+        assert lib.vct_trace_backward_workspace_bytes(ctypes.byref(p)) == total
+        det = lib.vct_trace_backward_deterministic_workspace_bytes(ctypes.byref(p))
+        assert det == al(total) + sum(al(t * 32) for t in levels)
+        d = _abi.VctPyramid(n, L, 0, _abi.LAYOUT_DENSE)
+        assert lib.vct_trace_backward_workspace_bytes(ctypes.byref(d)) == lib.vct_pyramid_bytes(n, L, 0)
+    assert lib.vct_pyramid_bytes_aniso(64, 7, 1) == 0  # FP16 is not offered
+    assert lib.vct_pyramid_bytes_aniso(48, 6, 0) == 0  # not a power of two
