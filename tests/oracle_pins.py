@@ -1255,8 +1255,16 @@ def check_gradient_fd_aniso():
     """Central differences of the FP64 loss through an anisotropic pyramid
     against the adjoint (trace scatter into the directional volumes weighted
     by w_a^2, then the transpose of the pair-composite build), with opacities
-    in [0.05, 0.3]: no cone saturates and every pair composite is smooth."""
+    in [0.05, 0.3]: no cone saturates and every pair composite is smooth;
+    plain, and with the occlusion fade, the angular grace and premultiplied
+    colour together."""
+    import vct_synth as vs
     g, view, prm, targets = _small_diff_problem(seed=66)
+    _fd_aniso(g, view, prm, targets)
+    _fd_aniso(g, view, dict(vs.variant_params(prm, 1 | 2 | 32), occ_max_dist=1.0), targets)
+
+
+def _fd_aniso(g, view, prm, targets):
     g[..., 3] = np.random.default_rng(67).uniform(0.05, 0.3, g.shape[:3])
     tD, tS, tV = targets
 
