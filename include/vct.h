@@ -48,7 +48,7 @@ typedef enum {
   VCT_ERR_INVALID_ARG = 1, /* a pointer, size or parameter is out of range   */
   VCT_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed     */
   VCT_ERR_WORKSPACE = 3,   /* workspace missing or smaller than required      */
-  VCT_ERR_UNSUPPORTED = 4, /* valid request this build does not implement     */
+  VCT_ERR_UNSUPPORTED = 4, /* valid request the library does not implement     */
   VCT_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up              */
 } vct_status;
 
