@@ -95,14 +95,15 @@ __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const uint32_t 
   // valid corner but its lower corner outside starts at -1 on some axes (its
   // spread code there is that of 1023, the 10-bit wrap of -1).  Such a cell
   // is keyed by bit 31, the mask of those axes (bits 28-30) and the offset
-  // code of the cell moved to 0 on them, which is unique while every key
-  // offset stays below 2^28 (code_off[kKeyTotal], n <= 512); above that
+  // code of the cell moved to 0 on them, which is unique, and below the
+  // per-lane keys 0xffffff00 + lane and the inactive key, while every key
+  // offset stays below 0x0fffff00 (code_off[kKeyTotal]; n <= 512); above that
   // the lane takes a key of its own and scatters alone.
   uint32_t key = 0xffffffffu;
   if (act) {
     if (s.valid & 1u) {
       key = code_off[l] + vbase + (s.sx[0] | s.sy[0] | s.sz[0]);
-    } else if (code_off[kKeyTotal] < (1u << 28)) {
+    } else if (code_off[kKeyTotal] < 0x0fffff00u) {
       const uint32_t mx = s.sx[0] == kMortonX ? 1u : 0u;
       const uint32_t my = s.sy[0] == (kMortonX << 1) ? 2u : 0u;
       const uint32_t mz = s.sz[0] == (kMortonX << 2) ? 4u : 0u;

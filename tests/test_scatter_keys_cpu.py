@@ -44,7 +44,7 @@ def all_keys(n, aniso):
                 if valid & 1:
                     key = off[l] + vbase + (sx0 | sy0 | sz0)
                 else:
-                    assert acc < (1 << 28)
+                    assert acc < 0x0fffff00
                     mx = 1 if sx0 == M else 0
                     my = 2 if sy0 == M << 1 else 0
                     mz = 4 if sz0 == M << 2 else 0
@@ -65,10 +65,13 @@ def test_keys_unique(n, aniso):
 
 
 def test_packed_keys_fit_up_to_512():
-    """The packed keys need every offset below 2^28: true for n <= 512 in
-    both layouts (the kernel falls back to per-lane keys beyond)."""
+    """The packed keys need every offset below 0x0fffff00 (then the largest,
+    mask 7, stays below the per-lane keys 0xffffff00 + lane): true for
+    n <= 512 in both layouts; the kernel falls back to per-lane keys beyond,
+    and the in-range keys of n = 1024 stay below 2^31."""
     for aniso in (False, True):
         total = sum((512 >> l) ** 3 * (6 if aniso and l >= 1 else 1) for l in range(10))
-        assert total < 1 << 28
-    total = sum((1024 >> l) ** 3 for l in range(11))
-    assert total >= 1 << 28
+        assert total < 0x0fffff00
+        assert (0x80000000 | (7 << 28) | (total - 1)) < 0xffffff00
+        big = sum((1024 >> l) ** 3 * (6 if aniso and l >= 1 else 1) for l in range(11))
+        assert 0x0fffff00 <= big < 1 << 31
