@@ -72,6 +72,8 @@ MUTANTS = {
                                                           "gf[3] = G[3] / 4.0;"),
     "aniso adjoint: back colour partial without a_b": (
         "gb[c] = gC * (1.0 - af) * ab / alpha;", "gb[c] = gC * (1.0 - af) / alpha;"),
+    "aniso adjoint: colour gradient through an empty pair": ("if (alpha > 0.0) {",
+                                                             "if (alpha >= 0.0) {"),
     "aniso adjoint: front and back swapped": (
         "const size_t fi = neg ? ci[1] : ci[0], bi = neg ? ci[0] : ci[1];",
         "const size_t fi = neg ? ci[0] : ci[1], bi = neg ? ci[1] : ci[0];"),
