@@ -290,3 +290,18 @@ def test_aniso_layout_and_adjoint_workspace_sizes(lib):
         assert lib.vct_trace_backward_workspace_bytes(ctypes.byref(d)) == lib.vct_pyramid_bytes(n, L, 0)
     assert lib.vct_pyramid_bytes_aniso(64, 7, 1) == 0  # FP16 is not offered
     assert lib.vct_pyramid_bytes_aniso(48, 6, 0) == 0  # not a power of two
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without the compiled library the binding raises, and a
+    failed build raises rather than leaving a stale or empty library."""
+    from paper_2104_00618_gb300 import build as _build
+    monkeypatch.setattr(_build, "library_file", lambda variant="release": str(tmp_path / "none.so"))
+    with pytest.raises(RuntimeError, match="not found"):
+        _abi.open_library("release", build_if_missing=False)
+
+    def no_nvcc():
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libvct")
+    monkeypatch.setattr(_build, "nvcc", no_nvcc)
+    with pytest.raises(RuntimeError):
+        _build.build(force=True)
