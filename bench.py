@@ -670,9 +670,9 @@ def run_extras(torch, vct, dev, args):
             continue
         try:
             out[name] = fn(torch, vct, dev)
+            torch.cuda.empty_cache()
         except Exception as e:  # report, keep the main line
             out[name] = {"error": f"{type(e).__name__}: {e}"}
-        torch.cuda.empty_cache()
     return out
 
 
