@@ -100,25 +100,51 @@ def ncu_traffic(kernel: str, workload: str):
     return float(e["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in e else None
 
 
-# Instruction issue of the whole GPU: 152 SMs x 4 sub-partitions, each issuing
-# at most one warp instruction per clock.
-ISSUE_SLOTS_PER_CLOCK = 152 * 4
+# Instruction issue: every SM has 4 sub-partitions, each issuing at most one
+# warp instruction per clock.
+ISSUE_PER_SM_PER_CLOCK = 4
 
 
-def issue_roofline(kernel: str, workload: str, launch_ms: float, clocks: dict):
-    """Warp instructions per launch (ncu) over the event-timed launch, against
-    the issue peak at the SM clock seen during the timed region."""
+def issue_roofline(kernel: str, workload: str, launch_ms: float, clocks: dict, sms: int,
+                   gather_bytes: float, hbm_peak: float, hbm_kind: str):
+    """The trace kernel against the limiter that binds it: warp instructions
+    per launch (ncu smsp__inst_executed.sum of one full-size launch) over the
+    event-timed launch, against the issue peak of the device's SMs at the
+    median SM clock sampled during the timed region.  Secondary keys: L1
+    throughput (ncu), DRAM traffic against the HBM peak, and the algorithmic
+    gather bytes per launch (16 texels per sample), which are delivered
+    mostly by L1 and so exceed the HBM peak."""
     e = ncu_counters(kernel, workload)
     inst = e.get("warp_inst_per_launch")
-    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    peak = ISSUE_SLOTS_PER_CLOCK * mhz * 1e6 / 1e9  # G warp instructions / s
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = sms * ISSUE_PER_SM_PER_CLOCK * mhz * 1e6 / 1e9  # G warp instructions / s
+    t = launch_ms / 1e3
+    out = {"bound": "alu", "limiter": "instruction issue", "achieved": None, "peak": peak,
+           "unit": "Gwarp-inst/s", "frac": None, "traffic": None, "kernel": kernel,
+           "peak_source": f"{sms} SMs x {ISSUE_PER_SM_PER_CLOCK} issue slots/clock x "
+                          f"{mhz:.0f} MHz (median SM clock sampled in the timed region)"}
+    gather = {"achieved_gbs": gather_bytes / t / 1e9,
+              "bytes_per_launch": gather_bytes,
+              "of_hbm_peak": gather_bytes / t / 1e9 / hbm_peak,
+              "note": "algorithmic texel bytes (16 texels x texel size per sample + pixel I/O) "
+                      "per event-timed launch; served mostly by L1, so not an HBM figure"}
+    out["gather_delivery"] = gather
     if inst is None:
-        return {"bound": "issue", "achieved": None, "peak": peak, "unit": "Gwarp-inst/s",
-                "frac": None, "kernel": kernel}
-    achieved = inst / (launch_ms / 1e3) / 1e9
-    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
-            "frac": achieved / peak, "kernel": kernel, "warp_inst_per_launch": inst,
-            "peak_source": f"{ISSUE_SLOTS_PER_CLOCK} issue slots/clock x {mhz:.0f} MHz"}
+        return out
+    out.update({"achieved": inst / t / 1e9, "frac": inst / t / 1e9 / peak,
+                "warp_inst_per_launch": inst,
+                "warp_inst_per_sample": e.get("warp_inst_per_sample")})
+    dram = e.get("dram_bytes_per_launch")
+    if dram is not None:
+        out["traffic"] = dram
+        out["dram"] = {"bytes_per_launch": dram, "achieved_gbs": dram / t / 1e9,
+                       "peak_gbs": hbm_peak, "frac": dram / t / 1e9 / hbm_peak,
+                       "peak_source": hbm_kind}
+    if e.get("l1tex_bytes_per_launch") is not None:
+        l1 = e["l1tex_bytes_per_launch"]
+        out["l1"] = {"bytes_per_launch": l1, "achieved_gbs": l1 / t / 1e9,
+                     "ncu_throughput_pct": e.get("l1tex_throughput_pct")}
+    return out
 
 
 class ClockSampler:
@@ -183,27 +209,32 @@ def make_workload(width=1920, height=1080):
     return vs.config_room_1080p(width=width, height=height)
 
 
-def cpu_baseline(cfg, frac=1.0 / 8.0, seed=0):
-    """The FP64 oracle as it stands, on this host's cores: full FP64 mip build
-    plus a seeded pixel subset, extrapolated to one frame."""
-    import oracle
-    scene, view, prm = cfg["scenes"][0], cfg["views"][0], cfg["params"]
-    npx = view["width"] * view["height"]
-    rng = np.random.default_rng(seed)
-    idx = np.sort(rng.choice(npx, int(npx * frac), replace=False))
+def oracle_frame(oracle, scene, view, prm, idx=None):
+    """One step of the workload on the FP64 oracle: mip build of the level-0
+    grid, then the trace of the view's pixels (all, or the listed subset).
+    Returns (seconds, cone samples)."""
     t0 = time.perf_counter()
     O = oracle.build_mips(scene["grid"])
-    t1 = time.perf_counter()
     r = oracle.trace(O, view, prm, idx=idx)
-    t2 = time.perf_counter()
-    samples = int(np.sum(r["steps"]))
-    frame_s = (t1 - t0) + (t2 - t1) / frac
-    return {"value": samples / frac / frame_s / 1e9, "unit": "Gcone-samples/s",
+    return time.perf_counter() - t0, int(np.sum(r["steps"]))
+
+
+def cpu_baseline(cfg, frames=3):
+    """The FP64 oracle as it stands, on this host's cores: whole frames (mip
+    build of the 256^3 grid + trace of all 1920x1080 pixels), median of
+    `frames` runs."""
+    import oracle
+    scene, view, prm = cfg["scenes"][0], cfg["views"][0], cfg["params"]
+    runs = [oracle_frame(oracle, scene, view, prm) for _ in range(frames)]
+    secs = sorted(t for t, _ in runs)
+    frame_s = secs[len(secs) // 2]
+    samples = runs[0][1]
+    return {"value": samples / frame_s / 1e9, "unit": "Gcone-samples/s",
             "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"FP64 mip build of the 256^3 grid ({t1 - t0:.2f} s) + trace of "
-                      f"{len(idx)} seeded pixels ({frac:.3f} of the 1920x1080 frame, "
-                      f"{samples} samples, {t2 - t1:.2f} s), extrapolated to one frame",
-            "frame_s": frame_s}
+            "sample": f"{frames} whole frames (FP64 mip build of the 256^3 grid + trace of all "
+                      f"{view['width']}x{view['height']} pixels, {samples} samples), median "
+                      f"frame {frame_s:.2f} s",
+            "frame_s": frame_s, "frames_s": secs}
 
 
 # ---------------------------------------------------------------------------
@@ -233,6 +264,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     def step(ev=None):
+        if ev is not None:
+            ev[2].record(stream)
         vct.build_mips(level0, out=P)
         if ev is not None:
             ev[0].record(stream)
@@ -253,7 +286,7 @@ def run_ours(args):
                 "height": args.height, "steps": args.steps, "warmup": max(3, args.warmup)}
 
     clocks = ClockSampler(dev.index)
-    tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    tev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3))
            for _ in range(args.steps)]
     e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if ws > 1:
@@ -270,13 +303,15 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     total_ms = e_start.elapsed_time(e_end)
-    trace_ms = [a.elapsed_time(b) for a, b in tev]
+    trace_ms = [a.elapsed_time(b) for a, b, _ in tev]
+    build_ms = [c.elapsed_time(a) for a, _, c in tev]
     if ws > 1:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_step = total_ms / args.steps
     trace_avg = sum(trace_ms) / len(trace_ms)
+    build_avg = sum(build_ms) / len(build_ms)
     value = samples * ws * args.steps / (total_ms / 1e3) / 1e9
 
     # e2e: host buffers, copies inside the timed region
@@ -286,9 +321,13 @@ def run_ours(args):
     if rank == 0:
         hbm, peak_kind = measured_peaks()
         algo_bytes = samples * 16 * TEXEL_BYTES[args.dtype] + hv["width"] * hv["height"] * PIXEL_IO_BYTES
-        achieved = algo_bytes / (trace_avg / 1e3) / 1e9
         workload = f"room{n}_1080p_{args.dtype}"
-        traffic = ncu_traffic("trace_kernel", workload)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        roof = issue_roofline("trace_kernel", workload, trace_avg, clk, sms, algo_bytes, hbm,
+                              peak_kind)
+        # the mip build streams level 0 once and writes the pyramid once
+        tb = TEXEL_BYTES[args.dtype]
+        mip_bytes = n ** 3 * 16 + sum((n >> l) ** 3 for l in range(P.levels)) * tb
         line = {
             "metric": "Gcone-samples/s (256^3 room, 1920x1080, 11 cones/px: mip build + trace)",
             "value": value, "unit": "Gcone-samples/s", "n_gpus": ws, "steps": args.steps,
@@ -302,11 +341,13 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (268 MB level-0 grid, 307 MB pyramid)",
                        "parallelism": f"replica x{ws}"},
             "trace_ms": trace_avg,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": "trace_kernel", "peak_source": peak_kind,
-                         "algorithmic_bytes_per_launch": algo_bytes},
-            "roofline_issue": issue_roofline("trace_kernel", workload, trace_avg, clk),
+            "roofline": roof,
+            "mip_build": {"ms": build_avg, "bytes": mip_bytes,
+                          "achieved_gbs": mip_bytes / (build_avg / 1e3) / 1e9,
+                          "frac_of_hbm_peak": mip_bytes / (build_avg / 1e3) / 1e9 / hbm,
+                          "peak_source": peak_kind,
+                          "note": "level 0 read once (16 B/texel) + the whole pyramid written "
+                                  "once, over the event-timed vct_build_mips"},
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,
@@ -391,6 +432,37 @@ def extra_fp16_single(torch, vct, dev):
     samples = int(sum(vct.read_stats(ws)["samples"]))
     return {"workload": "room256_1080p_f16", "trace_ms": tr_ms, "ms_per_step": step_ms,
             "gsamples_per_s": samples / (step_ms / 1e3) / 1e9, "samples_per_frame": samples}
+
+
+def extra_small(torch, vct, dev):
+    """The 64^3 box scene with 128x128 surface samples (6 x 60 degree diffuse
+    cones + one 10 degree specular cone), pyramid stored FP32 and FP16 (the
+    same scene), each at the accuracy its GPU test asserts against the FP64
+    oracle."""
+    import vct_synth as vs
+    c = vs.config_small_fp32()
+    scene, hv, prm = c["scenes"][0], c["views"][0], c["params"]
+    level0 = torch.from_numpy(scene["grid"]).to(dev)
+    view = vct.View.from_host(hv, device=dev)
+    params = vct.make_params(prm)
+    ws = torch.zeros(256, dtype=torch.uint8, device=dev)
+    out = {"workload": "small64_128x128", "grid": scene["n"],
+           "pixels": hv["width"] * hv["height"]}
+    acc = {"f32": "max floored relative error <= 1e-4 per channel vs the FP64 oracle, whole "
+                  "frame (tests/test_gpu_parity.py::test_small_config_full_frame)",
+           "f16": "every pixel and channel within the binary16-storage bound (2^-11 per texel "
+                  "through lerps and compositing, + 1e-4 floored), mean floored relative error "
+                  "<= 2^-11 (tests/test_gpu_parity.py::test_fp16_storage_error_report)"}
+    for dt in ("f32", "f16"):
+        P = vct.Pyramid(scene["n"], None, dt, device=dev)
+        vct.build_mips(level0, out=P)
+        tr_ms = _time(torch, lambda: vct.trace([P], [view], params, workspace=ws), 50, warm=5)
+        st_ms = _time(torch, lambda: (vct.build_mips(level0, out=P),
+                                      vct.trace([P], [view], params, workspace=ws)), 50, warm=5)
+        samples = int(sum(vct.read_stats(ws)["samples"]))
+        out[dt] = {"trace_ms": tr_ms, "ms_per_step": st_ms, "samples_per_frame": samples,
+                   "gsamples_per_s": samples / (st_ms / 1e3) / 1e9, "accuracy": acc[dt]}
+    return out
 
 
 def extra_variants(torch, vct, dev):
@@ -606,12 +678,20 @@ def extra_fwd_bwd(torch, vct, dev, n=128, n_views=32, res=512):
 
     use_state(False)
     f_ms = _time(torch, fwd, 5)         # the plain forward
+    fbr_ms = _time(torch, fwd_bwd, 5)   # the adjoint re-marches every cone to find its length
     use_state(True)
-    fb_ms = _time(torch, fwd_bwd, 5)    # forward with cone state + adjoint
+    fb_ms = _time(torch, fwd_bwd, 5)    # forward records each cone's length for the adjoint
     fbd_ms = _time(torch, fwd_bwd_det, 3)  # the same with the reproducible adjoint
     samples = int(sum(vct.read_stats(ws)["samples"]))
     return {"workload": f"learnable{n}_{n_views}x{res}^2_f32", "fwd_ms": f_ms, "fwd_bwd_ms": fb_ms,
-            "fwd_bwd_over_fwd": fb_ms / f_ms, "samples_per_fwd": samples,
+            "fwd_bwd_over_fwd": fb_ms / f_ms,
+            "fwd_bwd_mode": "forward stores per cone its sample count and transmittance before "
+                            "the last sample (8 B per cone); the adjoint recomputes every "
+                            "sample from the pyramid (no per-sample state)",
+            "fwd_bwd_recompute_ms": fbr_ms, "fwd_bwd_recompute_over_fwd": fbr_ms / f_ms,
+            "fwd_bwd_recompute_mode": "no state at all: the adjoint marches each cone forwards "
+                                      "to find its length, then walks it back recomputing",
+            "samples_per_fwd": samples,
             "fwd_gsamples_per_s": samples / (f_ms / 1e3) / 1e9,
             "fwd_bwd_deterministic_ms": fbd_ms}
 
@@ -670,9 +750,13 @@ def run_extras(torch, vct, dev, args):
             continue
         try:
             out[name] = fn(torch, vct, dev)
-            torch.cuda.empty_cache()
         except Exception as e:  # report, keep the main line
             out[name] = {"error": f"{type(e).__name__}: {e}"}
+        finally:
+            try:  # release what the measurement cached, even after a failure
+                torch.cuda.empty_cache()
+            except Exception as e:
+                out.setdefault("cache_release_errors", []).append(f"{name}: {e}")
     return out
 
 
@@ -687,7 +771,8 @@ def run_only_extra(args):
 
 
 def _register_extras():
-    for name, fn in (("fp16_single_view", extra_fp16_single), ("variants", extra_variants),
+    for name, fn in (("small_64", extra_small),
+                     ("fp16_single_view", extra_fp16_single), ("variants", extra_variants),
                      ("revoxelize", extra_revoxelize), ("bricks_512", extra_bricks),
                      ("aniso", extra_aniso),
                      ("fwd_bwd", extra_fwd_bwd),
@@ -701,6 +786,14 @@ _register_extras()
 # ---------------------------------------------------------------------------
 # reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
+# Wall-clock budget of the reference arm's warm-up + timed steps, and the
+# FP64 oracle's frame time for this workload on 16 host cores (about 3.1 s):
+# each step is a whole frame while that fits the budget, else a seeded
+# pixel subset of the frame (with the whole mip build) sized to fit it.
+REFERENCE_BUDGET_S = 150.0
+REFERENCE_FRAME_S_EST = 3.2
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -709,33 +802,34 @@ def run_reference(args):
     cfg = make_workload()
     scene, view, prm = cfg["scenes"][0], cfg["views"][0], cfg["params"]
     npx = view["width"] * view["height"]
-    frac = 1.0 / 64.0
-    rng = np.random.default_rng(1)
-    idx = np.sort(rng.choice(npx, int(npx * frac), replace=False))
-    t0 = time.perf_counter()
-    O = oracle.build_mips(scene["grid"])
-    t_mip = time.perf_counter() - t0
-    for _ in range(args.warmup):
-        oracle.trace(O, view, prm, idx=idx)
-    t0 = time.perf_counter()
-    samples = 0
-    for _ in range(args.steps):
-        r = oracle.trace(O, view, prm, idx=idx)
-        samples += int(np.sum(r["steps"]))
-    t_trace = (time.perf_counter() - t0) / args.steps
-    samples //= args.steps
-    frame_s = t_mip + t_trace / frac
-    value = samples / frac / frame_s / 1e9
+    steps, warm = args.steps, max(0, args.warmup)
+    frac = min(1.0, REFERENCE_BUDGET_S / ((steps + warm) * REFERENCE_FRAME_S_EST))
+    idx = None
+    if frac < 1.0:
+        rng = np.random.default_rng(1)
+        idx = np.sort(rng.choice(npx, max(1, int(npx * frac)), replace=False))
+    for _ in range(warm):
+        oracle_frame(oracle, scene, view, prm, idx)
+    total_s, samples = 0.0, 0
+    for _ in range(steps):
+        t, k = oracle_frame(oracle, scene, view, prm, idx)
+        total_s += t
+        samples += k
+    value = samples / total_s / 1e9
+    what = ("a whole frame" if idx is None else
+            f"the FP64 mip build + {len(idx)} seeded pixels ({len(idx) / npx:.4f} of the frame)")
     base = {"kind": "oracle", "cores": oracle.num_threads(), "value": value,
             "unit": "Gcone-samples/s",
-            "sample": f"each step traces {len(idx)} seeded pixels ({frac:.4f} of the frame); "
-                      f"the FP64 mip build ({t_mip:.2f} s, once) is added per frame"}
+            "sample": f"each step is {what}: FP64 mip build of the 256^3 grid + trace; "
+                      f"{samples // steps} cone samples per step"}
     return {"metric": "Gcone-samples/s (256^3 room, 1920x1080, 11 cones/px: mip build + trace)",
-            "value": value, "unit": "Gcone-samples/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": frame_s * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "room256_1080p_f32"}, "impl": "reference",
-            "cpu_baseline": base,
+            "value": value, "unit": "Gcone-samples/s", "n_gpus": ws, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": total_s / steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded box room, raycast G-buffer)",
+            "config": {"workload": "room256_1080p_f32", "samples_per_step": samples // steps,
+                       "pixels_per_step": npx if idx is None else len(idx)},
+            "impl": "reference", "cpu_baseline": base,
             "e2e": {"value": value, "unit": "Gcone-samples/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 

@@ -265,8 +265,10 @@ typedef struct {
   float light_dir[3];    /* unit vector towards the (directional) light      */
   float beta;            /* step factor: t += beta * d (Ch. 4.3.2), > 0      */
   float t0_voxels;       /* first sample at t0 = t0_voxels * h0, > 0         */
-  float normal_offset_voxels; /* apex = x + normal_offset_voxels * h0 * N    */
-  float t_max;           /* the march stops once t > t_max (scene units)     */
+  float normal_offset_voxels; /* apex = x + normal_offset_voxels * h0 * N;
+                                 |normal_offset_voxels| <= 2^19              */
+  float t_max;           /* the march stops once t > t_max (scene units);
+                            t_max * n / size <= 2^20 voxels                  */
   float shadow_str;      /* VCT_FLAG_OCC_SMOOTH strength                     */
   float occ_max_dist;    /* VCT_FLAG_OCC_SMOOTH upper edge (scene units), > 0 */
   float shininess;       /* Phong exponent; angular grace p = 0.008 pi this  */
@@ -437,13 +439,19 @@ vct_status vct_trace_backward_deterministic(const vct_pyramid *pyr, const vct_vi
  * is a packaging variant of the adjoint above, with the same arguments,
  * results and errors except that the scratch comes from the library.
  *   - Scratch: a 5 MiB array in the library's device memory, enough for the
- *     gradient pyramid of any grid up to 64^3.  Every GPU that loads the
- *     library holds it until the process exits.  Larger pyramids are
- *     rejected with VCT_ERR_WORKSPACE (and a message naming the limit).
+ *     gradient pyramid of a dense or bricked grid up to 64^3, or of an
+ *     anisotropic grid up to 32^3 (whose coarse levels hold six volumes).
+ *     Every GPU that loads the library holds it until the process exits.
+ *     Larger pyramids are rejected with VCT_ERR_WORKSPACE; the message gives
+ *     the bytes the pyramid needs, its layout and the limit.
  *   - Allocation: none (no cudaMalloc/cudaFree or allocating library call).
- *   - Set-up: the first call on a device looks the array's device address up
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - Set-up: the array's address differs from one CUDA context to another
+ *     (each device's primary context, contexts the caller creates).  A call
+ *     made outside a stream capture looks the address up in the current
+ *     context (cudaGetSymbolAddress) and keeps it under the context's unique
+ *     ID; a call made while `stream` is being captured uses the address kept
+ *     for the current context, so make one call in a context before
+ *     capturing it there (else VCT_ERR_CUDA).
  *   - Sharing: every call uses the same array and leaves its contents behind;
  *     each call clears what must start at zero.  Calls whose GPU work
  *     overlaps (other streams, other host threads) race on the array.

@@ -159,6 +159,10 @@ vct_status check_params(const vct_trace_params *P, bool backward) {
   if (!(P->beta > 0.0f) || !finite(P->beta) || !(P->t0_voxels > 0.0f) || !finite(P->t0_voxels) ||
       !(P->t_max > 0.0f) || !finite(P->t_max) || !finite(P->normal_offset_voxels))
     return fail(VCT_ERR_INVALID_ARG, "params: beta, t0_voxels, t_max must be > 0 and finite");
+  // with t_max <= 2^20 voxels (checked per pyramid), sample positions stay
+  // within 2^21 voxels of the apex's voxel
+  if (!(fabsf(P->normal_offset_voxels) <= 524288.0f))
+    return fail(VCT_ERR_INVALID_ARG, "params: |normal_offset_voxels| must be <= 2^19");
   return VCT_OK;
 }
 
@@ -305,7 +309,11 @@ int assign_tail_tiles(DevView *v, int nv, int tile_w, int tile_h, int64_t tail_p
   int cursor = 0;
   for (int i = 0; i < nv; ++i) {
     v[i].tile_begin = cursor;
-    cursor += v[i].tiles_x * (v[i].y_split / tile_h);
+    // a view outside the tail keeps all its big-tile rows, the last one
+    // partial when tile_h does not divide its height
+    const int big_rows = v[i].y_split >= v[i].H ? (v[i].H + tile_h - 1) / tile_h
+                                                 : v[i].y_split / tile_h;
+    cursor += v[i].tiles_x * big_rows;
   }
   n_big = cursor;
   for (int i = 0; i < nv; ++i) {

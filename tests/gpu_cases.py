@@ -57,3 +57,48 @@ def room_case(n=64, n_boxes=8, width=203, height=117, seed=7, roughness=True, ma
         view["mask"] = (rng.random(width * height) >= mask_frac).astype(np.uint8)
     prm = vs.params_room9(scene["light"])
     return scene, view, prm
+
+
+def spec_near_ties(view, prm, n, idx, tol=1e-5):
+    """Split the listed pixels into (plain, ties): ties are pixels whose
+    specular cone has a step within `tol` (relative) of t_max, where the
+    float32 march (per-pixel schedule in float32) and the FP64 oracle may
+    legitimately disagree on whether that last step is taken.  The cone's
+    steps are t_k = t0 r^k with r = 1 + 2 beta tan(gamma/2) and the
+    aperture gamma from the pixel's roughness; step k lands on t_max when
+    k = e = log2(t_max / t0) / log2(r)."""
+    idx = np.asarray(idx)
+    if not prm["spec_enable"] or view.get("roughness") is None:
+        return idx, idx[:0]
+    rho = np.asarray(view["roughness"], dtype=np.float64)[idx]
+    rmin = float(prm["roughness_min"])
+    f = np.clip((rho - rmin) / (1.0 - rmin), 0.0, 1.0)
+    g = prm["spec_aperture_min"] + f * (prm["spec_aperture_max"] - prm["spec_aperture_min"])
+    l2r = np.log2(1.0 + 2.0 * prm["beta"] * np.tan(0.5 * g))
+    e = np.log2(prm["t_max"] * n / prm["t0_voxels"]) / l2r
+    dist = np.abs(e - np.round(e)) * l2r * np.log(2.0)
+    tie = dist < tol
+    return idx[~tie], idx[tie]
+
+
+def oracle_with_spec_ties(O, view, prm, idx, gpu_S, tol=1e-5):
+    """The oracle's outputs for the listed pixels, with the specular near-ties
+    of spec_near_ties resolved: for such a pixel S is taken from the oracle
+    run with t_max moved by -2 tol or +2 tol (the near step left out, or
+    taken), whichever is closer to the GPU's S (gpu_S(idx) -> [k, 4]); D and
+    Vis do not depend on it.  The oracle's own step margin over the other
+    pixels must exceed MIN_STEP_MARGIN.  Returns (ref, number of ties)."""
+    plain, ties = spec_near_ties(view, prm, O.n, idx, tol)
+    ref = oracle.trace(O, view, prm, idx=idx)
+    if len(plain):
+        r0 = oracle.trace(O, view, prm, idx=plain)
+        assert r0["margin"] > MIN_STEP_MARGIN, r0["margin"]
+    if len(ties):
+        pos = np.searchsorted(idx, ties)
+        assert np.array_equal(np.asarray(idx)[pos], ties)
+        lo = oracle.trace(O, view, dict(prm, t_max=prm["t_max"] * (1 - 2 * tol)), idx=ties)
+        hi = oracle.trace(O, view, dict(prm, t_max=prm["t_max"] * (1 + 2 * tol)), idx=ties)
+        g = np.asarray(gpu_S(ties), dtype=np.float64).reshape(-1, 4)
+        use_hi = np.abs(g - hi["S"]).max(axis=1) < np.abs(g - lo["S"]).max(axis=1)
+        ref["S"][pos] = np.where(use_hi[:, None], hi["S"], lo["S"])
+    return ref, len(ties)

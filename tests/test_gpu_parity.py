@@ -8,9 +8,10 @@ import torch
 import oracle
 import paper_2104_00618_gb300 as vct
 import vct_synth as vs
-from gpu_cases import (FP32_BOUND, MIN_STEP_MARGIN, compare, gpu_pyramid, gpu_trace, room_case,
+from gpu_cases import (FP32_BOUND, MIN_STEP_MARGIN, compare, gpu_pyramid, gpu_trace,
+                       oracle_with_spec_ties, room_case,
                        worst)
-from metrics import report
+from metrics import U16, check_fp16_outputs, report
 
 pytestmark = pytest.mark.gpu
 
@@ -162,19 +163,24 @@ def test_room_1080p_full_size_sampled():
 
 def test_fp16_storage_error_report():
     """Same scene as the small config with the pyramid stored in binary16;
-    compositing stays float32.  No bound is set for this variant: the
-    measured error is reported and sanity-checked."""
+    compositing stays float32.  Every output channel of every pixel lies
+    within the binary16-storage bound (tests/metrics.py: one rounding of
+    2^-11 per texel carried through the convex lerps and the compositing,
+    plus the float32 path's own 1e-4), and the mean floored relative error
+    stays below 2^-11."""
     c = vs.config_small_fp32()
     prm = dict(c["params"], occ_enable=1)
     view = c["views"][0]
-    P = gpu_pyramid(c["scenes"][0]["grid"], dtype="f16")
-    O = oracle.build_mips(c["scenes"][0]["grid"])
+    grid = c["scenes"][0]["grid"]
+    P = gpu_pyramid(grid, dtype="f16")
+    O = oracle.build_mips(grid)
     (out,), _ = gpu_trace([P], [view], prm)
     ref = oracle.trace(O, view, prm)
-    res = compare(out, ref, prm=prm)
-    print("fp16 storage errors (max, mean):", {k: (v[0].tolist(), v[1].tolist()) for k, v in res.items()})
-    assert worst(res) < 5e-2
-    assert max(float(v[1].max()) for v in res.values()) < 5e-3
+    c_max = grid[..., :3].reshape(-1, 3).max(axis=0)
+    ratio, res = check_fp16_outputs(out, ref, c_max, k_max=150)
+    print("fp16 storage errors (max, mean):", {k: (v[0].tolist(), v[1].tolist()) for k, v in res.items()},
+          "worst |err| / bound:", ratio)
+    assert max(float(v[1].max()) for v in res.values()) <= U16
 
 
 def test_batched_views_over_several_pyramids():
@@ -194,6 +200,29 @@ def test_batched_views_over_several_pyramids():
         ref = oracle.trace(O, v, prm)
         res = compare(out, ref, prm=prm)
         assert worst(res) <= FP32_BOUND, res
+
+
+@pytest.mark.parametrize("tile", [(8, 16), (16, 16), (4, 8)])
+def test_multi_view_partial_tile_rows(tile):
+    """Views whose height the tile height does not divide, large enough that
+    the first ones lie outside the launch's small-tile tail: every pixel is
+    traced (one specular cone each) and matches the oracle, including the
+    last, partial row of tiles of each view."""
+    scene = vs.box_scene(32, 6, 12, room=True)
+    rng = np.random.default_rng(13)
+    hv = [vs.interior_view(scene, 500, h, rng) for h in (333, 301, 250, 77)]
+    prm = vs.params_room9(scene["light"])
+    P = gpu_pyramid(scene["grid"])
+    outs, stats = gpu_trace([P], hv, prm, cfg=vct.launch_config(*tile, 1))
+    assert stats["cones"][1] == sum(v["width"] * v["height"] for v in hv)
+    O = oracle.build_mips(scene["grid"])
+    for v, out in zip(hv, outs):
+        W, H = v["width"], v["height"]
+        last_rows = np.arange((H - H % tile[1] if H % tile[1] else H - tile[1]) * W, H * W)
+        idx = np.unique(np.concatenate([rng.choice(W * H, 500, replace=False),
+                                        last_rows[::7]]))
+        ref, _ = oracle_with_spec_ties(O, v, prm, idx, lambda ii: out[1][ii])
+        assert worst(compare(out, ref, idx=idx, prm=prm)) <= FP32_BOUND
 
 
 def test_null_outputs_and_no_specular():
@@ -398,13 +427,15 @@ def test_autotune_then_graph_replay_matches_direct_call():
 def test_batched_fp16_pyramids_against_oracle():
     scenes, hv, prm, pyrs = _batch("f16")
     outs, _ = gpu_trace(pyrs, hv, prm)
-    worst_fp16 = 0.0
+    worst_fp16, worst_ratio = 0.0, 0.0
     for v, out in zip(hv, outs):
-        ref = oracle.trace(oracle.build_mips(scenes[v["pyramid"]]["grid"]), v, prm)
-        res = compare(out, ref, prm=prm)
+        grid = scenes[v["pyramid"]]["grid"]
+        ref = oracle.trace(oracle.build_mips(grid), v, prm)
+        ratio, res = check_fp16_outputs(out, ref, grid[..., :3].reshape(-1, 3).max(axis=0),
+                                        k_max=150)
+        worst_ratio = max(worst_ratio, ratio)
         worst_fp16 = max(worst_fp16, worst(res))
-    print("batched fp16 worst floored rel error:", worst_fp16)
-    assert worst_fp16 < 5e-2
+    print("batched fp16 worst floored rel error:", worst_fp16, "worst |err| / bound:", worst_ratio)
 
 
 def test_backward_with_cone_state_matches_recomputed_march():
