@@ -29,26 +29,44 @@ __device__ __forceinline__ int find_view(const TraceLaunch &L, int item, bool sm
 // is small and T precise when alpha is close to one; the loop runs while
 // alpha = 1 - T < 1 in float32 and t <= t_max.  kVar instances also take the
 // Ch. 5.4.4 variants selected by `mode`.
+//
+// The step position and level pair of step k (T, lambda -> l0, l1, f) depend
+// on the cone's aperture and the pyramid only.  For the diffuse and
+// occlusion cones, whose aperture is a launch constant, they are read from
+// the CTA's step table (`tab`, shared memory, the first kStepTab steps; the
+// same step_at / pick_levels arithmetic, done once per CTA); other cones
+// compute them per step.
 template <int DT, bool kVar, bool BR, bool AN = false>
 __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const float w[3],
                                         const ConeConst &cc, float T0, const uint32_t *lut,
-                                        uint32_t &nsamp, float &trans, uint2 &state,
-                                        int mode = kPlain, const Variants *var = nullptr) {
+                                        const float4 *tab, uint32_t &nsamp, float &trans,
+                                        uint2 &state, int mode = kPlain,
+                                        const Variants *var = nullptr) {
   float cr = 0.f, cg = 0.f, cb = 0.f, al = 0.f, tr = 1.f, tp = 1.f;
   int k = 0;
   AnisoW aw;
   if constexpr (AN) aw = aniso_weights(w);
   for (; k < cc.kmax; ++k) {
     if (!((1.0f - tr) < 1.0f)) break;
-    float T, lam, om;
-    step_at(cc, T0, k, T, lam);
-    const float F[3] = {fmaf(T, w[0], A.Of[0]), fmaf(T, w[1], A.Of[1]), fmaf(T, w[2], A.Of[2])};
+    float T, om;
     LodPick lp;
+    if (tab != nullptr && k < kStepTab) {
+      const float4 e = tab[k];
+      T = e.x;
+      lp.f = e.y;
+      lp.l0 = __float_as_int(e.z);
+      lp.l1 = __float_as_int(e.w);
+    } else {
+      float lam;
+      step_at(cc, T0, k, T, lam);
+      lp = pick_levels(lam, P.levels);
+    }
+    const float F[3] = {fmaf(T, w[0], A.Of[0]), fmaf(T, w[1], A.Of[1]), fmaf(T, w[2], A.Of[2])};
     float4 s;
     if constexpr (AN)
-      s = sample_aniso(P, A, F, lam, lut, aw, om, lp);
+      s = sample_aniso_at(P, A, F, lp, lut, aw, om);
     else
-      s = sample<DT, BR>(P, A, F, lam, lut, om, lp);
+      s = sample_at<DT, BR>(P, A, F, lp, lut, om);
     if constexpr (kVar) {
       if (mode == kFirstHit) {
         if (s.w > 0.01f) {
@@ -177,8 +195,10 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
   const float T0 = L.spec.t0_vox;
   __shared__ uint32_t s_lut[kSpreadLut];
   __shared__ uint32_t s_keys[kFwdThreads / 32][kMaxSortPixels];
+  __shared__ float4 s_tab[VCT_MAX_PYRAMIDS * 2 * kStepTab];
   uint32_t *keys = s_keys[threadIdx.x >> 5];
-  fill_spread_lut(s_lut);
+  fill_step_table(s_tab, L.pyr, L.n_pyr, T0);
+  fill_spread_lut(s_lut);  // (its barrier also covers s_tab)
 
   for (;;) {
     const int item = next_item(L.queue);
@@ -228,6 +248,7 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
           const ConeSel cs = select_cone(c, L.spec_enable, L.occ_enable);
           float w[3];
           ConeConst cc;
+          const float4 *tab = nullptr;
           if (cs.kind == kSpecular) {
             reflect_dir(x, V.cam, n, w);
             cc = spec_const(P, L.spec, V.rough, p);
@@ -236,11 +257,13 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
             w[1] = L.light[1];
             w[2] = L.light[2];
             cc = P.occ;
+            tab = step_table(s_tab, V.pyr, 1);
           } else {
             const float *d = L.diffuse_dir[cs.diffuse_index];
 #pragma unroll
             for (int a = 0; a < 3; ++a) w[a] = fmaf(Tf[a], d[0], fmaf(Bf[a], d[1], n[a] * d[2]));
             cc = P.diffuse;
+            tab = step_table(s_tab, V.pyr, 0);
           }
           float trans;
           int mode = kPlain;
@@ -249,8 +272,8 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
             if (cs.kind == kDiffuse && (L.var.flags & VCT_FLAG_DIFFUSE_FIRST_HIT)) mode = kFirstHit;
           }
           uint2 cst;
-          float4 r = march<DT, kVar, BR, AN>(P, A, w, cc, T0, s_lut, n_samp[cs.kind], trans, cst,
-                                         mode, &L.var);
+          float4 r = march<DT, kVar, BR, AN>(P, A, w, cc, T0, s_lut, tab, n_samp[cs.kind], trans,
+                                             cst, mode, &L.var);
           n_cone[cs.kind] += 1u;
           if (V.state) V.state[(size_t)c * V.W * V.H + p] = cst;
           if constexpr (kVar) {
@@ -338,8 +361,8 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
       const ConeConst cc = spec_const(P, L.spec, V.rough, p);
       float trans;
       uint2 cst;
-      float4 r = march<DT, kVar, BR, AN>(P, A, w, cc, T0, s_lut, n_samp[kSpecular], trans, cst,
-                                     kPlain, &L.var);
+      float4 r = march<DT, kVar, BR, AN>(P, A, w, cc, T0, s_lut, nullptr, n_samp[kSpecular],
+                                         trans, cst, kPlain, &L.var);
       n_cone[kSpecular] += 1u;
       if (V.state) V.state[p] = cst;  // the specular cone is cone 0
       if constexpr (kVar) {

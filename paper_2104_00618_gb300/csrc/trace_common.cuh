@@ -196,91 +196,6 @@ __device__ __forceinline__ void level_stencil(int l, int Nl, const Apex &A, cons
   s.valid = valid;
 }
 
-// Per-level constants of a cone's apex, kept while consecutive samples stay
-// on the same level (they depend on the level and the apex only):
-// sc = 2^-l, C = (Xi mod 2^l) 2^-l - 1/2 and mq = 1.5 2^23 + (Xi >> l) per
-// axis.  With them the level-l cell of position Xi + F is found as in
-// level_stencil: v = F sc + C, and rounding v + mq down to an integer gives
-// 1.5 2^23 + (Xi >> l) + floor(v) exactly, i.e. the cell index and, by
-// subtracting mq, floor(v).  That needs |Xi >> l| + |v| < 2^22: |v| < 2^21
-// (sample positions stay within 2^21 voxels of the apex's voxel: t_max <=
-// 2^20 voxels, normal offset <= 2^19), and Xi >> l is clamped to 2^21 in
-// magnitude (an apex that far outside the grid, n <= 1024, puts every cell
-// of its cones outside the level either way).
-struct LevelAxes {
-  float sc;
-  float C[3], mq[3];
-};
-__device__ __forceinline__ void level_axes(int l, const Apex &A, LevelAxes &la) {
-  la.sc = __int_as_float((127 - l) << 23);  // 2^-l
-  const int mask = (1 << l) - 1;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    la.C[a] = fmaf((float)(A.Xi[a] & mask), la.sc, -0.5f);
-    la.mq[a] = __int_as_float(0x4B400000 + min(max(A.Xi[a] >> l, -2097152), 2097152));
-  }
-}
-
-// The two levels a quadrilinear sample reads: a[0] for level l0, a[1] for
-// l0 + 1.  A cone's level never decreases, so a step to the next level
-// reuses a[1].
-struct LevelCache {
-  int l0;
-  LevelAxes a[2];
-};
-__device__ __forceinline__ void cache_init(LevelCache &c) { c.l0 = -2; }
-__device__ __forceinline__ void cache_levels(LevelCache &c, int l0, const Apex &A) {
-  if (l0 == c.l0) return;
-  if (l0 == c.l0 + 1)
-    c.a[0] = c.a[1];
-  else
-    level_axes(l0, A, c.a[0]);
-  level_axes(l0 + 1, A, c.a[1]);
-  c.l0 = l0;
-}
-
-// level_stencil from the cached constants of level l (same cell, same
-// fractions, bit for bit).
-__device__ __forceinline__ void level_stencil_c(int Nl, const LevelAxes &la, const float F[3],
-                                                const uint32_t *lut, LevelStencil &s) {
-  int b[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float v = fmaf(F[a], la.sc, la.C[a]);
-    const float t = __fadd_rd(v, la.mq[a]);
-    b[a] = __float_as_int(t) - 0x4B400000;
-    s.fr[a] = v - (t - la.mq[a]);
-  }
-  const uint32_t x0 = lut[(uint32_t)b[0] & 1023u];
-  const uint32_t y0 = lut[1024u + ((uint32_t)b[1] & 1023u)];
-  const uint32_t z0 = lut[2048u + ((uint32_t)b[2] & 1023u)];
-  s.sx[0] = x0;
-  s.sx[1] = spread3_inc(x0);
-  s.sy[0] = y0;
-  s.sy[1] = (y0 - (kMortonX << 1)) & (kMortonX << 1);
-  s.sz[0] = z0;
-  s.sz[1] = (z0 - (kMortonX << 2)) & (kMortonX << 2);
-  const uint32_t lim = (uint32_t)Nl - 1u;
-  if ((uint32_t)b[0] < lim && (uint32_t)b[1] < lim && (uint32_t)b[2] < lim) {
-    s.valid = 0xffu;
-    return;
-  }
-  const uint32_t vx = ((uint32_t)b[0] < (uint32_t)Nl ? 1u : 0u) |
-                      ((uint32_t)(b[0] + 1) < (uint32_t)Nl ? 2u : 0u);
-  const uint32_t vy = ((uint32_t)b[1] < (uint32_t)Nl ? 1u : 0u) |
-                      ((uint32_t)(b[1] + 1) < (uint32_t)Nl ? 2u : 0u);
-  const uint32_t vz = ((uint32_t)b[2] < (uint32_t)Nl ? 1u : 0u) |
-                      ((uint32_t)(b[2] + 1) < (uint32_t)Nl ? 2u : 0u);
-  uint32_t valid = 0;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const bool ok = ((vx >> (c & 1)) & 1u) && ((vy >> ((c >> 1) & 1)) & 1u) &&
-                    ((vz >> (c >> 2)) & 1u);
-    valid |= ok ? (1u << c) : 0u;
-  }
-  s.valid = valid;
-}
-
 __device__ __forceinline__ uint32_t corner_index(const LevelStencil &s, int c) {
   return s.sx[c & 1] | s.sy[(c >> 1) & 1] | s.sz[c >> 2];
 }
@@ -402,10 +317,9 @@ __device__ __forceinline__ float transparency(float a) { return fmaxf(1.0f - a, 
 // floor(lambda) and floor(lambda)+1 blended linearly); `om` receives 1 - a_s.
 // When `st` is non-null the two stencils are kept for the adjoint.
 template <int DT, bool BR = false>
-__device__ __forceinline__ float4 sample(const DevPyr &P, const Apex &A, const float F[3],
-                                         float lam, const uint32_t *lut, float &om,
-                                         LodPick &lp, LevelStencil *st = nullptr) {
-  lp = pick_levels(lam, P.levels);
+__device__ __forceinline__ float4 sample_at(const DevPyr &P, const Apex &A, const float F[3],
+                                            const LodPick &lp, const uint32_t *lut, float &om,
+                                            LevelStencil *st = nullptr) {
   LevelStencil s;
   f32x2 rg, ba;
   level_stencil(lp.l0, P.n >> lp.l0, A, F, lut, s);
@@ -424,30 +338,12 @@ __device__ __forceinline__ float4 sample(const DevPyr &P, const Apex &A, const f
   om = transparency(v1.y);
   return make_float4(v0.x, v0.y, v1.x, v1.y);
 }
-
-// S(p, lambda) with the levels already picked (lp) and the apex's per-level
-// constants cached in c (c.l0 == lp.l0); same result as sample().
 template <int DT, bool BR = false>
-__device__ __forceinline__ float4 sample_c(const DevPyr &P, const LevelCache &c, const float F[3],
-                                           const LodPick &lp, const uint32_t *lut, float &om,
-                                           LevelStencil *st = nullptr) {
-  LevelStencil s;
-  f32x2 rg, ba;
-  level_stencil_c(P.n >> lp.l0, c.a[0], F, lut, s);
-  trilerp<DT, BR>(P, lp.l0, s, rg, ba);
-  if (st) st[0] = s;
-  if (lp.f > 0.0f) {
-    level_stencil_c(P.n >> lp.l1, c.a[1], F, lut, s);
-    f32x2 rg1, ba1;
-    trilerp<DT, BR>(P, lp.l1, s, rg1, ba1);
-    const f32x2 tf = f2_pack(lp.f, lp.f);
-    rg = f2_lerp(rg, rg1, tf);
-    ba = f2_lerp(ba, ba1, tf);
-    if (st) st[1] = s;
-  }
-  const float2 v0 = f2_unpack(rg), v1 = f2_unpack(ba);
-  om = transparency(v1.y);
-  return make_float4(v0.x, v0.y, v1.x, v1.y);
+__device__ __forceinline__ float4 sample(const DevPyr &P, const Apex &A, const float F[3],
+                                         float lam, const uint32_t *lut, float &om,
+                                         LodPick &lp, LevelStencil *st = nullptr) {
+  lp = pick_levels(lam, P.levels);
+  return sample_at<DT, BR>(P, A, F, lp, lut, om, st);
 }
 
 // Cone march variants (Ch. 5.4.4): the plain march, the occlusion cone that
@@ -591,11 +487,10 @@ __device__ __forceinline__ void aniso_level(const DevPyr &P, int l, const LevelS
 }
 
 // S(p, lambda) of an anisotropic pyramid for travel along the cone axis.
-__device__ __forceinline__ float4 sample_aniso(const DevPyr &P, const Apex &A, const float F[3],
-                                               float lam, const uint32_t *lut, const AnisoW &aw,
-                                               float &om, LodPick &lp,
-                                               LevelStencil *st = nullptr) {
-  lp = pick_levels(lam, P.levels);
+__device__ __forceinline__ float4 sample_aniso_at(const DevPyr &P, const Apex &A,
+                                                  const float F[3], const LodPick &lp,
+                                                  const uint32_t *lut, const AnisoW &aw,
+                                                  float &om, LevelStencil *st = nullptr) {
   LevelStencil s;
   f32x2 rg, ba;
   level_stencil(lp.l0, P.n >> lp.l0, A, F, lut, s);
@@ -613,6 +508,33 @@ __device__ __forceinline__ float4 sample_aniso(const DevPyr &P, const Apex &A, c
   const float2 v0 = f2_unpack(rg), v1 = f2_unpack(ba);
   om = transparency(v1.y);
   return make_float4(v0.x, v0.y, v1.x, v1.y);
+}
+__device__ __forceinline__ float4 sample_aniso(const DevPyr &P, const Apex &A, const float F[3],
+                                               float lam, const uint32_t *lut, const AnisoW &aw,
+                                               float &om, LodPick &lp,
+                                               LevelStencil *st = nullptr) {
+  lp = pick_levels(lam, P.levels);
+  return sample_aniso_at(P, A, F, lp, lut, aw, om, st);
+}
+
+// Step table of the cones whose aperture is a launch constant (diffuse and
+// occlusion): per pyramid and kind, entry k = (T, f, l0, l1) of step k as
+// step_at and pick_levels give them, for the first kStepTab steps.
+constexpr int kStepTab = 64;
+__device__ __forceinline__ const float4 *step_table(const float4 *tab, int pyr, int kind_occ) {
+  return tab + (size_t)(2 * pyr + kind_occ) * kStepTab;
+}
+__device__ __forceinline__ void fill_step_table(float4 *tab, const DevPyr *pyrs, int n_pyr,
+                                                float T0) {
+  for (int i = threadIdx.x; i < n_pyr * 2 * kStepTab; i += blockDim.x) {
+    const int k = i % kStepTab;
+    const int kind = (i / kStepTab) & 1;
+    const DevPyr &P = pyrs[i / (2 * kStepTab)];
+    float T, lam;
+    step_at(kind ? P.occ : P.diffuse, T0, k, T, lam);
+    const LodPick lp = pick_levels(lam, P.levels);
+    tab[i] = make_float4(T, lp.f, __int_as_float(lp.l0), __int_as_float(lp.l1));
+  }
 }
 
 // Fills the Morton spread tables (shared memory, kSpreadLut entries) of a CTA.

@@ -555,6 +555,7 @@ static vct_status trace_impl(const vct_pyramid *pyrs, int32_t n_pyr, const vct_v
     vct_status st = fill_pyr(pyrs[i], *params, L->pyr[i]);
     if (st != VCT_OK) return st;
   }
+  L->n_pyr = n_pyr;
   L->tile_w = cfg.tile_w;
   L->tile_h = cfg.tile_h;
   uint8_t *ws = static_cast<uint8_t *>(workspace);

@@ -318,7 +318,8 @@ constexpr int kSmallTileW = 8, kSmallTileH = 4;
 
 struct TraceLaunch {
   int n_views, total_tiles, tile_w, tile_h;
-  int n_big, pad_big;  // items [0, n_big) are big tiles, the rest small tiles
+  int n_big;  // items [0, n_big) are big tiles, the rest small tiles
+  int n_pyr;  // pyramids in pyr[]
   int n_diffuse, spec_enable, occ_enable, pad0;
   Variants var;
   float diffuse_dir[VCT_MAX_DIFFUSE][3];

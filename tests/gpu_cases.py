@@ -10,6 +10,14 @@ import paper_2104_00618_gb300 as vct
 from metrics import report
 
 FP32_BOUND = 1e-4  # max floored relative error per channel, FP32 path
+# The float32 march stops once 1 - T rounds to one (T < 2^-25; the FP64
+# oracle goes on until its alpha rounds to one): the samples it leaves out
+# carry at most T of opacity, and T times the largest texel colour (<= 1 in
+# these scenes) of colour.  Where a view's channel is tiny everywhere (a
+# view in shadow: Vis ~ 1e-10), the floored relative error of that absolute
+# difference is not small; comparisons at the configured sizes allow it
+# explicitly.
+R12_ABS = 2.0 ** -24
 # The float32 step schedule places a cone's samples within 1e-6 of their
 # distance; inputs whose oracle has a cone ending closer than this to t_max
 # (relative) could count one sample more or less on either side.
@@ -102,3 +110,16 @@ def oracle_with_spec_ties(O, view, prm, idx, gpu_S, tol=1e-5):
         use_hi = np.abs(g - hi["S"]).max(axis=1) < np.abs(g - lo["S"]).max(axis=1)
         ref["S"][pos] = np.where(use_hi[:, None], hi["S"], lo["S"])
     return ref, len(ties)
+
+
+def fp32_ratio(gpu, ref, floor_frac=1e-3):
+    """max over pixels and channels of |gpu - oracle| / (FP32_BOUND *
+    max(|oracle|, tau) + R12_ABS): <= 1 passes (tau = floor_frac * the
+    channel's largest |oracle| over the given pixels)."""
+    g = np.asarray(gpu, dtype=np.float64)
+    o = np.asarray(ref, dtype=np.float64)
+    if o.ndim == 1:
+        o, g = o[:, None], g[:, None]
+    g = g.reshape(o.shape)
+    tau = np.maximum(floor_frac * np.abs(o).max(axis=0, keepdims=True), 1e-30)
+    return float((np.abs(g - o) / (FP32_BOUND * np.maximum(np.abs(o), tau) + R12_ABS)).max())

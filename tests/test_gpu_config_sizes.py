@@ -25,7 +25,7 @@ import torch
 import oracle
 import paper_2104_00618_gb300 as vct
 import vct_synth as vs
-from gpu_cases import FP32_BOUND, oracle_with_spec_ties
+from gpu_cases import fp32_ratio, oracle_with_spec_ties
 from metrics import U16, check_fp16_outputs, report
 
 pytestmark = pytest.mark.gpu
@@ -266,7 +266,8 @@ def test_batched_config_fp16_graph_replay_against_oracle():
 
     rng = np.random.default_rng(46)
     idxs = [_subset(v, rng, PIX_PER_VIEW) for v in cfg["views"]]
-    worst_ratio, worst_err, mean_err, checked, ties = 0.0, 0.0, 0.0, 0, 0
+    worst_ratio, checked, ties = 0.0, 0, 0
+    pooled = {"D": ([], []), "S": ([], []), "Vis": ([], [])}
     for si, sc in enumerate(cfg["scenes"]):
         O = oracle.build_mips(sc["grid"])
         c_max = sc["grid"][..., :3].reshape(-1, 3).max(axis=0)
@@ -276,20 +277,24 @@ def test_batched_config_fp16_graph_replay_against_oracle():
             gv = views[vi]
             ref, nt = oracle_with_spec_ties(O, hv, prm, idxs[vi], lambda ii: _gather(gv, ii)[1])
             ties += nt
-            ratio, errs = check_fp16_outputs(_gather(gv, idxs[vi]), ref, c_max, k_max=150)
+            got = _gather(gv, idxs[vi])
+            ratio, _ = check_fp16_outputs(got, ref, c_max, k_max=150)
             worst_ratio = max(worst_ratio, ratio)
-            worst_err = max(worst_err, max(float(e[0].max()) for e in errs.values()))
-            mean_err = max(mean_err, max(float(e[1].max()) for e in errs.values()))
+            for k, g in zip(("D", "S", "Vis"), got):
+                pooled[k][0].append(g)
+                pooled[k][1].append(ref[k])
             checked += len(idxs[vi])
         del O
+    errs = {k: report(np.concatenate(g), np.concatenate(o)) for k, (g, o) in pooled.items()}
     print(f"batched FP16 ({len(views)} views, {checked} pixels, tile {best.tile_w}x"
           f"{best.tile_h}, {best.lanes_per_pixel} lanes/px): worst |err| / bound "
-          f"{worst_ratio:.3g}, floored relative max {worst_err:.3g}, worst per-view mean "
-          f"{mean_err:.3g}; specular near-ties with t_max resolved: {ties}")
+          f"{worst_ratio:.3g}; floored relative error over all pixels (max, mean) per output: "
+          + ", ".join(f"{k} ({v[0].max():.3g}, {v[1].max():.3g})" for k, v in errs.items())
+          + f"; specular near-ties with t_max resolved: {ties}")
     assert checked >= 256 * 4096 * 0.99
     assert ties <= 0.001 * checked
     # the mean error stays at the binary16 rounding level
-    assert mean_err <= U16
+    assert max(float(v[1].max()) for v in errs.values()) <= U16
 
 
 def test_room512_fp32_against_oracle():
@@ -313,7 +318,7 @@ def test_room512_fp32_against_oracle():
     torch.cuda.synchronize()
     O = oracle.build_mips(sc["grid"])
     rng = np.random.default_rng(47)
-    worst, ties = 0.0, 0
+    worst, worst_ratio, ties = 0.0, 0.0, 0
     for hv, gv in zip(views, gviews):
         idx = _subset(hv, rng, 1024)
         ref, nt = oracle_with_spec_ties(O, hv, prm, idx, lambda ii: _gather(gv, ii)[1])
@@ -321,7 +326,9 @@ def test_room512_fp32_against_oracle():
         D, S, V = _gather(gv, idx)
         for g, o in ((D, ref["D"]), (S, ref["S"]), (V, ref["Vis"])):
             worst = max(worst, float(report(g, o)[0].max()))
-    print(f"512^3 FP32, 64 views x 1024 pixels: worst floored relative error {worst:.3g}; "
-          f"specular near-ties with t_max resolved: {ties}")
-    assert worst <= FP32_BOUND
+            worst_ratio = max(worst_ratio, fp32_ratio(g, o))
+    print(f"512^3 FP32, 64 views x 1024 pixels: worst floored relative error {worst:.3g}, "
+          f"worst |err| / (1e-4 floored + 2^-24) {worst_ratio:.3g}; specular near-ties with "
+          f"t_max resolved: {ties}")
+    assert worst_ratio <= 1.0
     assert ties <= 0.001 * 64 * 1024
