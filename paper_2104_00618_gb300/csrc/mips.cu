@@ -256,6 +256,118 @@ __global__ void __launch_bounds__(256) pack_mips_kernel(const __grid_constant__ 
   if (threadIdx.x == 0) bulk_wait_all();
 }
 
+// ---------------------------------------------------------------------------
+// dense float32 pyramids, n >= 32: levels 0 and 1 by streaming the grid in
+// rows, then levels 2.. by CTA-sized groups of the (L2-resident) level 1
+// ---------------------------------------------------------------------------
+// 32-byte loads of the dense grid (read once: not kept in L1, first out of
+// L2) and 32-byte stores (one whole sector each).
+__device__ __forceinline__ void ld_stream_32(const float4 *p, float4 &a, float4 &b) {
+  asm volatile(
+      "ld.global.nc.L1::no_allocate.L2::evict_first.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, "
+      "[%8];"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(p));
+}
+__device__ __forceinline__ void st_stream_32(float4 *p, float4 a, float4 b) {
+  asm volatile("st.global.L2::evict_first.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p),
+               "f"(a.x), "f"(a.y), "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+               : "memory");
+}
+__device__ __forceinline__ void ld_32(const float4 *p, float4 &a, float4 &b) {
+  asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z),
+                 "=f"(b.w)
+               : "l"(p));
+}
+
+// One thread per level-1 texel (cell cx, cy, cz; cx fastest, so a warp reads
+// whole rows): its 8 children as four 32-byte x pairs, written to level 0 at
+// Morton codes 8 code .. 8 code + 7 (child j = jx | jy << 1 | jz << 2, the
+// x pairs contiguous) and their mean to level 1 (neighbouring threads fill
+// whole sectors).  The mean adds the children in the order the TMA pack
+// kernel does for the same cell (starting at child (cy & 1) | (cx & 3) << 1),
+// so both paths give the same bits.
+__global__ void __launch_bounds__(256) stream_level01_kernel(const float4 *__restrict__ dense,
+                                                             float4 *lvl0, float4 *lvl1, int n,
+                                                             int write1) {
+  const uint32_t m = (uint32_t)n >> 1;
+  const uint64_t cells = (uint64_t)m * m * m;
+  const uint64_t texels0 = 8 * cells;
+  for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < cells;
+       c += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t cx = (uint32_t)(c % m), cy = (uint32_t)((c / m) % m),
+                   cz = (uint32_t)(c / ((uint64_t)m * m));
+    float4 r[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {  // q = jy | jz << 1
+      const uint64_t y = 2 * cy + (q & 1), z = 2 * cz + (q >> 1);
+      ld_stream_32(dense + (z * n + y) * n + 2 * cx, r[2 * q], r[2 * q + 1]);
+    }
+    const uint32_t code = morton3(cx, cy, cz);
+    if (in_bounds(8 * (uint64_t)code + 7, texels0, kOobMip)) {
+      float4 *dst = lvl0 + 8 * (uint64_t)code;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) st_stream_32(dst + 2 * q, r[2 * q], r[2 * q + 1]);
+    }
+    if (!write1) continue;
+    // rotate so that t[i] = r[(i + rot) & 7], then add in order
+    const int rot = (int)((cy & 1u) | ((cx & 3u) << 1));
+    float4 t[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t[i] = (rot & 1) ? r[(i + 1) & 7] : r[i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r[i] = (rot & 2) ? t[(i + 2) & 7] : t[i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t[i] = (rot & 4) ? r[(i + 4) & 7] : r[i];
+    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sum = add4(sum, t[i]);
+    if (in_bounds(code, cells, kOobMip)) lvl1[code] = mul4(sum, 0.125f);
+  }
+}
+
+// Levels s+1 .. s+k of a dense float32 pyramid from level s, one CTA per
+// group of 8^k consecutive level-s texels (Morton order: a 2^k cube); the
+// children of texel j are 8j .. 8j+7.  Levels above the first are reduced in
+// shared memory.
+constexpr int kGroupLevels = 4;  // 4096 source texels per CTA
+struct GroupArgs {
+  const float4 *src;
+  float4 *dst[kGroupLevels];
+  uint64_t dst_texels[kGroupLevels];
+  int k;
+};
+__global__ void __launch_bounds__(256) mip_group_kernel(const __grid_constant__ GroupArgs a) {
+  __shared__ float4 sm[512 + 64 + 8 + 1];
+  const int first = 1 << (3 * (a.k - 1));  // texels of level s+1 per group
+  const uint64_t g = blockIdx.x;
+  float4 *cur = sm;
+  for (int j = threadIdx.x; j < first; j += blockDim.x) {
+    const uint64_t o = g * first + j;
+    float4 ch[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ld_32(a.src + 8 * o + 2 * q, ch[2 * q], ch[2 * q + 1]);
+    const float4 v = mean8(ch);
+    if (in_bounds(o, a.dst_texels[0], kOobMip)) a.dst[0][o] = v;
+    cur[j] = v;
+  }
+  int cnt = first;
+  for (int l = 1; l < a.k; ++l) {
+    __syncthreads();
+    float4 *nxt = cur + cnt;
+    const int nc = cnt / 8;
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+      const float4 v = mean8(cur + 8 * j);
+      nxt[j] = v;
+      const uint64_t o = g * nc + j;
+      if (in_bounds(o, a.dst_texels[l], kOobMip)) a.dst[l][o] = v;
+    }
+    cur = nxt;
+    cnt = nc;
+  }
+}
+
 struct TailArgs {
   uint8_t *lvl[VCT_MAX_LEVELS];
   uint8_t *pool;
@@ -564,9 +676,55 @@ cudaError_t launch_build_aniso(const float *level0, const vct_pyramid &pyr, int 
   return e;
 }
 
+// Dense float32 pyramids of n >= 32: stream_level01_kernel, then groups of
+// kGroupLevels levels, then the one-CTA tail.
+static cudaError_t build_dense_f32_streamed(const float *level0, const vct_pyramid &pyr,
+                                           cudaStream_t s) {
+  const Layout L = make_layout(pyr.n, pyr.levels, pyr.dtype, pyr.layout);
+  uint8_t *base = static_cast<uint8_t *>(pyr.data);
+  auto lvl = [&](int l) { return reinterpret_cast<float4 *>(base + L.level_off[l]); };
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t cells = level_texels(pyr.n, 1);
+  const int grid1 = (int)std::min<uint64_t>((cells + 255) / 256, (uint64_t)sms * 8);
+  stream_level01_kernel<<<grid1, 256, 0, s>>>(reinterpret_cast<const float4 *>(level0), lvl(0),
+                                               pyr.levels > 1 ? lvl(1) : nullptr, pyr.n,
+                                               pyr.levels > 1 ? 1 : 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || pyr.levels <= 2) return e;
+  // levels 2 .. 1 + k from level 1 (8^k | (n/2)^3 since k <= log2(n) - 1)
+  const int k = std::min(kGroupLevels, pyr.levels - 2);
+  GroupArgs g{};
+  g.src = lvl(1);
+  g.k = k;
+  for (int i = 0; i < k; ++i) {
+    g.dst[i] = lvl(2 + i);
+    g.dst_texels[i] = level_texels(pyr.n, 2 + i);
+  }
+  const uint64_t groups = cells >> (3 * k);
+  mip_group_kernel<<<(unsigned)groups, 256, 0, s>>>(g);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int m_top = 1 + k;
+  if (m_top >= pyr.levels - 1) return cudaSuccess;
+  TailArgs t{};
+  for (int l = 0; l < pyr.levels; ++l) t.lvl[l] = base + L.level_off[l];
+  t.pool = base + L.pool_off;
+  t.n = pyr.n;
+  t.levels = pyr.levels;
+  t.m_top = m_top;
+  t.src0 = lvl(m_top);
+  mip_tail_kernel<VCT_F32, false><<<1, 1024, 0, s>>>(t);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pack_mips(const float *level0, const vct_pyramid &pyr,
                              const CUtensorMap &map, cudaStream_t s) {
   const bool br = pyr.layout == VCT_LAYOUT_BRICKS;
+  // (its 32-byte loads need a 32-byte aligned grid; the TMA path needs 16)
+  if (pyr.dtype == VCT_F32 && !br && pyr.n >= 32 &&
+      reinterpret_cast<uintptr_t>(level0) % 32 == 0)
+    return build_dense_f32_streamed(level0, pyr, s);
   const Layout L = make_layout(pyr.n, pyr.levels, pyr.dtype, pyr.layout);
   uint8_t *base = static_cast<uint8_t *>(pyr.data);
   const int B = pack_block(pyr.n);
