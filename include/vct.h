@@ -162,8 +162,11 @@ uint64_t vct_pyramid_level_offset(int32_t n, int32_t levels, int32_t dtype,
                                   int32_t level);
 
 /*
- * Builds every level of `pyr` from a dense level-0 grid (rows a1 + a2 of the
- * hot path: Morton packing fused with the 2x2x2 box filter of Ch. 4.3.3).
+ * Builds every level of `pyr` from a dense level-0 grid: the mipmaps of the
+ * voxel texture (Ch. 4.3.3, "Mipmaps" and "Texture Filtering": each level
+ * halves the resolution, a texel the average of the 2x2x2 texels below it;
+ * Ch. 5.4.4 voxelize(): generated after every voxelization), stored in
+ * Morton order.
  *   level0_dense: device float32 [n][n][n][4] laid out z, y, x, channel
  *                 (RGB radiance, A opacity), 16-byte aligned, read only.
  *   pyr:          describes the destination; pyr->data is written.
@@ -326,7 +329,15 @@ typedef struct {
 size_t vct_trace_workspace_bytes(void);
 
 /*
- * Traces every pixel of every view (rows a3-a6 of the hot path) in one
+ * Traces every pixel of every view: per pixel the cone set of Ch. 4.2 (the
+ * diffuse cones over the normal hemisphere, the specular cone along the
+ * reflected view ray, the occlusion cone towards the light; Ch. 4.2.1 cone
+ * apex on the surface, Ch. 5.4.4 cone configurations), each cone marched by
+ * the cone trace function of Ch. 4.3.2 (d = 2 t tan(gamma/2), t += beta d,
+ * front-to-back accumulation until alpha reaches 1) through the sampler of
+ * Ch. 4.5 (mip level from the cone diameter over the voxel size), and the
+ * outputs of Ch. 4.1 / 4.2.2 (D = the weighted sum of the diffuse cones, S
+ * the specular cone, Vis = 1 - alpha of the occlusion cone).  One
  * persistent launch per group of up to 256 views: CTAs pull pixel tiles
  * from a queue in `workspace` and march each pixel's cones.
  *   pyrs[n_pyramids]: pyramids referenced by views[i].pyramid (any dtype).
@@ -384,8 +395,11 @@ typedef struct {
 size_t vct_trace_backward_workspace_bytes(const vct_pyramid *pyr);
 
 /*
- * Gradient of a loss with respect to the dense level-0 grid (rows a7 + a8):
- * recomputes each cone's march, walks it backwards to form the derivatives
+ * Gradient of a loss with respect to the dense level-0 grid: the adjoint of
+ * vct_trace and vct_build_mips (no counterpart in the thesis, which has no
+ * gradients; the transpose of the Ch. 4.3.2 accumulation, of the Ch. 4.5
+ * quadrilinear sampler and of the Ch. 4.3.3 box filter).  Recomputes each
+ * cone's march, walks it backwards to form the derivatives
  * of the front-to-back accumulation, scatters them through the quadrilinear
  * weights into a float32 gradient pyramid in `workspace`, then pushes each
  * level down to its children (1/8 each) and ADDS the level-0 result into

@@ -6,10 +6,10 @@ structs and calls the C ABI on PyTorch's current stream.  There is no
 fallback: if libvct cannot be built or loaded, every call raises.
 
 Main entry points
-    build_mips(level0, ...)          -> Pyramid            (rows a1 + a2)
-    trace(pyramids, views, params)   -> per-view outputs   (rows a3 .. a6)
-    trace_backward(...)              -> dL/d level-0 grid   (rows a7 + a8)
-    voxelize(mesh, n, ...)           -> dense level-0 grid  (row f2)
+    build_mips(level0, ...)          -> Pyramid            (Ch. 4.3.3 mipmaps)
+    trace(pyramids, views, params)   -> per-view outputs   (Ch. 4.2, 4.3.2, 4.5)
+    trace_backward(...)              -> dL/d level-0 grid   (adjoint of both)
+    voxelize(mesh, n, ...)           -> dense level-0 grid  (Ch. 4.4)
     TraceFn / render(...)            -> torch.autograd wrapper
 """
 from __future__ import annotations

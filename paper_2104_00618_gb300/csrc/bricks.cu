@@ -1,5 +1,5 @@
-// Brick occupancy and slot tables of a VCT_LAYOUT_BRICKS pyramid (row f4):
-// which 8^3 bricks of every bricked level hold a non-zero texel, and where
+// Brick occupancy and slot tables of a VCT_LAYOUT_BRICKS pyramid (Ch. 5.1:
+// sparse storage in place of a full 3D texture): which 8^3 bricks of every bricked level hold a non-zero texel, and where
 // in the pool each occupied brick goes.
 #include <algorithm>
 

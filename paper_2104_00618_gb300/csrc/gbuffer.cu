@@ -1,6 +1,6 @@
-// Camera G-buffer (row f2): the geometry pass that fills the per-pixel
-// position, normal and material buffers the cone tracer reads (Ch. 5.4: the
-// scene is drawn into these buffers before the cone-tracing pass).
+// Camera G-buffer: the geometry pass that fills the per-pixel position,
+// normal and material buffers the cone tracer reads (Ch. 5.4: the scene is
+// drawn into these buffers before the cone-tracing pass).
 //
 // Every coverage and depth decision is exact integer arithmetic on vertices,
 // eye and pixel directions snapped to a fixed-point frame, so the result does

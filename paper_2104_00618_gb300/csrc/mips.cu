@@ -343,14 +343,31 @@ __global__ void __launch_bounds__(256) mip_group_kernel(const __grid_constant__ 
   const int first = 1 << (3 * (a.k - 1));  // texels of level s+1 per group
   const uint64_t g = blockIdx.x;
   float4 *cur = sm;
-  for (int j = threadIdx.x; j < first; j += blockDim.x) {
-    const uint64_t o = g * first + j;
-    float4 ch[8];
+  // two level-(s+1) texels per thread (blockDim.x = 256, first <= 512), the
+  // loads of both issued before either mean
+  const int j0 = threadIdx.x, j1 = threadIdx.x + blockDim.x;
+  float4 ch0[8], ch1[8];
+  if (j0 < first) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) ld_32(a.src + 8 * o + 2 * q, ch[2 * q], ch[2 * q + 1]);
-    const float4 v = mean8(ch);
+    for (int q = 0; q < 4; ++q)
+      ld_32(a.src + 8 * (g * first + j0) + 2 * q, ch0[2 * q], ch0[2 * q + 1]);
+  }
+  if (j1 < first) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      ld_32(a.src + 8 * (g * first + j1) + 2 * q, ch1[2 * q], ch1[2 * q + 1]);
+  }
+  if (j0 < first) {
+    const uint64_t o = g * first + j0;
+    const float4 v = mean8(ch0);
     if (in_bounds(o, a.dst_texels[0], kOobMip)) a.dst[0][o] = v;
-    cur[j] = v;
+    cur[j0] = v;
+  }
+  if (j1 < first) {
+    const uint64_t o = g * first + j1;
+    const float4 v = mean8(ch1);
+    if (in_bounds(o, a.dst_texels[0], kOobMip)) a.dst[0][o] = v;
+    cur[j1] = v;
   }
   int cnt = first;
   for (int l = 1; l < a.k; ++l) {
@@ -703,7 +720,7 @@ static cudaError_t build_dense_f32_streamed(const float *level0, const vct_pyram
     g.dst_texels[i] = level_texels(pyr.n, 2 + i);
   }
   const uint64_t groups = cells >> (3 * k);
-  mip_group_kernel<<<(unsigned)groups, 256, 0, s>>>(g);
+  mip_group_kernel<<<(unsigned)groups, 256, 0, s>>>(g);  // 256 threads: see the kernel
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int m_top = 1 + k;
   if (m_top >= pyr.levels - 1) return cudaSuccess;

@@ -1,6 +1,6 @@
-// Forward cone trace (rows a3-a6): persistent CTAs pull pixel tiles from a
-// queue; every pixel marches its diffuse, specular and occlusion cones
-// through the Morton-ordered pyramid (Ch. 4.2, Ch. 4.3.2, Ch. 4.5).
+// Forward cone trace: persistent CTAs pull pixel tiles from a queue; every
+// pixel marches its diffuse, specular and occlusion cones through the
+// Morton-ordered pyramid (Ch. 4.2 cone set, Ch. 4.3.2 march, Ch. 4.5 sampler).
 #include "trace_common.cuh"
 
 namespace vct {

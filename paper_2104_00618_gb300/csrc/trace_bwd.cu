@@ -1,6 +1,7 @@
-// Adjoint of the cone trace (row a7).  No per-sample state is stored: each
-// cone is marched forwards once (same stopping rule as the forward kernel:
-// alpha = 1 - T < 1 in float32) to find its length K and its transmittance
+// Adjoint of the cone trace (no counterpart in the thesis: the transpose of
+// the Ch. 4.3.2 accumulation and the Ch. 4.5 sampler).  No per-sample state
+// is stored: each cone is marched forwards once (same stopping rule as the
+// forward kernel: alpha = 1 - T < 1 in float32) to find its length K and its transmittance
 // before the last sample, then walked backwards k = K-1 .. 0, recomputing
 // every sample.  For samples (c_k, a_k) and T_k = prod_{j<k} (1 - a_j):
 //   C = sum_k T_k a_k c_k,  A = 1 - prod_k (1 - a_k)

@@ -1,4 +1,4 @@
-// Mesh voxelization (row f2): every triangle is rasterised once along its
+// Mesh voxelization (Ch. 4.4): every triangle is rasterised once along its
 // dominant axis into the level-0 grid (Ch. 4.4, Ch. 5.4.4 voxelize()).
 //
 // Coverage, depth and the winner of each voxel are exact integer decisions
