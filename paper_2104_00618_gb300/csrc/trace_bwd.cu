@@ -41,26 +41,41 @@ __device__ __forceinline__ unsigned long long *fix_texel(const BwdLaunch &L, int
   return L.gfix_lvl[l] + 4 * (size_t)idx;
 }
 
+// The 8 trilinear corner weights of a stencil times the level weight lw,
+// corner c = cx | cy << 1 | cz << 2: products of the per-axis weights.
+__device__ __forceinline__ void corner_weights(const LevelStencil &s, float lw, float w[8]) {
+  const float wx[2] = {1.0f - s.fr[0], s.fr[0]};
+  const float wy[2] = {1.0f - s.fr[1], s.fr[1]};
+  const float wz[2] = {lw * (1.0f - s.fr[2]), lw * s.fr[2]};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float wyz = wy[k & 1] * wz[k >> 1];
+    w[2 * k] = wx[0] * wyz;
+    w[2 * k + 1] = wx[1] * wyz;
+  }
+}
+
 // Per-lane scatter of one level's 8 corners (lanes in different cells) into
 // the gradient texels vbase + code (vbase: the volume's first texel in an
 // anisotropic level, else 0; lim: the texels of the gradient level).
 __device__ __forceinline__ void scatter_lane(const BwdLaunch &L, int l, uint32_t vbase,
                                              uint32_t lim, const LevelStencil &s, float lw,
                                              const float g[4]) {
+  float w[8];
+  corner_weights(s, lw, w);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     if (!((s.valid >> c) & 1u)) continue;
-    const float w = corner_weight(s, lw, c);
-    if (w == 0.0f) continue;
     const uint32_t idx = vbase + corner_index(s, c);
     if (!in_bounds(idx, lim, kOobGrad)) continue;
     if (L.deterministic) {
+      if (w[c] == 0.0f) continue;
       unsigned long long *q = fix_texel(L, l, idx);
 #pragma unroll
-      for (int ch = 0; ch < 4; ++ch) atomicAdd(q + ch, to_fix(w * g[ch]));
+      for (int ch = 0; ch < 4; ++ch) atomicAdd(q + ch, to_fix(w[c] * g[ch]));
     } else {
       atomicAdd(reinterpret_cast<float4 *>(grad_texel(L, l, idx)),
-                make_float4(w * g[0], w * g[1], w * g[2], w * g[3]));
+                make_float4(w[c] * g[0], w[c] * g[1], w[c] * g[2], w[c] * g[3]));
     }
   }
 }
@@ -124,11 +139,13 @@ __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const uint32_t 
     const unsigned lgrp = __shfl_sync(full, grp, leader);
     const bool in = (lgrp >> lane) & 1u;
     float v[32];
+    {
+      float w[8];
+      corner_weights(s, in ? lw : 0.0f, w);
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const float w = in ? corner_weight(s, lw, c) : 0.0f;
+      for (int c = 0; c < 8; ++c)
 #pragma unroll
-      for (int ch = 0; ch < 4; ++ch) v[4 * c + ch] = w * g[ch];
+        for (int ch = 0; ch < 4; ++ch) v[4 * c + ch] = w[c] * g[ch];
     }
 #pragma unroll
     for (int half = 16; half >= 1; half >>= 1) {
