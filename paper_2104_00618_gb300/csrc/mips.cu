@@ -281,6 +281,17 @@ __device__ __forceinline__ void ld_32(const float4 *p, float4 &a, float4 &b) {
                : "l"(p));
 }
 
+// Programmatic dependent launch: a kernel launched after this one with the
+// programmatic-serialization attribute may be scheduled before this one
+// ends; it waits (griddepcontrol.wait) until this grid has completed and its
+// memory is visible before it reads what this grid wrote.
+__device__ __forceinline__ void allow_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void wait_for_previous_grid() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // One thread per level-1 texel (cell cx, cy, cz; cx fastest, so a warp reads
 // whole rows): its 8 children as four 32-byte x pairs, written to level 0 at
 // Morton codes 8 code .. 8 code + 7 (child j = jx | jy << 1 | jz << 2, the
@@ -291,6 +302,7 @@ __device__ __forceinline__ void ld_32(const float4 *p, float4 &a, float4 &b) {
 __global__ void __launch_bounds__(256) stream_level01_kernel(const float4 *__restrict__ dense,
                                                              float4 *lvl0, float4 *lvl1, int n,
                                                              int write1) {
+  allow_dependents();
   const uint32_t m = (uint32_t)n >> 1;
   const uint64_t cells = (uint64_t)m * m * m;
   const uint64_t texels0 = 8 * cells;
@@ -340,6 +352,8 @@ struct GroupArgs {
 };
 __global__ void __launch_bounds__(256) mip_group_kernel(const __grid_constant__ GroupArgs a) {
   __shared__ float4 sm[512 + 64 + 8 + 1];
+  wait_for_previous_grid();  // level s comes from the previous kernel
+  allow_dependents();
   const int first = 1 << (3 * (a.k - 1));  // texels of level s+1 per group
   const uint64_t g = blockIdx.x;
   float4 *cur = sm;
@@ -396,8 +410,9 @@ struct TailArgs {
 };
 
 // One CTA: levels m_top+1 .. levels-1 from the FP32 values of level m_top.
-template <int DT, bool BR>
+template <int DT, bool BR, bool kAfterPdl = false>
 __global__ void __launch_bounds__(1024) mip_tail_kernel(const TailArgs a) {
+  if constexpr (kAfterPdl) wait_for_previous_grid();
   // A dense FP32 level doubles as the FP32 source of the next one.
   constexpr bool kInPlace = DT == VCT_F32 && !BR;
   const float4 *src = a.src0;
@@ -720,8 +735,16 @@ static cudaError_t build_dense_f32_streamed(const float *level0, const vct_pyram
     g.dst_texels[i] = level_texels(pyr.n, 2 + i);
   }
   const uint64_t groups = cells >> (3 * k);
-  mip_group_kernel<<<(unsigned)groups, 256, 0, s>>>(g);  // 256 threads: see the kernel
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cudaLaunchAttribute pdl[1];
+  pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  pdl[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t lc{};
+  lc.gridDim = dim3((unsigned)groups);
+  lc.blockDim = dim3(256);  // 256 threads: see the kernel
+  lc.stream = s;
+  lc.attrs = pdl;
+  lc.numAttrs = 1;
+  if ((e = cudaLaunchKernelEx(&lc, mip_group_kernel, g)) != cudaSuccess) return e;
   const int m_top = 1 + k;
   if (m_top >= pyr.levels - 1) return cudaSuccess;
   TailArgs t{};
@@ -731,8 +754,9 @@ static cudaError_t build_dense_f32_streamed(const float *level0, const vct_pyram
   t.levels = pyr.levels;
   t.m_top = m_top;
   t.src0 = lvl(m_top);
-  mip_tail_kernel<VCT_F32, false><<<1, 1024, 0, s>>>(t);
-  return cudaGetLastError();
+  lc.gridDim = dim3(1);
+  lc.blockDim = dim3(1024);
+  return cudaLaunchKernelEx(&lc, mip_tail_kernel<VCT_F32, false, true>, t);
 }
 
 cudaError_t launch_pack_mips(const float *level0, const vct_pyramid &pyr,
