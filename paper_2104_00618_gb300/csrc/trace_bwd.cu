@@ -140,12 +140,14 @@ __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const uint32_t 
     const bool in = (lgrp >> lane) & 1u;
     float v[32];
     {
+      // lanes outside the group contribute zeros by selection: an inactive
+      // lane's stencil fractions are never set, so no arithmetic may touch them
       float w[8];
-      corner_weights(s, in ? lw : 0.0f, w);
+      corner_weights(s, lw, w);
 #pragma unroll
       for (int c = 0; c < 8; ++c)
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) v[4 * c + ch] = w[c] * g[ch];
+        for (int ch = 0; ch < 4; ++ch) v[4 * c + ch] = in ? w[c] * g[ch] : 0.0f;
     }
 #pragma unroll
     for (int half = 16; half >= 1; half >>= 1) {
@@ -283,7 +285,7 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t 
       if constexpr (AN)
         v = sample_aniso(P, A, F, lam, lut, aw, om, lp, st);
       else
-        v = sample<DT, BR>(P, A, F, lam, lut, om, lp, st);
+        v = sample<DT, BR, false>(P, A, F, lam, lut, om, lp, st);
       if (kVar && mode == kOccSmooth) {  // as the forward march
         fade = smoothstep0(L.var.occ_max_dist, sqrtf(T * P.h0) * L.var.shadow_str);
         v.w *= fade;
@@ -310,7 +312,9 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t 
         g[2] = gc2;
       }
     } else if (act) {
-      const float tr = (kr == K - 1) ? prod_last : tr_next / om;
+      // (om > 0 before the last sample, else the forward would have ended
+      // there; the guard keeps a mismatch from spreading NaN)
+      const float tr = (kr == K - 1) ? prod_last : (om > 0.0f ? tr_next / om : 0.0f);
       if (premul) {
         g[0] = gc0 * tr;
         g[1] = gc1 * tr;

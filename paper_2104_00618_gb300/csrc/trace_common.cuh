@@ -1,4 +1,12 @@
 // Device code shared by the forward and adjoint cone-trace kernels.
+//
+// The adjoint recomputes the forward's samples, and with the forward's
+// per-cone state (sample count, transmittance before the last sample) it
+// relies on recomputing them bit for bit in another kernel.  Every value a
+// sample depends on is therefore written with explicit roundings (fmaf,
+// __fmul_rn, __fadd_rn, ...), never as a multiply followed by an add that
+// the compiler may or may not contract into an fma depending on the code
+// around it.
 #pragma once
 
 #include "vct_internal.cuh"
@@ -37,7 +45,9 @@ __device__ __forceinline__ void make_apex(const DevPyr &P, const float x[3], con
     const float pe = fmaf(sd, P.scale_hi, -p);      // sd * scale_hi = p + pe exactly
     const float fl = floorf(p);
     A.Xi[a] = (int)fl;
-    A.Of[a] = (p - fl) + (pe + fmaf(sd, P.scale_lo, e * P.scale_hi)) + normal_offset * n[a];
+    A.Of[a] = __fadd_rn(__fadd_rn(__fsub_rn(p, fl),
+                                  __fadd_rn(pe, fmaf(sd, P.scale_lo, __fmul_rn(e, P.scale_hi)))),
+                        __fmul_rn(normal_offset, n[a]));
   }
 }
 
@@ -46,16 +56,16 @@ __device__ __forceinline__ void make_apex(const DevPyr &P, const float x[3], con
 __device__ __forceinline__ void tangent_frame(const float n[3], float T[3], float B[3]) {
   const float ax = fabsf(n[0]) < 0.9f ? 1.0f : 0.0f;
   const float ay = 1.0f - ax;
-  float t0 = ay * n[2];
-  float t1 = -ax * n[2];
-  float t2 = ax * n[1] - ay * n[0];
-  const float inv = 1.0f / sqrtf(t0 * t0 + t1 * t1 + t2 * t2);
-  T[0] = t0 * inv;
-  T[1] = t1 * inv;
-  T[2] = t2 * inv;
-  B[0] = n[1] * T[2] - n[2] * T[1];
-  B[1] = n[2] * T[0] - n[0] * T[2];
-  B[2] = n[0] * T[1] - n[1] * T[0];
+  float t0 = __fmul_rn(ay, n[2]);
+  float t1 = __fmul_rn(-ax, n[2]);
+  float t2 = fmaf(ax, n[1], -__fmul_rn(ay, n[0]));
+  const float inv = 1.0f / sqrtf(fmaf(t0, t0, fmaf(t1, t1, __fmul_rn(t2, t2))));
+  T[0] = __fmul_rn(t0, inv);
+  T[1] = __fmul_rn(t1, inv);
+  T[2] = __fmul_rn(t2, inv);
+  B[0] = fmaf(n[1], T[2], -__fmul_rn(n[2], T[1]));
+  B[1] = fmaf(n[2], T[0], -__fmul_rn(n[0], T[2]));
+  B[2] = fmaf(n[0], T[1], -__fmul_rn(n[1], T[0]));
 }
 
 // Reflection of the view ray about the normal.
@@ -64,10 +74,10 @@ __device__ __forceinline__ void reflect_dir(const float x[3], const float cam[3]
   float v[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) v[a] = x[a] - cam[a];
-  const float len = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  const float len = sqrtf(fmaf(v[0], v[0], fmaf(v[1], v[1], __fmul_rn(v[2], v[2]))));
 #pragma unroll
   for (int a = 0; a < 3; ++a) v[a] = v[a] / len;
-  const float vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+  const float vn = fmaf(v[0], n[0], fmaf(v[1], n[1], __fmul_rn(v[2], n[2])));
 #pragma unroll
   for (int a = 0; a < 3; ++a) R[a] = fmaf(-2.0f * vn, n[a], v[a]);
 }
@@ -86,14 +96,14 @@ __device__ __forceinline__ float floor_split(float v, int &iv) {
 __device__ __forceinline__ void step_at(const ConeConst &cc, float T0, int k, float &T,
                                         float &lam) {
   const float kf = (float)k;
-  const float p = kf * cc.l2r_hi;
+  const float p = __fmul_rn(kf, cc.l2r_hi);
   float q = fmaf(kf, cc.l2r_hi, -p);
   q = fmaf(kf, cc.l2r_lo, q);
   int ie;
   const float e = floor_split(p, ie);
-  const float phi = (p - e) + q;
-  T = T0 * exp2f(phi) * __int_as_float((ie + 127) << 23);
-  lam = (cc.lam0_hi + p) + (q + cc.lam0_lo);
+  const float phi = __fadd_rn(__fsub_rn(p, e), q);
+  T = __fmul_rn(__fmul_rn(T0, exp2f(phi)), __int_as_float((ie + 127) << 23));
+  lam = __fadd_rn(__fadd_rn(cc.lam0_hi, p), __fadd_rn(q, cc.lam0_lo));
 }
 
 // ---------------------------------------------------------------------------
@@ -120,6 +130,12 @@ __device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
 __device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
   f32x2 d;
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// a + b rounded towards minus infinity, both lanes
+__device__ __forceinline__ f32x2 f2_add_rm(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
 // a + t (b - a), both lanes
@@ -149,21 +165,38 @@ struct LevelStencil {
 
 // lut: three tables of 1024 entries (shared memory): spread3(i), spread3(i)
 // << 1 and spread3(i) << 2, the Morton bits of x, y and z already in place.
+// kPacked: x and y as float32 pairs (the same operations per element, so
+// the same bits): the forward's isotropic sampler; the anisotropic sampler
+// (measured slower packed) and the adjoint use the scalar form.
+template <bool kPacked = true>
 __device__ __forceinline__ void level_stencil(int l, int Nl, const Apex &A, const float F[3],
                                               const uint32_t *lut, LevelStencil &s) {
   const float sc = __int_as_float((127 - l) << 23);  // 2^-l
   const int mask = (1 << l) - 1;
   int b[3];
+  // u = (Xi + F) / 2^l - 1/2, formed from small numbers only; floor(u) by
+  // the magic-number add of floor_split.
+  if constexpr (kPacked) {
+    const f32x2 sc2 = f2_pack(sc, sc);
+    const f32x2 c = f2_fma(f2_pack((float)(A.Xi[0] & mask), (float)(A.Xi[1] & mask)), sc2,
+                           f2_pack(-0.5f, -0.5f));
+    const f32x2 v = f2_fma(f2_pack(F[0], F[1]), sc2, c);
+    const f32x2 magic = f2_pack(kFloorMagic, kFloorMagic);
+    const f32x2 t = f2_add_rm(v, magic);
+    const float2 fr = f2_unpack(f2_sub(v, f2_sub(t, magic)));
+    const float2 tt = f2_unpack(t);
+    s.fr[0] = fr.x;
+    s.fr[1] = fr.y;
+    b[0] = (A.Xi[0] >> l) + (__float_as_int(tt.x) - 0x4B400000);
+    b[1] = (A.Xi[1] >> l) + (__float_as_int(tt.y) - 0x4B400000);
+  }
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const int ri = A.Xi[a] & mask;
-    const int qi = A.Xi[a] >> l;
-    // u = (Xi + F) / 2^l - 1/2, formed from small numbers only
-    const float v = fmaf(F[a], sc, fmaf((float)ri, sc, -0.5f));
+  for (int a = kPacked ? 2 : 0; a < 3; ++a) {
+    const float v = fmaf(F[a], sc, fmaf((float)(A.Xi[a] & mask), sc, -0.5f));
     int iv;
     const float fl = floor_split(v, iv);
     s.fr[a] = v - fl;
-    b[a] = qi + iv;
+    b[a] = (A.Xi[a] >> l) + iv;
   }
   const uint32_t x0 = lut[(uint32_t)b[0] & 1023u];
   const uint32_t y0 = lut[1024u + ((uint32_t)b[1] & 1023u)];
@@ -316,17 +349,17 @@ __device__ __forceinline__ float transparency(float a) { return fmaxf(1.0f - a, 
 // The full sample S(p, lambda) at apex-relative voxel coordinates F (levels
 // floor(lambda) and floor(lambda)+1 blended linearly); `om` receives 1 - a_s.
 // When `st` is non-null the two stencils are kept for the adjoint.
-template <int DT, bool BR = false>
+template <int DT, bool BR = false, bool kPacked = true>
 __device__ __forceinline__ float4 sample_at(const DevPyr &P, const Apex &A, const float F[3],
                                             const LodPick &lp, const uint32_t *lut, float &om,
                                             LevelStencil *st = nullptr) {
   LevelStencil s;
   f32x2 rg, ba;
-  level_stencil(lp.l0, P.n >> lp.l0, A, F, lut, s);
+  level_stencil<kPacked>(lp.l0, P.n >> lp.l0, A, F, lut, s);
   trilerp<DT, BR>(P, lp.l0, s, rg, ba);
   if (st) st[0] = s;
   if (lp.f > 0.0f) {
-    level_stencil(lp.l1, P.n >> lp.l1, A, F, lut, s);
+    level_stencil<kPacked>(lp.l1, P.n >> lp.l1, A, F, lut, s);
     f32x2 rg1, ba1;
     trilerp<DT, BR>(P, lp.l1, s, rg1, ba1);
     const f32x2 tf = f2_pack(lp.f, lp.f);
@@ -338,12 +371,12 @@ __device__ __forceinline__ float4 sample_at(const DevPyr &P, const Apex &A, cons
   om = transparency(v1.y);
   return make_float4(v0.x, v0.y, v1.x, v1.y);
 }
-template <int DT, bool BR = false>
+template <int DT, bool BR = false, bool kPacked = true>
 __device__ __forceinline__ float4 sample(const DevPyr &P, const Apex &A, const float F[3],
                                          float lam, const uint32_t *lut, float &om,
                                          LodPick &lp, LevelStencil *st = nullptr) {
   lp = pick_levels(lam, P.levels);
-  return sample_at<DT, BR>(P, A, F, lp, lut, om, st);
+  return sample_at<DT, BR, kPacked>(P, A, F, lp, lut, om, st);
 }
 
 // Cone march variants (Ch. 5.4.4): the plain march, the occlusion cone that
@@ -354,7 +387,7 @@ enum MarchMode { kPlain = 0, kOccSmooth = 1, kFirstHit = 2 };
 // GLSL smoothstep(0, e1, x).
 __device__ __forceinline__ float smoothstep0(float e1, float x) {
   const float u = fminf(fmaxf(x / e1, 0.0f), 1.0f);
-  return u * u * (3.0f - 2.0f * u);
+  return __fmul_rn(__fmul_rn(u, u), fmaf(-2.0f, u, 3.0f));
 }
 
 // Angular-grace specular BRDF (Ch. 5.4.4): (1 - max(0, g - p) / pi)^q with g
@@ -362,11 +395,11 @@ __device__ __forceinline__ float smoothstep0(float e1, float x) {
 // atan2(|w x l|, w . l) (well conditioned at every angle).
 __device__ __forceinline__ float spec_grace(const Variants &v, const float w[3]) {
   const float *l = v.light_dir;
-  const float cx = w[1] * l[2] - w[2] * l[1];
-  const float cy = w[2] * l[0] - w[0] * l[2];
-  const float cz = w[0] * l[1] - w[1] * l[0];
-  const float d = w[0] * l[0] + w[1] * l[1] + w[2] * l[2];
-  const float g = atan2f(sqrtf(cx * cx + cy * cy + cz * cz), d);
+  const float cx = fmaf(w[1], l[2], -__fmul_rn(w[2], l[1]));
+  const float cy = fmaf(w[2], l[0], -__fmul_rn(w[0], l[2]));
+  const float cz = fmaf(w[0], l[1], -__fmul_rn(w[1], l[0]));
+  const float d = fmaf(w[0], l[0], fmaf(w[1], l[1], __fmul_rn(w[2], l[2])));
+  const float g = atan2f(sqrtf(fmaf(cx, cx, fmaf(cy, cy, __fmul_rn(cz, cz)))), d);
   const float e = fmaxf(g - v.grace, 0.0f);
   return powf(1.0f - e * 0.318309886f, v.falloff);
 }
@@ -413,10 +446,10 @@ struct AnisoW {
 };
 __device__ __forceinline__ AnisoW aniso_weights(const float w[3]) {
   AnisoW r;
-  const float inv = 1.0f / (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  const float inv = 1.0f / fmaf(w[0], w[0], fmaf(w[1], w[1], __fmul_rn(w[2], w[2])));
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    r.wt[a] = w[a] * w[a] * inv;
+    r.wt[a] = __fmul_rn(__fmul_rn(w[a], w[a]), inv);
     r.vol[a] = 2 * a + (w[a] < 0.0f ? 1 : 0);
   }
   return r;
@@ -493,11 +526,11 @@ __device__ __forceinline__ float4 sample_aniso_at(const DevPyr &P, const Apex &A
                                                   float &om, LevelStencil *st = nullptr) {
   LevelStencil s;
   f32x2 rg, ba;
-  level_stencil(lp.l0, P.n >> lp.l0, A, F, lut, s);
+  level_stencil<false>(lp.l0, P.n >> lp.l0, A, F, lut, s);
   aniso_level(P, lp.l0, s, aw, rg, ba);
   if (st) st[0] = s;
   if (lp.f > 0.0f) {
-    level_stencil(lp.l1, P.n >> lp.l1, A, F, lut, s);
+    level_stencil<false>(lp.l1, P.n >> lp.l1, A, F, lut, s);
     f32x2 rg1, ba1;
     aniso_level(P, lp.l1, s, aw, rg1, ba1);
     const f32x2 tf = f2_pack(lp.f, lp.f);
