@@ -41,12 +41,12 @@ __device__ __forceinline__ unsigned long long *fix_texel(const BwdLaunch &L, int
   return L.gfix_lvl[l] + 4 * (size_t)idx;
 }
 
-// The 8 trilinear corner weights of a stencil times the level weight lw,
-// corner c = cx | cy << 1 | cz << 2: products of the per-axis weights.
-__device__ __forceinline__ void corner_weights(const LevelStencil &s, float lw, float w[8]) {
-  const float wx[2] = {1.0f - s.fr[0], s.fr[0]};
-  const float wy[2] = {1.0f - s.fr[1], s.fr[1]};
-  const float wz[2] = {lw * (1.0f - s.fr[2]), lw * s.fr[2]};
+// The 8 trilinear corner weights of a stencil (fractions fr) times the level
+// weight lw, corner c = cx | cy << 1 | cz << 2: products of the per-axis weights.
+__device__ __forceinline__ void corner_weights(const float fr[3], float lw, float w[8]) {
+  const float wx[2] = {1.0f - fr[0], fr[0]};
+  const float wy[2] = {1.0f - fr[1], fr[1]};
+  const float wz[2] = {lw * (1.0f - fr[2]), lw * fr[2]};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const float wyz = wy[k & 1] * wz[k >> 1];
@@ -62,7 +62,7 @@ __device__ __forceinline__ void scatter_lane(const BwdLaunch &L, int l, uint32_t
                                              uint32_t lim, const LevelStencil &s, float lw,
                                              const float g[4]) {
   float w[8];
-  corner_weights(s, lw, w);
+  corner_weights(s.fr, lw, w);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     if (!((s.valid >> c) & 1u)) continue;
@@ -134,20 +134,28 @@ __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const uint32_t 
   const bool big = act && __popc(grp) >= kReduceMin;
   if (act && !big) scatter_lane(L, l, vbase, lim, s, lw, g);
   unsigned pending = __ballot_sync(full, big);
+  if (pending == 0u) return;
+  // A lane without a sample here holds unset fractions and derivatives: its
+  // operands are replaced by zeros once, so that every product below is of
+  // finite values and a lane outside a group adds exact zeros (level weight
+  // 0).  The weight is selected inside the loop, which also keeps the 32
+  // products from being hoisted out of it and held in registers.
+  const float fr[3] = {act ? s.fr[0] : 0.0f, act ? s.fr[1] : 0.0f, act ? s.fr[2] : 0.0f};
+  const float ga[4] = {act ? g[0] : 0.0f, act ? g[1] : 0.0f, act ? g[2] : 0.0f,
+                       act ? g[3] : 0.0f};
+  const float lwa = act ? lw : 0.0f;
   while (pending) {
     const int leader = __ffs(pending) - 1;
     const unsigned lgrp = __shfl_sync(full, grp, leader);
     const bool in = (lgrp >> lane) & 1u;
     float v[32];
     {
-      // lanes outside the group contribute zeros by selection: an inactive
-      // lane's stencil fractions are never set, so no arithmetic may touch them
       float w[8];
-      corner_weights(s, lw, w);
+      corner_weights(fr, in ? lwa : 0.0f, w);
 #pragma unroll
       for (int c = 0; c < 8; ++c)
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) v[4 * c + ch] = in ? w[c] * g[ch] : 0.0f;
+        for (int ch = 0; ch < 4; ++ch) v[4 * c + ch] = w[c] * ga[ch];
     }
 #pragma unroll
     for (int half = 16; half >= 1; half >>= 1) {

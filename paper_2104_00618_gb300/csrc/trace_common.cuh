@@ -54,18 +54,18 @@ __device__ __forceinline__ void make_apex(const DevPyr &P, const float x[3], con
 // Tangent frame: T = normalize(a x n), B = n x T, a = x-axis unless n is
 // close to it.
 __device__ __forceinline__ void tangent_frame(const float n[3], float T[3], float B[3]) {
-  const float ax = fabsf(n[0]) < 0.9f ? 1.0f : 0.0f;
-  const float ay = 1.0f - ax;
-  float t0 = __fmul_rn(ay, n[2]);
-  float t1 = __fmul_rn(-ax, n[2]);
-  float t2 = fmaf(ax, n[1], -__fmul_rn(ay, n[0]));
+  // a x n is (0, -n_z, n_y) for a = x and (n_z, 0, -n_x) for a = y
+  const bool ax = fabsf(n[0]) < 0.9f;
+  const float t0 = ax ? 0.0f : n[2];
+  const float t1 = ax ? -n[2] : 0.0f;
+  const float t2 = ax ? n[1] : -n[0];
   const float inv = 1.0f / sqrtf(fmaf(t0, t0, fmaf(t1, t1, __fmul_rn(t2, t2))));
   T[0] = __fmul_rn(t0, inv);
   T[1] = __fmul_rn(t1, inv);
   T[2] = __fmul_rn(t2, inv);
-  B[0] = fmaf(n[1], T[2], -__fmul_rn(n[2], T[1]));
-  B[1] = fmaf(n[2], T[0], -__fmul_rn(n[0], T[2]));
-  B[2] = fmaf(n[0], T[1], -__fmul_rn(n[1], T[0]));
+  B[0] = __fsub_rn(__fmul_rn(n[1], T[2]), __fmul_rn(n[2], T[1]));
+  B[1] = __fsub_rn(__fmul_rn(n[2], T[0]), __fmul_rn(n[0], T[2]));
+  B[2] = __fsub_rn(__fmul_rn(n[0], T[1]), __fmul_rn(n[1], T[0]));
 }
 
 // Reflection of the view ray about the normal.
