@@ -292,50 +292,158 @@ __device__ __forceinline__ void wait_for_previous_grid() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-// One thread per level-1 texel (cell cx, cy, cz; cx fastest, so a warp reads
-// whole rows): its 8 children as four 32-byte x pairs, written to level 0 at
-// Morton codes 8 code .. 8 code + 7 (child j = jx | jy << 1 | jz << 2, the
-// x pairs contiguous) and their mean to level 1 (neighbouring threads fill
-// whole sectors).  The mean adds the children in the order the TMA pack
-// kernel does for the same cell (starting at child (cy & 1) | (cx & 3) << 1),
-// so both paths give the same bits.
-__global__ void __launch_bounds__(256) stream_level01_kernel(const float4 *__restrict__ dense,
-                                                             float4 *lvl0, float4 *lvl1, int n,
-                                                             int write1) {
+// Levels 0 .. top (top <= 4) of one patch of X x 16 x 16 level-0 voxels per
+// CTA (X = min(n, 256); the patch's origin a multiple of its extent), so
+// that the levels above 1 are reduced on chip instead of re-reading level 1.
+// The patch is taken in 16 phases, one per level-2 row (qy, qz) of it, each
+// phase the four level-1 rows (2 qy + iy, 2 qz + iz), in units of 8 x 4
+// level-1 cells: lane = cx' | row << 3 (row = iy | iz << 1), so a unit holds
+// four whole level-2 cells and a warp reduces them with shuffles, with no
+// barrier between phases.  Warp w takes units w and w + 8 of each phase.  A
+// lane's cell: its 8 children as four 32-byte x pairs (rows of a unit are
+// 256-byte pieces), written to level 0 at Morton codes 8 code .. 8 code + 7
+// (child jx | jy << 1 | jz << 2, the x pairs contiguous), and their mean to
+// level 1.  The loads of the next phase are issued as soon as the stores have
+// taken the registers.  After the 16 phases the patch's level-3 and level-4
+// texels come from its level-2 values, kept in shared memory.  Level-1 means
+// add the children in the order the TMA pack kernel does for the same cell
+// (starting at child (cy & 1) | (cx & 3) << 1); coarser levels add them in
+// child order (mean8), as the group and pack kernels do, so every path gives
+// the same bits.
+constexpr int kStreamTop = 4;    // levels made by the streaming kernel: 0 .. 4
+constexpr int kPatchX = 256;     // longest x extent of a patch
+constexpr int kPatchYZ = 16;     // y and z extent of a patch (2^kStreamTop)
+struct StreamArgs {
+  const float4 *dense;
+  float4 *lvl[kStreamTop + 1];
+  uint64_t texels[kStreamTop + 1];
+  int n, X, top;
+};
+__global__ void __launch_bounds__(256, 2) stream_levels_kernel(const __grid_constant__ StreamArgs a) {
+  __shared__ float4 s2[16 * (kPatchX / 4)];  // the patch's level 2, row qz * 4 + qy
+  __shared__ float4 s3[4 * (kPatchX / 8)];   // level 3, row rz * 2 + ry
   allow_dependents();
-  const uint32_t m = (uint32_t)n >> 1;
-  const uint64_t cells = (uint64_t)m * m * m;
-  const uint64_t texels0 = 8 * cells;
-  for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < cells;
-       c += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t cx = (uint32_t)(c % m), cy = (uint32_t)((c / m) % m),
-                   cz = (uint32_t)(c / ((uint64_t)m * m));
-    float4 r[8];
+  const uint32_t n = (uint32_t)a.n, X = (uint32_t)a.X, hx = X >> 1;
+  const uint32_t pxn = n / X, pyn = n / kPatchYZ;
+  const uint64_t patches = (uint64_t)pxn * pyn * pyn;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t units = hx / 8;  // units per phase (2 .. 16)
+  const uint32_t row = lane >> 3;
+  float4 r[2][8];
+  // level-1 cell (gx, gy, gz) of this lane in unit slot k of phase p of patch P
+  auto cell = [&](uint64_t P, int p, int k, uint32_t &gx, uint32_t &gy, uint32_t &gz) {
+    const uint32_t u = warp + 8u * (uint32_t)k;
+    const uint32_t px = (uint32_t)(P % pxn), py = (uint32_t)((P / pxn) % pyn),
+                   pz = (uint32_t)(P / ((uint64_t)pxn * pyn));
+    gx = px * hx + 8u * u + (lane & 7u);
+    gy = py * (kPatchYZ / 2) + 2u * (uint32_t)(p & 3) + (row & 1u);
+    gz = pz * (kPatchYZ / 2) + 2u * (uint32_t)(p >> 2) + (row >> 1);
+    return u < units;
+  };
+  auto load = [&](uint64_t P, int p) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {  // q = jy | jz << 1
-      const uint64_t y = 2 * cy + (q & 1), z = 2 * cz + (q >> 1);
-      ld_stream_32(dense + (z * n + y) * n + 2 * cx, r[2 * q], r[2 * q + 1]);
+    for (int k = 0; k < 2; ++k) {
+      uint32_t gx, gy, gz;
+      if (!cell(P, p, k, gx, gy, gz)) continue;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {  // q = jy | jz << 1
+        const uint64_t y = 2 * gy + (q & 1), z = 2 * gz + (q >> 1);
+        ld_stream_32(a.dense + (z * n + y) * n + 2 * gx, r[k][2 * q], r[k][2 * q + 1]);
+      }
     }
-    const uint32_t code = morton3(cx, cy, cz);
-    if (in_bounds(8 * (uint64_t)code + 7, texels0, kOobMip)) {
-      float4 *dst = lvl0 + 8 * (uint64_t)code;
+  };
+  if (blockIdx.x < patches) load(blockIdx.x, 0);
+  for (uint64_t P = blockIdx.x; P < patches; P += gridDim.x) {
+    const uint32_t px = (uint32_t)(P % pxn), py = (uint32_t)((P / pxn) % pyn),
+                   pz = (uint32_t)(P / ((uint64_t)pxn * pyn));
+    for (int p = 0; p < 16; ++p) {
+      float4 m[2];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) st_stream_32(dst + 2 * q, r[2 * q], r[2 * q + 1]);
+      for (int k = 0; k < 2; ++k) {
+        uint32_t gx, gy, gz;
+        m[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!cell(P, p, k, gx, gy, gz)) continue;
+        const uint32_t code = morton3(gx, gy, gz);
+        if (in_bounds(8 * (uint64_t)code + 7, a.texels[0], kOobMip)) {
+          float4 *dst = a.lvl[0] + 8 * (uint64_t)code;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) st_stream_32(dst + 2 * q, r[k][2 * q], r[k][2 * q + 1]);
+        }
+        if (a.top < 1) continue;
+        // rotate so that u[i] = r[(i + rot) & 7], then add in order
+        const int rot = (int)((gy & 1u) | ((gx & 3u) << 1));
+        float4 u[8], w[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) u[i] = (rot & 1) ? r[k][(i + 1) & 7] : r[k][i];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w[i] = (rot & 2) ? u[(i + 2) & 7] : u[i];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) u[i] = (rot & 4) ? w[(i + 4) & 7] : w[i];
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sum = add4(sum, u[i]);
+        m[k] = mul4(sum, 0.125f);
+        if (in_bounds(code, a.texels[1], kOobMip)) a.lvl[1][code] = m[k];
+      }
+      // the next phase's loads (the stores above have taken r)
+      if (p + 1 < 16)
+        load(P, p + 1);
+      else if (P + gridDim.x < patches)
+        load(P + gridDim.x, 0);
+      if (a.top < 2) continue;
+      // level-2 cells of each unit: lanes 0..3 take cell c = lane, children
+      // i at lane 2c + (i & 1) + (i >> 1) * 8 (child order, as mean8)
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const uint32_t u = warp + 8u * (uint32_t)k;
+        if (u >= units) continue;  // warp-uniform
+        const uint32_t c = lane & 3u;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int src = (int)(2u * c) + (i & 1) + (i >> 1) * 8;
+          float4 ch;
+          ch.x = __shfl_sync(0xffffffffu, m[k].x, src);
+          ch.y = __shfl_sync(0xffffffffu, m[k].y, src);
+          ch.z = __shfl_sync(0xffffffffu, m[k].z, src);
+          ch.w = __shfl_sync(0xffffffffu, m[k].w, src);
+          v = i == 0 ? ch : add4(v, ch);
+        }
+        v = mul4(v, 0.125f);
+        if (lane < 4u) {
+          const uint32_t qx = 4u * u + c;
+          const uint32_t code = morton3(px * (X / 4) + qx, py * (kPatchYZ / 4) + (p & 3),
+                                        pz * (kPatchYZ / 4) + (p >> 2));
+          if (in_bounds(code, a.texels[2], kOobMip)) a.lvl[2][code] = v;
+          s2[p * (X / 4) + qx] = v;
+        }
+      }
     }
-    if (!write1) continue;
-    // rotate so that t[i] = r[(i + rot) & 7], then add in order
-    const int rot = (int)((cy & 1u) | ((cx & 3u) << 1));
-    float4 t[8];
+    __syncthreads();
+    const uint32_t t = threadIdx.x;
+    const uint32_t w3 = X / 8;  // level-3 texels per row of the patch
+    if (a.top >= 3 && t < 4 * w3) {
+      const uint32_t rx = t % w3, ry = (t / w3) & 1u, rz = t / (2 * w3);
+      float4 c[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) t[i] = (rot & 1) ? r[(i + 1) & 7] : r[i];
+      for (int i = 0; i < 8; ++i)
+        c[i] = s2[((2 * rz + (i >> 2)) * 4 + 2 * ry + ((i >> 1) & 1)) * (X / 4) + 2 * rx + (i & 1)];
+      const float4 v = mean8(c);
+      const uint32_t code = morton3(px * w3 + rx, py * 2 + ry, pz * 2 + rz);
+      if (in_bounds(code, a.texels[3], kOobMip)) a.lvl[3][code] = v;
+      s3[(rz * 2 + ry) * w3 + rx] = v;
+    }
+    __syncthreads();
+    if (a.top >= 4 && t < X / 16) {
+      float4 c[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) r[i] = (rot & 2) ? t[(i + 2) & 7] : t[i];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) t[i] = (rot & 4) ? r[(i + 4) & 7] : r[i];
-    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) sum = add4(sum, t[i]);
-    if (in_bounds(code, cells, kOobMip)) lvl1[code] = mul4(sum, 0.125f);
+      for (int i = 0; i < 8; ++i) c[i] = s3[(i >> 1) * w3 + 2 * t + (i & 1)];
+      const float4 v = mean8(c);
+      const uint32_t code = morton3(px * (X / 16) + t, py, pz);
+      if (in_bounds(code, a.texels[4], kOobMip)) a.lvl[4][code] = v;
+    }
+    // the next patch's level-2 writes to s2 must not overtake the reads above
+    __syncthreads();
   }
 }
 
@@ -344,6 +452,8 @@ __global__ void __launch_bounds__(256) stream_level01_kernel(const float4 *__res
 // children of texel j are 8j .. 8j+7.  Levels above the first are reduced in
 // shared memory.
 constexpr int kGroupLevels = 4;  // 4096 source texels per CTA
+// The one-CTA tail starts from a level of at most this many texels.
+constexpr uint64_t kTailSourceTexels = 4096;
 struct GroupArgs {
   const float4 *src;
   float4 *dst[kGroupLevels];
@@ -708,8 +818,9 @@ cudaError_t launch_build_aniso(const float *level0, const vct_pyramid &pyr, int 
   return e;
 }
 
-// Dense float32 pyramids of n >= 32: stream_level01_kernel, then groups of
-// kGroupLevels levels, then the one-CTA tail.
+// Dense float32 pyramids of n >= 32: stream_levels_kernel (levels 0 .. 4),
+// then groups of kGroupLevels levels while the level below holds more than
+// one tail CTA's worth of texels, then the one-CTA tail.
 static cudaError_t build_dense_f32_streamed(const float *level0, const vct_pyramid &pyr,
                                            cudaStream_t s) {
   const Layout L = make_layout(pyr.n, pyr.levels, pyr.dtype, pyr.layout);
@@ -718,42 +829,51 @@ static cudaError_t build_dense_f32_streamed(const float *level0, const vct_pyram
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint64_t cells = level_texels(pyr.n, 1);
-  const int grid1 = (int)std::min<uint64_t>((cells + 255) / 256, (uint64_t)sms * 8);
-  stream_level01_kernel<<<grid1, 256, 0, s>>>(reinterpret_cast<const float4 *>(level0), lvl(0),
-                                               pyr.levels > 1 ? lvl(1) : nullptr, pyr.n,
-                                               pyr.levels > 1 ? 1 : 0);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || pyr.levels <= 2) return e;
-  // levels 2 .. 1 + k from level 1 (8^k | (n/2)^3 since k <= log2(n) - 1)
-  const int k = std::min(kGroupLevels, pyr.levels - 2);
-  GroupArgs g{};
-  g.src = lvl(1);
-  g.k = k;
-  for (int i = 0; i < k; ++i) {
-    g.dst[i] = lvl(2 + i);
-    g.dst_texels[i] = level_texels(pyr.n, 2 + i);
+  StreamArgs sa{};
+  sa.dense = reinterpret_cast<const float4 *>(level0);
+  sa.n = pyr.n;
+  sa.X = std::min(pyr.n, kPatchX);
+  sa.top = std::min(kStreamTop, pyr.levels - 1);
+  for (int l = 0; l <= sa.top; ++l) {
+    sa.lvl[l] = lvl(l);
+    sa.texels[l] = level_texels(pyr.n, l);
   }
-  const uint64_t groups = cells >> (3 * k);
+  const uint64_t patches = (uint64_t)(pyr.n / sa.X) * (pyr.n / kPatchYZ) * (pyr.n / kPatchYZ);
+  const int grid1 = (int)std::min<uint64_t>(patches, (uint64_t)sms * 2);
+  stream_levels_kernel<<<grid1, 256, 0, s>>>(sa);
+  cudaError_t e = cudaGetLastError();
+  int m = sa.top;  // the last level made so far
+  if (e != cudaSuccess || m >= pyr.levels - 1) return e;
   cudaLaunchAttribute pdl[1];
   pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   pdl[0].val.programmaticStreamSerializationAllowed = 1;
   cudaLaunchConfig_t lc{};
-  lc.gridDim = dim3((unsigned)groups);
-  lc.blockDim = dim3(256);  // 256 threads: see the kernel
   lc.stream = s;
   lc.attrs = pdl;
   lc.numAttrs = 1;
-  if ((e = cudaLaunchKernelEx(&lc, mip_group_kernel, g)) != cudaSuccess) return e;
-  const int m_top = 1 + k;
-  if (m_top >= pyr.levels - 1) return cudaSuccess;
+  // levels m+1 .. m+k from level m (8^k divides its texels: k <= log2(n) - m)
+  while (m < pyr.levels - 1 && level_texels(pyr.n, m) > kTailSourceTexels) {
+    const int k = std::min(kGroupLevels, pyr.levels - 1 - m);
+    GroupArgs g{};
+    g.src = lvl(m);
+    g.k = k;
+    for (int i = 0; i < k; ++i) {
+      g.dst[i] = lvl(m + 1 + i);
+      g.dst_texels[i] = level_texels(pyr.n, m + 1 + i);
+    }
+    lc.gridDim = dim3((unsigned)(level_texels(pyr.n, m) >> (3 * k)));
+    lc.blockDim = dim3(256);  // 256 threads: see the kernel
+    if ((e = cudaLaunchKernelEx(&lc, mip_group_kernel, g)) != cudaSuccess) return e;
+    m += k;
+  }
+  if (m >= pyr.levels - 1) return cudaSuccess;
   TailArgs t{};
   for (int l = 0; l < pyr.levels; ++l) t.lvl[l] = base + L.level_off[l];
   t.pool = base + L.pool_off;
   t.n = pyr.n;
   t.levels = pyr.levels;
-  t.m_top = m_top;
-  t.src0 = lvl(m_top);
+  t.m_top = m;
+  t.src0 = lvl(m);
   lc.gridDim = dim3(1);
   lc.blockDim = dim3(1024);
   return cudaLaunchKernelEx(&lc, mip_tail_kernel<VCT_F32, false, true>, t);
