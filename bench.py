@@ -95,6 +95,15 @@ def _code_only(text: str) -> str:
     return " ".join("".join(out).split())
 
 
+def percentiles(xs):
+    """p10 / median / p90 of per-step event times (nearest rank)."""
+    v = sorted(xs)
+    if not v:
+        return None
+    pick = lambda q: v[min(len(v) - 1, max(0, int(round(q * (len(v) - 1)))))]
+    return {"p10": pick(0.1), "p50": pick(0.5), "p90": pick(0.9), "n": len(v)}
+
+
 def sources_hash(files) -> str:
     """sha1[:16] of the code (comments and spacing removed) of the files."""
     h = hashlib.sha1()
@@ -365,8 +374,9 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (268 MB level-0 grid, 307 MB pyramid)",
                        "parallelism": f"replica x{ws}"},
             "trace_ms": trace_avg,
+            "trace_ms_percentiles": percentiles(trace_ms),
             "roofline": roof,
-            "mip_build": {"ms": build_avg, "bytes": mip_bytes,
+            "mip_build": {"ms": build_avg, "ms_percentiles": percentiles(build_ms), "bytes": mip_bytes,
                           "achieved_gbs": mip_bytes / (build_avg / 1e3) / 1e9,
                           "frac_of_hbm_peak": mip_bytes / (build_avg / 1e3) / 1e9 / hbm,
                           "peak_source": peak_kind,
