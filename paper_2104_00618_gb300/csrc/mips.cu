@@ -879,13 +879,17 @@ static cudaError_t build_dense_f32_streamed(const float *level0, const vct_pyram
   return cudaLaunchKernelEx(&lc, mip_tail_kernel<VCT_F32, false, true>, t);
 }
 
-cudaError_t launch_pack_mips(const float *level0, const vct_pyramid &pyr,
-                             const CUtensorMap &map, cudaStream_t s) {
-  const bool br = pyr.layout == VCT_LAYOUT_BRICKS;
+bool streamed_build(const float *level0, const vct_pyramid &pyr) {
   // (its 32-byte loads need a 32-byte aligned grid; the TMA path needs 16)
-  if (pyr.dtype == VCT_F32 && !br && pyr.n >= 32 &&
-      reinterpret_cast<uintptr_t>(level0) % 32 == 0)
-    return build_dense_f32_streamed(level0, pyr, s);
+  return pyr.dtype == VCT_F32 && pyr.layout == VCT_LAYOUT_DENSE && pyr.n >= 32 &&
+         reinterpret_cast<uintptr_t>(level0) % 32 == 0;
+}
+
+cudaError_t launch_pack_mips(const float *level0, const vct_pyramid &pyr,
+                             const CUtensorMap *map, cudaStream_t s) {
+  const bool br = pyr.layout == VCT_LAYOUT_BRICKS;
+  if (streamed_build(level0, pyr)) return build_dense_f32_streamed(level0, pyr, s);
+  if (map == nullptr) return cudaErrorInvalidValue;
   const Layout L = make_layout(pyr.n, pyr.levels, pyr.dtype, pyr.layout);
   uint8_t *base = static_cast<uint8_t *>(pyr.data);
   const int B = pack_block(pyr.n);
@@ -928,11 +932,11 @@ cudaError_t launch_pack_mips(const float *level0, const vct_pyramid &pyr,
   const int blocks = (int)level_texels(pyr.n, mB);  // (n/B)^3
   a.nblocks = (uint32_t)blocks;
   if (pyr.dtype == VCT_F32)
-    e = br ? pack_t<VCT_F32, true>(map, a, blocks, smem, s)
-           : pack_t<VCT_F32, false>(map, a, blocks, smem, s);
+    e = br ? pack_t<VCT_F32, true>(*map, a, blocks, smem, s)
+           : pack_t<VCT_F32, false>(*map, a, blocks, smem, s);
   else
-    e = br ? pack_t<VCT_F16, true>(map, a, blocks, smem, s)
-           : pack_t<VCT_F16, false>(map, a, blocks, smem, s);
+    e = br ? pack_t<VCT_F16, true>(*map, a, blocks, smem, s)
+           : pack_t<VCT_F16, false>(*map, a, blocks, smem, s);
   if (e != cudaSuccess || !tail) return e;
 
   TailArgs t{};

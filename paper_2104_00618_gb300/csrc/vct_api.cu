@@ -438,6 +438,11 @@ vct_status vct_build_mips(const float *level0_dense, const vct_pyramid *pyr, vct
     if (e != cudaSuccess) return cuda_fail(e, "vct_build_mips (anisotropic) launch");
     return VCT_OK;
   }
+  if (streamed_build(level0_dense, *pyr)) {  // no tensor map to encode
+    cudaError_t e = launch_pack_mips(level0_dense, *pyr, nullptr, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "vct_build_mips launch");
+    return VCT_OK;
+  }
   auto enc = encode_fn();
   if (!enc) return fail(VCT_ERR_CUDA, "vct_build_mips: cuTensorMapEncodeTiled unavailable");
   const int n = pyr->n, B = pack_block(n);
@@ -451,7 +456,7 @@ vct_status vct_build_mips(const float *level0_dense, const vct_pyramid *pyr, vct
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(VCT_ERR_CUDA, "vct_build_mips: tensor map encode failed (%d)", (int)r);
-  cudaError_t e = launch_pack_mips(level0_dense, *pyr, map, (cudaStream_t)stream);
+  cudaError_t e = launch_pack_mips(level0_dense, *pyr, &map, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "vct_build_mips launch");
   return VCT_OK;
 }

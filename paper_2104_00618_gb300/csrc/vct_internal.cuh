@@ -390,8 +390,13 @@ inline ConeConst cone_const(double gamma, double beta, double t0_vox,
 vct_status set_last_error(vct_status st, const char *fmt, ...);
 
 // Host entry points implemented in the .cu files (internal linkage across TUs).
+// True when launch_pack_mips streams the grid (dense float32, n >= 32, a
+// 32-byte aligned level 0) and needs no tensor map.
+bool streamed_build(const float *level0, const vct_pyramid &pyr);
+// `map`: the level-0 tensor map of the TMA path; unused (may be null) when
+// streamed_build() holds.
 cudaError_t launch_pack_mips(const float *level0, const vct_pyramid &pyr,
-                             const CUtensorMap &map, cudaStream_t s);
+                             const CUtensorMap *map, cudaStream_t s);
 cudaError_t launch_read_level(const vct_pyramid &pyr, int level, float *out, cudaStream_t s,
                               int direction = 0);
 cudaError_t launch_build_aniso(const float *level0, const vct_pyramid &pyr, int sms,
