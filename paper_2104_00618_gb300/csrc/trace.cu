@@ -38,7 +38,7 @@ __device__ __forceinline__ int find_view(const TraceLaunch &L, int item, bool sm
 // compute them per step.
 template <int DT, bool kVar, bool BR, bool AN = false>
 __device__ __forceinline__ float4 march(const DevPyr &P, const Apex &A, const float w[3],
-                                        const ConeConst &cc, float T0, const uint32_t *lut,
+                                        const ConeConst &cc, float T0, const uint2 *lut,
                                         const float4 *tab, uint32_t &nsamp, float &trans,
                                         uint2 &state, int mode = kPlain,
                                         const Variants *var = nullptr) {
@@ -193,9 +193,9 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
   const int n_cones = L.n_diffuse + L.spec_enable + L.occ_enable;
   const int first_cone = defer_spec ? 1 : 0;  // the specular cone is cone 0
   const float T0 = L.spec.t0_vox;
-  __shared__ uint32_t s_lut[kSpreadLut];
+  __shared__ uint2 s_lut[kSpreadLut];
   __shared__ uint32_t s_keys[kFwdThreads / 32][kMaxSortPixels];
-  __shared__ float4 s_tab[VCT_MAX_PYRAMIDS * 2 * kStepTab];
+  extern __shared__ __align__(16) float4 s_tab[];  // n_pyr * 2 * kStepTab entries
   uint32_t *keys = s_keys[threadIdx.x >> 5];
   fill_step_table(s_tab, L.pyr, L.n_pyr, T0);
   fill_spread_lut(s_lut);  // (its barrier also covers s_tab)
@@ -395,12 +395,16 @@ __global__ void __launch_bounds__(kFwdThreads, kTraceMinBlocks) trace_kernel(con
   }
 }
 
+// Dynamic shared memory of a launch: the step tables of its pyramids.
+inline size_t step_table_bytes(int n_pyr) { return (size_t)n_pyr * 2 * kStepTab * sizeof(float4); }
+
 template <int LPP, int DT, bool BR, bool AN = false>
 cudaError_t launch_t(const TraceLaunch &L, int grid, cudaStream_t s) {
+  const size_t dyn = step_table_bytes(L.n_pyr);
   if (L.var.flags)
-    trace_kernel<LPP, DT, true, BR, AN><<<grid, kFwdThreads, 0, s>>>(L);
+    trace_kernel<LPP, DT, true, BR, AN><<<grid, kFwdThreads, dyn, s>>>(L);
   else
-    trace_kernel<LPP, DT, false, BR, AN><<<grid, kFwdThreads, 0, s>>>(L);
+    trace_kernel<LPP, DT, false, BR, AN><<<grid, kFwdThreads, dyn, s>>>(L);
   return cudaGetLastError();
 }
 
@@ -419,10 +423,10 @@ int occ_t(bool var) {
   int b = 0;
   if (var)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<LPP, DT, true, false, false>,
-                                                  kFwdThreads, 0);
+                                                  kFwdThreads, step_table_bytes(VCT_MAX_PYRAMIDS));
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<LPP, DT, false, false, false>,
-                                                  kFwdThreads, 0);
+                                                  kFwdThreads, step_table_bytes(VCT_MAX_PYRAMIDS));
   return b;
 }
 

@@ -231,7 +231,7 @@ __device__ __forceinline__ void scatter_level(const BwdLaunch &L, const uint32_t
 // (1 - a_k) R'_{k+1}.
 template <int DT, bool BR, bool kVar, bool AN = false>
 __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t *code_off,
-                                             const uint32_t *lut, bool active,
+                                             const uint2 *lut, bool active,
                                              const Apex &A, const float w[3],
                                              const ConeConst &cc, float T0, float gc0, float gc1,
                                              float gc2, float ga, const uint2 *state, int mode) {
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(kTraceThreads, 2) trace_bwd_kernel(const __gri
     }
     s_code_off[kKeyTotal] = acc;
   }
-  __shared__ uint32_t s_lut[kSpreadLut];
+  __shared__ uint2 s_lut[kSpreadLut];
   fill_spread_lut(s_lut);  // (its barrier also covers s_code_off)
 
   for (;;) {

@@ -163,14 +163,14 @@ struct LevelStencil {
   uint32_t valid;  // bit c set if corner c = dx | dy<<1 | dz<<2 is inside the level
 };
 
-// lut: three tables of 1024 entries (shared memory): spread3(i), spread3(i)
-// << 1 and spread3(i) << 2, the Morton bits of x, y and z already in place.
+// lut: three tables of 1024 entries (shared memory, fill_spread_lut): the
+// Morton bits of x, y and z (spread3(i), << 1, << 2), each with those of i + 1.
 // kPacked: x and y as float32 pairs (the same operations per element, so
 // the same bits): the forward's isotropic sampler; the anisotropic sampler
 // (measured slower packed) and the adjoint use the scalar form.
 template <bool kPacked = true>
 __device__ __forceinline__ void level_stencil(int l, int Nl, const Apex &A, const float F[3],
-                                              const uint32_t *lut, LevelStencil &s) {
+                                              const uint2 *lut, LevelStencil &s) {
   const float sc = __int_as_float((127 - l) << 23);  // 2^-l
   const int mask = (1 << l) - 1;
   int b[3];
@@ -198,15 +198,15 @@ __device__ __forceinline__ void level_stencil(int l, int Nl, const Apex &A, cons
     s.fr[a] = v - fl;
     b[a] = (A.Xi[a] >> l) + iv;
   }
-  const uint32_t x0 = lut[(uint32_t)b[0] & 1023u];
-  const uint32_t y0 = lut[1024u + ((uint32_t)b[1] & 1023u)];
-  const uint32_t z0 = lut[2048u + ((uint32_t)b[2] & 1023u)];
-  s.sx[0] = x0;
-  s.sx[1] = spread3_inc(x0);
-  s.sy[0] = y0;
-  s.sy[1] = (y0 - (kMortonX << 1)) & (kMortonX << 1);  // spread3_inc in place
-  s.sz[0] = z0;
-  s.sz[1] = (z0 - (kMortonX << 2)) & (kMortonX << 2);
+  const uint2 xe = lut[(uint32_t)b[0] & 1023u];
+  const uint2 ye = lut[1024u + ((uint32_t)b[1] & 1023u)];
+  const uint2 ze = lut[2048u + ((uint32_t)b[2] & 1023u)];
+  s.sx[0] = xe.x;
+  s.sx[1] = xe.y;
+  s.sy[0] = ye.x;
+  s.sy[1] = ye.y;
+  s.sz[0] = ze.x;
+  s.sz[1] = ze.y;
   // Interior cells (the common case) need no per-corner test.
   const uint32_t lim = (uint32_t)Nl - 1u;
   if ((uint32_t)b[0] < lim && (uint32_t)b[1] < lim && (uint32_t)b[2] < lim) {
@@ -351,7 +351,7 @@ __device__ __forceinline__ float transparency(float a) { return fmaxf(1.0f - a, 
 // When `st` is non-null the two stencils are kept for the adjoint.
 template <int DT, bool BR = false, bool kPacked = true>
 __device__ __forceinline__ float4 sample_at(const DevPyr &P, const Apex &A, const float F[3],
-                                            const LodPick &lp, const uint32_t *lut, float &om,
+                                            const LodPick &lp, const uint2 *lut, float &om,
                                             LevelStencil *st = nullptr) {
   LevelStencil s;
   f32x2 rg, ba;
@@ -373,7 +373,7 @@ __device__ __forceinline__ float4 sample_at(const DevPyr &P, const Apex &A, cons
 }
 template <int DT, bool BR = false, bool kPacked = true>
 __device__ __forceinline__ float4 sample(const DevPyr &P, const Apex &A, const float F[3],
-                                         float lam, const uint32_t *lut, float &om,
+                                         float lam, const uint2 *lut, float &om,
                                          LodPick &lp, LevelStencil *st = nullptr) {
   lp = pick_levels(lam, P.levels);
   return sample_at<DT, BR, kPacked>(P, A, F, lp, lut, om, st);
@@ -522,7 +522,7 @@ __device__ __forceinline__ void aniso_level(const DevPyr &P, int l, const LevelS
 // S(p, lambda) of an anisotropic pyramid for travel along the cone axis.
 __device__ __forceinline__ float4 sample_aniso_at(const DevPyr &P, const Apex &A,
                                                   const float F[3], const LodPick &lp,
-                                                  const uint32_t *lut, const AnisoW &aw,
+                                                  const uint2 *lut, const AnisoW &aw,
                                                   float &om, LevelStencil *st = nullptr) {
   LevelStencil s;
   f32x2 rg, ba;
@@ -543,7 +543,7 @@ __device__ __forceinline__ float4 sample_aniso_at(const DevPyr &P, const Apex &A
   return make_float4(v0.x, v0.y, v1.x, v1.y);
 }
 __device__ __forceinline__ float4 sample_aniso(const DevPyr &P, const Apex &A, const float F[3],
-                                               float lam, const uint32_t *lut, const AnisoW &aw,
+                                               float lam, const uint2 *lut, const AnisoW &aw,
                                                float &om, LodPick &lp,
                                                LevelStencil *st = nullptr) {
   lp = pick_levels(lam, P.levels);
@@ -570,11 +570,15 @@ __device__ __forceinline__ void fill_step_table(float4 *tab, const DevPyr *pyrs,
   }
 }
 
-// Fills the Morton spread tables (shared memory, kSpreadLut entries) of a CTA.
+// Fills the Morton spread tables (shared memory, kSpreadLut entries) of a
+// CTA: for axis a = i >> 10 and coordinate c = i & 1023 the spread bits of c
+// and of c + 1 (10-bit wrap), in place for the axis (shifted left by a).
 constexpr int kSpreadLut = 3 * 1024;
-__device__ __forceinline__ void fill_spread_lut(uint32_t *lut) {
-  for (int i = threadIdx.x; i < kSpreadLut; i += blockDim.x)
-    lut[i] = spread3((uint32_t)i & 1023u) << (i >> 10);
+__device__ __forceinline__ void fill_spread_lut(uint2 *lut) {
+  for (int i = threadIdx.x; i < kSpreadLut; i += blockDim.x) {
+    const uint32_t c = (uint32_t)i & 1023u;
+    lut[i] = make_uint2(spread3(c) << (i >> 10), spread3((c + 1u) & 1023u) << (i >> 10));
+  }
   __syncthreads();
 }
 
