@@ -408,7 +408,7 @@ def run_e2e(torch, vct, dev, scene, hv, params, args, stream, steps=None):
     every step copies its inputs from page-locked host memory, builds the
     mips, traces and copies its outputs back; the library overlaps the
     copies of one step with the kernels of its neighbours."""
-    steps = steps or max(3, min(args.steps, 10))
+    steps = steps or max(3, min(args.steps, 30))  # the timed steps of the device leg, up to 30
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     h_grid = pin(scene["grid"])
     h_pos, h_nrm = pin(hv["position"]), pin(hv["normal"])
