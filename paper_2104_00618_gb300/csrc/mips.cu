@@ -458,39 +458,50 @@ struct GroupArgs {
   const float4 *src;
   float4 *dst[kGroupLevels];
   uint64_t dst_texels[kGroupLevels];
+  uint64_t src_texels;  // texels of one volume of level s (the volume stride)
   int k;
 };
+// The plain box filter: the mean of the 8 children (volume unused).
+struct MeanOf8 {
+  __device__ __forceinline__ float4 operator()(const float4 *c, int) const { return mean8(c); }
+};
+// Reduce(children, volume): the texel from its 8 children; blockIdx.y is the
+// volume (the direction of an anisotropic level, 0 for a dense pyramid).
+template <class Reduce>
 __global__ void __launch_bounds__(256) mip_group_kernel(const __grid_constant__ GroupArgs a) {
   __shared__ float4 sm[512 + 64 + 8 + 1];
   wait_for_previous_grid();  // level s comes from the previous kernel
   allow_dependents();
+  const Reduce red;
+  const int vol = (int)blockIdx.y;
+  const float4 *src = a.src + (uint64_t)vol * a.src_texels;
   const int first = 1 << (3 * (a.k - 1));  // texels of level s+1 per group
   const uint64_t g = blockIdx.x;
   float4 *cur = sm;
   // two level-(s+1) texels per thread (blockDim.x = 256, first <= 512), the
-  // loads of both issued before either mean
+  // loads of both issued before either reduction
   const int j0 = threadIdx.x, j1 = threadIdx.x + blockDim.x;
   float4 ch0[8], ch1[8];
   if (j0 < first) {
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-      ld_32(a.src + 8 * (g * first + j0) + 2 * q, ch0[2 * q], ch0[2 * q + 1]);
+      ld_32(src + 8 * (g * first + j0) + 2 * q, ch0[2 * q], ch0[2 * q + 1]);
   }
   if (j1 < first) {
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-      ld_32(a.src + 8 * (g * first + j1) + 2 * q, ch1[2 * q], ch1[2 * q + 1]);
+      ld_32(src + 8 * (g * first + j1) + 2 * q, ch1[2 * q], ch1[2 * q + 1]);
   }
   if (j0 < first) {
     const uint64_t o = g * first + j0;
-    const float4 v = mean8(ch0);
-    if (in_bounds(o, a.dst_texels[0], kOobMip)) a.dst[0][o] = v;
+    const float4 v = red(ch0, vol);
+    if (in_bounds(o, a.dst_texels[0], kOobMip)) a.dst[0][(uint64_t)vol * a.dst_texels[0] + o] = v;
     cur[j0] = v;
   }
   if (j1 < first) {
     const uint64_t o = g * first + j1;
-    const float4 v = mean8(ch1);
-    if (in_bounds(o, a.dst_texels[0], kOobMip)) a.dst[0][o] = v;
+    const float4 v = red(ch1, vol);
+    if (in_bounds(o, a.dst_texels[0], kOobMip)) a.dst[0][(uint64_t)vol * a.dst_texels[0] + o] = v;
     cur[j1] = v;
   }
   int cnt = first;
@@ -499,10 +510,10 @@ __global__ void __launch_bounds__(256) mip_group_kernel(const __grid_constant__ 
     float4 *nxt = cur + cnt;
     const int nc = cnt / 8;
     for (int j = threadIdx.x; j < nc; j += blockDim.x) {
-      const float4 v = mean8(cur + 8 * j);
+      const float4 v = red(cur + 8 * j, vol);
       nxt[j] = v;
       const uint64_t o = g * nc + j;
-      if (in_bounds(o, a.dst_texels[l], kOobMip)) a.dst[l][o] = v;
+      if (in_bounds(o, a.dst_texels[l], kOobMip)) a.dst[l][(uint64_t)vol * a.dst_texels[l] + o] = v;
     }
     cur = nxt;
     cnt = nc;
@@ -584,8 +595,9 @@ __device__ __forceinline__ float4 pair_composite(float4 f, float4 b) {
   const float a = fmaf(t, b.w, f.w);
   const float tb = t * b.w;
   if (!(a > 0.0f)) return make_float4(0.f, 0.f, 0.f, 0.f);
-  return make_float4(__fdiv_rn(fmaf(f.w, f.x, tb * b.x), a), __fdiv_rn(fmaf(f.w, f.y, tb * b.y), a),
-                     __fdiv_rn(fmaf(f.w, f.z, tb * b.z), a), a);
+  const float inv = __frcp_rn(a);  // one reciprocal for the three channels
+  return make_float4(fmaf(f.w, f.x, tb * b.x) * inv, fmaf(f.w, f.y, tb * b.y) * inv,
+                     fmaf(f.w, f.z, tb * b.z) * inv, a);
 }
 
 // Texel of direction d (axis d >> 1, negative travel if d & 1) from its 8
@@ -605,6 +617,35 @@ __device__ __forceinline__ float4 aniso_texel(const float4 ch[8], int d) {
     acc.w += p.w;
   }
   return make_float4(acc.x * 0.25f, acc.y * 0.25f, acc.z * 0.25f, acc.w * 0.25f);
+}
+
+// The texels of both directions of one axis (travel towards +axis into
+// `pos`, towards -axis into `neg`) from the same 8 children: a pair's
+// opacity 1 - (1 - a_f)(1 - a_b) is the same for either order of travel, so
+// each pair's opacity and its reciprocal serve both directions.
+__device__ __forceinline__ void aniso_axis(const float4 ch[8], int axis, float4 &pos,
+                                           float4 &neg) {
+  pos = make_float4(0.f, 0.f, 0.f, 0.f);
+  neg = pos;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if ((c >> axis) & 1) continue;
+    const float4 lo = ch[c], hi = ch[c | (1 << axis)];
+    const float a = fmaf(1.0f - lo.w, hi.w, lo.w);
+    if (!(a > 0.0f)) continue;
+    const float inv = __fdividef(1.0f, a);  // a in (0, 1]: within 2 ulp of 1 / a
+    const float tl = (1.0f - lo.w) * hi.w, th = (1.0f - hi.w) * lo.w;
+    pos.x += fmaf(lo.w, lo.x, tl * hi.x) * inv;
+    pos.y += fmaf(lo.w, lo.y, tl * hi.y) * inv;
+    pos.z += fmaf(lo.w, lo.z, tl * hi.z) * inv;
+    neg.x += fmaf(hi.w, hi.x, th * lo.x) * inv;
+    neg.y += fmaf(hi.w, hi.y, th * lo.y) * inv;
+    neg.z += fmaf(hi.w, hi.z, th * lo.z) * inv;
+    pos.w += a;
+    neg.w += a;
+  }
+  pos = make_float4(pos.x * 0.25f, pos.y * 0.25f, pos.z * 0.25f, pos.w * 0.25f);
+  neg = make_float4(neg.x * 0.25f, neg.y * 0.25f, neg.z * 0.25f, neg.w * 0.25f);
 }
 
 // Levels 0 and 1 in one pass: one thread per level-1 texel j reads its 2x2x2
@@ -630,6 +671,109 @@ __global__ void aniso_level01_kernel(const float4 *__restrict__ dense, float4 *_
 #pragma unroll
     for (int d = 0; d < 6; ++d)
       if (in_bounds(j, texels1, kOobMip)) lvl1[(uint64_t)d * texels1 + j] = aniso_texel(ch, d);
+  }
+}
+
+// The anisotropic reduction for the level-group kernel (volume = direction;
+// the switch keeps the children's indices compile-time constants, so they
+// stay in registers).
+struct AnisoOf8 {
+  __device__ __forceinline__ float4 operator()(const float4 *c, int d) const {
+    switch (d) {
+      case 0: return aniso_texel(c, 0);
+      case 1: return aniso_texel(c, 1);
+      case 2: return aniso_texel(c, 2);
+      case 3: return aniso_texel(c, 3);
+      case 4: return aniso_texel(c, 4);
+      default: return aniso_texel(c, 5);
+    }
+  }
+};
+
+// Levels 0, 1 and 2 of an anisotropic pyramid from a 32-byte aligned dense
+// grid (n >= 16), in units of 8 x 4 level-1 cells: the four level-1 rows
+// (2 uy + iy, 2 uz + iz) under level-2 row (uy, uz), x cells 8 ux .. 8 ux +
+// 7, lane = cx' | row << 3 (row = iy | iz << 1), ux fastest, so a warp reads
+// 256-byte pieces of 16 rows of the grid.  A lane's cell: its 8 children as
+// four 32-byte x pairs, written to level 0 at Morton codes 8 code .. 8 code
+// + 7, and texel `code` of the six level-1 volumes; a unit holds four whole
+// level-2 cells, whose six directional texels lanes 0..3 form from the
+// level-1 texels of their children, gathered by shuffles.  The next unit's
+// loads are issued before the level-2 work of this one.
+__global__ void __launch_bounds__(256) aniso_stream012_kernel(const float4 *__restrict__ dense,
+                                                              float4 *__restrict__ lvl0,
+                                                              float4 *__restrict__ lvl1,
+                                                              float4 *__restrict__ lvl2, int n,
+                                                              int top) {
+  allow_dependents();
+  const uint32_t un = (uint32_t)n;
+  const uint32_t uxn = un / 16, uyn = un / 4;
+  const uint64_t units = (uint64_t)uxn * uyn * uyn;
+  const uint64_t texels1 = (uint64_t)(un / 2) * (un / 2) * (un / 2), texels0 = 8 * texels1;
+  const uint64_t texels2 = texels1 / 8;
+  const uint32_t lane = threadIdx.x & 31u, row = lane >> 3, c = lane & 3u;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  // cell of this lane in unit u
+  auto cell = [&](uint64_t u, uint32_t &cx, uint32_t &cy, uint32_t &cz) {
+    const uint32_t ux = (uint32_t)(u % uxn), uy = (uint32_t)((u / uxn) % uyn),
+                   uz = (uint32_t)(u / ((uint64_t)uxn * uyn));
+    cx = 8u * ux + (lane & 7u);
+    cy = 2u * uy + (row & 1u);
+    cz = 2u * uz + (row >> 1);
+  };
+  auto load = [&](uint64_t u, float4 ch[8]) {
+    uint32_t cx, cy, cz;
+    cell(u, cx, cy, cz);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {  // q = jy | jz << 1
+      const uint64_t y = 2 * cy + (q & 1), z = 2 * cz + (q >> 1);
+      ld_stream_32(dense + (z * un + y) * un + 2 * cx, ch[2 * q], ch[2 * q + 1]);
+    }
+  };
+  const uint64_t u0 = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  float4 ch[8];
+  if (u0 < units) load(u0, ch);
+  for (uint64_t u = u0; u < units; u += warps) {
+    uint32_t cx, cy, cz;
+    cell(u, cx, cy, cz);
+    const uint32_t code = morton3(cx, cy, cz);
+    if (in_bounds(8 * (uint64_t)code + 7, texels0, kOobMip)) {
+      float4 *dst = lvl0 + 8 * (uint64_t)code;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) st_stream_32(dst + 2 * q, ch[2 * q], ch[2 * q + 1]);
+    }
+    if (top < 1) {
+      if (u + warps < units) load(u + warps, ch);
+      continue;
+    }
+    float4 t[6];
+#pragma unroll
+    for (int axis = 0; axis < 3; ++axis) aniso_axis(ch, axis, t[2 * axis], t[2 * axis + 1]);
+#pragma unroll
+    for (int d = 0; d < 6; ++d)
+      if (in_bounds(code, texels1, kOobMip)) lvl1[(uint64_t)d * texels1 + code] = t[d];
+    // the next unit's loads (ch is no longer needed) overlap the level-2 work
+    if (u + warps < units) load(u + warps, ch);
+    if (top < 2) continue;
+    // lane c < 4 holds cell (8 ux + c, 2 uy, 2 uz): its level-2 cell is 4 ux + c
+    const uint32_t code2 = morton3((cx + c) / 2u, cy / 2u, cz / 2u);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      // children i of lane c's level-2 cell at lanes 2c + (i & 1) + (i >> 1) * 8
+      float4 k[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int src = (int)(2u * c) + (i & 1) + (i >> 1) * 8;
+        k[i].x = __shfl_sync(0xffffffffu, t[d].x, src);
+        k[i].y = __shfl_sync(0xffffffffu, t[d].y, src);
+        k[i].z = __shfl_sync(0xffffffffu, t[d].z, src);
+        k[i].w = __shfl_sync(0xffffffffu, t[d].w, src);
+      }
+      if (lane < 4u) {
+        const float4 v = aniso_texel(k, d);
+        if (in_bounds(code2, texels2, kOobMip)) lvl2[(uint64_t)d * texels2 + code2] = v;
+      }
+    }
   }
 }
 
@@ -805,9 +949,41 @@ cudaError_t launch_build_aniso(const float *level0, const vct_pyramid &pyr, int 
         n);
     return cudaGetLastError();
   }
+  auto lvl = [&](int l) { return reinterpret_cast<float4 *>(base + L.level_off[l]); };
+  if (n >= 16 && reinterpret_cast<uintptr_t>(level0) % 32 == 0) {
+    // levels 0..2 streamed, then level groups (programmatic dependents)
+    const int top = std::min(2, pyr.levels - 1);
+    aniso_stream012_kernel<<<sms * 8, 256, 0, s>>>(reinterpret_cast<const float4 *>(level0),
+                                                    lvl(0), lvl(1), top >= 2 ? lvl(2) : nullptr,
+                                                    n, top);
+    cudaError_t e = cudaGetLastError();
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t lc{};
+    lc.stream = s;
+    lc.attrs = pdl;
+    lc.numAttrs = 1;
+    lc.blockDim = dim3(256);  // 256 threads: see the kernel
+    for (int m = top; m < pyr.levels - 1 && e == cudaSuccess;) {
+      // levels m+1 .. m+k of all six volumes from level m (8^k divides its texels)
+      const int k = std::min(kGroupLevels, pyr.levels - 1 - m);
+      GroupArgs g{};
+      g.src = lvl(m);
+      g.src_texels = level_texels(n, m);
+      g.k = k;
+      for (int i = 0; i < k; ++i) {
+        g.dst[i] = lvl(m + 1 + i);
+        g.dst_texels[i] = level_texels(n, m + 1 + i);
+      }
+      lc.gridDim = dim3((unsigned)(level_texels(n, m) >> (3 * k)), 6);
+      e = cudaLaunchKernelEx(&lc, mip_group_kernel<AnisoOf8>, g);
+      m += k;
+    }
+    return e;
+  }
   aniso_level01_kernel<<<grid_of(level_texels(n, 1)), 256, 0, s>>>(
-      reinterpret_cast<const float4 *>(level0), reinterpret_cast<float4 *>(base + L.level_off[0]),
-      reinterpret_cast<float4 *>(base + L.level_off[1]), n);
+      reinterpret_cast<const float4 *>(level0), lvl(0), lvl(1), n);
   cudaError_t e = cudaGetLastError();
   for (int l = 2; l < pyr.levels && e == cudaSuccess; ++l) {
     aniso_level_kernel<<<grid_of(6 * level_texels(n, l)), 256, 0, s>>>(
@@ -863,7 +1039,8 @@ static cudaError_t build_dense_f32_streamed(const float *level0, const vct_pyram
     }
     lc.gridDim = dim3((unsigned)(level_texels(pyr.n, m) >> (3 * k)));
     lc.blockDim = dim3(256);  // 256 threads: see the kernel
-    if ((e = cudaLaunchKernelEx(&lc, mip_group_kernel, g)) != cudaSuccess) return e;
+    g.src_texels = level_texels(pyr.n, m);
+    if ((e = cudaLaunchKernelEx(&lc, mip_group_kernel<MeanOf8>, g)) != cudaSuccess) return e;
     m += k;
   }
   if (m >= pyr.levels - 1) return cudaSuccess;
