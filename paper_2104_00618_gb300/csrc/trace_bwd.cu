@@ -293,7 +293,7 @@ __device__ __forceinline__ void cone_adjoint(const BwdLaunch &L, const uint32_t 
       if constexpr (AN)
         v = sample_aniso(P, A, F, lam, lut, aw, om, lp, st);
       else
-        v = sample<DT, BR, false>(P, A, F, lam, lut, om, lp, st);
+        v = sample<DT, BR>(P, A, F, lam, lut, om, lp, st);
       if (kVar && mode == kOccSmooth) {  // as the forward march
         fade = smoothstep0(L.var.occ_max_dist, sqrtf(T * P.h0) * L.var.shadow_str);
         v.w *= fade;

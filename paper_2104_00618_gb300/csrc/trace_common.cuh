@@ -166,8 +166,8 @@ struct LevelStencil {
 // lut: three tables of 1024 entries (shared memory, fill_spread_lut): the
 // Morton bits of x, y and z (spread3(i), << 1, << 2), each with those of i + 1.
 // kPacked: x and y as float32 pairs (the same operations per element, so
-// the same bits): the forward's isotropic sampler; the anisotropic sampler
-// (measured slower packed) and the adjoint use the scalar form.
+// the same bits): the isotropic sampler of both passes; the anisotropic
+// sampler (measured slower packed) uses the scalar form.
 template <bool kPacked = true>
 __device__ __forceinline__ void level_stencil(int l, int Nl, const Apex &A, const float F[3],
                                               const uint2 *lut, LevelStencil &s) {
