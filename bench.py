@@ -497,12 +497,18 @@ def extra_small(torch, vct, dev):
     for dt in ("f32", "f16"):
         P = vct.Pyramid(scene["n"], None, dt, device=dev)
         vct.build_mips(level0, out=P)
+        # 16 K pixels fill few of the default 16x16 tiles: let the library's
+        # tuner pick the tile and lanes per pixel for this shape (vct_trace
+        # then uses its choice)
+        tuned = vct.autotune([P], [view], params, workspace=ws)
         tr_ms = _time(torch, lambda: vct.trace([P], [view], params, workspace=ws), 50, warm=5)
         st_ms = _time(torch, lambda: (vct.build_mips(level0, out=P),
                                       vct.trace([P], [view], params, workspace=ws)), 50, warm=5)
         samples = int(sum(vct.read_stats(ws)["samples"]))
         out[dt] = {"trace_ms": tr_ms, "ms_per_step": st_ms, "samples_per_frame": samples,
-                   "gsamples_per_s": samples / (st_ms / 1e3) / 1e9, "accuracy": acc[dt]}
+                   "gsamples_per_s": samples / (st_ms / 1e3) / 1e9, "accuracy": acc[dt],
+                   "tuned": {"tile": [tuned.tile_w, tuned.tile_h],
+                             "lanes_per_pixel": tuned.lanes_per_pixel}}
     return out
 
 
