@@ -196,7 +196,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -205,9 +205,12 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """Median SM clock and throttle reasons of the samples taken between
+        host times t0 and t1 (the timed region), or of all samples if none
+        fall there."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -218,7 +221,11 @@ class ClockSampler:
         self.t.join(timeout=2)
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = [ln for t, ln in self.lines
+                 if t0 is not None and t1 is not None and t0 <= t <= t1]
+        if not lines:
+            lines = [ln for _, ln in self.lines]
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -306,6 +313,13 @@ def run_ours(args):
         if ev is not None:
             ev[1].record(stream)
 
+    clocks = None
+    if not args.profile:
+        # the clock sampler starts before the warm-up, so that the GPU does
+        # not idle between the warm-up and the timed steps
+        clocks = ClockSampler(dev.index)
+        clocks.start()
+        time.sleep(0.3)
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -318,23 +332,22 @@ def run_ours(args):
         return {"profile": True, "samples_per_frame": samples, "width": args.width,
                 "height": args.height, "steps": args.steps, "warmup": max(3, args.warmup)}
 
-    clocks = ClockSampler(dev.index)
     tev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3))
            for _ in range(args.steps)]
     e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
+    t_host0 = time.monotonic()
     e_start.record(stream)
     for i in range(args.steps):
         step(tev[i])
     e_end.record(stream)
     torch.cuda.synchronize()
+    t_host1 = time.monotonic()
     if ws > 1:
         dist.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(t_host0, t_host1)
     total_ms = e_start.elapsed_time(e_end)
     trace_ms = [a.elapsed_time(b) for a, b, _ in tev]
     build_ms = [c.elapsed_time(a) for a, _, c in tev]
