@@ -401,9 +401,9 @@ def run_ours(args):
                                   "of the timed steps)"},
             "clocks": clk,
             "e2e": e2e,
-            # per step: vct_build_mips of the 256^3 grid (dense FP32: the
-            # streaming kernel for levels 0..4 and the one-CTA tail; FP16: the
-            # TMA pack kernel and the tail) and the persistent trace kernel
+            # per step: vct_build_mips of the 256^3 grid (the streaming kernel
+            # for levels 0..4 and the one-CTA tail, FP32 or FP16) and the
+            # persistent trace kernel
             "gpu_launches": 3 * args.steps,
         }
         if not args.no_extras:

@@ -315,10 +315,23 @@ constexpr int kPatchX = 256;     // longest x extent of a patch
 constexpr int kPatchYZ = 16;     // y and z extent of a patch (2^kStreamTop)
 struct StreamArgs {
   const float4 *dense;
-  float4 *lvl[kStreamTop + 1];
+  void *lvl[kStreamTop + 1];        // texels as stored (float4 or binary16 x 4)
   uint64_t texels[kStreamTop + 1];
+  float4 *staging;                  // float32 copy of level 4 (binary16 pyramids), or null
   int n, X, top;
 };
+// 32 bytes of four binary16 texels (one whole sector), first out of L2
+__device__ __forceinline__ void st_stream_32(uint2 *p, uint2 a, uint2 b, uint2 c, uint2 d) {
+  asm volatile("st.global.L2::evict_first.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p),
+               "r"(a.x), "r"(a.y), "r"(b.x), "r"(b.y), "r"(c.x), "r"(c.y), "r"(d.x), "r"(d.y)
+               : "memory");
+}
+// Stored texels of one level (DT: float32 or binary16).
+template <int DT>
+__device__ __forceinline__ typename Tex<DT>::T *level_ptr(const StreamArgs &a, int l) {
+  return reinterpret_cast<typename Tex<DT>::T *>(a.lvl[l]);
+}
+template <int DT>
 __global__ void __launch_bounds__(256, 2) stream_levels_kernel(const __grid_constant__ StreamArgs a) {
   __shared__ float4 s2[16 * (kPatchX / 4)];  // the patch's level 2, row qz * 4 + qy
   __shared__ float4 s3[4 * (kPatchX / 8)];   // level 3, row rz * 2 + ry
@@ -365,9 +378,17 @@ __global__ void __launch_bounds__(256, 2) stream_levels_kernel(const __grid_cons
         if (!cell(P, p, k, gx, gy, gz)) continue;
         const uint32_t code = morton3(gx, gy, gz);
         if (in_bounds(8 * (uint64_t)code + 7, a.texels[0], kOobMip)) {
-          float4 *dst = a.lvl[0] + 8 * (uint64_t)code;
+          if constexpr (DT == VCT_F32) {
+            float4 *dst = level_ptr<DT>(a, 0) + 8 * (uint64_t)code;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) st_stream_32(dst + 2 * q, r[k][2 * q], r[k][2 * q + 1]);
+            for (int q = 0; q < 4; ++q) st_stream_32(dst + 2 * q, r[k][2 * q], r[k][2 * q + 1]);
+          } else {
+            uint2 *dst = level_ptr<DT>(a, 0) + 8 * (uint64_t)code;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+              st_stream_32(dst + 4 * h, pack_half4(r[k][4 * h]), pack_half4(r[k][4 * h + 1]),
+                           pack_half4(r[k][4 * h + 2]), pack_half4(r[k][4 * h + 3]));
+          }
         }
         if (a.top < 1) continue;
         // rotate so that u[i] = r[(i + rot) & 7], then add in order
@@ -383,7 +404,7 @@ __global__ void __launch_bounds__(256, 2) stream_levels_kernel(const __grid_cons
 #pragma unroll
         for (int i = 0; i < 8; ++i) sum = add4(sum, u[i]);
         m[k] = mul4(sum, 0.125f);
-        if (in_bounds(code, a.texels[1], kOobMip)) a.lvl[1][code] = m[k];
+        if (in_bounds(code, a.texels[1], kOobMip)) st_texel(level_ptr<DT>(a, 1) + code, m[k]);
       }
       // the next phase's loads (the stores above have taken r)
       if (p + 1 < 16)
@@ -414,7 +435,7 @@ __global__ void __launch_bounds__(256, 2) stream_levels_kernel(const __grid_cons
           const uint32_t qx = 4u * u + c;
           const uint32_t code = morton3(px * (X / 4) + qx, py * (kPatchYZ / 4) + (p & 3),
                                         pz * (kPatchYZ / 4) + (p >> 2));
-          if (in_bounds(code, a.texels[2], kOobMip)) a.lvl[2][code] = v;
+          if (in_bounds(code, a.texels[2], kOobMip)) st_texel(level_ptr<DT>(a, 2) + code, v);
           s2[p * (X / 4) + qx] = v;
         }
       }
@@ -430,7 +451,7 @@ __global__ void __launch_bounds__(256, 2) stream_levels_kernel(const __grid_cons
         c[i] = s2[((2 * rz + (i >> 2)) * 4 + 2 * ry + ((i >> 1) & 1)) * (X / 4) + 2 * rx + (i & 1)];
       const float4 v = mean8(c);
       const uint32_t code = morton3(px * w3 + rx, py * 2 + ry, pz * 2 + rz);
-      if (in_bounds(code, a.texels[3], kOobMip)) a.lvl[3][code] = v;
+      if (in_bounds(code, a.texels[3], kOobMip)) st_texel(level_ptr<DT>(a, 3) + code, v);
       s3[(rz * 2 + ry) * w3 + rx] = v;
     }
     __syncthreads();
@@ -440,7 +461,10 @@ __global__ void __launch_bounds__(256, 2) stream_levels_kernel(const __grid_cons
       for (int i = 0; i < 8; ++i) c[i] = s3[(i >> 1) * w3 + 2 * t + (i & 1)];
       const float4 v = mean8(c);
       const uint32_t code = morton3(px * (X / 16) + t, py, pz);
-      if (in_bounds(code, a.texels[4], kOobMip)) a.lvl[4][code] = v;
+      if (in_bounds(code, a.texels[4], kOobMip)) {
+        st_texel(level_ptr<DT>(a, 4) + code, v);
+        if (a.staging != nullptr) a.staging[code] = v;  // the tail's float32 source
+      }
     }
     // the next patch's level-2 writes to s2 must not overtake the reads above
     __syncthreads();
@@ -994,14 +1018,17 @@ cudaError_t launch_build_aniso(const float *level0, const vct_pyramid &pyr, int 
   return e;
 }
 
-// Dense float32 pyramids of n >= 32: stream_levels_kernel (levels 0 .. 4),
-// then groups of kGroupLevels levels while the level below holds more than
-// one tail CTA's worth of texels, then the one-CTA tail.
-static cudaError_t build_dense_f32_streamed(const float *level0, const vct_pyramid &pyr,
-                                           cudaStream_t s) {
+// Dense pyramids from a 32-byte aligned grid, n >= 32 (binary16: n <= 256):
+// stream_levels_kernel (levels 0 .. 4), then, for float32, groups of
+// kGroupLevels levels while the level below holds more than one tail CTA's
+// worth of texels, then the one-CTA tail (binary16: from the float32 copy of
+// level 4 in the staging area, as the TMA path hands it over).
+static cudaError_t build_dense_streamed(const float *level0, const vct_pyramid &pyr,
+                                        cudaStream_t s) {
   const Layout L = make_layout(pyr.n, pyr.levels, pyr.dtype, pyr.layout);
   uint8_t *base = static_cast<uint8_t *>(pyr.data);
   auto lvl = [&](int l) { return reinterpret_cast<float4 *>(base + L.level_off[l]); };
+  const bool f16 = pyr.dtype == VCT_F16;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1011,15 +1038,20 @@ static cudaError_t build_dense_f32_streamed(const float *level0, const vct_pyram
   sa.X = std::min(pyr.n, kPatchX);
   sa.top = std::min(kStreamTop, pyr.levels - 1);
   for (int l = 0; l <= sa.top; ++l) {
-    sa.lvl[l] = lvl(l);
+    sa.lvl[l] = base + L.level_off[l];
     sa.texels[l] = level_texels(pyr.n, l);
   }
+  const bool tail = sa.top < pyr.levels - 1;
+  sa.staging = (f16 && tail) ? reinterpret_cast<float4 *>(base + L.staging_off[0]) : nullptr;
   const uint64_t patches = (uint64_t)(pyr.n / sa.X) * (pyr.n / kPatchYZ) * (pyr.n / kPatchYZ);
   const int grid1 = (int)std::min<uint64_t>(patches, (uint64_t)sms * 2);
-  stream_levels_kernel<<<grid1, 256, 0, s>>>(sa);
+  if (f16)
+    stream_levels_kernel<VCT_F16><<<grid1, 256, 0, s>>>(sa);
+  else
+    stream_levels_kernel<VCT_F32><<<grid1, 256, 0, s>>>(sa);
   cudaError_t e = cudaGetLastError();
   int m = sa.top;  // the last level made so far
-  if (e != cudaSuccess || m >= pyr.levels - 1) return e;
+  if (e != cudaSuccess || !tail) return e;
   cudaLaunchAttribute pdl[1];
   pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   pdl[0].val.programmaticStreamSerializationAllowed = 1;
@@ -1028,7 +1060,7 @@ static cudaError_t build_dense_f32_streamed(const float *level0, const vct_pyram
   lc.attrs = pdl;
   lc.numAttrs = 1;
   // levels m+1 .. m+k from level m (8^k divides its texels: k <= log2(n) - m)
-  while (m < pyr.levels - 1 && level_texels(pyr.n, m) > kTailSourceTexels) {
+  while (!f16 && m < pyr.levels - 1 && level_texels(pyr.n, m) > kTailSourceTexels) {
     const int k = std::min(kGroupLevels, pyr.levels - 1 - m);
     GroupArgs g{};
     g.src = lvl(m);
@@ -1050,22 +1082,31 @@ static cudaError_t build_dense_f32_streamed(const float *level0, const vct_pyram
   t.n = pyr.n;
   t.levels = pyr.levels;
   t.m_top = m;
-  t.src0 = lvl(m);
   lc.gridDim = dim3(1);
   lc.blockDim = dim3(1024);
-  return cudaLaunchKernelEx(&lc, mip_tail_kernel<VCT_F32, false, true>, t);
+  if (!f16) {
+    t.src0 = lvl(m);
+    return cudaLaunchKernelEx(&lc, mip_tail_kernel<VCT_F32, false, true>, t);
+  }
+  t.src0 = reinterpret_cast<const float4 *>(base + L.staging_off[0]);
+  t.ping[0] = reinterpret_cast<float4 *>(base + L.staging_off[1]);
+  // levels above m+1 are at most 1/8 of staging_off[1] and land at the start
+  // of staging_off[0], whose values were consumed
+  t.ping[1] = reinterpret_cast<float4 *>(base + L.staging_off[0]);
+  return cudaLaunchKernelEx(&lc, mip_tail_kernel<VCT_F16, false, true>, t);
 }
 
 bool streamed_build(const float *level0, const vct_pyramid &pyr) {
   // (its 32-byte loads need a 32-byte aligned grid; the TMA path needs 16)
-  return pyr.dtype == VCT_F32 && pyr.layout == VCT_LAYOUT_DENSE && pyr.n >= 32 &&
+  return pyr.layout == VCT_LAYOUT_DENSE && pyr.n >= 32 &&
+         (pyr.dtype == VCT_F32 || (pyr.dtype == VCT_F16 && pyr.n <= 256)) &&
          reinterpret_cast<uintptr_t>(level0) % 32 == 0;
 }
 
 cudaError_t launch_pack_mips(const float *level0, const vct_pyramid &pyr,
                              const CUtensorMap *map, cudaStream_t s) {
   const bool br = pyr.layout == VCT_LAYOUT_BRICKS;
-  if (streamed_build(level0, pyr)) return build_dense_f32_streamed(level0, pyr, s);
+  if (streamed_build(level0, pyr)) return build_dense_streamed(level0, pyr, s);
   if (map == nullptr) return cudaErrorInvalidValue;
   const Layout L = make_layout(pyr.n, pyr.levels, pyr.dtype, pyr.layout);
   uint8_t *base = static_cast<uint8_t *>(pyr.data);

@@ -390,8 +390,9 @@ inline ConeConst cone_const(double gamma, double beta, double t0_vox,
 vct_status set_last_error(vct_status st, const char *fmt, ...);
 
 // Host entry points implemented in the .cu files (internal linkage across TUs).
-// True when launch_pack_mips streams the grid (dense float32, n >= 32, a
-// 32-byte aligned level 0) and needs no tensor map.
+// True when launch_pack_mips streams the grid (dense layout, float32 with
+// n >= 32 or binary16 with 32 <= n <= 256, a 32-byte aligned level 0) and
+// needs no tensor map.
 bool streamed_build(const float *level0, const vct_pyramid &pyr);
 // `map`: the level-0 tensor map of the TMA path; unused (may be null) when
 // streamed_build() holds.
