@@ -24,24 +24,34 @@ def _cuda():
     vct.lib()
 
 
-def aniso_gpu(grid):
-    return vct.build_mips(torch.from_numpy(np.ascontiguousarray(grid, np.float32)).cuda(),
-                          layout="aniso")
+def aniso_gpu(grid, offset16=False):
+    """Anisotropic pyramid of a grid; offset16: level 0 placed 16 bytes past a
+    32-byte boundary (the build then takes its one-launch-per-level path
+    instead of the streaming kernel, which wants 32-byte alignment)."""
+    g = torch.from_numpy(np.ascontiguousarray(grid, np.float32)).cuda()
+    if offset16:
+        buf = torch.empty(g.numel() + 8, dtype=torch.float32, device="cuda")
+        assert buf.data_ptr() % 32 == 0
+        g2 = buf[4:4 + g.numel()].view(g.shape)
+        g2.copy_(g)
+        g = g2
+    return vct.build_mips(g, layout="aniso")
 
 
-@pytest.mark.parametrize("n", [2, 8, 32])
-def test_aniso_levels_match_oracle(n):
+@pytest.mark.parametrize("n,offset16", [(2, False), (8, False), (32, False), (64, False),
+                                        (128, False), (64, True)])
+def test_aniso_levels_match_oracle(n, offset16):
     rng = np.random.default_rng(n)
     g = rng.random((n, n, n, 4)).astype(np.float32)
     g[rng.random((n, n, n)) < 0.4] = 0.0  # empty voxels: alpha-0 pairs
-    P = aniso_gpu(g)
+    P = aniso_gpu(g, offset16)
     O = oracle.build_mips_aniso(g)
     assert np.array_equal(vct.read_level(P, 0).cpu().numpy(), g)
     for l in range(1, P.levels):
         for d in range(6):
             got = vct.read_volume(P, l, d).cpu().numpy().astype(np.float64)
             want = O.level(l, d)
-            assert np.allclose(got, want, rtol=2e-6, atol=1e-7), (n, l, d,
+            assert np.allclose(got, want, rtol=2e-6, atol=1e-7), (n, offset16, l, d,
                                                                   np.abs(got - want).max())
     dense = vct.build_mips(torch.from_numpy(g).cuda())
     print("aniso / dense bytes:", P.storage.numel() / dense.storage.numel())
