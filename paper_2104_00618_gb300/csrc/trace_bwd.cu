@@ -91,6 +91,10 @@ __device__ __forceinline__ void scatter_lane(const BwdLaunch &L, int l, uint32_t
 // 55.4 / 53.7 / 57.1 / 91.2 ms for thresholds 2 / 4 / 8 / 16 / 20 / 32, and
 // 544 ms without the reduction.
 constexpr int kReduceMin = 16;
+// The reproducible mode pays four 64-bit atomics per corner and channel
+// group, so there every cell shared by two or more lanes is summed first
+// (fwd + adjoint on the same workload: 108.6 ms with 16, 64.7 ms with 2).
+constexpr int kReduceMinFix = 2;
 
 // Slot of the key-offset table holding the total (after the per-level offsets).
 constexpr int kKeyTotal = VCT_MAX_LEVELS;
@@ -131,7 +135,7 @@ __device__ __forceinline__ void scatter_warp(const BwdLaunch &L, const uint32_t 
     }
   }
   const unsigned grp = __match_any_sync(full, key);
-  const bool big = act && __popc(grp) >= kReduceMin;
+  const bool big = act && __popc(grp) >= (L.deterministic ? kReduceMinFix : kReduceMin);
   if (act && !big) scatter_lane(L, l, vbase, lim, s, lw, g);
   unsigned pending = __ballot_sync(full, big);
   if (pending == 0u) return;
