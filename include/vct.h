@@ -173,9 +173,11 @@ uint64_t vct_pyramid_level_offset(int32_t n, int32_t levels, int32_t dtype,
  * Level l+1 is the plain average of the 8 children of level l, computed in
  * float32 from the float32 values of level l; VCT_F16 pyramids store each
  * level rounded to nearest-even after it has been computed in float32.
- * Every path gives the same bits: a 32-byte aligned level0_dense of n >= 32
- * (binary16: n <= 256) is read once in rows by one streaming kernel (the
- * faster path), any other through shared-memory blocks.
+ * A 32-byte aligned level0_dense of n >= 32 (binary16: n <= 256) is read
+ * once in rows by one streaming kernel (the faster path), any other through
+ * shared-memory blocks; for the dense and brick layouts both give the same
+ * bits, for VCT_LAYOUT_ANISO (streamed for n >= 16) they agree within a few
+ * ulps (reciprocals are rounded differently).
  * A VCT_LAYOUT_BRICKS pyramid gets the same texel values; its occupancy is
  * recomputed from level0_dense.  If its pool cannot hold the occupied bricks
  * (pyr->bytes below vct_pyramid_bytes_bricks() for this grid) every brick is
