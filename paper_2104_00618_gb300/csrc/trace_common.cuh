@@ -232,13 +232,6 @@ __device__ __forceinline__ void level_stencil(int l, int Nl, const Apex &A, cons
 __device__ __forceinline__ uint32_t corner_index(const LevelStencil &s, int c) {
   return s.sx[c & 1] | s.sy[(c >> 1) & 1] | s.sz[c >> 2];
 }
-// Trilinear weight of corner c times the level weight lw (adjoint scatter).
-__device__ __forceinline__ float corner_weight(const LevelStencil &s, float lw, int c) {
-  const float wx = (c & 1) ? s.fr[0] : 1.0f - s.fr[0];
-  const float wy = ((c >> 1) & 1) ? s.fr[1] : 1.0f - s.fr[1];
-  const float wz = (c >> 2) ? s.fr[2] : 1.0f - s.fr[2];
-  return lw * wx * wy * wz;
-}
 
 // Address of the texel with Morton code `code` in a bricked level: its
 // brick's pool slot (slot 0, the zero brick, for an empty brick).

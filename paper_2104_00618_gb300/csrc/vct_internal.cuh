@@ -108,10 +108,6 @@ __host__ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
   v = (v | (v << 2)) & 0x09249249u;
   return v;
 }
-// spread3(v + 1) from s = spread3(v) (10-bit wrap-around).
-__host__ __device__ __forceinline__ uint32_t spread3_inc(uint32_t s) {
-  return (s - kMortonX) & kMortonX;
-}
 __host__ __device__ __forceinline__ uint32_t compact3(uint32_t v) {
   v &= 0x09249249u;
   v = (v | (v >> 2)) & 0x030C30C3u;
